@@ -1,0 +1,172 @@
+"""Plain two-site ab initio DMRG with the U(1)xU(1) NC partition (oracle side).
+
+Follows Appendix A: for each sweep iteration at sites (i, i+1),
+  (i)  blocking: enlarged blocks L_i x s_i and s_{i+1} x R_{i+2}
+       (Eq. blocked-ops; formulas in nc.blocking_left / blocking_right);
+  (ii) solving: lowest eigenpair of H_eff (Eq. eff-eigsh) by Davidson, with
+       the NC sigma of sigma.sigma_blocks;
+  (iii) decimation by SVD of psi per sector block and truncation to M, then
+       transformation of the growing block's operators (Eq. op-trans).
+Forward sweeps move the canonical centre right (keep U), backward sweeps
+move it left (keep V^T).
+
+Fixed readings of points the paper leaves open:
+  * Initial MPS: right blocks R_j (spatial orbitals j..K-1) are built right to
+    left; the kept sectors of s_j x R_{j+1} are those the left part
+    (2j spin orbitals) can complement to the target (N, 2Sz); if their total
+    dimension exceeds M_init, sector dims are the largest-remainder rounding
+    of M_init * d_Q / D (ties by ascending Q). The basis of sector Q is the
+    orthonormalised column space of a random d_Q x m_Q matrix whose entries
+    are SplitMix64 normals (key = seed ^ KEY_MPS, counter = running flat
+    offset over j descending, Q ascending, row-major).
+  * Truncation: all singular values of all psi blocks sorted by
+    (s descending, q_L ascending, index ascending); the first
+    min(M, count) are kept, zero singular values included.
+  * Davidson guess at each step: SplitMix64 normals (key = seed ^ KEY_GUESS,
+    counter = step_id * 2^32 + element index, step_id = sweep * K + i).
+  * Sweep energy: the lowest Davidson eigenvalue of the sweep.
+
+Parity status: pinned (tests/test_oracle_dmrg.py): at full bond dimension
+every sweep energy equals the FCI energy; blocked operators equal their
+Fock-space matrices; renormalized bases are orthonormal.
+"""
+
+import numpy as np
+
+from . import splitmix
+from .blocks import Basis, BlockOp, qadd, qsub
+from .davidson import davidson
+from .nc import (Integrals, assemble_all, blocking_left, blocking_right, nc_terms,
+                 transform, vacuum_left, vacuum_right)
+from .sigma import heff_diagonal, psi_layout, psi_to_blocks, sigma_blocks
+
+
+def can_hold(n_modes, q):
+    N, s = q
+    return 0 <= N <= n_modes and (s - N) % 2 == 0 and abs(s) <= min(N, n_modes - N)
+
+
+def largest_remainder(total, weights):
+    w = np.asarray(weights, dtype=np.float64)
+    exact = total * w / w.sum()
+    base = np.floor(exact).astype(np.int64)
+    short = int(total - base.sum())
+    order = sorted(range(len(w)), key=lambda a: (-(exact[a] - base[a]), a))
+    for a in order[:short]:
+        base[a] += 1
+    return base
+
+
+def orthonormal_columns(G):
+    Q, R = np.linalg.qr(G)
+    return Q
+
+
+class PlainDMRG:
+    def __init__(self, t, v, N, two_sz, seed=0, dav_tol=1e-10, dav_max_space=24,
+                 dav_max_iter=200):
+        self.ints = Integrals(t, v)
+        self.K = self.ints.K
+        self.Q = (N, two_sz)
+        self.seed = seed
+        self.dav = dict(tol=dav_tol, max_space=dav_max_space, max_iter=dav_max_iter)
+        self.L = {}
+        self.R = {}
+        self.log = []
+
+    # ------------------------------------------------------ initial blocks
+    def build_blocks(self, M_init):
+        K = self.K
+        self.R[K] = vacuum_right(self.ints)
+        key = splitmix.stream_key(self.seed, splitmix.KEY_MPS)
+        off = 0
+        for j in range(K - 1, 0, -1):
+            bR, opsR = self.R[j + 1]
+            E, chunks, enl = blocking_right(self.ints, bR, opsR, j)
+            comp = [(Q, E.dim(Q)) for Q in E.qs if can_hold(2 * j, qsub(self.Q, Q))]
+            D = sum(d for _, d in comp)
+            dims = [d for _, d in comp] if D <= M_init else list(largest_remainder(M_init, [d for _, d in comp]))
+            U, secs = {}, []
+            for (Q, d), m in zip(comp, dims):
+                if m <= 0:
+                    continue
+                g = splitmix.normal(key, np.arange(off, off + d * m, dtype=np.uint64)).reshape(d, m)
+                off += d * m
+                U[Q] = orthonormal_columns(g)
+                secs.append((Q, m))
+            nb = Basis(secs)
+            ops = {k: transform(e.assemble(E, chunks), U, nb) for k, e in enl.items()}
+            self.R[j] = (nb, ops)
+        self.L[0] = vacuum_left(self.ints)
+
+    # ------------------------------------------------------------- a step
+    def enlarged(self, i):
+        bL, opsL = self.L[i]
+        bR, opsR = self.R[i + 2]
+        EL, chL, enlL = blocking_left(self.ints, bL, opsL, i)
+        ER, chR, enlR = blocking_right(self.ints, bR, opsR, i + 1)
+        return EL, assemble_all(enlL, EL, chL), ER, assemble_all(enlR, ER, chR)
+
+    def solve(self, i, step_id, EL, oL, ER, oR):
+        terms = nc_terms(2 * (i + 1), self.ints.n)
+        layout, size = psi_layout(EL, ER, self.Q)
+        diag = heff_diagonal(layout, terms, oL, oR)
+        key = splitmix.stream_key(self.seed, splitmix.KEY_GUESS)
+        g = splitmix.normal(key, (np.uint64(step_id) << np.uint64(32)) + np.arange(size, dtype=np.uint64))
+        mv = lambda x: sigma_blocks(x, layout, terms, oL, oR)
+        th, x, nmv, conv = davidson(mv, diag, g, **self.dav)
+        return th, x, layout, nmv, conv
+
+    @staticmethod
+    def decimate(x, layout, M):
+        """Per-block SVD and global truncation. Returns (kept per q_L, U, V, discarded weight, svals)."""
+        blocks = psi_to_blocks(x, layout)
+        svd, cand = {}, []
+        for qL, qR, mL, mR, off in layout:
+            u, s, vt = np.linalg.svd(blocks[qL], full_matrices=False)
+            svd[qL] = (u, s, vt, qR)
+            cand += [(-float(sv), qL, k) for k, sv in enumerate(s)]
+        cand.sort()
+        keep = min(M, len(cand))
+        kept = {}
+        for _, qL, k in cand[:keep]:
+            kept[qL] = kept.get(qL, 0) + 1
+        disc = sum(c[0] ** 2 for c in cand[keep:])
+        return kept, svd, disc
+
+    def step(self, i, forward, M, step_id):
+        EL, oL, ER, oR = self.enlarged(i)
+        th, x, layout, nmv, conv = self.solve(i, step_id, EL, oL, ER, oR)
+        kept, svd, disc = self.decimate(x, layout, M)
+        if forward:
+            U = {qL: svd[qL][0][:, :m] for qL, m in kept.items()}
+            nb = Basis(list(kept.items()))
+            self.L[i + 1] = (nb, {k: transform(o, U, nb) for k, o in oL.items()})
+        else:
+            V, secs = {}, []
+            for qL, m in kept.items():
+                qR = svd[qL][3]
+                V[qR] = svd[qL][2][:m, :].T
+                secs.append((qR, m))
+            nb = Basis(secs)
+            self.R[i + 1] = (nb, {k: transform(o, V, nb) for k, o in oR.items()})
+        self.log.append(dict(i=i, forward=forward, M=M, energy=th, nmv=nmv,
+                             converged=conv, discarded=disc, dim=len(x)))
+        return th, disc
+
+    def sweep(self, M_schedule):
+        """One entry of M_schedule per sweep (forward, backward, forward, ...).
+        Returns (energies per sweep, max discarded weight per sweep)."""
+        K = self.K
+        energies, discs = [], []
+        for s, M in enumerate(M_schedule):
+            fwd = s % 2 == 0
+            sites = range(0, K - 1) if fwd else range(K - 2, -1, -1)
+            es, ds = [], []
+            for i in sites:
+                e, d = self.step(i, fwd, M, s * K + i)
+                es.append(e)
+                ds.append(d)
+            energies.append(min(es))
+            discs.append(max(ds))
+        return energies, discs
