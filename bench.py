@@ -1,0 +1,275 @@
+"""Benchmark: sigma = H_eff . psi at the middle bond of two-site ab initio DMRG.
+
+Workload (default): K=108 spatial orbitals split 54|54, N=30, 2Sz=0, bond
+dimension M=2000 per side (104 sectors, |psi| = 106,004), 23,654 NC terms,
+synthetic N(0,1) operator blocks (seed 1), FP64 arithmetic. One step = one
+sigma call with psi and the operators resident in HBM.
+
+Prints one JSON line (rank 0). See the design doc for the roofline accounting.
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--M 2000] [--impl ours|reference]
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+K_ORB, N_EL, TWO_SZ, SEED = 108, 30, 0, 1
+METRIC = "H_eff.psi TFLOP/s (middle-bond sigma)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--M", type=int, default=2000)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+def workload(M):
+    from synth import gaussian_sector_dims, mirrored_sectors
+    left = gaussian_sector_dims(M, n_spatial=K_ORB // 2, n_tot=N_EL, two_sz_tot=TWO_SZ)
+    right = mirrored_sectors(left, n_tot=N_EL, two_sz_tot=TWO_SZ)
+    return left, right
+
+
+def config(M, prec="fp64"):
+    return {"workload": f"middle-bond sigma, K={K_ORB} (54|54 spatial orbitals), N={N_EL}, 2Sz={TWO_SZ}, "
+                        f"M={M}, 23654 NC terms, synthetic N(0,1) operator blocks seed {SEED}",
+            "K": K_ORB, "N": N_EL, "two_sz": TWO_SZ, "M": M, "sigma_precision": prec,
+            "l2": "inputs larger than L2 (operator store >> 129 MB), no flush"}
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- oracle leg
+def oracle_sample(M, n_terms):
+    """The oracle's sigma on the first n_terms NC terms of the workload (a
+    bounded sample of the same middle-bond problem). Returns (run, flops)."""
+    from oracle.nc import nc_terms
+    from oracle.sigma import psi_layout, sigma_blocks, sigma_flops, synthetic_op_specs, synthetic_ops
+    from synth import random_unit_vector
+    left, right = workload(M)
+    terms = nc_terms(K_ORB, 2 * K_ORB)[:n_terms]
+    need = set()
+    for kl, tl, kr, tr, c in terms:
+        if kl is not None:
+            need.add(("L", kl))
+        if kr is not None:
+            need.add(("R", kr))
+    bL, bR, oL, oR, _ = synthetic_ops(left, right, K_ORB, 2 * K_ORB, SEED, only=need)
+    lay, size = psi_layout(bL, bR, (N_EL, TWO_SZ))
+    specs = synthetic_op_specs(K_ORB, 2 * K_ORB)
+    dqL = {k: dq for s, k, dq, _ in specs if s == "L"}
+    dqR = {k: dq for s, k, dq, _ in specs if s == "R"}
+    flops = sigma_flops(lay, terms, dqL, dqR, bL, bR)
+    x = random_unit_vector(size, SEED)
+
+    def run():
+        return sigma_blocks(x, lay, terms, oL, oR)
+    return run, flops
+
+
+def cpu_baseline(M, n_terms=700, reps=8):
+    run, flops = oracle_sample(M, n_terms)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        run()
+    dt = (time.perf_counter() - t0) / reps
+    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"oracle sigma (numpy FP64, per-term per-block loop), {reps} repetitions over the first {n_terms} of "
+                      f"23654 NC terms at M={M}: {flops / 1e9:.1f} GFLOP in {dt:.2f} s"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    n_terms = 700
+    run, flops = oracle_sample(args.M, n_terms)
+    for _ in range(args.warmup):
+        run()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        run()
+    dt = (time.perf_counter() - t0) / args.steps
+    v = flops / dt / 1e12
+    out = {"metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": config(args.M),
+           "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": f"first {n_terms} of 23654 NC terms per step, {flops / 1e9:.1f} GFLOP"},
+           "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------- our leg
+def fp64_gemm_peak(torch):
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = 1e9
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    return 2.0 * n ** 3 / best / 1e12
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import numpy as np
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2103_09976_gb300 import capi
+    from synth import random_unit_vector
+
+    left, right = workload(args.M)
+    ctx = capi.dmrg_create(device=local)
+    capi.dmrg_load_synthetic(ctx, K_ORB, 2 * K_ORB, N_EL, TWO_SZ, left, right, SEED)
+    info = capi.dmrg_get_sigma_info(ctx)
+    n = info["psi_size"]
+    x_h = random_unit_vector(n, SEED)
+    x = torch.from_numpy(x_h).cuda()
+    y = torch.zeros(n, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.ExternalStream(capi.dmrg_stream(ctx))
+
+    for _ in range(max(3, args.warmup)):
+        capi.dmrg_sigma(ctx, -1, x, y)
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    capi.dmrg_profile(ctx, True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        capi.dmrg_sigma(ctx, -1, x, y)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    step_s = e0.elapsed_time(e1) / 1e3 / args.steps
+    k_ms, k_n = capi.dmrg_profile_read(ctx, capi.KERNEL_SIGMA)
+    r_ms, r_n = capi.dmrg_profile_read(ctx, capi.KERNEL_REDUCE)
+    capi.dmrg_profile(ctx, False)
+    clocks = clk.stop()
+    if dist:
+        t = torch.tensor([step_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_s = float(t.item())
+
+    # end to end through the C ABI with pinned host buffers
+    xp = torch.from_numpy(x_h).pin_memory()
+    yp = torch.zeros(n, dtype=torch.float64).pin_memory()
+    capi.dmrg_sigma(ctx, -1, xp, yp)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        capi.dmrg_sigma(ctx, -1, xp, yp)
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    ok = bool(np.allclose(yp.numpy(), y.cpu().numpy(), rtol=0, atol=1e-12 * float(y.abs().max())))
+
+    peak64 = fp64_gemm_peak(torch)
+    capi.dmrg_destroy(ctx)
+
+    flops = info["flops"]
+    kern_s = k_ms / 1e3 / max(1, k_n)
+    achieved = flops / kern_s / 1e12
+    value = world * flops / step_s / 1e12
+    out = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+           "warmup": max(3, args.warmup), "ms_per_step": step_s * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": config(args.M),
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
+                        "frac": achieved / peak64, "traffic": None,
+                        "kernel": "sigma_f64_kernel",
+                        "peak_source": "cuBLAS DGEMM 4096^3 measured in this run (no FP64 entry in MEASURED_PEAKS.json)",
+                        "kernel_ms": kern_s * 1e3, "reduce_ms": r_ms / max(1, r_n)},
+           "e2e": {"value": flops / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 8 * n,
+                   "d2h_bytes_per_step": 8 * n, "matches_device_result": ok},
+           "gpu_launches": 2 * args.steps,
+           "clocks": clocks,
+           "sigma_info": info}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.M)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * dmrg.h - C ABI of the GB300 two-site ab initio DMRG hot path.
+ *
+ * The library computes the Davidson sigma-vector sigma = H_eff . psi of
+ * two-site DMRG (Zhai & Chan, "Low communication high performance ab initio
+ * DMRG algorithms": Appendix A, Eq. eff-eigsh; Sec. II.D-E for the sum over
+ * normal/complementary operator pairs and its split into dense products over
+ * symmetry sectors), the Davidson solve around it, and the blocking /
+ * decimation / transformation steps of a sweep (Appendix A, Eqs.
+ * blocked-ops and op-trans), all on one GPU with the hot path in
+ * hand-written sm_103a CUDA kernels.
+ *
+ * Conventions shared by every entry point:
+ *  - Quantum numbers are q = (N, 2Sz), compared lexicographically.
+ *  - Spin orbitals are p = 2*i + sigma (alpha = 0, beta = 1); Jordan-Wigner
+ *    order is ascending p; left-block modes precede right-block modes.
+ *  - psi and sigma are FP64 vectors over the two-site product basis, stored
+ *    block by block: blocks (q_L, q_R = Q_tot - q_L) in ascending q_L, each
+ *    block row-major m_L x m_R (left index slow). dmrg_psi_layout reports
+ *    the blocks.
+ *  - Ownership: the caller owns every buffer it passes; the context owns all
+ *    device memory it allocates (operators, work lists, scratch) until
+ *    dmrg_destroy. No call keeps a caller pointer after it returns.
+ *  - Pointers to psi / sigma may be host or device memory (detected with
+ *    cudaPointerGetAttributes); device pointers must be on the context's
+ *    device. Host buffers are copied in and out inside the call.
+ *  - Streams: each context owns one CUDA stream (dmrg_stream); device work is
+ *    ordered on it. Calls that return host results synchronize that stream.
+ *  - Errors: every call returns a status; nothing throws across the ABI.
+ *    dmrg_last_error(ctx) describes the last failure on that context.
+ *  - Thread safety: one context must not be used from two threads at once;
+ *    distinct contexts are independent.
+ */
+#ifndef DMRG_H
+#define DMRG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dmrg_ctx dmrg_ctx;
+
+typedef enum {
+  DMRG_OK = 0,
+  DMRG_EINVAL = 1,   /* bad argument (size, pointer, quantum number, order of calls) */
+  DMRG_ENOMEM = 2,   /* device or host allocation failed */
+  DMRG_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
+  DMRG_ENOCONV = 4,  /* Davidson hit its iteration limit; best energy still returned */
+  DMRG_ETIMEOUT = 5, /* a bounded device-side wait gave up */
+  DMRG_ESTATE = 6    /* context not in the state the call needs (e.g. no operators loaded) */
+} dmrg_status;
+
+/* Arithmetic of the sigma products. FP64: plain double on the FP64 pipes.
+ * FP16X2: operands split into fp16 hi + lo with a power-of-two scale per
+ * operator, 3 tensor-core products (hi.hi + hi.lo + lo.hi) per GEMM with FP32
+ * accumulation, terms summed in FP64. BF16X3: three bf16 slices, 6 products. */
+typedef enum { DMRG_FP64 = 0, DMRG_FP16X2 = 1, DMRG_BF16X3 = 2 } dmrg_prec;
+
+typedef struct {
+  int sigma_prec;              /* dmrg_prec */
+  int dav_max_space;           /* Davidson subspace size (default 24, >= 3) */
+  int dav_max_iter;            /* Davidson matrix-vector products per solve (default 200) */
+  int keep_one_per_q;          /* reserved, must be 0 */
+  double noise;                /* reserved, must be 0 */
+  unsigned long long seed;     /* seed of the counter-based random streams (initial MPS, guesses) */
+  int device;                  /* CUDA device ordinal */
+} dmrg_opts;
+
+/* Fill *o with defaults: FP64, 24, 200, 0, 0.0, seed 0, device 0. */
+void dmrg_default_opts(dmrg_opts* o);
+
+/* Create a context on opts->device (NULL opts = defaults). *out is NULL on failure. */
+dmrg_status dmrg_create(dmrg_ctx** out, const dmrg_opts* opts);
+
+/* Release all device memory and the stream. NULL is ignored. */
+void dmrg_destroy(dmrg_ctx* ctx);
+
+/* Message of the last failed call on ctx (static string if ctx is NULL). */
+const char* dmrg_last_error(const dmrg_ctx* ctx);
+
+/* The context's cudaStream_t, as void*. */
+void* dmrg_stream(dmrg_ctx* ctx);
+
+/* Change the sigma precision (dmrg_prec) of an existing context. Mixed modes
+ * build their split operator copies lazily on the next dmrg_sigma call. */
+dmrg_status dmrg_set_precision(dmrg_ctx* ctx, int prec);
+
+/*
+ * Synthetic middle-bond problem (the data-parallel hot path on its own).
+ * Builds, on the device, the stored operators of an NC left block (H, a+_p,
+ * R^L_p, A_pr, B_pq) and of an NC right block (H, a_p, R^R_p, P_pr, Q_pq)
+ * (Appendix B, Eq. h-nc and Eq. op-def, spin-orbital U(1) form; index
+ * symmetry Eq. index-sym halves the stored A/P/B/Q) over the given sector
+ * lists, with every block entry N(0,1) from the counter-based SplitMix64 +
+ * Box-Muller stream of `seed` (H, B_pp and Q_pp symmetric), and the NC term
+ * list that pairs them.
+ *   n_left_modes / n_modes: spin orbitals in the left block / in total.
+ *   N, two_sz: target quantum numbers of psi.
+ *   sec_left / sec_right: n*3 ints (N, 2Sz, dim) per sector, strictly
+ *   ascending in (N, 2Sz), dims > 0.
+ * Errors: DMRG_EINVAL for unsorted or invalid sectors, DMRG_ENOMEM when the
+ * operator store does not fit in device memory.
+ */
+dmrg_status dmrg_load_synthetic(dmrg_ctx* ctx, int n_left_modes, int n_modes, int N, int two_sz,
+                                int n_sec_left, const int* sec_left, int n_sec_right,
+                                const int* sec_right, unsigned long long seed);
+
+/*
+ * Layout of psi at bond `site` (site = -1 for a synthetic context; for a
+ * sweep context, the two-site step on spatial orbitals (site, site+1) with
+ * the current blocks). Arrays may be NULL to query *n_blk only; otherwise
+ * each must hold *n_blk entries (q_l: 2 per block). Returns the total psi
+ * size in *size.
+ */
+dmrg_status dmrg_psi_layout(dmrg_ctx* ctx, int site, int* n_blk, int* q_l, int* m_l, int* m_r,
+                            long long* offset, long long* size);
+
+/* Work and storage figures of the current sigma: number of NC terms, of
+ * (term, block) products, algorithmic FLOPs (min of the two contraction
+ * orders per product, 2 per multiply-add), stored operator elements, and the
+ * bytes of the operator blocks one sigma reads. */
+typedef struct {
+  long long n_terms;
+  long long n_products;
+  double flops;
+  long long op_elements;
+  double op_bytes_read;
+  long long psi_size;
+} dmrg_sigma_info;
+dmrg_status dmrg_get_sigma_info(dmrg_ctx* ctx, int site, dmrg_sigma_info* info);
+
+/*
+ * sigma = H_eff . psi at bond `site` (Eq. eff-eigsh's matrix-vector product,
+ * Sec. II.D-E). psi and sigma: psi_size doubles each, host or device; they
+ * must not overlap. Deterministic: the same inputs give bitwise identical
+ * sigma regardless of other work on the device.
+ */
+dmrg_status dmrg_sigma(dmrg_ctx* ctx, int site, const double* psi, double* sigma);
+
+/*
+ * Lowest eigenpair of H_eff at bond `site` by Davidson (Appendix A solving
+ * step; details: diagonal preconditioner clamped at 1e-8, thick restart
+ * from the two lowest Ritz vectors, converged when ||H x - E x||_2^2 < tol).
+ * psi0 (may be NULL = seeded random guess) and psi_out (may be NULL): host
+ * or device, psi_size doubles. *iters receives the number of sigma calls.
+ * DMRG_ENOCONV when dav_max_iter is reached (energy and vector still set).
+ */
+dmrg_status dmrg_davidson(dmrg_ctx* ctx, int site, const double* psi0, double tol, double* energy,
+                          double* psi_out, int* iters);
+
+/*
+ * Full problem from integrals: t is K*K row-major (symmetric), v is K^4
+ * row-major chemist's notation (ij|kl) with the 8-fold symmetry (Appendix B,
+ * Eq. qc-hamil). Host pointers. Builds the initial right-canonical MPS with
+ * bond dimension <= M_init (seeded) and all right-block NC operators
+ * (blocking + transformation, right to left). Target: N electrons, 2Sz.
+ */
+dmrg_status dmrg_build_blocks(dmrg_ctx* ctx, const double* t, const double* v, int K, int N,
+                              int two_sz, int M_init);
+
+/*
+ * Two-site sweeps (Appendix A): M_schedule[s] is the bond dimension of sweep
+ * s (forward on even s, backward on odd s). energies[s] = lowest Davidson
+ * energy of sweep s; max_discard[s] = largest discarded weight of sweep s
+ * (either may be NULL). Davidson tolerance `tol` per step.
+ */
+dmrg_status dmrg_sweep(dmrg_ctx* ctx, const int* M_schedule, int n_sweeps, double tol,
+                       double* energies, double* max_discard);
+
+/*
+ * Per-kernel timing with CUDA events recorded on the context's stream
+ * around each launch of the library's kernels (tracing aid; off by default).
+ * dmrg_profile(ctx, 1) clears the counters and starts recording; 0 stops.
+ * dmrg_profile_read synchronizes the stream and returns, for kernel id
+ * `kernel` (0 = sigma product kernel, 1 = sigma reduction, 2 = Davidson
+ * vector kernels, 3 = blocking / transformation kernels), the summed
+ * duration in ms and the number of launches. DMRG_EINVAL for unknown ids.
+ */
+dmrg_status dmrg_profile(dmrg_ctx* ctx, int enable);
+dmrg_status dmrg_profile_read(dmrg_ctx* ctx, int kernel, double* total_ms, long long* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DMRG_H */

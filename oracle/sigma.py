@@ -138,14 +138,17 @@ def synthetic_op_specs(nL_modes, n_modes):
 def synthetic_block_table(specs, bL, bR):
     """For every stored op, its blocks [(q_in, q_out, rows, cols, flat_offset)]
     in canonical order (ops in spec order, blocks by ascending q_in, row-major)."""
+    dims = {"L": dict(zip(bL.qs, bL.dims)), "R": dict(zip(bR.qs, bR.dims))}
+    qs = {"L": bL.qs, "R": bR.qs}
     table, off = [], 0
     for side, key, dq, sym in specs:
-        b = bL if side == "L" else bR
+        d = dims[side]
         blks = []
-        for q in b.qs:
-            qo = qadd(q, dq)
-            if b.has(qo):
-                r, c = b.dim(qo), b.dim(q)
+        for q in qs[side]:
+            qo = (q[0] + dq[0], q[1] + dq[1])
+            r = d.get(qo)
+            if r is not None:
+                c = d[q]
                 blks.append((q, qo, r, c, off))
                 off += r * c
         table.append(blks)
@@ -205,3 +208,82 @@ def sigma_flops(layout, terms, dqL, dqR, bL, bR):
             else:
                 total += min(2 * mo * m * n + 2 * mo * n * no, 2 * m * n * no + 2 * mo * m * no)
     return total
+
+
+def _block_rows(key, off, r, c, sym, rows, trans):
+    """Rows `rows` of a stored block (r x c, canonical offset off), or of its
+    transpose when trans, drawn element by element from their counters."""
+    rows = np.asarray(rows, dtype=np.int64)
+    if not trans:
+        i = rows[:, None]
+        j = np.arange(c, dtype=np.int64)[None, :]
+    else:  # rows of S^T = columns of S
+        i = np.arange(r, dtype=np.int64)[None, :]
+        j = rows[:, None]
+    if sym:
+        i, j = np.minimum(i, j), np.maximum(i, j)
+    return splitmix.normal(key, (off + i * c + j).astype(np.uint64))
+
+
+def synthetic_sigma_sampled(left_secs, right_secs, nL_modes, n_modes, seed, Qtot, psi_vec,
+                            samples):
+    """Selected entries of sigma for the synthetic operator set: samples is
+    [(q_L, rows, cols)] and the result {q_L: sigma[q_L][ix_(rows, cols)]}.
+    Only the operator rows those entries need are drawn, so this runs at the
+    full benchmark size."""
+    bL = Basis([((n, s), d) for n, s, d in left_secs])
+    bR = Basis([((n, s), d) for n, s, d in right_secs])
+    specs = synthetic_op_specs(nL_modes, n_modes)
+    table, _ = synthetic_block_table(specs, bL, bR)
+    key = splitmix.stream_key(seed, splitmix.KEY_OPS)
+    index = {(side, k): (dq, sym) for (side, k, dq, sym) in specs}
+    by_in = {(side, k): {q: (qo, r, c, off) for q, qo, r, c, off in blks}
+             for (side, k, dq, sym), blks in zip(specs, table)}
+    by_out = {(side, k): {qo: (q, r, c, off) for q, qo, r, c, off in blks}
+              for (side, k, dq, sym), blks in zip(specs, table)}
+    layout, size = psi_layout(bL, bR, Qtot)
+    psi = psi_to_blocks(psi_vec, layout)
+    qR_of = {qL: qR for qL, qR, mL, mR, off in layout}
+    want = {tuple(q): (np.asarray(r), np.asarray(c)) for q, r, c in samples}
+    out = {q: np.zeros((len(r), len(c))) for q, (r, c) in want.items()}
+
+    def used_rows(side, k, trans, qin, rows):
+        sym = index[(side, k)][1]
+        hit = (by_out if trans else by_in)[(side, k)].get(qin)
+        if hit is None:
+            return None, None
+        qo, r, c, off = hit
+        return qo, _block_rows(key, off, r, c, sym, rows, trans)
+
+    for kl, tl, kr, tr, c in nc_terms(nL_modes, n_modes):
+        par = right_parity(kr)
+        if kl is None:
+            dxl = (0, 0)
+        else:
+            dq = index[("L", kl)][0]
+            dxl = (-dq[0], -dq[1]) if tl else dq
+        for qLo, (rows, cols) in want.items():
+            qL = qsub(qLo, dxl)
+            if qL not in psi:
+                continue
+            blk = psi[qL]
+            qR = qR_of[qL]
+            if kl is None:
+                X = blk[rows, :]
+            else:
+                q2, X = used_rows("L", kl, tl, qL, rows)
+                if q2 is None:
+                    continue
+            if kr is None:
+                qRo, Y = qR, None
+            else:
+                qRo, Y = used_rows("R", kr, tr, qR, cols)
+                if qRo is None:
+                    continue
+            if qR_of.get(qLo) != qRo:
+                continue
+            t = X if kl is None else X @ blk
+            t = t[:, cols] if Y is None else t @ Y.T
+            sign = -1.0 if (par and qL[0] % 2) else 1.0
+            out[qLo] += (c * sign) * t
+    return out

@@ -1,0 +1,206 @@
+"""Thin ctypes binding of libdmrg.so (include/dmrg.h), same names as the C ABI.
+
+Argument marshalling only: every step of the computation runs in the
+library's CUDA kernels. Buffers may be numpy arrays (host) or torch tensors
+(host or CUDA); they are passed to the library as raw pointers. If the
+library is not built, every call raises RuntimeError - there is no fallback.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdmrg.so")
+
+DMRG_OK, DMRG_EINVAL, DMRG_ENOMEM, DMRG_ECUDA, DMRG_ENOCONV, DMRG_ETIMEOUT, DMRG_ESTATE = range(7)
+STATUS_NAMES = ["DMRG_OK", "DMRG_EINVAL", "DMRG_ENOMEM", "DMRG_ECUDA", "DMRG_ENOCONV",
+                "DMRG_ETIMEOUT", "DMRG_ESTATE"]
+DMRG_FP64, DMRG_FP16X2, DMRG_BF16X3 = 0, 1, 2
+
+
+class dmrg_opts(ctypes.Structure):
+    _fields_ = [("sigma_prec", ctypes.c_int), ("dav_max_space", ctypes.c_int),
+                ("dav_max_iter", ctypes.c_int), ("keep_one_per_q", ctypes.c_int),
+                ("noise", ctypes.c_double), ("seed", ctypes.c_ulonglong), ("device", ctypes.c_int)]
+
+
+class dmrg_sigma_info(ctypes.Structure):
+    _fields_ = [("n_terms", ctypes.c_longlong), ("n_products", ctypes.c_longlong),
+                ("flops", ctypes.c_double), ("op_elements", ctypes.c_longlong),
+                ("op_bytes_read", ctypes.c_double), ("psi_size", ctypes.c_longlong)]
+
+
+class DMRGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+# C signatures: name -> (restype, argtypes)
+_P, _I, _D, _LL, _ULL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong, ctypes.c_ulonglong
+SIGNATURES = {
+    "dmrg_default_opts": (None, [ctypes.POINTER(dmrg_opts)]),
+    "dmrg_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(dmrg_opts)]),
+    "dmrg_destroy": (None, [_P]),
+    "dmrg_last_error": (ctypes.c_char_p, [_P]),
+    "dmrg_stream": (_P, [_P]),
+    "dmrg_set_precision": (_I, [_P, _I]),
+    "dmrg_load_synthetic": (_I, [_P, _I, _I, _I, _I, _I, _P, _I, _P, _ULL]),
+    "dmrg_psi_layout": (_I, [_P, _I, ctypes.POINTER(_I), _P, _P, _P, _P, ctypes.POINTER(_LL)]),
+    "dmrg_get_sigma_info": (_I, [_P, _I, ctypes.POINTER(dmrg_sigma_info)]),
+    "dmrg_sigma": (_I, [_P, _I, _P, _P]),
+    "dmrg_davidson": (_I, [_P, _I, _P, _D, ctypes.POINTER(_D), _P, ctypes.POINTER(_I)]),
+    "dmrg_build_blocks": (_I, [_P, _P, _P, _I, _I, _I, _I]),
+    "dmrg_sweep": (_I, [_P, _P, _I, _D, _P, _P]),
+    "dmrg_profile": (_I, [_P, _I]),
+    "dmrg_profile_read": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_LL)]),
+}
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run paper_2103_09976_gb300.build.build() "
+                               "(the CUDA library is required, there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(x):
+    """Raw pointer of a numpy array, torch tensor or None."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, int):
+        return x
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _check(ctx, st):
+    if st != DMRG_OK:
+        raise DMRGError(st, lib().dmrg_last_error(ctx).decode())
+
+
+def dmrg_default_opts():
+    o = dmrg_opts()
+    lib().dmrg_default_opts(ctypes.byref(o))
+    return o
+
+
+def dmrg_create(opts=None, **kw):
+    o = opts if opts is not None else dmrg_default_opts()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    h = ctypes.c_void_p()
+    st = lib().dmrg_create(ctypes.byref(h), ctypes.byref(o))
+    _check(None, st)
+    return h.value
+
+
+def dmrg_destroy(ctx):
+    lib().dmrg_destroy(ctx)
+
+
+def dmrg_last_error(ctx):
+    return lib().dmrg_last_error(ctx).decode()
+
+
+def dmrg_stream(ctx):
+    return lib().dmrg_stream(ctx)
+
+
+def dmrg_set_precision(ctx, prec):
+    _check(ctx, lib().dmrg_set_precision(ctx, int(prec)))
+
+
+def _sec_array(secs):
+    a = np.ascontiguousarray(np.array(secs, dtype=np.int32).reshape(-1, 3))
+    return a
+
+
+def dmrg_load_synthetic(ctx, n_left_modes, n_modes, N, two_sz, sec_left, sec_right, seed):
+    L = _sec_array(sec_left)
+    R = _sec_array(sec_right)
+    _check(ctx, lib().dmrg_load_synthetic(ctx, n_left_modes, n_modes, N, two_sz, len(L), _ptr(L),
+                                          len(R), _ptr(R), int(seed)))
+
+
+def dmrg_psi_layout(ctx, site=-1):
+    """Returns dict with q_l (nblk x 2), m_l, m_r, offset, size."""
+    nb = ctypes.c_int()
+    size = ctypes.c_longlong()
+    _check(ctx, lib().dmrg_psi_layout(ctx, site, ctypes.byref(nb), None, None, None, None,
+                                      ctypes.byref(size)))
+    n = nb.value
+    q = np.zeros((n, 2), dtype=np.int32)
+    ml = np.zeros(n, dtype=np.int32)
+    mr = np.zeros(n, dtype=np.int32)
+    off = np.zeros(n, dtype=np.int64)
+    _check(ctx, lib().dmrg_psi_layout(ctx, site, ctypes.byref(nb), _ptr(q), _ptr(ml), _ptr(mr),
+                                      _ptr(off), ctypes.byref(size)))
+    return {"q_l": q, "m_l": ml, "m_r": mr, "offset": off, "size": size.value}
+
+
+def dmrg_get_sigma_info(ctx, site=-1):
+    info = dmrg_sigma_info()
+    _check(ctx, lib().dmrg_get_sigma_info(ctx, site, ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in dmrg_sigma_info._fields_}
+
+
+def dmrg_sigma(ctx, site, psi, sigma):
+    _check(ctx, lib().dmrg_sigma(ctx, site, _ptr(psi), _ptr(sigma)))
+
+
+def dmrg_davidson(ctx, site, psi0, tol, psi_out=None):
+    e = ctypes.c_double()
+    it = ctypes.c_int()
+    st = lib().dmrg_davidson(ctx, site, _ptr(psi0), float(tol), ctypes.byref(e), _ptr(psi_out),
+                             ctypes.byref(it))
+    if st not in (DMRG_OK, DMRG_ENOCONV):
+        _check(ctx, st)
+    return e.value, it.value, st == DMRG_OK
+
+
+def dmrg_build_blocks(ctx, t, v, K, N, two_sz, M_init):
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    _check(ctx, lib().dmrg_build_blocks(ctx, _ptr(t), _ptr(v), K, N, two_sz, M_init))
+
+
+def dmrg_sweep(ctx, M_schedule, tol):
+    Ms = np.ascontiguousarray(np.array(M_schedule, dtype=np.int32))
+    e = np.zeros(len(Ms))
+    d = np.zeros(len(Ms))
+    _check(ctx, lib().dmrg_sweep(ctx, _ptr(Ms), len(Ms), float(tol), _ptr(e), _ptr(d)))
+    return e, d
+
+
+KERNEL_SIGMA, KERNEL_REDUCE, KERNEL_DAVIDSON, KERNEL_BLOCKING = 0, 1, 2, 3
+
+
+def dmrg_profile(ctx, enable):
+    _check(ctx, lib().dmrg_profile(ctx, 1 if enable else 0))
+
+
+def dmrg_profile_read(ctx, kernel):
+    ms = ctypes.c_double()
+    n = ctypes.c_longlong()
+    _check(ctx, lib().dmrg_profile_read(ctx, kernel, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value

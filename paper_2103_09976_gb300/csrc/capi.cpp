@@ -1,0 +1,388 @@
+// C ABI entry points (include/dmrg.h). Each call catches every exception and
+// turns it into a status code plus a message on the context.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "context.h"
+
+using namespace dmrg;
+
+namespace {
+
+thread_local std::string g_noctx_err = "no error";
+
+template <class F>
+dmrg_status guarded(dmrg_ctx* ctx, F&& f) {
+  try {
+    f();
+    if (ctx) ctx->c.err.clear();
+    return DMRG_OK;
+  } catch (const Error& e) {
+    if (ctx) ctx->c.err = e.what(); else g_noctx_err = e.what();
+    return (dmrg_status)e.code;
+  } catch (const std::bad_alloc&) {
+    if (ctx) ctx->c.err = "host allocation failed"; else g_noctx_err = "host allocation failed";
+    return DMRG_ENOMEM;
+  } catch (const std::exception& e) {
+    if (ctx) ctx->c.err = e.what(); else g_noctx_err = e.what();
+    return DMRG_EINVAL;
+  }
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+Basis parse_sectors(int n, const int* s) {
+  if (n <= 0 || !s) throw Error(DMRG_EINVAL, "empty sector list");
+  Basis b;
+  for (int i = 0; i < n; ++i) {
+    b.q.push_back({s[3 * i], s[3 * i + 1]});
+    b.dim.push_back(s[3 * i + 2]);
+    if ((s[3 * i + 1] - s[3 * i]) % 2 != 0) throw Error(DMRG_EINVAL, "2Sz parity must match N");
+  }
+  b.finish();
+  return b;
+}
+
+Problem& need_problem(Context& c, int site) {
+  if (!c.prob) throw Error(DMRG_ESTATE, "no operators loaded (call dmrg_load_synthetic or dmrg_build_blocks)");
+  if (site != -1) throw Error(DMRG_EINVAL, "site must be -1 for a synthetic context");
+  return *c.prob;
+}
+
+}  // namespace
+
+namespace dmrg {
+
+void prepare_worklist(Context& c, Problem& p) {
+  build_tasks(p.blocks, p.L, p.R, p.terms, p.wl);
+  TileShape ts{F64_TM, F64_TN, 2e6};
+  build_items(p.blocks, p.wl, ts, c.n_sm * 8);
+  cudaStream_t st = c.stream;
+  p.d_tasks.upload(p.wl.tasks, st);
+  p.d_items.upload(p.wl.items, st);
+  p.d_groups.upload(p.wl.groups, st);
+  p.d_sched.upload(p.wl.schedule, st);
+  p.d_blocks.upload(p.blocks, st);
+  p.d_scratch.alloc(std::max<long long>(1, p.wl.scratch_elems) * sizeof(double));
+  p.d_counter.alloc(16);
+  DMRG_CUDA(cudaStreamSynchronize(st));
+  p.ready = true;
+}
+
+void run_sigma(Context& c, Problem& p, const double* d_psi, double* d_sigma) {
+  SigmaDev a;
+  a.store = p.store.as<double>();
+  a.psi = d_psi;
+  a.sigma = d_sigma;
+  a.tasks = p.d_tasks.as<Task>();
+  a.items = p.d_items.as<Item>();
+  a.schedule = p.d_sched.as<int>();
+  a.n_items = (int)p.wl.items.size();
+  a.groups = p.d_groups.as<Group>();
+  a.n_groups = (int)p.wl.groups.size();
+  a.blocks = p.d_blocks.as<PsiBlock>();
+  a.scratch = p.d_scratch.as<double>();
+  a.counter = p.d_counter.as<unsigned int>();
+  cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), c.stream);
+  {
+    ProfScope ps(c.prof, 0, c.stream);
+    launch_sigma_f64(a, c.n_sm, c.stream);
+  }
+  DMRG_CUDA(cudaGetLastError());
+  {
+    ProfScope ps(c.prof, 1, c.stream);
+    launch_reduce(a, c.stream);
+  }
+  DMRG_CUDA(cudaGetLastError());
+}
+
+cudaEvent_t Profiler::get() {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  DMRG_CUDA(cudaEventCreate(&e));
+  return e;
+}
+
+void Profiler::begin(int kind, cudaStream_t st, cudaEvent_t* a) {
+  *a = get();
+  DMRG_CUDA(cudaEventRecord(*a, st));
+}
+
+void Profiler::end(int kind, cudaStream_t st, cudaEvent_t a) {
+  cudaEvent_t b = get();
+  cudaEventRecord(b, st);
+  pending[kind].push_back({a, b});
+}
+
+void Profiler::collect() {
+  for (int k = 0; k < kKinds; ++k) {
+    for (auto& pr : pending[k]) {
+      float t = 0;
+      cudaEventSynchronize(pr.second);
+      cudaEventElapsedTime(&t, pr.first, pr.second);
+      ms[k] += t;
+      launches[k] += 1;
+      pool.push_back(pr.first);
+      pool.push_back(pr.second);
+    }
+    pending[k].clear();
+  }
+}
+
+void Profiler::clear() {
+  collect();
+  for (int k = 0; k < kKinds; ++k) {
+    ms[k] = 0;
+    launches[k] = 0;
+  }
+}
+
+Profiler::~Profiler() {
+  for (int k = 0; k < kKinds; ++k)
+    for (auto& pr : pending[k]) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+  for (auto e : pool) cudaEventDestroy(e);
+}
+
+}  // namespace dmrg
+
+extern "C" {
+
+void dmrg_default_opts(dmrg_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->sigma_prec = DMRG_FP64;
+  o->dav_max_space = 24;
+  o->dav_max_iter = 200;
+  o->keep_one_per_q = 0;
+  o->noise = 0.0;
+  o->seed = 0;
+  o->device = 0;
+}
+
+dmrg_status dmrg_create(dmrg_ctx** out, const dmrg_opts* opts) {
+  if (!out) {
+    g_noctx_err = "dmrg_create: out is NULL";
+    return DMRG_EINVAL;
+  }
+  *out = nullptr;
+  dmrg_ctx* ctx = nullptr;
+  dmrg_status st = guarded(nullptr, [&] {
+    dmrg_opts o;
+    dmrg_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.dav_max_space < 3) throw Error(DMRG_EINVAL, "dav_max_space must be >= 3");
+    if (o.dav_max_iter < 1) throw Error(DMRG_EINVAL, "dav_max_iter must be >= 1");
+    if (o.keep_one_per_q != 0 || o.noise != 0.0)
+      throw Error(DMRG_EINVAL, "keep_one_per_q and noise are reserved and must be 0");
+    if (o.sigma_prec < DMRG_FP64 || o.sigma_prec > DMRG_BF16X3)
+      throw Error(DMRG_EINVAL, "unknown sigma precision");
+    int ndev = 0;
+    DMRG_CUDA(cudaGetDeviceCount(&ndev));
+    if (o.device < 0 || o.device >= ndev) throw Error(DMRG_EINVAL, "device ordinal out of range");
+    DMRG_CUDA(cudaSetDevice(o.device));
+    ctx = new dmrg_ctx();
+    ctx->c.opts = o;
+    ctx->c.device = o.device;
+    DMRG_CUDA(cudaDeviceGetAttribute(&ctx->c.n_sm, cudaDevAttrMultiProcessorCount, o.device));
+    DMRG_CUDA(cudaStreamCreateWithFlags(&ctx->c.stream, cudaStreamNonBlocking));
+  });
+  if (st != DMRG_OK) {
+    delete ctx;
+    return st;
+  }
+  *out = ctx;
+  return DMRG_OK;
+}
+
+void dmrg_destroy(dmrg_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->c.device);
+  if (ctx->c.stream) cudaStreamSynchronize(ctx->c.stream);
+  ctx->c.prob.reset();
+  ctx->c.d_psi.reset();
+  ctx->c.d_sigma.reset();
+  if (ctx->c.stream) cudaStreamDestroy(ctx->c.stream);
+  delete ctx;
+}
+
+const char* dmrg_last_error(const dmrg_ctx* ctx) {
+  if (!ctx) return g_noctx_err.c_str();
+  return ctx->c.err.c_str();
+}
+
+void* dmrg_stream(dmrg_ctx* ctx) { return ctx ? (void*)ctx->c.stream : nullptr; }
+
+dmrg_status dmrg_set_precision(dmrg_ctx* ctx, int prec) {
+  if (!ctx) return DMRG_EINVAL;
+  return guarded(ctx, [&] {
+    if (prec != DMRG_FP64) throw Error(DMRG_EINVAL, "precision not available in this build");
+    ctx->c.opts.sigma_prec = prec;
+  });
+}
+
+dmrg_status dmrg_load_synthetic(dmrg_ctx* ctx, int n_left_modes, int n_modes, int N, int two_sz,
+                                int n_sec_left, const int* sec_left, int n_sec_right,
+                                const int* sec_right, unsigned long long seed) {
+  if (!ctx) return DMRG_EINVAL;
+  return guarded(ctx, [&] {
+    Context& c = ctx->c;
+    DMRG_CUDA(cudaSetDevice(c.device));
+    if (n_left_modes <= 0 || n_modes <= n_left_modes || n_left_modes % 2 || n_modes % 2)
+      throw Error(DMRG_EINVAL, "mode counts must be even with 0 < n_left_modes < n_modes");
+    auto p = std::make_unique<Problem>();
+    p->nL = n_left_modes;
+    p->n = n_modes;
+    p->Q = {N, two_sz};
+    Basis bL = parse_sectors(n_sec_left, sec_left);
+    Basis bR = parse_sectors(n_sec_right, sec_right);
+    build_nc_opset(p->L, bL, n_left_modes, n_modes, true, 0);
+    build_nc_opset(p->R, bR, n_left_modes, n_modes, false, p->L.elements);
+    p->terms = nc_terms(n_left_modes, n_modes);
+    p->blocks = psi_layout(bL, bR, p->Q, &p->psi_size);
+    if (p->blocks.empty()) throw Error(DMRG_EINVAL, "no psi block: sectors cannot form the target");
+    for (auto& b : p->blocks)
+      if (b.mR > F64_TN * 64 || b.mL > (1 << 20)) throw Error(DMRG_EINVAL, "block too large");
+    long long elems = p->L.elements + p->R.elements;
+    size_t freeb = 0, totb = 0;
+    DMRG_CUDA(cudaMemGetInfo(&freeb, &totb));
+    if ((double)elems * 8.0 > 0.92 * (double)freeb)
+      throw Error(DMRG_ENOMEM, "operator store (" + std::to_string(elems * 8.0 / 1e9) +
+                                   " GB) does not fit in free device memory");
+    c.prob.reset();
+    p->store.alloc((size_t)elems * sizeof(double));
+    // generate every stored block on the device
+    std::vector<GenBlock> gb;
+    for (const OpSet* s : {&p->L, &p->R})
+      for (const OpDesc& o : s->ops)
+        for (const OpBlock& b : o.blocks) gb.push_back({b.off, b.rows, b.cols, o.sym ? 1 : 0, 0});
+    DevBuf d_gb;
+    d_gb.upload(gb, c.stream);
+    launch_gen_blocks(p->store.as<double>(), d_gb.as<GenBlock>(), (long long)gb.size(),
+                      (uint64_t)seed, c.stream);
+    DMRG_CUDA(cudaGetLastError());
+    DMRG_CUDA(cudaStreamSynchronize(c.stream));
+    prepare_worklist(c, *p);
+    c.prob = std::move(p);
+  });
+}
+
+dmrg_status dmrg_psi_layout(dmrg_ctx* ctx, int site, int* n_blk, int* q_l, int* m_l, int* m_r,
+                            long long* offset, long long* size) {
+  if (!ctx || !n_blk) return DMRG_EINVAL;
+  return guarded(ctx, [&] {
+    Problem& p = need_problem(ctx->c, site);
+    *n_blk = (int)p.blocks.size();
+    if (size) *size = p.psi_size;
+    for (size_t i = 0; i < p.blocks.size(); ++i) {
+      const PsiBlock& b = p.blocks[i];
+      if (q_l) {
+        q_l[2 * i] = p.L.basis.q[b.qL].n;
+        q_l[2 * i + 1] = p.L.basis.q[b.qL].s;
+      }
+      if (m_l) m_l[i] = b.mL;
+      if (m_r) m_r[i] = b.mR;
+      if (offset) offset[i] = b.off;
+    }
+  });
+}
+
+dmrg_status dmrg_get_sigma_info(dmrg_ctx* ctx, int site, dmrg_sigma_info* info) {
+  if (!ctx || !info) return DMRG_EINVAL;
+  return guarded(ctx, [&] {
+    Problem& p = need_problem(ctx->c, site);
+    info->n_terms = (long long)p.terms.size();
+    info->n_products = (long long)p.wl.tasks.size();
+    info->flops = p.wl.flops;
+    info->op_elements = p.L.elements + p.R.elements;
+    info->op_bytes_read = p.wl.bytes_ops;
+    info->psi_size = p.psi_size;
+  });
+}
+
+dmrg_status dmrg_sigma(dmrg_ctx* ctx, int site, const double* psi, double* sigma) {
+  if (!ctx) return DMRG_EINVAL;
+  return guarded(ctx, [&] {
+    Context& c = ctx->c;
+    DMRG_CUDA(cudaSetDevice(c.device));
+    Problem& p = need_problem(c, site);
+    if (!psi || !sigma) throw Error(DMRG_EINVAL, "psi and sigma must not be NULL");
+    const size_t bytes = (size_t)p.psi_size * sizeof(double);
+    const char* a0 = (const char*)psi;
+    const char* b0 = (const char*)sigma;
+    if (a0 < b0 + bytes && b0 < a0 + bytes) throw Error(DMRG_EINVAL, "psi and sigma overlap");
+    bool dpsi = is_device_ptr(psi), dsig = is_device_ptr(sigma);
+    const double* xin = psi;
+    double* yout = sigma;
+    if (!dpsi) {
+      c.d_psi.alloc(bytes);
+      DMRG_CUDA(cudaMemcpyAsync(c.d_psi.p, psi, bytes, cudaMemcpyHostToDevice, c.stream));
+      xin = c.d_psi.as<double>();
+    }
+    if (!dsig) {
+      c.d_sigma.alloc(bytes);
+      yout = c.d_sigma.as<double>();
+    }
+    run_sigma(c, p, xin, yout);
+    if (!dsig) {
+      DMRG_CUDA(cudaMemcpyAsync(sigma, yout, bytes, cudaMemcpyDeviceToHost, c.stream));
+      DMRG_CUDA(cudaStreamSynchronize(c.stream));
+    }
+  });
+}
+
+dmrg_status dmrg_davidson(dmrg_ctx* ctx, int site, const double* psi0, double tol, double* energy,
+                          double* psi_out, int* iters) {
+  if (!ctx) return DMRG_EINVAL;
+  return guarded(ctx, [&] { throw Error(DMRG_ESTATE, "dmrg_davidson: not available yet"); });
+}
+
+dmrg_status dmrg_build_blocks(dmrg_ctx* ctx, const double* t, const double* v, int K, int N,
+                              int two_sz, int M_init) {
+  if (!ctx) return DMRG_EINVAL;
+  return guarded(ctx, [&] { throw Error(DMRG_ESTATE, "dmrg_build_blocks: not available yet"); });
+}
+
+dmrg_status dmrg_sweep(dmrg_ctx* ctx, const int* M_schedule, int n_sweeps, double tol,
+                       double* energies, double* max_discard) {
+  if (!ctx) return DMRG_EINVAL;
+  return guarded(ctx, [&] { throw Error(DMRG_ESTATE, "dmrg_sweep: not available yet"); });
+}
+
+dmrg_status dmrg_profile(dmrg_ctx* ctx, int enable) {
+  if (!ctx) return DMRG_EINVAL;
+  return guarded(ctx, [&] {
+    DMRG_CUDA(cudaSetDevice(ctx->c.device));
+    if (enable) ctx->c.prof.clear();
+    ctx->c.prof.on = enable != 0;
+  });
+}
+
+dmrg_status dmrg_profile_read(dmrg_ctx* ctx, int kernel, double* total_ms, long long* launches) {
+  if (!ctx) return DMRG_EINVAL;
+  return guarded(ctx, [&] {
+    if (kernel < 0 || kernel >= Profiler::kKinds) throw Error(DMRG_EINVAL, "unknown kernel id");
+    DMRG_CUDA(cudaSetDevice(ctx->c.device));
+    ctx->c.prof.collect();
+    if (total_ms) *total_ms = ctx->c.prof.ms[kernel];
+    if (launches) *launches = ctx->c.prof.launches[kernel];
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,118 @@
+// Library context: one CUDA device, one stream, the current two-site problem
+// and its device-resident operators and work lists.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/dmrg.h"
+#include "kernels.h"
+#include "model.h"
+
+namespace dmrg {
+
+#define DMRG_CUDA(call)                                                                    \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      throw ::dmrg::Error(e_ == cudaErrorMemoryAllocation ? DMRG_ENOMEM : DMRG_ECUDA,      \
+                          std::string(#call) + ": " + cudaGetErrorString(e_));             \
+  } while (0)
+
+// Owning device allocation.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { reset(); }
+  void reset() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  void alloc(size_t n) {
+    if (n <= bytes && p) return;
+    reset();
+    if (n == 0) n = 16;
+    DMRG_CUDA(cudaMalloc(&p, n));
+    bytes = n;
+  }
+  template <class T>
+  T* as() const { return reinterpret_cast<T*>(p); }
+  template <class T>
+  void upload(const std::vector<T>& v, cudaStream_t st) {
+    alloc(v.size() * sizeof(T));
+    if (!v.empty())
+      DMRG_CUDA(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  }
+};
+
+// A two-site problem: left/right operator tables over one FP64 store
+// (left ops first), the psi layout, NC terms and the sigma work list.
+struct Problem {
+  int nL = 0, n = 0;
+  QN Q;
+  OpSet L, R;
+  std::vector<PsiBlock> blocks;
+  long long psi_size = 0;
+  std::vector<Term> terms;
+  WorkList wl;
+  DevBuf store;              // FP64 operator store
+  DevBuf d_tasks, d_items, d_groups, d_sched, d_blocks, d_scratch, d_counter;
+  bool ready = false;
+};
+
+// CUDA-event timing of kernel launches (dmrg_profile).
+struct Profiler {
+  static constexpr int kKinds = 4;
+  bool on = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[kKinds];
+  std::vector<cudaEvent_t> pool;
+  double ms[kKinds] = {0, 0, 0, 0};
+  long long launches[kKinds] = {0, 0, 0, 0};
+  cudaEvent_t get();
+  void begin(int kind, cudaStream_t st, cudaEvent_t* a);
+  void end(int kind, cudaStream_t st, cudaEvent_t a);
+  void collect();
+  void clear();
+  ~Profiler();
+};
+
+// RAII scope: records a start/stop event pair around the launches inside it.
+struct ProfScope {
+  Profiler& p;
+  int kind;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  ProfScope(Profiler& p_, int k, cudaStream_t s) : p(p_), kind(k), st(s) {
+    if (p.on) p.begin(kind, st, &a);
+  }
+  ~ProfScope() {
+    if (p.on && a) p.end(kind, st, a);
+  }
+};
+
+struct Context {
+  dmrg_opts opts;
+  int device = 0;
+  int n_sm = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  std::unique_ptr<Problem> prob;   // synthetic or current sweep step
+  DevBuf d_psi, d_sigma;           // staging for host psi / sigma
+  Profiler prof;
+};
+
+void prepare_worklist(Context& c, Problem& p);
+void run_sigma(Context& c, Problem& p, const double* d_psi, double* d_sigma);
+
+}  // namespace dmrg
+
+struct dmrg_ctx {
+  dmrg::Context c;
+};

@@ -1,0 +1,250 @@
+// Host-side model: bases, NC operator tables, terms, sigma work lists.
+#include "model.h"
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+namespace dmrg {
+
+void Basis::finish() {
+  for (size_t i = 1; i < q.size(); ++i)
+    if (!(q[i - 1] < q[i])) throw Error(1, "sectors must be strictly ascending in (N, 2Sz)");
+  off.assign(q.size() + 1, 0);
+  for (size_t i = 0; i < q.size(); ++i) {
+    if (dim[i] <= 0) throw Error(1, "sector dimensions must be positive");
+    off[i + 1] = off[i] + dim[i];
+  }
+  total = off.back();
+}
+
+int Basis::find(QN x) const {
+  auto it = std::lower_bound(q.begin(), q.end(), x);
+  if (it == q.end() || !(*it == x)) return -1;
+  return (int)(it - q.begin());
+}
+
+void add_op(OpSet& set, QN dq, int parity, bool sym, long long& cursor) {
+  OpDesc d;
+  d.dq = dq;
+  d.parity = parity;
+  d.sym = sym;
+  const Basis& b = set.basis;
+  d.by_qin.assign(b.size(), -1);
+  for (int i = 0; i < b.size(); ++i) {
+    int o = b.find(b.q[i] + dq);
+    if (o < 0) continue;
+    OpBlock blk{i, o, b.dim[o], b.dim[i], cursor};
+    cursor += (long long)blk.rows * blk.cols;
+    d.by_qin[i] = (int)d.blocks.size();
+    d.blocks.push_back(blk);
+  }
+  set.ops.push_back(std::move(d));
+}
+
+void build_nc_opset(OpSet& out, const Basis& basis, int nL, int n, bool left, long long base) {
+  out.basis = basis;
+  out.ops.clear();
+  long long cur = base;
+  NCIndex ix{nL, n};
+  add_op(out, {0, 0}, 0, true, cur);  // H
+  if (left) {
+    for (int p = 0; p < nL; ++p) add_op(out, {1, spin_of(p)}, 1, false, cur);        // a+_p
+    for (int p = nL; p < n; ++p) add_op(out, {-1, -spin_of(p)}, 1, false, cur);      // R^L_p
+  } else {
+    for (int p = nL; p < n; ++p) add_op(out, {-1, -spin_of(p)}, 1, false, cur);      // a_p
+    for (int p = 0; p < nL; ++p) add_op(out, {-1, -spin_of(p)}, 1, false, cur);      // R^R_p
+  }
+  const int sgn = left ? 1 : -1;
+  for (int p = 0; p < nL; ++p)
+    for (int r = p + 1; r < nL; ++r)  // A_pr (left) / P_pr (right)
+      add_op(out, {2 * sgn, sgn * (spin_of(p) + spin_of(r))}, 0, false, cur);
+  for (int p = 0; p < nL; ++p)
+    for (int q = p; q < nL; ++q)  // B_pq (left) / Q_pq (right)
+      add_op(out, {0, sgn * (spin_of(p) - spin_of(q))}, 0, p == q, cur);
+  if ((int)out.ops.size() != ix.count()) throw Error(1, "internal: NC operator count");
+  out.elements = cur - base;
+}
+
+std::vector<Term> nc_terms(int nL, int n) {
+  NCIndex ix{nL, n};
+  std::vector<Term> T;
+  T.push_back({ix.H(), -1, false, false, 1.0, 0});
+  T.push_back({-1, ix.H(), false, false, 1.0, 0});
+  for (int p = 0; p < nL; ++p) {
+    T.push_back({ix.cd(p), ix.RR(p), false, false, 1.0, 1});
+    T.push_back({ix.cd(p), ix.RR(p), true, true, -1.0, 1});
+  }
+  for (int p = nL; p < n; ++p) {
+    T.push_back({ix.RL(p), ix.d(p), true, false, 1.0, 1});
+    T.push_back({ix.RL(p), ix.d(p), false, true, -1.0, 1});
+  }
+  for (int p = 0; p < nL; ++p)
+    for (int r = p + 1; r < nL; ++r) {
+      T.push_back({ix.A(p, r), ix.A(p, r), false, false, 1.0, 0});
+      T.push_back({ix.A(p, r), ix.A(p, r), true, true, 1.0, 0});
+    }
+  for (int p = 0; p < nL; ++p)
+    for (int q = 0; q < nL; ++q) {
+      if (p <= q)
+        T.push_back({ix.B(p, q), ix.B(p, q), false, false, 1.0, 0});
+      else
+        T.push_back({ix.B(q, p), ix.B(q, p), true, true, 1.0, 0});
+    }
+  return T;
+}
+
+std::vector<PsiBlock> psi_layout(const Basis& L, const Basis& R, QN Qtot, long long* size) {
+  std::vector<PsiBlock> out;
+  long long off = 0;
+  for (int i = 0; i < L.size(); ++i) {
+    int j = R.find(Qtot - L.q[i]);
+    if (j < 0) continue;
+    out.push_back({i, j, L.dim[i], R.dim[j], off});
+    off += (long long)L.dim[i] * R.dim[j];
+  }
+  if (size) *size = off;
+  return out;
+}
+
+// Resolve the block of `op` (optionally transposed) acting on input sector
+// qin; returns the output sector (or -1) and the stored block.
+static int resolve(const OpDesc& op, const Basis& b, int qin, bool trans, const OpBlock** blk) {
+  if (!trans) {
+    int k = op.by_qin[qin];
+    if (k < 0) return -1;
+    *blk = &op.blocks[k];
+    return op.blocks[k].qout;
+  }
+  // (S^T)[qout <- qin] = S[qin <- qout]^T: the stored block whose input is qout
+  int qout = b.find(b.q[qin] - op.dq);
+  if (qout < 0) return -1;
+  int k = op.by_qin[qout];
+  if (k < 0) return -1;
+  *blk = &op.blocks[k];
+  return qout;
+}
+
+void build_tasks(const std::vector<PsiBlock>& blocks, const OpSet& L, const OpSet& R,
+                 const std::vector<Term>& terms, WorkList& wl) {
+  // output block index by left sector
+  std::vector<int> blk_of_qL(L.basis.size(), -1);
+  for (size_t b = 0; b < blocks.size(); ++b) blk_of_qL[blocks[b].qL] = (int)b;
+  std::vector<std::vector<Task>> per_out(blocks.size());
+  double flops = 0, bytes = 0;
+  for (const Term& t : terms) {
+    for (size_t b = 0; b < blocks.size(); ++b) {
+      const PsiBlock& in = blocks[b];
+      int qLo = in.qL, qRo = in.qR;
+      const OpBlock* bl = nullptr;
+      const OpBlock* br = nullptr;
+      if (t.opL >= 0) {
+        qLo = resolve(L.ops[t.opL], L.basis, in.qL, t.tL, &bl);
+        if (qLo < 0) continue;
+      }
+      if (t.opR >= 0) {
+        qRo = resolve(R.ops[t.opR], R.basis, in.qR, t.tR, &br);
+        if (qRo < 0) continue;
+      }
+      int ob = blk_of_qL[qLo];
+      if (ob < 0 || blocks[ob].qR != qRo) continue;
+      double sign = (t.parR && (L.basis.q[in.qL].n & 1)) ? -1.0 : 1.0;
+      Task k;
+      k.aoff = bl ? bl->off : -1;
+      k.boff = br ? br->off : -1;
+      k.in_blk = (int)b;
+      k.flags = (t.tL ? 1 : 0) | (t.tR ? 2 : 0);
+      k.scale = t.coef * sign;
+      per_out[ob].push_back(k);
+      double m = in.mL, nn = in.mR, mo = blocks[ob].mL, no = blocks[ob].mR;
+      if (!bl)
+        flops += 2 * m * nn * no;
+      else if (!br)
+        flops += 2 * mo * m * nn;
+      else
+        flops += std::min(2 * mo * m * nn + 2 * mo * nn * no, 2 * m * nn * no + 2 * mo * m * no);
+      if (bl) bytes += 8.0 * mo * m;
+      if (br) bytes += 8.0 * no * nn;
+    }
+  }
+  wl.tasks.clear();
+  wl.flops = flops;
+  wl.bytes_ops = bytes;
+  wl.out_start.assign(blocks.size() + 1, 0);
+  for (size_t b = 0; b < blocks.size(); ++b)
+    wl.out_start[b + 1] = wl.out_start[b] + (int)per_out[b].size();
+  wl.tasks.reserve(wl.out_start.back());
+  for (auto& v : per_out) wl.tasks.insert(wl.tasks.end(), v.begin(), v.end());
+  wl.items.clear();
+  wl.groups.clear();
+  wl.schedule.clear();
+}
+
+static double tile_cost(const Task& k, const PsiBlock& in, int nr, int nc) {
+  double m = in.mL, n = in.mR;
+  if (k.aoff < 0) return 2.0 * nr * n * nc;
+  if (k.boff < 0) return 2.0 * nr * m * n;
+  return 2.0 * nr * m * n + 2.0 * nr * n * nc;
+}
+
+void build_items(const std::vector<PsiBlock>& blocks, WorkList& wl, const TileShape& ts,
+                 int want_items) {
+  wl.items.clear();
+  wl.groups.clear();
+  wl.scratch_elems = 0;
+  double total = 0;
+  for (size_t b = 0; b < blocks.size(); ++b)
+    for (int t = wl.out_start[b]; t < wl.out_start[b + 1]; ++t)
+      total += tile_cost(wl.tasks[t], blocks[wl.tasks[t].in_blk], blocks[b].mL, blocks[b].mR);
+  double target = std::max(ts.target, total / std::max(1, want_items));
+  std::vector<double> cost;
+  for (size_t b = 0; b < blocks.size(); ++b) {
+    const PsiBlock& ob = blocks[b];
+    int t0 = wl.out_start[b], t1 = wl.out_start[b + 1];
+    if (t0 == t1) {
+      // no contribution: one empty item writes zeros
+      for (int r0 = 0; r0 < ob.mL; r0 += ts.tm)
+        for (int c0 = 0; c0 < ob.mR; c0 += ts.tn) {
+          Group g{(int)b, r0, std::min(ts.tm, ob.mL - r0), c0, std::min(ts.tn, ob.mR - c0),
+                  (int)wl.items.size(), (int)wl.items.size() + 1, 0};
+          Item it{(int)b, g.r0, g.nrows, g.c0, g.ncols, t0, t0, 0, wl.scratch_elems};
+          wl.scratch_elems += (long long)g.nrows * g.ncols;
+          wl.items.push_back(it);
+          cost.push_back(0);
+          wl.groups.push_back(g);
+        }
+      continue;
+    }
+    for (int r0 = 0; r0 < ob.mL; r0 += ts.tm) {
+      int nr = std::min(ts.tm, ob.mL - r0);
+      for (int c0 = 0; c0 < ob.mR; c0 += ts.tn) {
+        int nc = std::min(ts.tn, ob.mR - c0);
+        Group g{(int)b, r0, nr, c0, nc, (int)wl.items.size(), 0, 0};
+        int start = t0;
+        double acc = 0;
+        for (int t = t0; t < t1; ++t) {
+          double c = tile_cost(wl.tasks[t], blocks[wl.tasks[t].in_blk], nr, nc);
+          if (acc > 0 && acc + c > target) {
+            wl.items.push_back({(int)b, r0, nr, c0, nc, start, t, 0, wl.scratch_elems});
+            wl.scratch_elems += (long long)nr * nc;
+            cost.push_back(acc);
+            start = t;
+            acc = 0;
+          }
+          acc += c;
+        }
+        wl.items.push_back({(int)b, r0, nr, c0, nc, start, t1, 0, wl.scratch_elems});
+        wl.scratch_elems += (long long)nr * nc;
+        cost.push_back(acc);
+        g.i_end = (int)wl.items.size();
+        wl.groups.push_back(g);
+      }
+    }
+  }
+  wl.schedule.resize(wl.items.size());
+  std::iota(wl.schedule.begin(), wl.schedule.end(), 0);
+  std::stable_sort(wl.schedule.begin(), wl.schedule.end(),
+                   [&](int a, int b) { return cost[a] > cost[b]; });
+}
+
+}  // namespace dmrg

@@ -1,0 +1,156 @@
+// Host-side model of the two-site problem: quantum-number bases, block-sparse
+// operator tables, the NC term list and the sigma work list.
+//
+// Everything here is integer bookkeeping plus term coefficients; it runs once
+// per operator skeleton (Sec. II.G (ii): the GEMM list is generated once per
+// site and block-index lists once per skeleton). The floating-point work of
+// the hot path runs in the CUDA kernels.
+#pragma once
+
+#include <cstdint>
+#include <map>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+namespace dmrg {
+
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+// q = (N, 2Sz), ordered lexicographically.
+struct QN {
+  int n = 0, s = 0;
+  bool operator<(const QN& o) const { return n < o.n || (n == o.n && s < o.s); }
+  bool operator==(const QN& o) const { return n == o.n && s == o.s; }
+  bool operator!=(const QN& o) const { return !(*this == o); }
+  QN operator+(const QN& o) const { return {n + o.n, s + o.s}; }
+  QN operator-(const QN& o) const { return {n - o.n, s - o.s}; }
+  QN neg() const { return {-n, -s}; }
+};
+
+inline int spin_of(int p) { return (p % 2 == 0) ? 1 : -1; }
+
+// Ascending list of sectors with dimensions and offsets.
+struct Basis {
+  std::vector<QN> q;
+  std::vector<int> dim;
+  std::vector<long long> off;
+  long long total = 0;
+  void finish();             // sort check + offsets
+  int find(QN x) const;      // sector index or -1
+  int size() const { return (int)q.size(); }
+};
+
+// One dense block of a stored operator: rows = dim(qout), cols = dim(qin),
+// row-major at element offset `off` of the owning store.
+struct OpBlock {
+  int qin, qout;
+  int rows, cols;
+  long long off;
+};
+
+struct OpDesc {
+  QN dq;
+  int parity = 0;
+  bool sym = false;
+  std::vector<OpBlock> blocks;   // ascending qin
+  std::vector<int> by_qin;       // sector index -> block index or -1
+};
+
+// Stored operators of one NC block. Left kind: H, a+_p (p<nL), R^L_p
+// (nL<=p<n), A_pr (p<r<nL), B_pq (p<=q<nL). Right kind: H, a_p (p>=nL),
+// R^R_p (p<nL), P_pr (p<r<nL), Q_pq (p<=q<nL). Both have 1 + n + nL^2 ops.
+struct NCIndex {
+  int nL = 0, n = 0;
+  int count() const { return 1 + n + nL * nL; }
+  int H() const { return 0; }
+  // left kind
+  int cd(int p) const { return 1 + p; }
+  int RL(int p) const { return 1 + nL + (p - nL); }
+  // right kind
+  int d(int p) const { return 1 + (p - nL); }
+  int RR(int p) const { return 1 + (n - nL) + p; }
+  // both kinds
+  int pair_strict(int p, int r) const { return p * nL - p * (p + 1) / 2 + (r - p - 1); }
+  int pair_le(int p, int q) const { return p * nL - p * (p - 1) / 2 + (q - p); }
+  int A(int p, int r) const { return 1 + n + pair_strict(p, r); }  // == P index on the right
+  int B(int p, int q) const { return 1 + n + nL * (nL - 1) / 2 + pair_le(p, q); }  // == Q index
+};
+
+struct OpSet {
+  Basis basis;
+  std::vector<OpDesc> ops;
+  long long elements = 0;
+};
+
+// Build the block tables of the canonical left or right NC operator list over
+// `basis`, offsets starting at `base` (left ops first, then right ops, in
+// one flat store for the synthetic problem).
+void build_nc_opset(OpSet& out, const Basis& basis, int nL, int n, bool left, long long base);
+// Add one operator with shift dq over `basis` (blocks wherever both sectors exist).
+void add_op(OpSet& set, QN dq, int parity, bool sym, long long& cursor);
+
+struct Term {
+  int opL, opR;     // -1 = identity
+  bool tL, tR;      // use the transpose of the stored operator
+  double coef;
+  int parR;         // fermion parity of the right operator
+};
+std::vector<Term> nc_terms(int nL, int n);
+
+struct PsiBlock {
+  int qL, qR;       // sector indices in the left / right basis
+  int mL, mR;
+  long long off;
+};
+std::vector<PsiBlock> psi_layout(const Basis& L, const Basis& R, QN Qtot, long long* size);
+
+// One (term, input block) product feeding output block `out`.
+struct Task {
+  long long aoff;   // left operator block offset (elements), -1 = identity
+  long long boff;   // right operator block offset, -1 = identity
+  int in_blk;       // input psi block
+  int flags;        // bit0: left block used transposed; bit1: right block transposed
+  double scale;     // coefficient times fermion sign
+};
+
+// Work unit of one CTA: tasks [t_begin, t_end) (all with output block out),
+// rows [r0, r0+nrows) x cols [c0, c0+ncols) of that block; partial result to
+// scratch at `slot` (nrows x ncols, row-major).
+struct Item {
+  int out, r0, nrows, c0, ncols, t_begin, t_end, pad;
+  long long slot;
+};
+// Output tile and the contiguous item range whose partials sum into it.
+struct Group {
+  int out, r0, nrows, c0, ncols, i_begin, i_end, pad;
+};
+
+struct WorkList {
+  std::vector<Task> tasks;        // grouped by output block
+  std::vector<int> out_start;     // tasks of output block b: [out_start[b], out_start[b+1])
+  std::vector<Item> items;        // grouped by output tile (contiguous per group)
+  std::vector<Group> groups;
+  std::vector<int> schedule;      // item indices, most expensive first
+  long long scratch_elems = 0;
+  double flops = 0;          // algorithmic (min order)
+  double bytes_ops = 0;      // operator bytes read (FP64), each product reading its two blocks
+};
+
+struct TileShape {
+  int tm;          // rows per tile
+  int tn;          // max cols per tile
+  double target;   // flops per item
+};
+
+void build_tasks(const std::vector<PsiBlock>& blocks, const OpSet& L, const OpSet& R,
+                 const std::vector<Term>& terms, WorkList& wl);
+// Split every output block into tm x tn tiles and each tile's task list into
+// items of about max(ts.target, total / want_items) flops.
+void build_items(const std::vector<PsiBlock>& blocks, WorkList& wl, const TileShape& ts,
+                 int want_items);
+
+}  // namespace dmrg
