@@ -51,10 +51,12 @@ typedef enum {
 } dmrg_status;
 
 /* Arithmetic of the sigma products. FP64: plain double on the FP64 pipes.
- * FP16X2: operands split into fp16 hi + lo with a power-of-two scale per
- * operator, 3 tensor-core products (hi.hi + hi.lo + lo.hi) per GEMM with FP32
- * accumulation, terms summed in FP64. BF16X3: three bf16 slices, 6 products. */
-typedef enum { DMRG_FP64 = 0, DMRG_FP16X2 = 1, DMRG_BF16X3 = 2 } dmrg_prec;
+ * BF16X3: every operand split into three bf16 slices x = hi + mid + lo
+ * (24 significant bits); each GEMM is the sum of the 6 slice products with
+ * i + j <= 2 on the tensor cores (tcgen05, FP32 accumulation); partial sums
+ * of at most 32 terms are added in FP64. BF16X2: the first two slices and
+ * the 3 products with i + j <= 1 (16 significant bits). */
+typedef enum { DMRG_FP64 = 0, DMRG_BF16X2 = 1, DMRG_BF16X3 = 2 } dmrg_prec;
 
 typedef struct {
   int sigma_prec;              /* dmrg_prec */
@@ -82,8 +84,14 @@ const char* dmrg_last_error(const dmrg_ctx* ctx);
 void* dmrg_stream(dmrg_ctx* ctx);
 
 /* Change the sigma precision (dmrg_prec) of an existing context. Mixed modes
- * build their split operator copies lazily on the next dmrg_sigma call. */
+ * build their split operator copies (bf16 slices, 6 bytes per stored element)
+ * lazily on the next dmrg_sigma call. */
 dmrg_status dmrg_set_precision(dmrg_ctx* ctx, int prec);
+
+/* Wait for all work queued on the context's stream. Returns DMRG_ETIMEOUT if
+ * a tensor-core sigma launched since the last check gave up on a bounded
+ * wait (its result is then invalid), DMRG_ECUDA on a CUDA error. */
+dmrg_status dmrg_sync(dmrg_ctx* ctx);
 
 /*
  * Synthetic middle-bond problem (the data-parallel hot path on its own).

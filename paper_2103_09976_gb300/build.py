@@ -21,6 +21,7 @@ SOURCES = [
     "capi.cpp",
     "generate.cu",
     "sigma_f64.cu",
+    "sigma_tc.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libdmrg.so")
 DMRG_OK, DMRG_EINVAL, DMRG_ENOMEM, DMRG_ECUDA, DMRG_ENOCONV, DMRG_ETIMEOUT, DMRG_ESTATE = range(7)
 STATUS_NAMES = ["DMRG_OK", "DMRG_EINVAL", "DMRG_ENOMEM", "DMRG_ECUDA", "DMRG_ENOCONV",
                 "DMRG_ETIMEOUT", "DMRG_ESTATE"]
-DMRG_FP64, DMRG_FP16X2, DMRG_BF16X3 = 0, 1, 2
+DMRG_FP64, DMRG_BF16X2, DMRG_BF16X3 = 0, 1, 2
 
 
 class dmrg_opts(ctypes.Structure):
@@ -56,6 +56,7 @@ SIGNATURES = {
     "dmrg_davidson": (_I, [_P, _I, _P, _D, ctypes.POINTER(_D), _P, ctypes.POINTER(_I)]),
     "dmrg_build_blocks": (_I, [_P, _P, _P, _I, _I, _I, _I]),
     "dmrg_sweep": (_I, [_P, _P, _I, _D, _P, _P]),
+    "dmrg_sync": (_I, [_P]),
     "dmrg_profile": (_I, [_P, _I]),
     "dmrg_profile_read": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_LL)]),
 }
@@ -128,6 +129,10 @@ def dmrg_stream(ctx):
 
 def dmrg_set_precision(ctx, prec):
     _check(ctx, lib().dmrg_set_precision(ctx, int(prec)))
+
+
+def dmrg_sync(ctx):
+    _check(ctx, lib().dmrg_sync(ctx))
 
 
 def _sec_array(secs):

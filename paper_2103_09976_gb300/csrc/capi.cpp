@@ -79,7 +79,111 @@ void prepare_worklist(Context& c, Problem& p) {
   p.ready = true;
 }
 
+static_assert(sizeof(TcItem) == sizeof(Item), "reduction reads TcItem as Item");
+
+void prepare_tc(Context& c, Problem& p) {
+  cudaStream_t st = c.stream;
+  build_tc_plan(p.blocks, p.L, p.R, p.wl, p.tc, c.n_sm * 16, 32);
+  const size_t slice_bytes = (size_t)p.tc.n_tiles * 128;
+  size_t freeb = 0, totb = 0;
+  DMRG_CUDA(cudaMemGetInfo(&freeb, &totb));
+  if (3.0 * slice_bytes > 0.92 * (double)freeb)
+    throw Error(DMRG_ENOMEM, "bf16 split operator store does not fit in free device memory");
+  for (int s = 0; s < 3; ++s) {
+    p.slices[s].alloc(slice_bytes);
+    DMRG_CUDA(cudaMemsetAsync(p.slices[s].p, 0, slice_bytes, st));
+    p.psi_slices[s].alloc((size_t)p.tc.psi_tiles * 128);
+    DMRG_CUDA(cudaMemsetAsync(p.psi_slices[s].p, 0, (size_t)p.tc.psi_tiles * 128, st));
+  }
+  std::vector<SplitJob> jobs;
+  jobs.reserve(p.tc.opblocks.size() + p.tc.identL.size() + p.tc.identR.size());
+  size_t k = 0;
+  for (const OpSet* set : {&p.L, &p.R})
+    for (const OpDesc& o : set->ops)
+      for (const OpBlock& b : o.blocks) {
+        const TcBlock& t = p.tc.opblocks[k++];
+        jobs.push_back({b.off, b.rows, b.cols, t.tile, t.R8, t.C8});
+      }
+  for (int side = 0; side < 2; ++side) {
+    const Basis& B = side == 0 ? p.L.basis : p.R.basis;
+    const auto& id = side == 0 ? p.tc.identL : p.tc.identR;
+    for (int i = 0; i < B.size(); ++i) jobs.push_back({-1, B.dim[i], B.dim[i], id[i].tile, id[i].R8, id[i].C8});
+  }
+  DevBuf d_jobs;
+  d_jobs.upload(jobs, st);
+  void* sl[3] = {p.slices[0].p, p.slices[1].p, p.slices[2].p};
+  launch_split_ops(p.store.as<double>(), d_jobs.as<SplitJob>(), (long long)jobs.size(), sl, st);
+  DMRG_CUDA(cudaGetLastError());
+  p.d_tc_tasks.upload(p.tc.tasks, st);
+  p.d_tc_items.upload(p.tc.items, st);
+  p.d_tc_groups.upload(p.tc.groups, st);
+  p.d_tc_sched.upload(p.tc.schedule, st);
+  p.d_tc_pblk.upload(p.tc.psi, st);
+  p.d_tc_scratch.alloc(std::max<long long>(1, p.tc.scratch_elems) * sizeof(double));
+  p.d_err.alloc(16);
+  DMRG_CUDA(cudaMemsetAsync(p.d_err.p, 0, 16, st));
+  DMRG_CUDA(cudaStreamSynchronize(st));
+  p.tc_ready = true;
+}
+
+void check_device_error(Context& c, Problem& p) {
+  DMRG_CUDA(cudaStreamSynchronize(c.stream));
+  if (!p.tc_ready) return;
+  int e = 0;
+  DMRG_CUDA(cudaMemcpy(&e, p.d_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) {
+    DMRG_CUDA(cudaMemset(p.d_err.p, 0, sizeof(int)));
+    throw Error(DMRG_ETIMEOUT, "tensor-core sigma: a bounded wait gave up (code " + std::to_string(e) +
+                                   "); the last sigma result is invalid");
+  }
+}
+
+static void run_sigma_tc(Context& c, Problem& p, const double* d_psi, double* d_sigma) {
+  if (!p.tc_ready) prepare_tc(c, p);
+  void* ps[3] = {p.psi_slices[0].p, p.psi_slices[1].p, p.psi_slices[2].p};
+  {
+    ProfScope ps_(c.prof, 2, c.stream);
+    launch_split_psi(d_psi, p.d_blocks.as<PsiBlock>(), p.d_tc_pblk.as<TcPsiBlock>(), (int)p.blocks.size(),
+                     ps, c.stream);
+  }
+  DMRG_CUDA(cudaGetLastError());
+  TcDev t;
+  for (int s = 0; s < 3; ++s) {
+    t.op[s] = p.slices[s].p;
+    t.psi[s] = p.psi_slices[s].p;
+  }
+  t.tasks = p.d_tc_tasks.as<TcTask>();
+  t.items = p.d_tc_items.as<TcItem>();
+  t.schedule = p.d_tc_sched.as<int>();
+  t.n_items = (int)p.tc.items.size();
+  t.pblk = p.d_tc_pblk.as<TcPsiBlock>();
+  t.scratch = p.d_tc_scratch.as<double>();
+  t.err = p.d_err.as<int>();
+  t.nprod = c.opts.sigma_prec == DMRG_BF16X3 ? 6 : 3;
+  {
+    ProfScope ps_(c.prof, 0, c.stream);
+    launch_sigma_tc(t, c.n_sm, c.stream);
+  }
+  DMRG_CUDA(cudaGetLastError());
+  SigmaDev r;
+  r.sigma = d_sigma;
+  r.items = reinterpret_cast<const Item*>(p.d_tc_items.p);
+  r.groups = p.d_tc_groups.as<Group>();
+  r.n_groups = (int)p.tc.groups.size();
+  r.blocks = p.d_blocks.as<PsiBlock>();
+  r.scratch = p.d_tc_scratch.as<double>();
+  {
+    ProfScope ps_(c.prof, 1, c.stream);
+    launch_reduce(r, c.stream);
+  }
+  DMRG_CUDA(cudaGetLastError());
+}
+
 void run_sigma(Context& c, Problem& p, const double* d_psi, double* d_sigma) {
+  if (c.opts.sigma_prec != DMRG_FP64) {
+    run_sigma_tc(c, p, d_psi, d_sigma);
+    return;
+  }
   SigmaDev a;
   a.store = p.store.as<double>();
   a.psi = d_psi;
@@ -232,7 +336,7 @@ void* dmrg_stream(dmrg_ctx* ctx) { return ctx ? (void*)ctx->c.stream : nullptr; 
 dmrg_status dmrg_set_precision(dmrg_ctx* ctx, int prec) {
   if (!ctx) return DMRG_EINVAL;
   return guarded(ctx, [&] {
-    if (prec != DMRG_FP64) throw Error(DMRG_EINVAL, "precision not available in this build");
+    if (prec < DMRG_FP64 || prec > DMRG_BF16X3) throw Error(DMRG_EINVAL, "unknown sigma precision");
     ctx->c.opts.sigma_prec = prec;
   });
 }
@@ -342,7 +446,7 @@ dmrg_status dmrg_sigma(dmrg_ctx* ctx, int site, const double* psi, double* sigma
     run_sigma(c, p, xin, yout);
     if (!dsig) {
       DMRG_CUDA(cudaMemcpyAsync(sigma, yout, bytes, cudaMemcpyDeviceToHost, c.stream));
-      DMRG_CUDA(cudaStreamSynchronize(c.stream));
+      check_device_error(c, p);
     }
   });
 }
@@ -363,6 +467,15 @@ dmrg_status dmrg_sweep(dmrg_ctx* ctx, const int* M_schedule, int n_sweeps, doubl
                        double* energies, double* max_discard) {
   if (!ctx) return DMRG_EINVAL;
   return guarded(ctx, [&] { throw Error(DMRG_ESTATE, "dmrg_sweep: not available yet"); });
+}
+
+dmrg_status dmrg_sync(dmrg_ctx* ctx) {
+  if (!ctx) return DMRG_EINVAL;
+  return guarded(ctx, [&] {
+    DMRG_CUDA(cudaSetDevice(ctx->c.device));
+    DMRG_CUDA(cudaStreamSynchronize(ctx->c.stream));
+    if (ctx->c.prob) check_device_error(ctx->c, *ctx->c.prob);
+  });
 }
 
 dmrg_status dmrg_profile(dmrg_ctx* ctx, int enable) {

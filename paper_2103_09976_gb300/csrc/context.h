@@ -65,6 +65,11 @@ struct Problem {
   DevBuf store;              // FP64 operator store
   DevBuf d_tasks, d_items, d_groups, d_sched, d_blocks, d_scratch, d_counter;
   bool ready = false;
+  // tensor-core path (built on first mixed-precision sigma)
+  TcPlan tc;
+  bool tc_ready = false;
+  DevBuf slices[3], psi_slices[3];
+  DevBuf d_tc_tasks, d_tc_items, d_tc_groups, d_tc_sched, d_tc_pblk, d_tc_scratch, d_err;
 };
 
 // CUDA-event timing of kernel launches (dmrg_profile).
@@ -109,6 +114,8 @@ struct Context {
 };
 
 void prepare_worklist(Context& c, Problem& p);
+void prepare_tc(Context& c, Problem& p);
+void check_device_error(Context& c, Problem& p);
 void run_sigma(Context& c, Problem& p, const double* d_psi, double* d_sigma);
 
 }  // namespace dmrg

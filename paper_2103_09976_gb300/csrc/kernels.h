@@ -44,4 +44,32 @@ struct SigmaDev {
 void launch_sigma_f64(const SigmaDev& a, int n_sm, cudaStream_t st);
 void launch_reduce(const SigmaDev& a, cudaStream_t st);
 
+// ------------------------------------------------------------ tensor cores
+// One stored block (or identity, src < 0) to split into three bf16 slices.
+struct SplitJob {
+  long long src;     // element offset in the FP64 store, -1 = identity
+  int rows, cols;
+  long long tile;    // first 128-byte tile in the slice arrays
+  int R8, C8;
+};
+
+struct TcDev {
+  const void* op[3];          // operator slices (bf16 tiles)
+  const void* psi[3];         // psi slices
+  const TcTask* tasks;
+  const TcItem* items;
+  const int* schedule;
+  int n_items;
+  const TcPsiBlock* pblk;
+  double* scratch;
+  int* err;                   // nonzero after a bounded wait gave up
+  int nprod;                  // 6 (three slices) or 3 (two slices)
+};
+
+void launch_split_ops(const double* store, const SplitJob* jobs, long long njobs, void* const slices[3],
+                      cudaStream_t st);
+void launch_split_psi(const double* psi, const PsiBlock* blocks, const TcPsiBlock* pb, int nblk,
+                      void* const slices[3], cudaStream_t st);
+void launch_sigma_tc(const TcDev& a, int n_sm, cudaStream_t st);
+
 }  // namespace dmrg

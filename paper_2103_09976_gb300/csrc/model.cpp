@@ -248,3 +248,114 @@ void build_items(const std::vector<PsiBlock>& blocks, WorkList& wl, const TileSh
 }
 
 }  // namespace dmrg
+
+namespace dmrg {
+
+static inline int ceil8(int x) { return (x + 7) / 8; }
+
+void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const OpSet& R,
+                   const WorkList& wl, TcPlan& plan, int want_items, int max_tasks_per_item) {
+  plan = TcPlan();
+  // tiles of every stored block, in store order (left ops, then right ops)
+  std::map<long long, TcBlock> by_off;  // element offset -> tiled block
+  long long tile = 0;
+  for (const OpSet* s : {&L, &R})
+    for (const OpDesc& o : s->ops) {
+      plan.op_first.push_back((long long)plan.opblocks.size());
+      for (const OpBlock& b : o.blocks) {
+        TcBlock t{tile, ceil8(b.rows), ceil8(b.cols)};
+        tile += (long long)t.R8 * t.C8;
+        plan.opblocks.push_back(t);
+        by_off[b.off] = t;
+      }
+    }
+  for (int i = 0; i < L.basis.size(); ++i) {
+    TcBlock t{tile, ceil8(L.basis.dim[i]), ceil8(L.basis.dim[i])};
+    tile += (long long)t.R8 * t.C8;
+    plan.identL.push_back(t);
+  }
+  for (int i = 0; i < R.basis.size(); ++i) {
+    TcBlock t{tile, ceil8(R.basis.dim[i]), ceil8(R.basis.dim[i])};
+    tile += (long long)t.R8 * t.C8;
+    plan.identR.push_back(t);
+  }
+  plan.n_tiles = tile + 64;  // slack: descriptor reads past the last tile stay in bounds
+  // psi tiles (rows padded to an even count of 8-row groups, zero filled)
+  long long pt = 0;
+  for (const PsiBlock& b : blocks) {
+    TcPsiBlock p{pt, 2 * ((b.mL + 15) / 16), ceil8(b.mR), b.mL, b.mR};
+    pt += (long long)p.R8 * p.C8;
+    plan.psi.push_back(p);
+  }
+  plan.psi_tiles = pt + 64;
+  // tasks: the FP64 task list with identity factors made explicit
+  plan.tasks.reserve(wl.tasks.size());
+  std::vector<int> task_out(wl.tasks.size());
+  for (size_t b = 0; b < blocks.size(); ++b)
+    for (int t = wl.out_start[b]; t < wl.out_start[b + 1]; ++t) task_out[t] = (int)b;
+  for (size_t t = 0; t < wl.tasks.size(); ++t) {
+    const Task& k = wl.tasks[t];
+    const PsiBlock& in = blocks[k.in_blk];
+    TcTask x;
+    TcBlock a = k.aoff >= 0 ? by_off.at(k.aoff) : plan.identL[in.qL];
+    TcBlock b = k.boff >= 0 ? by_off.at(k.boff) : plan.identR[in.qR];
+    x.a_tile = a.tile;
+    x.aR8 = a.R8;
+    x.aC8 = a.C8;
+    x.b_tile = b.tile;
+    x.bR8 = b.R8;
+    x.bC8 = b.C8;
+    x.in_blk = k.in_blk;
+    x.flags = (k.aoff >= 0 ? (k.flags & 1) : 0) | (k.boff >= 0 ? (k.flags & 2) : 0);
+    x.scale = (float)k.scale;
+    x.pad = 0;
+    plan.tasks.push_back(x);
+  }
+  // items: 128 x 128 output tiles, each task range split by cost and length
+  auto cost = [&](const TcTask& k, int nr, int nc) {
+    const PsiBlock& in = blocks[k.in_blk];
+    double n16 = 16.0 * ((in.mR + 15) / 16), m16 = 16.0 * ((in.mL + 15) / 16);
+    (void)nr;
+    return 128.0 * n16 * m16 + 128.0 * n16 * 16.0 * ((nc + 15) / 16);
+  };
+  double total = 0;
+  for (size_t b = 0; b < blocks.size(); ++b)
+    for (int t = wl.out_start[b]; t < wl.out_start[b + 1]; ++t)
+      total += cost(plan.tasks[t], blocks[b].mL, blocks[b].mR);
+  const double target = total / std::max(1, want_items);
+  std::vector<double> icost;
+  for (size_t b = 0; b < blocks.size(); ++b) {
+    const PsiBlock& ob = blocks[b];
+    int t0 = wl.out_start[b], t1 = wl.out_start[b + 1];
+    for (int r0 = 0; r0 < ob.mL; r0 += 128)
+      for (int c0 = 0; c0 < ob.mR; c0 += 128) {
+        int nr = std::min(128, ob.mL - r0), nc = std::min(128, ob.mR - c0);
+        Group g{(int)b, r0, nr, c0, nc, (int)plan.items.size(), 0, 0};
+        int start = t0;
+        double acc = 0;
+        for (int t = t0; t < t1; ++t) {
+          double c = cost(plan.tasks[t], nr, nc);
+          if (t > start && (acc + c > target || t - start >= max_tasks_per_item)) {
+            plan.items.push_back({(int)b, r0, nr, c0, nc, start, t, 0, plan.scratch_elems});
+            plan.scratch_elems += (long long)nr * nc;
+            icost.push_back(acc);
+            start = t;
+            acc = 0;
+          }
+          acc += c;
+        }
+        plan.items.push_back({(int)b, r0, nr, c0, nc, start, t1, 0, plan.scratch_elems});
+        plan.scratch_elems += (long long)nr * nc;
+        icost.push_back(acc);
+        g.i_end = (int)plan.items.size();
+        plan.groups.push_back(g);
+      }
+  }
+  plan.schedule.resize(plan.items.size());
+  std::iota(plan.schedule.begin(), plan.schedule.end(), 0);
+  std::stable_sort(plan.schedule.begin(), plan.schedule.end(),
+                   [&](int a, int b) { return icost[a] > icost[b]; });
+  (void)task_out;
+}
+
+}  // namespace dmrg

@@ -154,3 +154,56 @@ void build_items(const std::vector<PsiBlock>& blocks, WorkList& wl, const TileSh
                  int want_items);
 
 }  // namespace dmrg
+
+namespace dmrg {
+
+// ------------------------------------------------------------------ tensor-core path
+// Split operator store: every stored block S (r x c) is kept as three bf16
+// slices S = hi + mid + lo, each in 8x8 "core-matrix" tiles: tile (i8, j8)
+// holds rows 8*i8.., cols 8*j8.. as 8 rows of 8 contiguous elements (128 B),
+// tiles ordered j8 fastest; padding elements are zero. The same tiles serve
+// as a K-major operand (S as MN x K) or an MN-major one (S^T) of tcgen05.mma.
+struct TcBlock {
+  long long tile;   // first tile (128-byte units) in each slice array
+  int R8, C8;       // tile rows / cols of the stored block
+};
+
+struct TcTask {
+  long long a_tile, b_tile;   // tiles of the left / right operator block (identity blocks included)
+  int aR8, aC8;               // stored tile geometry of the left block
+  int bR8, bC8;               // stored tile geometry of the right block
+  int in_blk;
+  int flags;                  // bit0: left used transposed, bit1: right used transposed
+  float scale;
+  int pad;
+};
+
+struct TcItem {
+  int out, r0, nrows, c0, ncols, t_begin, t_end, pad;
+  long long slot;
+};
+
+struct TcPsiBlock {
+  long long tile;   // first tile of the block in the psi slice arrays
+  int R8, C8;       // rows padded to an even number of tile rows
+  int m, n;
+};
+
+struct TcPlan {
+  std::vector<TcBlock> opblocks;        // parallel to a flat list of (set, op, block)
+  std::vector<long long> op_first;      // index of the first TcBlock of op (L ops then R ops)
+  std::vector<TcBlock> identL, identR;  // identity blocks per sector of the left / right basis
+  long long n_tiles = 0;                // tiles per slice array
+  std::vector<TcPsiBlock> psi;
+  long long psi_tiles = 0;
+  std::vector<TcTask> tasks;
+  std::vector<TcItem> items;
+  std::vector<int> schedule;
+  std::vector<Group> groups;
+  long long scratch_elems = 0;
+};
+
+void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const OpSet& R,
+                   const WorkList& wl, TcPlan& plan, int want_items, int max_tasks_per_item);
+
+}  // namespace dmrg
