@@ -59,6 +59,7 @@ SIGNATURES = {
     "dmrg_sync": (_I, [_P]),
     "dmrg_profile": (_I, [_P, _I]),
     "dmrg_profile_read": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_LL)]),
+    "dmrg_profile_waits": (_I, [_P, _P, _I]),
 }
 
 
@@ -209,3 +210,15 @@ def dmrg_profile_read(ctx, kernel):
     n = ctypes.c_longlong()
     _check(ctx, lib().dmrg_profile_read(ctx, kernel, ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+WAIT_KINDS = {1: "stage free", 2: "sigma tile free", 3: "X tile free", 4: "stage loaded",
+              5: "second operand written", 6: "X tile computed", 7: "second operand free",
+              8: "sigma tile computed", 9: "record slot free", 10: "record loaded (producer)",
+              11: "terminator slot", 12: "record loaded (MMA)", 13: "record loaded (epilogue)"}
+
+
+def dmrg_profile_waits(ctx):
+    buf = np.zeros(17)
+    _check(ctx, lib().dmrg_profile_waits(ctx, _ptr(buf), 17))
+    return buf

@@ -83,18 +83,16 @@ static_assert(sizeof(TcItem) == sizeof(Item), "reduction reads TcItem as Item");
 
 void prepare_tc(Context& c, Problem& p) {
   cudaStream_t st = c.stream;
-  build_tc_plan(p.blocks, p.L, p.R, p.wl, p.tc, c.n_sm * 16, 32);
-  const size_t slice_bytes = (size_t)p.tc.n_tiles * 128;
+  build_tc_plan(p.blocks, p.L, p.R, p.wl, p.tc, c.n_sm * 4, 32);
+  const size_t split_bytes = (size_t)p.tc.n_tiles * 384;
   size_t freeb = 0, totb = 0;
   DMRG_CUDA(cudaMemGetInfo(&freeb, &totb));
-  if (3.0 * slice_bytes > 0.92 * (double)freeb)
+  if ((double)split_bytes > 0.92 * (double)freeb)
     throw Error(DMRG_ENOMEM, "bf16 split operator store does not fit in free device memory");
-  for (int s = 0; s < 3; ++s) {
-    p.slices[s].alloc(slice_bytes);
-    DMRG_CUDA(cudaMemsetAsync(p.slices[s].p, 0, slice_bytes, st));
-    p.psi_slices[s].alloc((size_t)p.tc.psi_tiles * 128);
-    DMRG_CUDA(cudaMemsetAsync(p.psi_slices[s].p, 0, (size_t)p.tc.psi_tiles * 128, st));
-  }
+  p.split.alloc(split_bytes);
+  DMRG_CUDA(cudaMemsetAsync(p.split.p, 0, split_bytes, st));
+  p.psi_split.alloc((size_t)p.tc.psi_tiles * 384);
+  DMRG_CUDA(cudaMemsetAsync(p.psi_split.p, 0, (size_t)p.tc.psi_tiles * 384, st));
   std::vector<SplitJob> jobs;
   jobs.reserve(p.tc.opblocks.size() + p.tc.identL.size() + p.tc.identR.size());
   size_t k = 0;
@@ -111,10 +109,10 @@ void prepare_tc(Context& c, Problem& p) {
   }
   DevBuf d_jobs;
   d_jobs.upload(jobs, st);
-  void* sl[3] = {p.slices[0].p, p.slices[1].p, p.slices[2].p};
-  launch_split_ops(p.store.as<double>(), d_jobs.as<SplitJob>(), (long long)jobs.size(), sl, st);
+  launch_split_ops(p.store.as<double>(), d_jobs.as<SplitJob>(), (long long)jobs.size(), p.split.p, st);
   DMRG_CUDA(cudaGetLastError());
-  p.d_tc_tasks.upload(p.tc.tasks, st);
+  p.d_tc_recs.upload(p.tc.recs, st);
+  p.d_tc_item_rec.upload(p.tc.item_rec, st);
   p.d_tc_items.upload(p.tc.items, st);
   p.d_tc_groups.upload(p.tc.groups, st);
   p.d_tc_sched.upload(p.tc.schedule, st);
@@ -140,26 +138,32 @@ void check_device_error(Context& c, Problem& p) {
 
 static void run_sigma_tc(Context& c, Problem& p, const double* d_psi, double* d_sigma) {
   if (!p.tc_ready) prepare_tc(c, p);
-  void* ps[3] = {p.psi_slices[0].p, p.psi_slices[1].p, p.psi_slices[2].p};
   {
     ProfScope ps_(c.prof, 2, c.stream);
     launch_split_psi(d_psi, p.d_blocks.as<PsiBlock>(), p.d_tc_pblk.as<TcPsiBlock>(), (int)p.blocks.size(),
-                     ps, c.stream);
+                     p.psi_split.p, c.stream);
   }
   DMRG_CUDA(cudaGetLastError());
   TcDev t;
-  for (int s = 0; s < 3; ++s) {
-    t.op[s] = p.slices[s].p;
-    t.psi[s] = p.psi_slices[s].p;
-  }
-  t.tasks = p.d_tc_tasks.as<TcTask>();
-  t.items = p.d_tc_items.as<TcItem>();
+  t.op = p.split.p;
+  t.psi = p.psi_split.p;
+  t.recs = p.d_tc_recs.as<TcRec>();
+  t.item_rec = p.d_tc_item_rec.as<int>();
   t.schedule = p.d_tc_sched.as<int>();
   t.n_items = (int)p.tc.items.size();
-  t.pblk = p.d_tc_pblk.as<TcPsiBlock>();
+  t.counter = p.d_counter.as<unsigned int>();
   t.scratch = p.d_tc_scratch.as<double>();
   t.err = p.d_err.as<int>();
   t.nprod = c.opts.sigma_prec == DMRG_BF16X3 ? 6 : 3;
+  t.wait_prof = nullptr;
+  if (c.prof.on) {
+    if (!c.d_wait_prof.p) {
+      c.d_wait_prof.alloc(32 * sizeof(unsigned long long));
+      DMRG_CUDA(cudaMemsetAsync(c.d_wait_prof.p, 0, 32 * sizeof(unsigned long long), c.stream));
+    }
+    t.wait_prof = c.d_wait_prof.as<unsigned long long>();
+  }
+  DMRG_CUDA(cudaMemsetAsync(p.d_counter.p, 0, sizeof(unsigned int), c.stream));
   {
     ProfScope ps_(c.prof, 0, c.stream);
     launch_sigma_tc(t, c.n_sm, c.stream);
@@ -478,10 +482,24 @@ dmrg_status dmrg_sync(dmrg_ctx* ctx) {
   });
 }
 
+dmrg_status dmrg_profile_waits(dmrg_ctx* ctx, double* cycles, int n) {
+  if (!ctx || !cycles || n <= 0) return DMRG_EINVAL;
+  return guarded(ctx, [&] {
+    DMRG_CUDA(cudaSetDevice(ctx->c.device));
+    DMRG_CUDA(cudaStreamSynchronize(ctx->c.stream));
+    unsigned long long h[32] = {0};
+    if (ctx->c.d_wait_prof.p)
+      DMRG_CUDA(cudaMemcpy(h, ctx->c.d_wait_prof.p, sizeof(h), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < n && i < 32; ++i) cycles[i] = (double)h[i];
+  });
+}
+
 dmrg_status dmrg_profile(dmrg_ctx* ctx, int enable) {
   if (!ctx) return DMRG_EINVAL;
   return guarded(ctx, [&] {
     DMRG_CUDA(cudaSetDevice(ctx->c.device));
+    if (enable && ctx->c.d_wait_prof.p)
+      DMRG_CUDA(cudaMemsetAsync(ctx->c.d_wait_prof.p, 0, 32 * sizeof(unsigned long long), ctx->c.stream));
     if (enable) ctx->c.prof.clear();
     ctx->c.prof.on = enable != 0;
   });

@@ -68,8 +68,8 @@ struct Problem {
   // tensor-core path (built on first mixed-precision sigma)
   TcPlan tc;
   bool tc_ready = false;
-  DevBuf slices[3], psi_slices[3];
-  DevBuf d_tc_tasks, d_tc_items, d_tc_groups, d_tc_sched, d_tc_pblk, d_tc_scratch, d_err;
+  DevBuf split, psi_split;         // slice-interleaved bf16 tiles of the operators / of psi
+  DevBuf d_tc_recs, d_tc_item_rec, d_tc_items, d_tc_groups, d_tc_sched, d_tc_pblk, d_tc_scratch, d_err;
 };
 
 // CUDA-event timing of kernel launches (dmrg_profile).
@@ -111,6 +111,7 @@ struct Context {
   std::unique_ptr<Problem> prob;   // synthetic or current sweep step
   DevBuf d_psi, d_sigma;           // staging for host psi / sigma
   Profiler prof;
+  DevBuf d_wait_prof;              // tensor-core kernel wait accounting (profiling only)
 };
 
 void prepare_worklist(Context& c, Problem& p);

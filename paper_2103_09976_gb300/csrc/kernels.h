@@ -54,22 +54,22 @@ struct SplitJob {
 };
 
 struct TcDev {
-  const void* op[3];          // operator slices (bf16 tiles)
-  const void* psi[3];         // psi slices
-  const TcTask* tasks;
-  const TcItem* items;
-  const int* schedule;
+  const void* op;             // operator tiles, slice-interleaved (3 x 128 B per tile position)
+  const void* psi;            // psi tiles, same layout
+  const TcRec* recs;          // unit records, grouped by item
+  const int* item_rec;        // records of item i: [item_rec[i], item_rec[i+1])
+  const int* schedule;        // item order, most expensive first
   int n_items;
-  const TcPsiBlock* pblk;
+  unsigned int* counter;      // next item to take; zero at launch
   double* scratch;
   int* err;                   // nonzero after a bounded wait gave up
   int nprod;                  // 6 (three slices) or 3 (two slices)
+  unsigned long long* wait_prof;  // optional [17]: wait cycles per barrier kind, total cycles
 };
 
-void launch_split_ops(const double* store, const SplitJob* jobs, long long njobs, void* const slices[3],
+void launch_split_ops(const double* store, const SplitJob* jobs, long long njobs, void* out, cudaStream_t st);
+void launch_split_psi(const double* psi, const PsiBlock* blocks, const TcPsiBlock* pb, int nblk, void* out,
                       cudaStream_t st);
-void launch_split_psi(const double* psi, const PsiBlock* blocks, const TcPsiBlock* pb, int nblk,
-                      void* const slices[3], cudaStream_t st);
 void launch_sigma_tc(const TcDev& a, int n_sm, cudaStream_t st);
 
 }  // namespace dmrg

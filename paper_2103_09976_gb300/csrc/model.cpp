@@ -253,10 +253,24 @@ namespace dmrg {
 
 static inline int ceil8(int x) { return (x + 7) / 8; }
 
+int tc_k1_tiles(const TcTask& t, const TcPsiBlock& ib, int r0) {
+  if (ib.R8 > 4 || ib.C8 > 8) return 0;               // m <= 32, n <= 64
+  const bool tA = t.flags & 1;
+  const int rg0 = r0 / 8;
+  int ol = tA ? t.aR8 * std::min(16, t.aC8 - rg0)      // K groups x M groups
+              : std::min(16, t.aR8 - rg0) * t.aC8;     // M groups x K groups
+  return ol + ib.R8 * ib.C8;
+}
+
+int tc_k2_tiles(const TcTask& t, int c0) {  // tiles of the right operand for one task
+  const bool tB = t.flags & 2;
+  const int cg0 = c0 / 8;
+  return tB ? t.bR8 * std::min(16, t.bC8 - cg0) : std::min(16, t.bR8 - cg0) * t.bC8;
+}
+
 void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const OpSet& R,
-                   const WorkList& wl, TcPlan& plan, int want_items, int max_tasks_per_item) {
+                   const WorkList& wl, TcPlan& plan, int want_items, int seg_tasks) {
   plan = TcPlan();
-  // tiles of every stored block, in store order (left ops, then right ops)
   std::map<long long, TcBlock> by_off;  // element offset -> tiled block
   long long tile = 0;
   for (const OpSet* s : {&L, &R})
@@ -280,7 +294,6 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
     plan.identR.push_back(t);
   }
   plan.n_tiles = tile + 64;  // slack: descriptor reads past the last tile stay in bounds
-  // psi tiles (rows padded to an even count of 8-row groups, zero filled)
   long long pt = 0;
   for (const PsiBlock& b : blocks) {
     TcPsiBlock p{pt, 2 * ((b.mL + 15) / 16), ceil8(b.mR), b.mL, b.mR};
@@ -288,17 +301,14 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
     plan.psi.push_back(p);
   }
   plan.psi_tiles = pt + 64;
-  // tasks: the FP64 task list with identity factors made explicit
-  plan.tasks.reserve(wl.tasks.size());
-  std::vector<int> task_out(wl.tasks.size());
-  for (size_t b = 0; b < blocks.size(); ++b)
-    for (int t = wl.out_start[b]; t < wl.out_start[b + 1]; ++t) task_out[t] = (int)b;
+  // base task records (identity factors made explicit)
+  std::vector<TcTask> base(wl.tasks.size());
   for (size_t t = 0; t < wl.tasks.size(); ++t) {
     const Task& k = wl.tasks[t];
     const PsiBlock& in = blocks[k.in_blk];
-    TcTask x;
     TcBlock a = k.aoff >= 0 ? by_off.at(k.aoff) : plan.identL[in.qL];
     TcBlock b = k.boff >= 0 ? by_off.at(k.boff) : plan.identR[in.qR];
+    TcTask x{};
     x.a_tile = a.tile;
     x.aR8 = a.R8;
     x.aC8 = a.C8;
@@ -308,45 +318,120 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
     x.in_blk = k.in_blk;
     x.flags = (k.aoff >= 0 ? (k.flags & 1) : 0) | (k.boff >= 0 ? (k.flags & 2) : 0);
     x.scale = (float)k.scale;
-    x.pad = 0;
-    plan.tasks.push_back(x);
+    base[t] = x;
   }
-  // items: 128 x 128 output tiles, each task range split by cost and length
-  auto cost = [&](const TcTask& k, int nr, int nc) {
-    const PsiBlock& in = blocks[k.in_blk];
-    double n16 = 16.0 * ((in.mR + 15) / 16), m16 = 16.0 * ((in.mL + 15) / 16);
-    (void)nr;
-    return 128.0 * n16 * m16 + 128.0 * n16 * 16.0 * ((nc + 15) / 16);
+  // order tasks of each output block by (right transposed, input block, left
+  // transposed): packed units then share the layout of their second product
+  // and consecutive tasks share psi tiles
+  for (size_t b = 0; b < blocks.size(); ++b) {
+    const int t0 = wl.out_start[b], t1 = wl.out_start[b + 1];
+    std::vector<int> idx(t1 - t0);
+    std::iota(idx.begin(), idx.end(), t0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+      const int kx = ((base[x].flags >> 1) & 1), ky = ((base[y].flags >> 1) & 1);
+      if (kx != ky) return kx < ky;
+      if (base[x].in_blk != base[y].in_blk) return base[x].in_blk < base[y].in_blk;
+      return (base[x].flags & 1) < (base[y].flags & 1);
+    });
+    std::vector<TcTask> tmp;
+    for (int i : idx) tmp.push_back(base[i]);
+    std::copy(tmp.begin(), tmp.end(), base.begin() + t0);
+  }
+  // MMA work of a task on one 128 x 128 tile (rows padded to 128)
+  auto cost = [&](const TcTask& k) {
+    const TcPsiBlock& in = plan.psi[k.in_blk];
+    double n16 = 16.0 * ((in.n + 15) / 16), m16 = 8.0 * in.R8;
+    return 128.0 * n16 * m16 + 128.0 * n16 * 128.0 + 4096.0;  // + fixed per-task overhead
   };
   double total = 0;
-  for (size_t b = 0; b < blocks.size(); ++b)
-    for (int t = wl.out_start[b]; t < wl.out_start[b + 1]; ++t)
-      total += cost(plan.tasks[t], blocks[b].mL, blocks[b].mR);
+  for (size_t b = 0; b < blocks.size(); ++b) {
+    int ntile = ((blocks[b].mL + 127) / 128) * ((blocks[b].mR + 127) / 128);
+    for (int t = wl.out_start[b]; t < wl.out_start[b + 1]; ++t) total += ntile * cost(base[t]);
+  }
   const double target = total / std::max(1, want_items);
   std::vector<double> icost;
   for (size_t b = 0; b < blocks.size(); ++b) {
     const PsiBlock& ob = blocks[b];
-    int t0 = wl.out_start[b], t1 = wl.out_start[b + 1];
+    const int t0 = wl.out_start[b], t1 = wl.out_start[b + 1];
     for (int r0 = 0; r0 < ob.mL; r0 += 128)
       for (int c0 = 0; c0 < ob.mR; c0 += 128) {
-        int nr = std::min(128, ob.mL - r0), nc = std::min(128, ob.mR - c0);
+        const int nr = std::min(128, ob.mL - r0), nc = std::min(128, ob.mR - c0);
         Group g{(int)b, r0, nr, c0, nc, (int)plan.items.size(), 0, 0};
-        int start = t0;
-        double acc = 0;
-        for (int t = t0; t < t1; ++t) {
-          double c = cost(plan.tasks[t], nr, nc);
-          if (t > start && (acc + c > target || t - start >= max_tasks_per_item)) {
-            plan.items.push_back({(int)b, r0, nr, c0, nc, start, t, 0, plan.scratch_elems});
-            plan.scratch_elems += (long long)nr * nc;
-            icost.push_back(acc);
-            start = t;
-            acc = 0;
+        int t = t0;
+        do {  // one item per iteration (at least one, even with no tasks)
+          TcItem it{(int)b, r0, nr, c0, nc, (int)plan.units.size(), 0, 0, plan.scratch_elems};
+          const int item_idx = (int)plan.items.size();
+          double acc = 0;
+          int seg = 0, seg_first_unit = (int)plan.units.size();
+          bool first_seg = true;
+          auto end_segment = [&]() {
+            if (plan.units.size() > (size_t)seg_first_unit) {
+              plan.units.back().flags |= UNIT_ENDS_SEGMENT | (first_seg ? UNIT_FIRST_SEGMENT : 0);
+              first_seg = false;
+            }
+            seg = 0;
+            seg_first_unit = (int)plan.units.size();
+          };
+          while (t < t1 && (acc == 0 || acc + cost(base[t]) <= target)) {
+            TcTask k = base[t];
+            const TcPsiBlock& ib = plan.psi[k.in_blk];
+            int k1 = tc_k1_tiles(k, ib, r0), k2 = tc_k2_tiles(k, c0);
+            if (k1 > 0 && k1 <= 128 && k2 <= 128) {
+              // packed unit: greedily add following small tasks with the same
+              // right-operand orientation; tasks on the same psi block share its tiles
+              TcUnit u{item_idx, (int)plan.tasks.size(), 0, 0, UNIT_PACKED, 0, {0, 0}};
+              int w = 0, s1 = 0, last_in = -1, last_k1b = 0;
+              const int tB0 = (k.flags >> 1) & 1;
+              while (t < t1 && seg < seg_tasks && (acc == 0 || acc + cost(base[t]) <= target)) {
+                TcTask x = base[t];
+                const TcPsiBlock& xb = plan.psi[x.in_blk];
+                int a1 = tc_k1_tiles(x, xb, r0);
+                const bool share = x.in_blk == last_in;
+                if (share) a1 -= xb.R8 * xb.C8;
+                int n16 = 16 * ((xb.n + 15) / 16);
+                if (tc_k1_tiles(x, xb, r0) == 0 || ((x.flags >> 1) & 1) != tB0 || w + n16 > 64 || s1 + a1 > 128) break;
+                x.xcol = w;
+                x.k1a = s1;
+                const bool tA = x.flags & 1;
+                const int rg0 = r0 / 8;
+                const int ol = tA ? x.aR8 * std::min(16, x.aC8 - rg0) : std::min(16, x.aR8 - rg0) * x.aC8;
+                if (share) {
+                  x.k1b = last_k1b;
+                  x.flags |= 4;  // psi tiles already in the stage
+                } else {
+                  x.k1b = s1 + ol;
+                  last_k1b = x.k1b;
+                }
+                x.k2 = 0;
+                last_in = x.in_blk;
+                w += n16;
+                s1 += a1;
+                plan.tasks.push_back(x);
+                acc += cost(x);
+                ++t;
+                ++seg;
+              }
+              u.t_end = (int)plan.tasks.size();
+              u.width = w;
+              plan.units.push_back(u);
+            } else {
+              plan.tasks.push_back(k);
+              const int npass = (ib.n + 127) / 128;
+              for (int p = 0; p < npass; ++p)
+                plan.units.push_back({item_idx, (int)plan.tasks.size() - 1, (int)plan.tasks.size(), p, 0,
+                                      std::min(128, ib.n - 128 * p), {0, 0}});
+              acc += cost(k);
+              ++t;
+              ++seg;
+            }
+            if (seg >= seg_tasks) end_segment();
           }
-          acc += c;
-        }
-        plan.items.push_back({(int)b, r0, nr, c0, nc, start, t1, 0, plan.scratch_elems});
-        plan.scratch_elems += (long long)nr * nc;
-        icost.push_back(acc);
+          end_segment();
+          it.u_end = (int)plan.units.size();
+          plan.items.push_back(it);
+          plan.scratch_elems += (long long)nr * nc;
+          icost.push_back(acc);
+        } while (t < t1);
         g.i_end = (int)plan.items.size();
         plan.groups.push_back(g);
       }
@@ -355,7 +440,61 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
   std::iota(plan.schedule.begin(), plan.schedule.end(), 0);
   std::stable_sort(plan.schedule.begin(), plan.schedule.end(),
                    [&](int a, int b) { return icost[a] > icost[b]; });
-  (void)task_out;
+  // records
+  static_assert(sizeof(TcTaskRec) == 64 && sizeof(TcRec) == 304, "record layout");
+  plan.recs.clear();
+  plan.item_rec.assign(plan.items.size() + 1, 0);
+  for (size_t i = 0; i < plan.items.size(); ++i) {
+    const TcItem& it = plan.items[i];
+    plan.item_rec[i] = (int)plan.recs.size();
+    auto header = [&](TcRec& r) {
+      r.r0 = it.r0;
+      r.nrows = it.nrows;
+      r.c0 = it.c0;
+      r.ncols = it.ncols;
+      r.slot = it.slot;
+    };
+    if (it.u_begin == it.u_end) {
+      TcRec r{};
+      r.flags = REC_ZERO;
+      header(r);
+      plan.recs.push_back(r);
+      continue;
+    }
+    for (int u = it.u_begin; u < it.u_end; ++u) {
+      const TcUnit& un = plan.units[u];
+      TcRec r{};
+      r.flags = un.flags;
+      r.ntask = un.t_end - un.t_begin;
+      r.pass = un.pass;
+      r.width = un.width;
+      r.pad[0] = un.width / 8;  // K groups of the packed second product
+      header(r);
+      for (int k = 0; k < r.ntask; ++k) {
+        const TcTask& t = plan.tasks[un.t_begin + k];
+        const TcPsiBlock& p = plan.psi[t.in_blk];
+        TcTaskRec& x = r.t[k];
+        x.a_tile = t.a_tile;
+        x.b_tile = t.b_tile;
+        x.p_tile = p.tile;
+        x.aR8 = (short)t.aR8;
+        x.aC8 = (short)t.aC8;
+        x.bR8 = (short)t.bR8;
+        x.bC8 = (short)t.bC8;
+        x.pR8 = (short)p.R8;
+        x.pC8 = (short)p.C8;
+        x.xcol = (short)t.xcol;
+        x.k1a = (short)t.k1a;
+        x.k1b = (short)t.k1b;
+        x.k2 = (short)t.k2;
+        x.pn = p.n;
+        x.flags = t.flags;
+        x.scale = t.scale;
+      }
+      plan.recs.push_back(r);
+    }
+  }
+  plan.item_rec.back() = (int)plan.recs.size();
 }
 
 }  // namespace dmrg

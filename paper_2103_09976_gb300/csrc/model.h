@@ -173,13 +173,32 @@ struct TcTask {
   int aR8, aC8;               // stored tile geometry of the left block
   int bR8, bC8;               // stored tile geometry of the right block
   int in_blk;
-  int flags;                  // bit0: left used transposed, bit1: right used transposed
+  int flags;                  // bit0: left used transposed, bit1: right used transposed, bit2: psi shared
   float scale;
+  int xcol;                   // packed units: first X column of this task (multiple of 16)
+  int k1a, k1b, k2;           // packed units: tile offsets of its regions in the stage slices
   int pad;
 };
 
+// A unit is what one pass of the pipeline processes: either several small
+// tasks packed side by side (one stage of operator/psi tiles, X columns
+// concatenated, second product K-concatenated) or one 128-column pass of a
+// large task. Units of an item form segments of at most 64 tasks; each
+// segment's FP32 sigma tile is added into the item's FP64 slot.
+enum { UNIT_PACKED = 1, UNIT_ENDS_SEGMENT = 2, UNIT_FIRST_SEGMENT = 4 };
+struct TcUnit {
+  int item;
+  int t_begin, t_end;
+  int pass;
+  int flags;
+  int width;                  // packed: X columns used (<= 64)
+  int pad[2];
+};
+
+// Output tile and its unit range; same layout as Item (u_begin/u_end in the
+// place of the task range) so the reduction can read it.
 struct TcItem {
-  int out, r0, nrows, c0, ncols, t_begin, t_end, pad;
+  int out, r0, nrows, c0, ncols, u_begin, u_end, pad;
   long long slot;
 };
 
@@ -189,21 +208,50 @@ struct TcPsiBlock {
   int m, n;
 };
 
+// Self-contained record of one unit as the kernel reads it (bulk-copied into
+// a shared-memory ring): the unit, its output tile, and up to 4 task records
+// with the geometry of their psi blocks inline.
+struct TcTaskRec {            // 64 bytes
+  long long a_tile, b_tile, p_tile;
+  short aR8, aC8, bR8, bC8, pR8, pC8;
+  short xcol, k1a, k1b, k2;
+  int pn;                     // psi block columns
+  int flags;                  // bit0: left transposed, bit1: right transposed, bit2: psi tiles shared
+  float scale;
+  int pad[2];
+};
+enum { REC_ZERO = 8, REC_DONE = 16 };
+struct TcRec {                // 304 bytes
+  int flags;                  // UNIT_* | REC_ZERO (item without tasks) | REC_DONE
+  int ntask;
+  int pass, width;
+  int r0, nrows, c0, ncols;
+  long long slot;
+  int pad[2];                 // pad[0]: K groups of a packed unit's second product
+  TcTaskRec t[4];
+};
+
 struct TcPlan {
-  std::vector<TcBlock> opblocks;        // parallel to a flat list of (set, op, block)
-  std::vector<long long> op_first;      // index of the first TcBlock of op (L ops then R ops)
+  std::vector<TcBlock> opblocks;        // tiles of every stored block, store order
+  std::vector<long long> op_first;      // index of the first TcBlock of each op (L ops then R ops)
   std::vector<TcBlock> identL, identR;  // identity blocks per sector of the left / right basis
   long long n_tiles = 0;                // tiles per slice array
   std::vector<TcPsiBlock> psi;
   long long psi_tiles = 0;
-  std::vector<TcTask> tasks;
+  std::vector<TcTask> tasks;            // in item order
+  std::vector<TcUnit> units;
   std::vector<TcItem> items;
   std::vector<int> schedule;
   std::vector<Group> groups;
   long long scratch_elems = 0;
+  std::vector<TcRec> recs;              // one per unit (or one REC_ZERO per empty item)
+  std::vector<int> item_rec;            // records of item i: [item_rec[i], item_rec[i+1])
 };
 
+// Tiles of a task's regions in a packed unit (0 if the task cannot be packed).
+int tc_k1_tiles(const TcTask& t, const TcPsiBlock& ib, int r0);
+int tc_k2_tiles(const TcTask& t, int c0);
 void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const OpSet& R,
-                   const WorkList& wl, TcPlan& plan, int want_items, int max_tasks_per_item);
+                   const WorkList& wl, TcPlan& plan, int want_items, int seg_tasks);
 
 }  // namespace dmrg

@@ -29,21 +29,34 @@ namespace dmrg {
 
 namespace {
 
-constexpr int NTHR = 192;
+constexpr int NEPI = 8;                         // epilogue warps
+constexpr int NTHR = 64 + 32 * NEPI;            // producer + MMA + epilogue
 constexpr int STAGES = 3;
-constexpr int SLICE_BYTES = 16 * 1024;          // one slice of a stage
-constexpr int STAGE_BYTES = 3 * SLICE_BYTES;    // 48 KB
-constexpr int PSI_OFF = 8 * 1024;               // psi tile inside a K1 stage slice
+// Operator and psi tiles are stored slice-interleaved: tile position k holds
+// its hi, mid and lo 8x8 bf16 tiles at bytes 384k, 384k+128, 384k+256, in
+// global memory and in the stages alike.
+constexpr int TILE3 = 384;                      // bytes per tile position (3 slices)
+constexpr int STAGE_TILES = 128;                // tile positions per stage
+constexpr int STAGE_BYTES = STAGE_TILES * TILE3;  // 48 KB
+constexpr int PSI_TILE = 64;                    // psi tiles of a large task's K1 stage start here
 constexpr int A2_SLICE = 16 * 1024;             // X chunk: 16 row groups x 8 K groups
-constexpr int A2_BYTES = 3 * A2_SLICE;
-constexpr int BAR_OFF = STAGES * STAGE_BYTES + A2_BYTES;
-constexpr int SMEM_BYTES = BAR_OFF + 256;
-constexpr long long WAIT_CYCLES = 2000000000ll;  // ~1 s at 2 GHz
+constexpr int A2_OFF = STAGES * STAGE_BYTES;
+constexpr int NMETA = 16;                       // unit records in the shared-memory ring
+constexpr int PREFETCH = 8;                     // records fetched ahead of the producer
+constexpr int META_OFF = A2_OFF + 3 * A2_SLICE;
+constexpr int BAR_OFF = META_OFF + NMETA * (int)sizeof(TcRec);
+constexpr int SLACK_OFF = BAR_OFF + 512;
+constexpr int SLACK = 8192;                     // descriptor reads past packed regions stay inside
+constexpr int SMEM_BYTES = SLACK_OFF + SLACK;
+constexpr long long WAIT_CYCLES = 2000000000ll; // ~1 s at 2 GHz
 
-// barrier slots (8 bytes each) after the operand buffers
+// barrier slots (8 bytes each)
 enum { B_FULL = 0, B_EMPTY = STAGES, B_XFULL = 2 * STAGES, B_XEMPTY = 2 * STAGES + 2,
        B_A2FULL = 2 * STAGES + 4, B_A2EMPTY = 2 * STAGES + 5, B_SFULL = 2 * STAGES + 6,
-       B_SEMPTY = 2 * STAGES + 8, B_TMEM = 2 * STAGES + 10, B_ABORT = 2 * STAGES + 11 };
+       B_SEMPTY = 2 * STAGES + 8, B_MFULL = 2 * STAGES + 10, B_MEMPTY = B_MFULL + NMETA,
+       B_TMEM = B_MEMPTY + NMETA, B_ABORT = B_TMEM + 1 };
+static_assert(8 * (B_ABORT + 1) <= 512, "barrier region");
+static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -76,14 +89,22 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Per-CTA wait-time accounting (profiling only): cycles spent blocked on
+// each kind of barrier, summed in shared memory, flushed to global memory.
+__shared__ unsigned long long s_wait[16];
+
 // Bounded wait; returns false (and raises the abort flag) on timeout or if
-// another role already aborted.
+// another role already aborted. `code` names the barrier kind (wait
+// accounting and the error report).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
                                           int* err, int code) {
   if (mbar_try(bar, parity)) return true;
   long long t0 = clock64();
   for (;;) {
-    if (mbar_try(bar, parity)) return true;
+    if (mbar_try(bar, parity)) {
+      atomicAdd(&s_wait[code & 15], (unsigned long long)(clock64() - t0));
+      return true;
+    }
     if (*abort_flag) return false;
     if (clock64() - t0 > WAIT_CYCLES) {
       *abort_flag = 1;
@@ -124,26 +145,104 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 }
 
 // slice products (i, j): i indexes the A slices, j the B slices
-__constant__ int c_prod_i[6] = {0, 0, 1, 0, 1, 2};
-__constant__ int c_prod_j[6] = {0, 1, 0, 2, 1, 0};
 
-// Geometry of the stages of one task pass, shared by all roles.
-struct Pass {
-  int n1;       // valid X columns in this pass (<= 128)
-  int nk1;      // K1 stages
-  int nh;       // K2 stages (64-column sub-chunks)
-};
+__device__ __forceinline__ int rec_k1(const TcRec& r) {
+  return (r.flags & UNIT_PACKED) ? 1 : (r.t[0].pR8 + 3) / 4;
+}
+__device__ __forceinline__ int rec_k2(const TcRec& r) {
+  return (r.flags & UNIT_PACKED) ? 1 : (r.width + 63) / 64;
+}
 
-__device__ __forceinline__ Pass pass_geom(const TcPsiBlock& ib, int pass) {
-  Pass p;
-  p.n1 = min(128, ib.n - pass * 128);
-  p.nk1 = (ib.R8 + 3) / 4;
-  p.nh = (p.n1 + 63) / 64;
-  return p;
+// The copies of one stage, distributed over the producer warp: lane `lane`
+// calls f(src_tile, operand (0 operator, 1 psi), dst_tile, n_tiles) for its
+// own copies only. Every copy moves n_tiles tile positions (all 3 slices).
+template <class F>
+__device__ __forceinline__ void lane_copies(const TcRec& u, int k1_stage, int k2_stage, int lane, F&& f) {
+  const int rg0 = u.r0 / 8, cg0 = u.c0 / 8;
+  if (u.flags & UNIT_PACKED) {
+    if (k1_stage >= 0) {
+      if (lane >= u.ntask) return;
+      const TcTaskRec& tk = u.t[lane];
+      const int aR8 = tk.aR8, aC8 = tk.aC8;
+      if (!(tk.flags & 1)) {
+        f(tk.a_tile + (long long)rg0 * aC8, 0, tk.k1a, min(16, aR8 - rg0) * aC8);
+      } else {
+        const int nmg = min(16, aC8 - rg0);
+        if (nmg == aC8) f(tk.a_tile, 0, tk.k1a, aR8 * aC8);
+        else
+          for (int kg = 0; kg < aR8; ++kg) f(tk.a_tile + (long long)kg * aC8 + rg0, 0, tk.k1a + kg * nmg, nmg);
+      }
+      if (!(tk.flags & 4)) f(tk.p_tile, 1, tk.k1b, (int)tk.pR8 * tk.pC8);
+    } else {
+      // unit-wide layout of the K-concatenated right operand: the K groups
+      // of task t start at xcol/8
+      const int kgu = u.pad[0];
+      const bool tB = u.t[0].flags & 2;
+      if (!tB) {
+        const int nng = min(16, u.t[0].bR8 - cg0);
+        for (int j = lane; j < u.ntask * nng; j += 32) {
+          const TcTaskRec& tk = u.t[j / nng];
+          const int ng = j % nng;
+          f(tk.b_tile + (long long)(cg0 + ng) * tk.bC8, 0, ng * kgu + tk.xcol / 8, tk.bC8);
+        }
+      } else {
+        if (lane >= u.ntask) return;
+        const TcTaskRec& tk = u.t[lane];
+        const int bR8 = tk.bR8, bC8 = tk.bC8, nng = min(16, bC8 - cg0), kx = tk.xcol / 8;
+        if (nng == bC8) f(tk.b_tile, 0, kx * nng, bR8 * bC8);
+        else
+          for (int kg = 0; kg < bR8; ++kg) f(tk.b_tile + (long long)kg * bC8 + cg0, 0, (kx + kg) * nng, nng);
+      }
+    }
+    return;
+  }
+  const TcTaskRec& tk = u.t[0];
+  const int aR8 = tk.aR8, aC8 = tk.aC8, bR8 = tk.bR8, bC8 = tk.bC8, pR8 = tk.pR8, pC8 = tk.pC8;
+  const bool tA = tk.flags & 1, tB = tk.flags & 2;
+  if (k1_stage >= 0) {  // one K chunk (4 K groups) of a large task
+    const int kg0 = 4 * k1_stage;
+    const int nA = !tA ? min(16, aR8 - rg0) : min(4, aR8 - kg0);
+    const int nB = min(4, pR8 - kg0);
+    if (lane < nA) {
+      if (!tA) f(tk.a_tile + (long long)(rg0 + lane) * aC8 + kg0, 0, lane * 4, min(4, aC8 - kg0));
+      else f(tk.a_tile + (long long)(kg0 + lane) * aC8 + rg0, 0, lane * 16, min(16, aC8 - rg0));
+    } else if (lane < nA + nB) {
+      const int r = lane - nA;
+      f(tk.p_tile + (long long)(kg0 + r) * pC8 + u.pass * 16, 1, PSI_TILE + r * 16, min(16, pC8 - u.pass * 16));
+    }
+  } else {  // one 64-column K chunk of the second product of a large task
+    const int kgx = u.pass * 16 + k2_stage * 8;
+    if (!tB) {
+      if (lane < min(16, bR8 - cg0)) f(tk.b_tile + (long long)(cg0 + lane) * bC8 + kgx, 0, lane * 8, min(8, bC8 - kgx));
+    } else {
+      if (lane < min(8, bR8 - kgx)) f(tk.b_tile + (long long)(kgx + lane) * bC8 + cg0, 0, lane * 16, min(16, bC8 - cg0));
+    }
+  }
 }
 
 }  // namespace
 
+// Slice pair of product p (i + j <= 2 ordering: hh, hm, mh, hl, mm, lh).
+__device__ __forceinline__ constexpr int prod_i(int p) { return (p == 2 || p == 4) ? 1 : (p == 5 ? 2 : 0); }
+__device__ __forceinline__ constexpr int prod_j(int p) { return (p == 1 || p == 4) ? 1 : (p == 3 ? 2 : 0); }
+
+// One K chain of slice products into tmem_d. Descriptors differ only in the
+// start-address field, so each MMA adds its byte offset >> 4 to a base.
+template <int NPROD>
+__device__ __forceinline__ void mma_chain(uint32_t tmem_d, uint64_t ad0, uint64_t bd0, uint32_t a_slice,
+                                          uint32_t b_slice, uint32_t a_kstep, uint32_t b_kstep, int nks,
+                                          uint32_t idesc, bool acc_first) {
+  for (int ks = 0; ks < nks; ++ks) {
+#pragma unroll
+    for (int p = 0; p < NPROD; ++p) {
+      const uint64_t ad = ad0 + ((prod_i(p) * a_slice + (uint32_t)ks * a_kstep) >> 4);
+      const uint64_t bd = bd0 + ((prod_j(p) * b_slice + (uint32_t)ks * b_kstep) >> 4);
+      mma(tmem_d, ad, bd, idesc, (acc_first || ks > 0 || p > 0) ? 1u : 0u);
+    }
+  }
+}
+
+template <int NPROD>
 __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -152,10 +251,15 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
   auto bar = [&](int k) { return bars + 8u * (uint32_t)k; };
   volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + BAR_OFF + 8 * B_ABORT);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + BAR_OFF + 8 * B_TMEM);
+  TcRec* ring = reinterpret_cast<TcRec*>(sm + META_OFF);
 
+  const long long t_start = clock64();
+  if (tid < 16) s_wait[tid] = 0ull;
   // zero all operand buffers once: afterwards shared memory only ever holds
-  // finite operand data or zeros, so padded K positions multiply to 0.
-  for (int i = tid; i < BAR_OFF / 16; i += NTHR) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
+  // finite operand data or zeros, so padded K positions multiply to 0 and
+  // padded rows stay finite.
+  for (int i = tid; i < META_OFF / 16; i += NTHR) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
+  for (int i = tid; i < SLACK / 16; i += NTHR) reinterpret_cast<uint4*>(sm + SLACK_OFF)[i] = make_uint4(0, 0, 0, 0);
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(bar(B_FULL + s), 1);
@@ -163,12 +267,16 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
     }
     for (int x = 0; x < 2; ++x) {
       mbar_init(bar(B_XFULL + x), 1);
-      mbar_init(bar(B_XEMPTY + x), 4);
+      mbar_init(bar(B_XEMPTY + x), NEPI);
       mbar_init(bar(B_SFULL + x), 1);
-      mbar_init(bar(B_SEMPTY + x), 4);
+      mbar_init(bar(B_SEMPTY + x), NEPI);
     }
-    mbar_init(bar(B_A2FULL), 4);
+    mbar_init(bar(B_A2FULL), NEPI);
     mbar_init(bar(B_A2EMPTY), 1);
+    for (int m = 0; m < NMETA; ++m) {
+      mbar_init(bar(B_MFULL + m), 1);
+      mbar_init(bar(B_MEMPTY + m), 2 + NEPI);  // producer + MMA + epilogue warps
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
@@ -181,82 +289,101 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n");
   const uint32_t tmem = *tmem_slot;
-  const int nprod = a.nprod;
-  const int nsl = nprod == 6 ? 3 : 2;  // slices read per operand
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     uint32_t stage = 0, phase = 1;  // empty barriers: first wait passes
-    const char* ops[3] = {(const char*)a.op[0], (const char*)a.op[1], (const char*)a.op[2]};
-    const char* ps[3] = {(const char*)a.psi[0], (const char*)a.psi[1], (const char*)a.psi[2]};
     bool ok = true;
-    for (int q = blockIdx.x; q < a.n_items && ok; q += gridDim.x) {
-      const TcItem it = a.items[a.schedule[q]];
-      for (int t = it.t_begin; t < it.t_end && ok; ++t) {
-        const TcTask tk = a.tasks[t];
-        const TcPsiBlock ib = a.pblk[tk.in_blk];
-        const bool tA = tk.flags & 1, tB = tk.flags & 2;
-        const int npass = (ib.n + 127) / 128;
-        for (int pass = 0; pass < npass && ok; ++pass) {
-          const Pass pg = pass_geom(ib, pass);
-          for (int k = 0; k < pg.nk1 + pg.nh && ok; ++k) {
-            if (!mbar_wait(bar(B_EMPTY + stage), phase, abort_flag, a.err, 1)) { ok = false; break; }
-            const uint32_t sdst = sbase + stage * STAGE_BYTES;
-            int nA, tilesA, nB, tilesB;
-            if (k < pg.nk1) {  // K1: left operator rows x K chunk, psi K chunk x pass columns
-              const int kg0 = 4 * k;
-              const int rg0 = it.r0 / 8;
-              if (!tA) { nA = min(16, tk.aR8 - rg0); tilesA = min(4, tk.aC8 - kg0); }
-              else     { nA = min(4, tk.aR8 - kg0);  tilesA = min(16, tk.aC8 - rg0); }
-              nB = min(4, ib.R8 - kg0);
-              tilesB = min(16, ib.C8 - pass * 16);
-            } else {           // K2: right operator K chunk x output columns
-              const int h = k - pg.nk1;
-              const int kgx = pass * 16 + h * 8;
-              const int cg0 = it.c0 / 8;
-              if (!tB) { nA = min(16, tk.bR8 - cg0); tilesA = min(8, tk.bC8 - kgx); }
-              else     { nA = min(8, tk.bR8 - kgx);  tilesA = min(16, tk.bC8 - cg0); }
-              nB = 0;
-              tilesB = 0;
-            }
-            const uint32_t bytes = (uint32_t)nsl * 128u * (uint32_t)(nA * tilesA + nB * tilesB);
-            if (lane == 0) mbar_expect_tx(bar(B_FULL + stage), bytes);
-            __syncwarp();
-            const int per_slice = nA + nB;
-            for (int j = lane; j < nsl * per_slice; j += 32) {
-              const int s = j / per_slice, r = j % per_slice;
-              const uint32_t slice_dst = sdst + s * SLICE_BYTES;
-              if (k < pg.nk1) {
-                const int kg0 = 4 * k, rg0 = it.r0 / 8;
-                if (r < nA) {
-                  long long src_tile;
-                  uint32_t dst;
-                  if (!tA) { src_tile = tk.a_tile + (long long)(rg0 + r) * tk.aC8 + kg0; dst = slice_dst + (r * 4) * 128; }
-                  else     { src_tile = tk.a_tile + (long long)(kg0 + r) * tk.aC8 + rg0; dst = slice_dst + (r * 16) * 128; }
-                  bulk_g2s(dst, ops[s] + src_tile * 128, 128u * tilesA, bar(B_FULL + stage));
-                } else {
-                  const int rr = r - nA;
-                  long long src_tile = ib.tile + (long long)(kg0 + rr) * ib.C8 + pass * 16;
-                  bulk_g2s(slice_dst + PSI_OFF + (rr * 16) * 128, ps[s] + src_tile * 128, 128u * tilesB,
-                           bar(B_FULL + stage));
-                }
-              } else {
-                const int h = k - pg.nk1;
-                const int kgx = pass * 16 + h * 8, cg0 = it.c0 / 8;
-                long long src_tile;
-                uint32_t dst;
-                if (!tB) { src_tile = tk.b_tile + (long long)(cg0 + r) * tk.bC8 + kgx; dst = slice_dst + (r * 8) * 128; }
-                else     { src_tile = tk.b_tile + (long long)(kgx + r) * tk.bC8 + cg0; dst = slice_dst + (r * 16) * 128; }
-                bulk_g2s(dst, ops[s] + src_tile * 128, 128u * tilesA, bar(B_FULL + stage));
-              }
-            }
-            if (++stage == STAGES) { stage = 0; phase ^= 1; }
-          }
+    const char* const ops = (const char*)a.op;
+    const char* const ps = (const char*)a.psi;
+    auto produce = [&](const TcRec& u, int k1, int k2) {
+      if (!ok) return;
+      if (!mbar_wait(bar(B_EMPTY + stage), phase, abort_flag, a.err, 1)) { ok = false; return; }
+      uint32_t tiles = 0;
+      lane_copies(u, k1, k2, lane, [&](long long, int, int, int n) { tiles += (uint32_t)n; });
+      tiles = __reduce_add_sync(0xffffffffu, tiles);
+      if (lane == 0) mbar_expect_tx(bar(B_FULL + stage), (uint32_t)TILE3 * tiles);
+      __syncwarp();
+      const uint32_t sdst = sbase + stage * STAGE_BYTES;
+      lane_copies(u, k1, k2, lane, [&](long long src, int which, int dst, int n) {
+        bulk_g2s(sdst + (uint32_t)dst * TILE3, (which ? ps : ops) + src * TILE3, (uint32_t)TILE3 * (uint32_t)n,
+                 bar(B_FULL + stage));
+      });
+      if (++stage == STAGES) { stage = 0; phase ^= 1; }
+    };
+    bool no_more = false;
+    int pf_r = 0, pf_end = 0;  // prefetch cursor: next record and end of its item
+    long long pf_s = 0;        // records pushed into the ring
+    auto prefetch_one = [&]() -> bool {
+      if (pf_r == pf_end) {    // take the next item
+        if (no_more) return false;
+        int q = 0;
+        if (lane == 0) q = (int)atomicAdd(a.counter, 1u);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        if (q >= a.n_items) { no_more = true; return false; }
+        const int it = a.schedule[q];
+        pf_r = a.item_rec[it];
+        pf_end = a.item_rec[it + 1];
+      }
+      const int slot = (int)(pf_s % NMETA);
+      const uint32_t par = (uint32_t)(((pf_s / NMETA) & 1) ^ 1);
+      if (!mbar_wait(bar(B_MEMPTY + slot), par, abort_flag, a.err, 9)) { ok = false; return false; }
+      if (lane == 0) {
+        mbar_expect_tx(bar(B_MFULL + slot), (uint32_t)sizeof(TcRec));
+        bulk_g2s(smem_u32(ring + slot), a.recs + pf_r, (uint32_t)sizeof(TcRec), bar(B_MFULL + slot));
+      }
+      __syncwarp();
+      ++pf_r;
+      ++pf_s;
+      return true;
+    };
+    long long s = 0;
+    int prev_slot = -1;
+    for (;;) {
+      while (ok && pf_s < s + PREFETCH && prefetch_one()) {
+      }
+      if (!ok) break;
+      if (s == pf_s) break;  // nothing left
+      const int slot = (int)(s % NMETA);
+      if (!mbar_wait(bar(B_MFULL + slot), (uint32_t)((s / NMETA) & 1), abort_flag, a.err, 10)) { ok = false; break; }
+      const TcRec& u = ring[slot];
+      if (!(u.flags & REC_ZERO))
+        for (int k = 0; k < rec_k1(u); ++k) produce(u, k, -1);
+      if (prev_slot >= 0) {
+        const TcRec& pu = ring[prev_slot];
+        for (int h = 0; h < rec_k2(pu); ++h) produce(pu, -1, h);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar(B_MEMPTY + prev_slot));
+      }
+      if (u.flags & REC_ZERO) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar(B_MEMPTY + slot));
+        prev_slot = -1;
+      } else {
+        prev_slot = slot;
+      }
+      ++s;
+    }
+    if (ok && prev_slot >= 0) {
+      const TcRec& pu = ring[prev_slot];
+      for (int h = 0; h < rec_k2(pu); ++h) produce(pu, -1, h);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(B_MEMPTY + prev_slot));
+    }
+    // terminator record
+    if (ok) {
+      const int slot = (int)(s % NMETA);
+      const uint32_t par = (uint32_t)(((s / NMETA) & 1) ^ 1);
+      if (mbar_wait(bar(B_MEMPTY + slot), par, abort_flag, a.err, 11)) {
+        if (lane == 0) {
+          ring[slot].flags = REC_DONE;
+          mbar_arrive(bar(B_MFULL + slot));
         }
       }
     }
+    __syncwarp();
     // drain: wait (bounded) until the MMA side released every stage we filled
-    for (int s = 0; s < STAGES; ++s) {
+    for (int k = 0; k < STAGES; ++k) {
       mbar_wait(bar(B_EMPTY + stage), phase, abort_flag, a.err, 0);
       if (++stage == STAGES) { stage = 0; phase ^= 1; }
     }
@@ -264,164 +391,249 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
     // --------------------------------------------------------------- MMA
     if (lane == 0) {
       uint32_t stage = 0, phase = 0;
-      uint32_t xb = 0, xph_empty[2] = {1, 1};
+      uint32_t xcnt = 0, xph_empty = 3u;   // bit b: expected parity of X-empty[b]
       uint32_t a2_full_ph = 0;
-      uint32_t sb = 0, sph_empty[2] = {1, 1};
-      bool ok = true;
-      for (int q = blockIdx.x; q < a.n_items && ok; q += gridDim.x) {
-        const TcItem it = a.items[a.schedule[q]];
-        if (it.t_begin == it.t_end) continue;
-        bool first_s = true;
-        const uint32_t tmem_s = tmem + 256 + sb * 128;
-        if (!mbar_wait(bar(B_SEMPTY + sb), sph_empty[sb], abort_flag, a.err, 2)) { ok = false; break; }
-        sph_empty[sb] ^= 1;
+      uint32_t sb = 0, sph_empty = 3u;     // bit b: expected parity of S-empty[b]
+      bool seg_open = false, ok = true;
+      auto acquire = [&]() -> uint32_t {
+        if (!mbar_wait(bar(B_FULL + stage), phase, abort_flag, a.err, 4)) { ok = false; return 0; }
         asm volatile("tcgen05.fence::after_thread_sync;\n");
-        const int n2 = 16 * ((it.ncols + 15) / 16);
-        for (int t = it.t_begin; t < it.t_end && ok; ++t) {
-          const TcTask tk = a.tasks[t];
-          const TcPsiBlock ib = a.pblk[tk.in_blk];
-          const int tA = tk.flags & 1, tB = (tk.flags >> 1) & 1;
-          const int npass = (ib.n + 127) / 128;
-          for (int pass = 0; pass < npass && ok; ++pass) {
-            const Pass pg = pass_geom(ib, pass);
-            const uint32_t tmem_x = tmem + xb * 128;
-            if (!mbar_wait(bar(B_XEMPTY + xb), xph_empty[xb], abort_flag, a.err, 3)) { ok = false; break; }
-            xph_empty[xb] ^= 1;
-            asm volatile("tcgen05.fence::after_thread_sync;\n");
-            const int n1 = 16 * ((pg.n1 + 15) / 16);
-            const uint32_t id1 = idesc_bf16(n1, tA, 1);
-            const uint32_t a_lbo = tA ? 2048u : 128u, a_sbo = tA ? 128u : 512u;
-            for (int k = 0; k < pg.nk1 + pg.nh; ++k) {
-              if (!mbar_wait(bar(B_FULL + stage), phase, abort_flag, a.err, 4)) { ok = false; break; }
-              asm volatile("tcgen05.fence::after_thread_sync;\n");
-              const uint32_t sst = sbase + stage * STAGE_BYTES;
-              if (k < pg.nk1) {
-                const int nks = min(4, ib.R8 - 4 * k) / 2;
-                for (int ks = 0; ks < nks; ++ks)
-                  for (int p = 0; p < nprod; ++p) {
-                    const uint32_t aa = sst + c_prod_i[p] * SLICE_BYTES + ks * 2 * a_lbo;
-                    const uint32_t bb = sst + c_prod_j[p] * SLICE_BYTES + PSI_OFF + ks * 2 * 2048u;
-                    mma(tmem_x, sdesc(aa, a_lbo, a_sbo), sdesc(bb, 2048u, 128u), id1,
-                        (k > 0 || ks > 0 || p > 0) ? 1u : 0u);
-                  }
-                commit(bar(B_EMPTY + stage));
-                if (k == pg.nk1 - 1) commit(bar(B_XFULL + xb));
-              } else {
-                const int h = k - pg.nk1;
-                const int valid = min(64, pg.n1 - h * 64);
-                const int nks = (valid + 15) / 16;
-                if (!mbar_wait(bar(B_A2FULL), a2_full_ph, abort_flag, a.err, 5)) { ok = false; break; }
-                a2_full_ph ^= 1;
-                asm volatile("tcgen05.fence::after_thread_sync;\n");
-                const uint32_t id2 = idesc_bf16(n2, 0, tB);
-                const uint32_t b_lbo = tB ? 2048u : 128u, b_sbo = tB ? 128u : 1024u;
-                const uint32_t a2 = sbase + STAGES * STAGE_BYTES;
-                for (int ks = 0; ks < nks; ++ks)
-                  for (int p = 0; p < nprod; ++p) {
-                    const uint32_t aa = a2 + c_prod_i[p] * A2_SLICE + ks * 2 * 128u;
-                    const uint32_t bb = sst + c_prod_j[p] * SLICE_BYTES + ks * 2 * b_lbo;
-                    mma(tmem_s, sdesc(aa, 128u, 1024u), sdesc(bb, b_lbo, b_sbo), id2,
-                        (!first_s || ks > 0 || p > 0) ? 1u : 0u);
-                  }
-                first_s = false;
-                commit(bar(B_EMPTY + stage));
-                commit(bar(B_A2EMPTY));
-              }
-              if (++stage == STAGES) { stage = 0; phase ^= 1; }
-            }
-            xb ^= 1;
+        return sbase + stage * STAGE_BYTES;
+      };
+      auto release = [&]() {
+        commit(bar(B_EMPTY + stage));
+        if (++stage == STAGES) { stage = 0; phase ^= 1; }
+      };
+      auto mma_k1 = [&](const TcRec& u) {
+        const uint32_t xb = xcnt & 1;
+        if (!mbar_wait(bar(B_XEMPTY + xb), (xph_empty >> xb) & 1u, abort_flag, a.err, 3)) { ok = false; return; }
+        xph_empty ^= 1u << xb;
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        const uint32_t tmem_x = tmem + xb * 128;
+        if (u.flags & UNIT_PACKED) {
+          const uint32_t sst = acquire();
+          if (!ok) return;
+          const int rg0 = u.r0 / 8;
+          for (int t = 0; t < u.ntask; ++t) {
+            const TcTaskRec& tk = u.t[t];
+            const int tA = tk.flags & 1;
+            const int aC8 = tk.aC8, pC8 = tk.pC8;
+            const int n16 = 16 * ((tk.pn + 15) / 16);
+            const uint32_t a_lbo = tA ? (uint32_t)min(16, aC8 - rg0) * TILE3 : TILE3;
+            const uint32_t a_sbo = tA ? TILE3 : (uint32_t)aC8 * TILE3;
+            const uint32_t b_lbo = (uint32_t)pC8 * TILE3;
+            mma_chain<NPROD>(tmem_x + tk.xcol, sdesc(sst + tk.k1a * TILE3, a_lbo, a_sbo),
+                             sdesc(sst + tk.k1b * TILE3, b_lbo, TILE3), 128u, 128u, 2 * a_lbo, 2 * b_lbo,
+                             tk.pR8 / 2, idesc_bf16(n16, tA, 1), false);
+          }
+          release();
+        } else {
+          const TcTaskRec& tk = u.t[0];
+          const int tA = tk.flags & 1;
+          const uint32_t id1 = idesc_bf16(16 * ((u.width + 15) / 16), tA, 1);
+          const uint32_t a_lbo = tA ? 16u * TILE3 : TILE3, a_sbo = tA ? TILE3 : 4u * TILE3;
+          const int pR8 = tk.pR8, nk = (pR8 + 3) / 4;
+          for (int k = 0; k < nk && ok; ++k) {
+            const uint32_t sst = acquire();
+            if (!ok) return;
+            mma_chain<NPROD>(tmem_x, sdesc(sst, a_lbo, a_sbo), sdesc(sst + PSI_TILE * TILE3, 16u * TILE3, TILE3),
+                             128u, 128u, 2 * a_lbo, 2 * 16u * TILE3, min(4, pR8 - 4 * k) / 2, id1, k > 0);
+            release();
           }
         }
-        if (!ok) break;
-        commit(bar(B_SFULL + sb));
-        sb ^= 1;
+        commit(bar(B_XFULL + xb));
+        ++xcnt;
+      };
+      auto mma_k2 = [&](const TcRec& u) {
+        const uint32_t id_n = (uint32_t)(16 * ((u.ncols + 15) / 16));
+        const uint32_t a2 = sbase + A2_OFF;
+        const int nk2 = rec_k2(u);
+        for (int h = 0; h < nk2 && ok; ++h) {
+          if (!mbar_wait(bar(B_A2FULL), a2_full_ph, abort_flag, a.err, 5)) { ok = false; return; }
+          a2_full_ph ^= 1;
+          if (!seg_open) {
+            if (!mbar_wait(bar(B_SEMPTY + sb), (sph_empty >> sb) & 1u, abort_flag, a.err, 2)) { ok = false; return; }
+            sph_empty ^= 1u << sb;
+          }
+          const uint32_t sst = acquire();
+          if (!ok) return;
+          const uint32_t tmem_s = tmem + 256 + sb * 128;
+          const int tB = (u.t[0].flags >> 1) & 1;
+          const uint32_t id2 = idesc_bf16((int)id_n, 0, tB);
+          uint32_t b_lbo, b_sbo;
+          int nks;
+          if (u.flags & UNIT_PACKED) {  // one K-concatenated chain for all tasks of the unit
+            const int nng = min(16, u.t[0].bC8 - u.c0 / 8);
+            b_lbo = tB ? (uint32_t)nng * TILE3 : TILE3;
+            b_sbo = tB ? TILE3 : (uint32_t)u.pad[0] * TILE3;
+            nks = u.width / 16;
+          } else {
+            b_lbo = tB ? 16u * TILE3 : TILE3;
+            b_sbo = tB ? TILE3 : 8u * TILE3;
+            nks = (min(64, u.width - h * 64) + 15) / 16;
+          }
+          mma_chain<NPROD>(tmem_s, sdesc(a2, 128u, 1024u), sdesc(sst, b_lbo, b_sbo), A2_SLICE, 128u, 2 * 128u,
+                           2 * b_lbo, nks, id2, seg_open);
+          seg_open = true;
+          release();
+          commit(bar(B_A2EMPTY));
+        }
+        if (ok && (u.flags & UNIT_ENDS_SEGMENT)) {
+          commit(bar(B_SFULL + sb));
+          sb ^= 1;
+          seg_open = false;
+        }
+      };
+      long long s = 0;
+      int prev_slot = -1;
+      while (ok) {
+        const int slot = (int)(s % NMETA);
+        if (!mbar_wait(bar(B_MFULL + slot), (uint32_t)((s / NMETA) & 1), abort_flag, a.err, 12)) { ok = false; break; }
+        const TcRec& u = ring[slot];
+        const int fl = u.flags;
+        if (fl & REC_DONE) break;
+        if (!(fl & REC_ZERO)) mma_k1(u);
+        if (prev_slot >= 0 && ok) {
+          mma_k2(ring[prev_slot]);
+          mbar_arrive(bar(B_MEMPTY + prev_slot));
+        }
+        if (fl & REC_ZERO) {
+          mbar_arrive(bar(B_MEMPTY + slot));
+          prev_slot = -1;
+        } else {
+          prev_slot = slot;
+        }
+        ++s;
+      }
+      if (ok && prev_slot >= 0) {
+        mma_k2(ring[prev_slot]);
+        mbar_arrive(bar(B_MEMPTY + prev_slot));
       }
     }
     __syncwarp();
   } else {
     // ---------------------------------------------------------- epilogue
+    const int e = warp - 2;                    // 0 .. NEPI-1
     const int quarter = warp & 3;              // TMEM lanes 32*quarter .. +31
+    const int half = e >> 2;                   // columns 32*half of each 64-column chunk
     const int row = quarter * 32 + lane;       // output / X row owned by this thread
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-    uint32_t xb = 0, xph_full[2] = {0, 0};
+    uint32_t xcnt = 0, xph_full = 0;    // bit b: expected parity of X-full[b]
     uint32_t a2_empty_ph = 1;
-    uint32_t sb = 0, sph_full[2] = {0, 0};
+    uint32_t sb = 0, sph_full = 0;      // bit b: expected parity of S-full[b]
     bool ok = true;
-    __nv_bfloat16* a2 = reinterpret_cast<__nv_bfloat16*>(sm + STAGES * STAGE_BYTES);
-    for (int q = blockIdx.x; q < a.n_items && ok; q += gridDim.x) {
-      const TcItem it = a.items[a.schedule[q]];
-      double* out = a.scratch + it.slot;
-      if (it.t_begin == it.t_end) {
-        if (row < it.nrows)
-          for (int c = 0; c < it.ncols; ++c) out[(long long)row * it.ncols + c] = 0.0;
-        continue;
-      }
-      for (int t = it.t_begin; t < it.t_end && ok; ++t) {
-        const TcTask tk = a.tasks[t];
-        const TcPsiBlock ib = a.pblk[tk.in_blk];
-        const int npass = (ib.n + 127) / 128;
-        for (int pass = 0; pass < npass && ok; ++pass) {
-          const Pass pg = pass_geom(ib, pass);
-          if (!mbar_wait(bar(B_XFULL + xb), xph_full[xb], abort_flag, a.err, 6)) { ok = false; break; }
-          xph_full[xb] ^= 1;
-          asm volatile("tcgen05.fence::after_thread_sync;\n");
-          for (int h = 0; h < pg.nh; ++h) {
-            float v[64];
-            tmem_ld32(tmem + lane_off + xb * 128 + h * 64, v);
-            tmem_ld32(tmem + lane_off + xb * 128 + h * 64 + 32, v + 32);
-            if (h == pg.nh - 1) {
-              asm volatile("tcgen05.fence::before_thread_sync;\n");
-              __syncwarp();
-              if (lane == 0) mbar_arrive(bar(B_XEMPTY + xb));
-            }
-            const int valid = min(64, pg.n1 - h * 64);
-            if (!mbar_wait(bar(B_A2EMPTY), a2_empty_ph, abort_flag, a.err, 7)) { ok = false; break; }
-            a2_empty_ph ^= 1;
-            // split scale*X into three bf16 slices, K-major 8x8 tiles
+    __nv_bfloat16* a2 = reinterpret_cast<__nv_bfloat16*>(sm + A2_OFF);
+    // write 32 K-columns (half of a 64-column chunk) of A2 for this row
+    auto write_a2 = [&](const float* v) {
 #pragma unroll
-            for (int g = 0; g < 8; ++g) {
-              __align__(16) __nv_bfloat16 hv[8], mv[8], lv[8];
+      for (int g = 0; g < 4; ++g) {
+        uint32_t hw[4], mw[4], lw[4];
 #pragma unroll
-              for (int e = 0; e < 8; ++e) {
-                const int j = g * 8 + e;
-                float x = (j < valid) ? v[j] * tk.scale : 0.0f;
-                __nv_bfloat16 h0 = __float2bfloat16_rn(x);
-                float r1 = x - __bfloat162float(h0);
-                __nv_bfloat16 m0 = __float2bfloat16_rn(r1);
-                float r2 = r1 - __bfloat162float(m0);
-                hv[e] = h0;
-                mv[e] = m0;
-                lv[e] = __float2bfloat16_rn(r2);
-              }
-              const int off = (((row >> 3) * 8 + g) * 64 + (row & 7) * 8);
-              *reinterpret_cast<uint4*>(a2 + off) = *reinterpret_cast<uint4*>(hv);
-              *reinterpret_cast<uint4*>(a2 + A2_SLICE / 2 + off) = *reinterpret_cast<uint4*>(mv);
-              *reinterpret_cast<uint4*>(a2 + A2_SLICE + off) = *reinterpret_cast<uint4*>(lv);
-            }
-            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(bar(B_A2FULL));
+        for (int q = 0; q < 4; ++q) {
+          uint32_t hp = 0, mp = 0, lp = 0;
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const float x = v[g * 8 + 2 * q + e];
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(x);
+            const float r1 = x - __bfloat162float(h0);
+            const __nv_bfloat16 m0 = __float2bfloat16_rn(r1);
+            const __nv_bfloat16 l0 = __float2bfloat16_rn(r1 - __bfloat162float(m0));
+            hp |= (uint32_t)__bfloat16_as_ushort(h0) << (16 * e);
+            mp |= (uint32_t)__bfloat16_as_ushort(m0) << (16 * e);
+            lp |= (uint32_t)__bfloat16_as_ushort(l0) << (16 * e);
           }
-          xb ^= 1;
+          hw[q] = hp;
+          mw[q] = mp;
+          lw[q] = lp;
         }
+        const int off = (((row >> 3) * 8 + half * 4 + g) * 64 + (row & 7) * 8);
+        *reinterpret_cast<uint4*>(a2 + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4*>(a2 + A2_SLICE / 2 + off) = make_uint4(mw[0], mw[1], mw[2], mw[3]);
+        *reinterpret_cast<uint4*>(a2 + A2_SLICE + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
       }
-      if (!ok) break;
-      // sigma tile -> FP64 partial slot
-      if (!mbar_wait(bar(B_SFULL + sb), sph_full[sb], abort_flag, a.err, 8)) { ok = false; break; }
-      sph_full[sb] ^= 1;
-      asm volatile("tcgen05.fence::after_thread_sync;\n");
-      for (int c0 = 0; c0 < it.ncols; c0 += 32) {
-        float v[32];
-        tmem_ld32(tmem + lane_off + 256 + sb * 128 + c0, v);
-        if (row < it.nrows) {
-          const int nc = min(32, it.ncols - c0);
-          for (int c = 0; c < nc; ++c) out[(long long)row * it.ncols + c0 + c] = (double)v[c];
-        }
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;\n");
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       __syncwarp();
-      if (lane == 0) mbar_arrive(bar(B_SEMPTY + sb));
-      sb ^= 1;
+      if (lane == 0) mbar_arrive(bar(B_A2FULL));
+    };
+    long long s = 0;
+    while (ok) {
+      const int slot = (int)(s % NMETA);
+      if (!mbar_wait(bar(B_MFULL + slot), (uint32_t)((s / NMETA) & 1), abort_flag, a.err, 13)) { ok = false; break; }
+      const TcRec& u = ring[slot];
+      const int fl = u.flags;
+      if (fl & REC_DONE) break;
+      double* out = a.scratch + u.slot;
+      if (fl & REC_ZERO) {
+        if (row < u.nrows)
+          for (int c = half * 64; c < min(u.ncols, half * 64 + 64); ++c) out[(long long)row * u.ncols + c] = 0.0;
+      } else {
+        const uint32_t xb = xcnt & 1;
+        if (!mbar_wait(bar(B_XFULL + xb), (xph_full >> xb) & 1u, abort_flag, a.err, 6)) { ok = false; break; }
+        xph_full ^= 1u << xb;
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        const uint32_t xaddr = tmem + lane_off + xb * 128;
+        float v[32];
+        const int nh = (fl & UNIT_PACKED) ? 1 : (u.width + 63) / 64;
+        for (int h = 0; h < nh; ++h) {
+          tmem_ld32(xaddr + h * 64 + half * 32, v);
+          if (h == nh - 1) {
+            asm volatile("tcgen05.fence::before_thread_sync;\n");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar(B_XEMPTY + xb));
+          }
+          // scale valid columns, zero the rest (K padding of the second product)
+          const int c0 = h * 64 + half * 32;
+          if (fl & UNIT_PACKED) {
+            float cs[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) cs[j] = 0.0f;
+            for (int t = 0; t < u.ntask; ++t) {
+              const int x0 = u.t[t].xcol - c0, x1 = x0 + u.t[t].pn;
+              const float sc = u.t[t].scale;
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                if (j >= x0 && j < x1) cs[j] = sc;
+            }
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = cs[j] != 0.0f ? v[j] * cs[j] : 0.0f;
+          } else {
+            const float sc = u.t[0].scale;
+            const int valid = u.width - c0;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = j < valid ? v[j] * sc : 0.0f;
+          }
+          if (!mbar_wait(bar(B_A2EMPTY), a2_empty_ph, abort_flag, a.err, 7)) { ok = false; break; }
+          a2_empty_ph ^= 1;
+          write_a2(v);
+        }
+        ++xcnt;
+        if (!ok) break;
+        if (fl & UNIT_ENDS_SEGMENT) {
+          // segment's FP32 sigma tile -> FP64 slot (store on the first segment, add after)
+          if (!mbar_wait(bar(B_SFULL + sb), (sph_full >> sb) & 1u, abort_flag, a.err, 8)) { ok = false; break; }
+          sph_full ^= 1u << sb;
+          asm volatile("tcgen05.fence::after_thread_sync;\n");
+          const bool first = fl & UNIT_FIRST_SEGMENT;
+          for (int c0 = half * 64; c0 < min(u.ncols, half * 64 + 64); c0 += 32) {
+            float w[32];
+            tmem_ld32(tmem + lane_off + 256 + sb * 128 + c0, w);
+            if (row < u.nrows) {
+              const int nc = min(32, u.ncols - c0);
+              double* o = out + (long long)row * u.ncols + c0;
+#pragma unroll
+              for (int c = 0; c < 32; ++c)
+                if (c < nc) o[c] = first ? (double)w[c] : o[c] + (double)w[c];
+            }
+          }
+          asm volatile("tcgen05.fence::before_thread_sync;\n");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(bar(B_SEMPTY + sb));
+          sb ^= 1;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(B_MEMPTY + slot));
+      ++s;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n");
@@ -429,6 +641,10 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;\n");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem));
+  }
+  if (a.wait_prof && tid < 16) {
+    atomicAdd(a.wait_prof + tid, s_wait[tid]);
+    if (tid == 0) atomicAdd(a.wait_prof + 16, (unsigned long long)(clock64() - t_start));
   }
 }
 
@@ -442,8 +658,7 @@ __device__ __forceinline__ void split3(double x, __nv_bfloat16& h, __nv_bfloat16
 }
 
 __global__ void split_ops_kernel(const double* __restrict__ store, const SplitJob* __restrict__ jobs,
-                                 long long njobs, __nv_bfloat16* __restrict__ s0,
-                                 __nv_bfloat16* __restrict__ s1, __nv_bfloat16* __restrict__ s2) {
+                                 long long njobs, __nv_bfloat16* __restrict__ out) {
   for (long long b = blockIdx.x; b < njobs; b += gridDim.x) {
     const SplitJob j = jobs[b];
     const long long n = (long long)j.R8 * j.C8 * 64;
@@ -455,17 +670,16 @@ __global__ void split_ops_kernel(const double* __restrict__ store, const SplitJo
       if (i < j.rows && c < j.cols) x = (j.src < 0) ? (i == c ? 1.0 : 0.0) : store[j.src + (long long)i * j.cols + c];
       __nv_bfloat16 h, m, l;
       split3(x, h, m, l);
-      const long long d = j.tile * 64 + e;
-      s0[d] = h;
-      s1[d] = m;
-      s2[d] = l;
+      const long long d = (j.tile + t) * 192 + w;
+      out[d] = h;
+      out[d + 64] = m;
+      out[d + 128] = l;
     }
   }
 }
 
 __global__ void split_psi_kernel(const double* __restrict__ psi, const PsiBlock* __restrict__ blocks,
-                                 const TcPsiBlock* __restrict__ pb, int nblk, __nv_bfloat16* __restrict__ s0,
-                                 __nv_bfloat16* __restrict__ s1, __nv_bfloat16* __restrict__ s2) {
+                                 const TcPsiBlock* __restrict__ pb, int nblk, __nv_bfloat16* __restrict__ out) {
   for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
     const TcPsiBlock p = pb[b];
     const long long off = blocks[b].off;
@@ -477,38 +691,39 @@ __global__ void split_psi_kernel(const double* __restrict__ psi, const PsiBlock*
       const double x = (i < p.m && c < p.n) ? psi[off + (long long)i * p.n + c] : 0.0;
       __nv_bfloat16 h, m, l;
       split3(x, h, m, l);
-      const long long d = p.tile * 64 + e;
-      s0[d] = h;
-      s1[d] = m;
-      s2[d] = l;
+      const long long d = (p.tile + t) * 192 + w;
+      out[d] = h;
+      out[d + 64] = m;
+      out[d + 128] = l;
     }
   }
 }
 
-void launch_split_ops(const double* store, const SplitJob* jobs, long long njobs, void* const slices[3],
-                      cudaStream_t st) {
+void launch_split_ops(const double* store, const SplitJob* jobs, long long njobs, void* out, cudaStream_t st) {
   if (njobs <= 0) return;
   long long grid = njobs < (1ll << 20) ? njobs : (1ll << 20);
-  split_ops_kernel<<<(unsigned)grid, 256, 0, st>>>(store, jobs, njobs, (__nv_bfloat16*)slices[0],
-                                                   (__nv_bfloat16*)slices[1], (__nv_bfloat16*)slices[2]);
+  split_ops_kernel<<<(unsigned)grid, 256, 0, st>>>(store, jobs, njobs, (__nv_bfloat16*)out);
 }
 
-void launch_split_psi(const double* psi, const PsiBlock* blocks, const TcPsiBlock* pb, int nblk,
-                      void* const slices[3], cudaStream_t st) {
+void launch_split_psi(const double* psi, const PsiBlock* blocks, const TcPsiBlock* pb, int nblk, void* out,
+                      cudaStream_t st) {
   if (nblk <= 0) return;
-  split_psi_kernel<<<nblk, 256, 0, st>>>(psi, blocks, pb, nblk, (__nv_bfloat16*)slices[0],
-                                         (__nv_bfloat16*)slices[1], (__nv_bfloat16*)slices[2]);
+  split_psi_kernel<<<nblk, 256, 0, st>>>(psi, blocks, pb, nblk, (__nv_bfloat16*)out);
 }
 
 void launch_sigma_tc(const TcDev& a, int n_sm, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(sigma_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaFuncSetAttribute(sigma_tc_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaFuncSetAttribute(sigma_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     attr = true;
   }
   int grid = n_sm < a.n_items ? n_sm : a.n_items;
   if (grid < 1) grid = 1;
-  sigma_tc_kernel<<<grid, NTHR, SMEM_BYTES, st>>>(a);
+  if (a.nprod == 6)
+    sigma_tc_kernel<6><<<grid, NTHR, SMEM_BYTES, st>>>(a);
+  else
+    sigma_tc_kernel<3><<<grid, NTHR, SMEM_BYTES, st>>>(a);
 }
 
 }  // namespace dmrg

@@ -2,12 +2,14 @@
 the CPU oracle and against the FP64 GPU path, through the C ABI.
 
 Tolerances follow from the arithmetic. BF16X3 represents every operand to
-24 significant bits and drops slice products below 2^-24 relative; products
-accumulate in FP32 over at most 128 x 16 terms per output tile per task and
-over at most 32 tasks per partial, then in FP64. The error of one output is
-a few units of 2^-24 times the sum of magnitudes entering it, which for these
-random operators stays below 2e-6 of max|sigma|: bar 2e-5. BF16X2 keeps 16
-bits (2^-17 representation error, dropped products ~2^-16): bar 2e-3.
+24 significant bits and drops slice products below 2^-24 relative, so the
+products themselves are good to a few 2^-24. The tensor cores accumulate in
+FP32: an output element of one segment (at most 32 tasks, then added in
+FP64) receives n ~ 6 x K x 32 rounded additions (K up to 355 here), so its
+rounding error is about 2^-24 sqrt(n) ~ 3e-6 of the magnitudes entering it,
+with a tail up to ~10x that over 1e5-1e6 outputs: bar 5e-5 of max|sigma|.
+BF16X2 keeps 16 bits (2^-17 representation error, dropped products ~2^-16):
+bar 2e-3.
 """
 
 import numpy as np
@@ -15,7 +17,7 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
-TOL = {1: 2e-3, 2: 2e-5}
+TOL = {1: 2e-3, 2: 5e-5}
 
 
 @pytest.fixture(scope="module")
