@@ -146,6 +146,29 @@ dmrg_status dmrg_get_sigma_info(dmrg_ctx* ctx, int site, dmrg_sigma_info* info);
 dmrg_status dmrg_sigma(dmrg_ctx* ctx, int site, const double* psi, double* sigma);
 
 /*
+ * Allocation-free FP64 sigma, for callers that cannot allocate device memory
+ * when they need a sigma (a serving process whose HBM is fully reserved up
+ * front, or a loop that must not call cudaMalloc/cudaFree because those calls
+ * can block on or synchronize with other work on the device). The paper has
+ * no counterpart: this is a deployment variant of dmrg_sigma.
+ * Computes the same FP64 sigma as dmrg_sigma (same kernel and work list,
+ * whatever the context's precision setting) but keeps the kernel's scratch
+ * (partial output tiles and a work counter) in fixed-size arrays compiled
+ * into the library instead of context-owned buffers; the call allocates
+ * nothing. psi and sigma must be device pointers on the context's device
+ * (DMRG_EINVAL for host pointers, which would need staging buffers).
+ * Limits and sharing: the scratch holds at most 4,194,304 doubles (32 MiB);
+ * a problem needing more is rejected with DMRG_EINVAL (use dmrg_sigma).
+ * Every GPU that loads the library keeps these arrays until the process
+ * exits, and all calls on a device share them: calls that overlap on the
+ * GPU (other streams or contexts on the same device) race and must not be
+ * issued. The first call on a device looks up the arrays' device addresses
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * The call is stream-ordered on dmrg_stream(ctx) and does not synchronize.
+ */
+dmrg_status dmrg_sigma_noalloc(dmrg_ctx* ctx, int site, const double* psi, double* sigma);
+
+/*
  * Lowest eigenpair of H_eff at bond `site` by Davidson (Appendix A solving
  * step; details: diagonal preconditioner clamped at 1e-8, thick restart
  * from the two lowest Ritz vectors, converged when ||H x - E x||_2^2 < tol).

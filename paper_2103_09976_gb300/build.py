@@ -22,6 +22,7 @@ SOURCES = [
     "generate.cu",
     "sigma_f64.cu",
     "sigma_tc.cu",
+    "sigma_noalloc.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

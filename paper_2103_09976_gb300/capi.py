@@ -53,6 +53,7 @@ SIGNATURES = {
     "dmrg_psi_layout": (_I, [_P, _I, ctypes.POINTER(_I), _P, _P, _P, _P, ctypes.POINTER(_LL)]),
     "dmrg_get_sigma_info": (_I, [_P, _I, ctypes.POINTER(dmrg_sigma_info)]),
     "dmrg_sigma": (_I, [_P, _I, _P, _P]),
+    "dmrg_sigma_noalloc": (_I, [_P, _I, _P, _P]),
     "dmrg_davidson": (_I, [_P, _I, _P, _D, ctypes.POINTER(_D), _P, ctypes.POINTER(_I)]),
     "dmrg_build_blocks": (_I, [_P, _P, _P, _I, _I, _I, _I]),
     "dmrg_sweep": (_I, [_P, _P, _I, _D, _P, _P]),
@@ -172,6 +173,12 @@ def dmrg_get_sigma_info(ctx, site=-1):
 
 def dmrg_sigma(ctx, site, psi, sigma):
     _check(ctx, lib().dmrg_sigma(ctx, site, _ptr(psi), _ptr(sigma)))
+
+
+def dmrg_sigma_noalloc(ctx, site, psi, sigma):
+    """FP64 sigma with the library's fixed 32 MiB device scratch (no allocation;
+    device pointers only; calls on one device must not overlap)."""
+    _check(ctx, lib().dmrg_sigma_noalloc(ctx, site, _ptr(psi), _ptr(sigma)))
 
 
 def dmrg_davidson(ctx, site, psi0, tol, psi_out=None):

@@ -455,6 +455,11 @@ dmrg_status dmrg_sigma(dmrg_ctx* ctx, int site, const double* psi, double* sigma
   });
 }
 
+dmrg_status dmrg_sigma_noalloc(dmrg_ctx* ctx, int site, const double* psi, double* sigma) {
+  if (!ctx) return DMRG_EINVAL;
+  return guarded(ctx, [&] { sigma_noalloc(ctx->c, need_problem(ctx->c, site), psi, sigma); });
+}
+
 dmrg_status dmrg_davidson(dmrg_ctx* ctx, int site, const double* psi0, double tol, double* energy,
                           double* psi_out, int* iters) {
   if (!ctx) return DMRG_EINVAL;

@@ -117,6 +117,7 @@ struct Context {
 void prepare_worklist(Context& c, Problem& p);
 void prepare_tc(Context& c, Problem& p);
 void check_device_error(Context& c, Problem& p);
+void sigma_noalloc(Context& c, Problem& p, const double* psi, double* sigma);
 void run_sigma(Context& c, Problem& p, const double* d_psi, double* d_sigma);
 
 }  // namespace dmrg
