@@ -53,9 +53,9 @@ def davidson(matvec, diag, x0, tol=1e-10, max_space=24, max_iter=200):
             x2 = Y[:, 1] @ Vm
             Ax2 = Y[:, 1] @ AVm
             V, AV = [x, x2], [Ax, Ax2]
-        for _ in range(2):
-            for v in V:
-                t = t - (v @ t) * v
+        Vm = np.array(V)
+        for _ in range(2):  # classical Gram-Schmidt, twice
+            t = t - (Vm @ t) @ Vm
         nt = np.linalg.norm(t)
         if nt < 1e-14:
             return theta, x, nmv, rr < tol
