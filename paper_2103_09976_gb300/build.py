@@ -23,6 +23,8 @@ SOURCES = [
     "sigma_f64.cu",
     "sigma_tc.cu",
     "sigma_noalloc.cu",
+    "davidson.cu",
+    "davidson_host.cpp",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -463,7 +463,33 @@ dmrg_status dmrg_sigma_noalloc(dmrg_ctx* ctx, int site, const double* psi, doubl
 dmrg_status dmrg_davidson(dmrg_ctx* ctx, int site, const double* psi0, double tol, double* energy,
                           double* psi_out, int* iters) {
   if (!ctx) return DMRG_EINVAL;
-  return guarded(ctx, [&] { throw Error(DMRG_ESTATE, "dmrg_davidson: not available yet"); });
+  return guarded(ctx, [&] {
+    Context& c = ctx->c;
+    DMRG_CUDA(cudaSetDevice(c.device));
+    Problem& p = need_problem(c, site);
+    if (!energy || !iters) throw Error(DMRG_EINVAL, "energy and iters must not be NULL");
+    if (!(tol > 0.0)) throw Error(DMRG_EINVAL, "tol must be positive");
+    if (c.opts.dav_max_space > 32) throw Error(DMRG_EINVAL, "dav_max_space must be <= 32");
+    const size_t bytes = (size_t)p.psi_size * sizeof(double);
+    const double* x0 = psi0;
+    if (psi0 && !is_device_ptr(psi0)) {
+      c.d_psi.alloc(bytes);
+      DMRG_CUDA(cudaMemcpyAsync(c.d_psi.p, psi0, bytes, cudaMemcpyHostToDevice, c.stream));
+      x0 = c.d_psi.as<double>();
+    }
+    double* xo = psi_out;
+    const bool host_out = psi_out && !is_device_ptr(psi_out);
+    if (host_out) {
+      c.d_sigma.alloc(bytes);
+      xo = c.d_sigma.as<double>();
+    }
+    const bool conv = run_davidson(c, p, x0, tol, energy, xo, iters, 0ull);
+    if (host_out) {
+      DMRG_CUDA(cudaMemcpyAsync(psi_out, xo, bytes, cudaMemcpyDeviceToHost, c.stream));
+      DMRG_CUDA(cudaStreamSynchronize(c.stream));
+    }
+    if (!conv) throw Error(DMRG_ENOCONV, "Davidson reached dav_max_iter before the residual tolerance");
+  });
 }
 
 dmrg_status dmrg_build_blocks(dmrg_ctx* ctx, const double* t, const double* v, int K, int N,

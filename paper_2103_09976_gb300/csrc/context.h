@@ -68,6 +68,11 @@ struct Problem {
   // tensor-core path (built on first mixed-precision sigma)
   TcPlan tc;
   bool tc_ready = false;
+  // Davidson workspace (built on first use)
+  bool dav_ready = false;
+  int dav_space = 0;
+  DevBuf dav_V, dav_AV, dav_diag, dav_x, dav_ax, dav_r, dav_t, dav_partial, dav_H, dav_w, dav_Y, dav_s;
+  DevBuf d_dstart, d_dtask;
   DevBuf split, psi_split;         // slice-interleaved bf16 tiles of the operators / of psi
   DevBuf d_tc_recs, d_tc_item_rec, d_tc_items, d_tc_groups, d_tc_sched, d_tc_pblk, d_tc_scratch, d_err;
 };
@@ -118,6 +123,10 @@ void prepare_worklist(Context& c, Problem& p);
 void prepare_tc(Context& c, Problem& p);
 void check_device_error(Context& c, Problem& p);
 void sigma_noalloc(Context& c, Problem& p, const double* psi, double* sigma);
+// Davidson on the device: x0 (device, may be null = seeded random) -> energy,
+// eigenvector in x_out (device, may be null). Returns false if not converged.
+bool run_davidson(Context& c, Problem& p, const double* x0, double tol, double* energy, double* x_out,
+                  int* iters, unsigned long long guess_counter_base);
 void run_sigma(Context& c, Problem& p, const double* d_psi, double* d_sigma);
 
 }  // namespace dmrg

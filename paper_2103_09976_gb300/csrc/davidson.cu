@@ -1,0 +1,234 @@
+// Davidson eigensolver on the device (FP64 control path).
+//
+// Appendix A (solving step, Eq. eff-eigsh) names the Davidson method. The
+// steps here: projected matrix V^T H V, its eigenpairs (one-warp cyclic
+// Jacobi), Ritz vector and residual, diagonal preconditioner clamped at
+// 1e-8, classical Gram-Schmidt twice, thick restart from the two lowest Ritz
+// vectors. Only two scalars per iteration (Ritz value, squared residual
+// norm) and the new direction's norm cross to the host. All reductions are
+// two-stage with a fixed order, so results are deterministic.
+#include "kernels.h"
+
+namespace dmrg {
+
+namespace {
+
+constexpr int RED_BLOCKS = 256;   // partial sums per dot product
+constexpr int RED_THREADS = 256;
+
+// partial[i * RED_BLOCKS + b] = sum over block b's elements of V[i][e] * w[e]
+__global__ void dots_partial(const double* __restrict__ V, long long ld, int k, const double* __restrict__ w,
+                             long long n, double* __restrict__ partial) {
+  __shared__ double red[RED_THREADS];
+  for (int i = 0; i < k; ++i) {
+    double s = 0.0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+      s = fma(V[i * ld + e], w[e], s);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+      if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[i * RED_BLOCKS + blockIdx.x] = red[0];
+    __syncthreads();
+  }
+}
+
+// out[i * out_stride] = sum_b partial[i * RED_BLOCKS + b] (fixed order)
+__global__ void dots_final(const double* __restrict__ partial, int k, double* __restrict__ out, int out_stride) {
+  __shared__ double red[RED_BLOCKS];
+  for (int i = 0; i < k; ++i) {
+    red[threadIdx.x] = partial[i * RED_BLOCKS + threadIdx.x];
+    __syncthreads();
+    for (int h = RED_BLOCKS / 2; h > 0; h >>= 1) {
+      if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[(long long)i * out_stride] = red[0];
+    __syncthreads();
+  }
+}
+
+// out = sum_i c[i*cs] V[i] (+ beta * out when add)
+__global__ void lincomb_kernel(const double* __restrict__ V, long long ld, int k, const double* __restrict__ c,
+                               int cs, double sign, double* __restrict__ out, long long n, int add) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int i = 0; i < k; ++i) s = fma(c[i * cs], V[i * ld + e], s);
+    out[e] = add ? out[e] + sign * s : sign * s;
+  }
+}
+
+// r = ax - theta x; t = r / clamp(theta - diag)
+__global__ void residual_precond(const double* __restrict__ x, const double* __restrict__ ax,
+                                 const double* __restrict__ diag, const double* __restrict__ theta,
+                                 double* __restrict__ r, double* __restrict__ t, long long n) {
+  const double th = *theta;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const double re = ax[e] - th * x[e];
+    r[e] = re;
+    double den = th - diag[e];
+    if (fabs(den) < 1e-8) den = den < 0.0 ? -1e-8 : 1e-8;
+    t[e] = re / den;
+  }
+}
+
+__global__ void scale_kernel(double* __restrict__ x, const double* __restrict__ nrm2, long long n) {
+  const double s = 1.0 / sqrt(*nrm2);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    x[e] *= s;
+}
+
+// Eigenpairs of the symmetric part of the k x k matrix H (row-major, leading
+// dimension ldh) by cyclic Jacobi rotations; w ascending, Y columns = vectors
+// (Y row-major k x ldh). One warp; lane r owns row/column r.
+__global__ void jacobi_eigh(const double* __restrict__ H, int k, int ldh, double* __restrict__ w,
+                            double* __restrict__ Y) {
+  __shared__ double A[32][33];
+  __shared__ double Q[32][33];
+  const int r = threadIdx.x;
+  for (int c = 0; c < k; ++c)
+    if (r < k) {
+      A[r][c] = 0.5 * (H[r * ldh + c] + H[c * ldh + r]);
+      Q[r][c] = (r == c) ? 1.0 : 0.0;
+    }
+  __syncwarp();
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    if (r < k)
+      for (int c = 0; c < k; ++c) {
+        tot += A[r][c] * A[r][c];
+        if (c != r) off += A[r][c] * A[r][c];
+      }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    if (off <= 1e-30 * tot || off == 0.0) break;
+    for (int p = 0; p < k - 1; ++p)
+      for (int q = p + 1; q < k; ++q) {
+        const double apq = A[p][q];
+        if (apq == 0.0) continue;
+        const double app = A[p][p], aqq = A[q][q];
+        const double th = (aqq - app) / (2.0 * apq);
+        const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+        __syncwarp();
+        if (r < k && r != p && r != q) {
+          const double arp = A[r][p], arq = A[r][q];
+          A[r][p] = cs * arp - sn * arq;
+          A[r][q] = sn * arp + cs * arq;
+        }
+        if (r < k) {
+          const double qp = Q[r][p], qq = Q[r][q];
+          Q[r][p] = cs * qp - sn * qq;
+          Q[r][q] = sn * qp + cs * qq;
+        }
+        __syncwarp();
+        if (r < k && r != p && r != q) {
+          A[p][r] = A[r][p];
+          A[q][r] = A[r][q];
+        }
+        if (r == 0) {
+          A[p][p] = app - t * apq;
+          A[q][q] = aqq + t * apq;
+          A[p][q] = 0.0;
+          A[q][p] = 0.0;
+        }
+        __syncwarp();
+      }
+  }
+  // sort ascending (selection sort on lane 0, columns of Q follow)
+  if (r == 0) {
+    int idx[32];
+    for (int i = 0; i < k; ++i) idx[i] = i;
+    for (int i = 0; i < k; ++i) {
+      int m = i;
+      for (int j = i + 1; j < k; ++j)
+        if (A[idx[j]][idx[j]] < A[idx[m]][idx[m]]) m = j;
+      const int tmp = idx[i];
+      idx[i] = idx[m];
+      idx[m] = tmp;
+    }
+    for (int i = 0; i < k; ++i) {
+      w[i] = A[idx[i]][idx[i]];
+      for (int rr = 0; rr < k; ++rr) Y[rr * ldh + i] = Q[rr][idx[i]];
+    }
+  }
+}
+
+}  // namespace
+
+void dav_dots(const double* V, long long ld, int k, const double* w, long long n, double* partial, double* out,
+              int out_stride, cudaStream_t st) {
+  if (k <= 0) return;
+  dots_partial<<<RED_BLOCKS, RED_THREADS, 0, st>>>(V, ld, k, w, n, partial);
+  dots_final<<<1, RED_BLOCKS, 0, st>>>(partial, k, out, out_stride);
+}
+
+void dav_lincomb(const double* V, long long ld, int k, const double* c, int cs, double sign, double* out,
+                 long long n, bool add, cudaStream_t st) {
+  long long grid = (n + 255) / 256;
+  if (grid > 152 * 8) grid = 152 * 8;
+  if (grid < 1) grid = 1;
+  lincomb_kernel<<<(unsigned)grid, 256, 0, st>>>(V, ld, k, c, cs, sign, out, n, add ? 1 : 0);
+}
+
+void dav_residual(const double* x, const double* ax, const double* diag, const double* theta, double* r,
+                  double* t, long long n, cudaStream_t st) {
+  long long grid = (n + 255) / 256;
+  if (grid > 152 * 8) grid = 152 * 8;
+  if (grid < 1) grid = 1;
+  residual_precond<<<(unsigned)grid, 256, 0, st>>>(x, ax, diag, theta, r, t, n);
+}
+
+void dav_scale(double* x, const double* nrm2, long long n, cudaStream_t st) {
+  long long grid = (n + 255) / 256;
+  if (grid > 152 * 8) grid = 152 * 8;
+  if (grid < 1) grid = 1;
+  scale_kernel<<<(unsigned)grid, 256, 0, st>>>(x, nrm2, n);
+}
+
+void dav_eigh(const double* H, int k, int ldh, double* w, double* Y, cudaStream_t st) {
+  jacobi_eigh<<<1, 32, 0, st>>>(H, k, ldh, w, Y);
+}
+
+}  // namespace dmrg
+
+namespace dmrg {
+
+namespace {
+
+// diag[b][i, j] = sum over the diagonal tasks of block b of
+// scale * X_L[i, i] * X_R[j, j] (identity factors contribute 1)
+__global__ void heff_diag_kernel(const double* __restrict__ store, const Task* __restrict__ tasks,
+                                 const int* __restrict__ dstart, const int* __restrict__ dtask,
+                                 const PsiBlock* __restrict__ blocks, int nblk, double* __restrict__ diag) {
+  for (int b = blockIdx.y; b < nblk; b += gridDim.y) {
+    const PsiBlock pb = blocks[b];
+    const long long ne = (long long)pb.mL * pb.mR;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x) {
+      const int i = (int)(e / pb.mR), j = (int)(e % pb.mR);
+      double s = 0.0;
+      for (int q = dstart[b]; q < dstart[b + 1]; ++q) {
+        const Task t = tasks[dtask[q]];
+        const double dl = t.aoff < 0 ? 1.0 : store[t.aoff + (long long)i * (pb.mL + 1)];
+        const double dr = t.boff < 0 ? 1.0 : store[t.boff + (long long)j * (pb.mR + 1)];
+        s = fma(t.scale * dl, dr, s);
+      }
+      diag[pb.off + e] = s;
+    }
+  }
+}
+
+}  // namespace
+
+void launch_heff_diag(const double* store, const Task* tasks, const int* dstart, const int* dtask,
+                      const PsiBlock* blocks, int nblk, double* diag, cudaStream_t st) {
+  if (nblk <= 0) return;
+  dim3 grid(64, nblk < 65535 ? nblk : 65535);
+  heff_diag_kernel<<<grid, 256, 0, st>>>(store, tasks, dstart, dtask, blocks, nblk, diag);
+}
+
+}  // namespace dmrg

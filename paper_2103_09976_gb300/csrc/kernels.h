@@ -72,4 +72,23 @@ void launch_split_psi(const double* psi, const PsiBlock* blocks, const TcPsiBloc
                       cudaStream_t st);
 void launch_sigma_tc(const TcDev& a, int n_sm, cudaStream_t st);
 
+// ---------------------------------------------------------------- Davidson
+// out[i*out_stride] = V[i] . w for i < k (V rows of length n, leading dim ld);
+// partial: k * 256 doubles of workspace. Fixed-order two-stage reduction.
+void dav_dots(const double* V, long long ld, int k, const double* w, long long n, double* partial, double* out,
+              int out_stride, cudaStream_t st);
+// out = sign * sum_i c[i*cs] V[i]  (or out += ... when add)
+void dav_lincomb(const double* V, long long ld, int k, const double* c, int cs, double sign, double* out,
+                 long long n, bool add, cudaStream_t st);
+// r = ax - theta x; t = r / (theta - diag) with |denominator| clamped at 1e-8
+void dav_residual(const double* x, const double* ax, const double* diag, const double* theta, double* r,
+                  double* t, long long n, cudaStream_t st);
+// x /= sqrt(*nrm2)
+void dav_scale(double* x, const double* nrm2, long long n, cudaStream_t st);
+// eigenpairs (ascending) of the symmetric part of a k x k matrix, k <= 32
+void dav_eigh(const double* H, int k, int ldh, double* w, double* Y, cudaStream_t st);
+// diagonal of H_eff from the diagonal tasks (output block = input block)
+void launch_heff_diag(const double* store, const Task* tasks, const int* dstart, const int* dtask,
+                      const PsiBlock* blocks, int nblk, double* diag, cudaStream_t st);
+
 }  // namespace dmrg
