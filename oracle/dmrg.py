@@ -58,8 +58,12 @@ def largest_remainder(total, weights):
 
 
 def orthonormal_columns(G):
+    """Orthonormal basis of the columns of G in Gram-Schmidt orientation:
+    the unique thin QR with a positive diagonal of R, so the basis (and every
+    block built on it) is a function of G alone, not of the QR routine."""
     Q, R = np.linalg.qr(G)
-    return Q
+    sgn = np.where(np.diag(R) < 0.0, -1.0, 1.0)
+    return Q * sgn
 
 
 class PlainDMRG:
@@ -72,6 +76,8 @@ class PlainDMRG:
         self.dav = dict(tol=dav_tol, max_space=dav_max_space, max_iter=dav_max_iter)
         self.L = {}
         self.R = {}
+        self.UL = {}  # i -> {sector of L[i-1] x site: kept columns}, for inspection
+        self.UR = {}  # j -> {sector of site x R[j+1]: kept columns}
         self.log = []
 
     # ------------------------------------------------------ initial blocks
@@ -97,6 +103,7 @@ class PlainDMRG:
             nb = Basis(secs)
             ops = {k: transform(e.assemble(E, chunks), U, nb) for k, e in enl.items()}
             self.R[j] = (nb, ops)
+            self.UR[j] = U
         self.L[0] = vacuum_left(self.ints)
 
     # ------------------------------------------------------------- a step
@@ -142,6 +149,7 @@ class PlainDMRG:
             U = {qL: svd[qL][0][:, :m] for qL, m in kept.items()}
             nb = Basis(list(kept.items()))
             self.L[i + 1] = (nb, {k: transform(o, U, nb) for k, o in oL.items()})
+            self.UL[i + 1] = U
         else:
             V, secs = {}, []
             for qL, m in kept.items():
@@ -150,6 +158,7 @@ class PlainDMRG:
                 secs.append((qR, m))
             nb = Basis(secs)
             self.R[i + 1] = (nb, {k: transform(o, V, nb) for k, o in oR.items()})
+            self.UR[i + 1] = V
         self.log.append(dict(i=i, forward=forward, M=M, energy=th, nmv=nmv,
                              converged=conv, discarded=disc, dim=len(x)))
         return th, disc
