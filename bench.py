@@ -242,10 +242,51 @@ def main():
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
     ok = bool(np.allclose(yp.numpy(), y.cpu().numpy(), rtol=0, atol=1e-12 * float(y.abs().max())))
 
+    # tensor-core sigma (bf16 slices) on the same context and psi
+    flops = info["flops"]
+    mixed = {}
+    y64 = y.clone()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        peaks = {}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    for name, prec, nprod, bytes_per_elem in (("bf16x3", capi.DMRG_BF16X3, 6, 6), ("bf16x2", capi.DMRG_BF16X2, 3, 6)):
+        capi.dmrg_set_precision(ctx, prec)
+        capi.dmrg_sigma(ctx, -1, x, y)  # builds the bf16 operator slices
+        capi.dmrg_sync(ctx)
+        for _ in range(max(3, args.warmup)):
+            capi.dmrg_sigma(ctx, -1, x, y)
+        capi.dmrg_sync(ctx)
+        capi.dmrg_profile(ctx, True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            capi.dmrg_sigma(ctx, -1, x, y)
+        e1.record(stream)
+        e1.synchronize()
+        capi.dmrg_sync(ctx)
+        tms, tn = capi.dmrg_profile_read(ctx, capi.KERNEL_SIGMA)
+        capi.dmrg_profile(ctx, False)
+        step = e0.elapsed_time(e1) / 1e3 / args.steps
+        kern = tms / 1e3 / max(1, tn)
+        d = (y - y64).abs().max().item() / y64.abs().max().item()
+        rq = abs(float(x @ y) - float(x @ y64)) / abs(float(x @ y64))
+        # algorithmic bytes: every stored operator element once (6 B as three
+        # bf16 slices) + psi read + sigma written (FP64)
+        alg_bytes = info["op_elements"] * bytes_per_elem + 16.0 * n
+        mixed[name] = {"value": flops / step / 1e12, "unit": "TFLOP/s", "ms_per_step": step * 1e3,
+                       "kernel_ms": kern * 1e3, "rel_err_vs_fp64_maxnorm": d, "rayleigh_rel_err_vs_fp64": rq,
+                       "roofline": {"bound": "hbm", "achieved": alg_bytes / kern / 1e9, "peak": hbm,
+                                    "unit": "GB/s", "frac": alg_bytes / kern / 1e9 / hbm, "traffic": None,
+                                    "kernel": "sigma_tc_kernel", "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                                    "tensor_tflops_issued": nprod * flops / kern / 1e12,
+                                    "tensor_frac_of_bf16_peak": nprod * flops / kern / 1e12 / bf16}}
+    capi.dmrg_set_precision(ctx, capi.DMRG_FP64)
     peak64 = fp64_gemm_peak(torch)
     capi.dmrg_destroy(ctx)
 
-    flops = info["flops"]
     kern_s = k_ms / 1e3 / max(1, k_n)
     achieved = flops / kern_s / 1e12
     value = world * flops / step_s / 1e12
@@ -261,6 +302,7 @@ def main():
            "e2e": {"value": flops / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 8 * n,
                    "d2h_bytes_per_step": 8 * n, "matches_device_result": ok},
            "gpu_launches": 2 * args.steps,
+           "mixed": mixed,
            "clocks": clocks,
            "sigma_info": info}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

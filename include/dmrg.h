@@ -199,6 +199,39 @@ dmrg_status dmrg_sweep(dmrg_ctx* ctx, const int* M_schedule, int n_sweeps, doubl
                        double* energies, double* max_discard);
 
 /*
+ * Renormalized block operators (Eq. op-trans results) held by the context
+ * after dmrg_build_blocks / dmrg_sweep, for inspection and checkpointing.
+ * side 0 = left block L[j] (spin orbitals [0, 2j)), side 1 = right block
+ * R[j] (spin orbitals [2j, 2K)). Operators are numbered in the canonical NC
+ * order with nL = 2j: left kind H, a+_p (p < nL), R^L_p (p >= nL), A_pr
+ * (p < r < nL, row-major pairs), B_pq (p <= q < nL); right kind H, a_p
+ * (p >= nL), R^R_p (p < nL), P_pr, Q_pq (same pair order).
+ * dmrg_block_info: *n_sectors, and when q / dims are not NULL the sectors'
+ * (N, 2Sz) pairs (2 ints each) and dimensions in ascending order; *n_ops.
+ * dmrg_block_read: operator `op` as a dense row-major total x total matrix
+ * (total = sum of dims) over that basis, written to host memory `dense`.
+ * DMRG_ESTATE when the block does not exist, DMRG_EINVAL for bad indices.
+ */
+dmrg_status dmrg_block_info(dmrg_ctx* ctx, int side, int j, int* n_sectors, int* q, int* dims, int* n_ops);
+dmrg_status dmrg_block_read(dmrg_ctx* ctx, int side, int j, int op, double* dense);
+
+/*
+ * Per-step record of the most recent dmrg_sweep call, one entry per
+ * two-site step (Appendix A steps i-iv) in execution order: sweep index,
+ * bond `site` (sites site, site+1), direction (1 = forward), psi size of the
+ * step, Davidson sigma calls and convergence flag, lowest energy, number of
+ * states kept and discarded weight (sum of the squared singular values not
+ * kept). Fills min(max_steps, available) entries of `out` (host memory,
+ * may be NULL with max_steps 0) and sets *n_steps to the number available.
+ */
+typedef struct dmrg_step_log {
+  int sweep, site, forward, iters, converged, kept;
+  long long psi_size;
+  double energy, discarded;
+} dmrg_step_log;
+dmrg_status dmrg_sweep_log(dmrg_ctx* ctx, dmrg_step_log* out, int max_steps, int* n_steps);
+
+/*
  * Per-kernel timing with CUDA events recorded on the context's stream
  * around each launch of the library's kernels (tracing aid; off by default).
  * dmrg_profile(ctx, 1) clears the counters and starts recording; 0 stops.

@@ -25,6 +25,8 @@ SOURCES = [
     "sigma_noalloc.cu",
     "davidson.cu",
     "davidson_host.cpp",
+    "blocking.cu",
+    "sweep.cpp",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -57,6 +57,9 @@ SIGNATURES = {
     "dmrg_davidson": (_I, [_P, _I, _P, _D, ctypes.POINTER(_D), _P, ctypes.POINTER(_I)]),
     "dmrg_build_blocks": (_I, [_P, _P, _P, _I, _I, _I, _I]),
     "dmrg_sweep": (_I, [_P, _P, _I, _D, _P, _P]),
+    "dmrg_sweep_log": (_I, [_P, _P, _I, _P]),
+    "dmrg_block_info": (_I, [_P, _I, _I, _P, _P, _P, _P]),
+    "dmrg_block_read": (_I, [_P, _I, _I, _I, _P]),
     "dmrg_sync": (_I, [_P]),
     "dmrg_profile": (_I, [_P, _I]),
     "dmrg_profile_read": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_LL)]),
@@ -203,6 +206,41 @@ def dmrg_sweep(ctx, M_schedule, tol):
     d = np.zeros(len(Ms))
     _check(ctx, lib().dmrg_sweep(ctx, _ptr(Ms), len(Ms), float(tol), _ptr(e), _ptr(d)))
     return e, d
+
+
+def dmrg_block_info(ctx, side, j):
+    """Returns (sectors as an (n, 2) int array, dims, number of operators)."""
+    ns, nops = ctypes.c_int(), ctypes.c_int()
+    _check(ctx, lib().dmrg_block_info(ctx, side, j, ctypes.byref(ns), None, None, ctypes.byref(nops)))
+    q = np.zeros((ns.value, 2), dtype=np.int32)
+    d = np.zeros(ns.value, dtype=np.int32)
+    _check(ctx, lib().dmrg_block_info(ctx, side, j, ctypes.byref(ns), _ptr(q), _ptr(d), ctypes.byref(nops)))
+    return q, d, nops.value
+
+
+def dmrg_block_read(ctx, side, j, op):
+    """Dense matrix of operator `op` of block (side, j) over its basis."""
+    _, d, _ = dmrg_block_info(ctx, side, j)
+    tot = int(d.sum())
+    out = np.zeros((tot, tot))
+    _check(ctx, lib().dmrg_block_read(ctx, side, j, op, _ptr(out)))
+    return out
+
+
+class dmrg_step_log(ctypes.Structure):
+    _fields_ = [("sweep", ctypes.c_int), ("site", ctypes.c_int), ("forward", ctypes.c_int),
+                ("iters", ctypes.c_int), ("converged", ctypes.c_int), ("kept", ctypes.c_int),
+                ("psi_size", ctypes.c_longlong), ("energy", ctypes.c_double),
+                ("discarded", ctypes.c_double)]
+
+
+def dmrg_sweep_log(ctx):
+    """Per-step records of the last dmrg_sweep call, as a list of dicts."""
+    n = ctypes.c_int()
+    _check(ctx, lib().dmrg_sweep_log(ctx, None, 0, ctypes.byref(n)))
+    buf = (dmrg_step_log * max(1, n.value))()
+    _check(ctx, lib().dmrg_sweep_log(ctx, buf, n.value, ctypes.byref(n)))
+    return [{f: getattr(buf[k], f) for f, _ in dmrg_step_log._fields_} for k in range(n.value)]
 
 
 KERNEL_SIGMA, KERNEL_REDUCE, KERNEL_DAVIDSON, KERNEL_BLOCKING = 0, 1, 2, 3

@@ -1,0 +1,254 @@
+// Sweep kernels: blocking (Eq. blocked-ops), decimation (per-sector Gram
+// matrix and Jacobi eigensolver), orthonormal bases for the initial MPS.
+// The transformation of Eq. op-trans runs on the FP64 sigma kernel with a
+// dedicated work list (see sweep.cpp).
+#include "kernels.h"
+
+namespace dmrg {
+
+namespace {
+
+// One destination block per CTA: zero it, then apply its jobs in order
+// (dst[i, j] += coef * src(i, j)), so the sum is deterministic.
+__global__ void blocking_kernel(double* __restrict__ dst_store, const double* __restrict__ src_store,
+                                const BlockJob* __restrict__ jobs, const DstBlock* __restrict__ dsts, int ndst) {
+  for (int d = blockIdx.x; d < ndst; d += gridDim.x) {
+    const DstBlock db = dsts[d];
+    double* dst = dst_store + db.off;
+    for (long long e = threadIdx.x; e < db.n; e += blockDim.x) dst[e] = 0.0;
+    __syncthreads();
+    for (int q = db.j0; q < db.j1; ++q) {
+      const BlockJob jb = jobs[q];
+      const long long ne = (long long)jb.rows * jb.cols;
+      for (long long e = threadIdx.x; e < ne; e += blockDim.x) {
+        const int i = (int)(e / jb.cols), j = (int)(e % jb.cols);
+        double v;
+        if (jb.src < 0) v = (i == j) ? 1.0 : 0.0;
+        else v = jb.trans ? src_store[jb.src + (long long)j * jb.src_ld + i] : src_store[jb.src + (long long)i * jb.src_ld + j];
+        dst[(long long)(jb.r0 + i) * db.ld + jb.c0 + j] += jb.coef * v;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// G[b] = X_b X_b^T (rows) or X_b^T X_b (cols) for every block b of psi.
+__global__ void gram_kernel(const double* __restrict__ psi, const GramBlock* __restrict__ gb, int nb,
+                            double* __restrict__ G, int left) {
+  for (int b = blockIdx.y; b < nb; b += gridDim.y) {
+    const GramBlock g = gb[b];
+    const long long ne = (long long)g.d * g.d;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x) {
+      const int i = (int)(e / g.d), j = (int)(e % g.d);
+      double s = 0.0;
+      if (left)
+        for (int k = 0; k < g.m; ++k) s = fma(psi[g.psi_off + (long long)i * g.m + k], psi[g.psi_off + (long long)j * g.m + k], s);
+      else
+        for (int k = 0; k < g.m; ++k) s = fma(psi[g.psi_off + (long long)k * g.d + i], psi[g.psi_off + (long long)k * g.d + j], s);
+      G[g.g_off + e] = s;
+    }
+  }
+}
+
+// Symmetric eigenproblem of each d x d matrix A (row-major, in place) by
+// cyclic Jacobi in round-robin order: each round rotates d/2 disjoint index
+// pairs at once. Q receives the eigenvectors (columns), w the eigenvalues,
+// both sorted by descending eigenvalue (ties by index).
+__global__ void jacobi_blocks_kernel(double* __restrict__ Aall, double* __restrict__ Qall, double* __restrict__ wall,
+                                     const GramBlock* __restrict__ gb, int nb, int max_sweeps) {
+  __shared__ double cs[512], sn[512];
+  __shared__ int pp[512], qq[512];
+  __shared__ double red[2][256];
+  __shared__ int stop;
+  for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+    const GramBlock g = gb[b];
+    const int d = g.d;
+    double* A = Aall + g.g_off;
+    double* Q = Qall + g.g_off;
+    double* w = wall + g.w_off;
+    for (long long e = threadIdx.x; e < (long long)d * d; e += blockDim.x) Q[e] = (e / d == e % d) ? 1.0 : 0.0;
+    __syncthreads();
+    const int dp = d + (d & 1);  // players (one dummy when d is odd)
+    for (int sweep = 0; sweep < max_sweeps && d > 1; ++sweep) {
+      double off = 0.0, tot = 0.0;
+      for (long long e = threadIdx.x; e < (long long)d * d; e += blockDim.x) {
+        const double a = A[e];
+        tot += a * a;
+        if (e / d != e % d) off += a * a;
+      }
+      red[0][threadIdx.x] = off;
+      red[1][threadIdx.x] = tot;
+      __syncthreads();
+      for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+          red[0][threadIdx.x] += red[0][threadIdx.x + h];
+          red[1][threadIdx.x] += red[1][threadIdx.x + h];
+        }
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) stop = (red[0][0] <= 1e-30 * red[1][0]) ? 1 : 0;
+      __syncthreads();
+      if (stop) break;
+      for (int round = 0; round < dp - 1; ++round) {
+        for (int k = threadIdx.x; k < dp / 2; k += blockDim.x) {
+          auto player = [&](int i) { return i == 0 ? 0 : 1 + (i - 1 + round) % (dp - 1); };
+          int p = player(k), q = player(dp - 1 - k);
+          if (p > q) { const int t = p; p = q; q = t; }
+          double c = 1.0, s = 0.0;
+          if (q < d) {
+            const double apq = A[(long long)p * d + q];
+            if (apq != 0.0) {
+              const double th = (A[(long long)q * d + q] - A[(long long)p * d + p]) / (2.0 * apq);
+              const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+              c = 1.0 / sqrt(t * t + 1.0);
+              s = t * c;
+            }
+          }
+          cs[k] = c;
+          sn[k] = s;
+          pp[k] = p;
+          qq[k] = q < d ? q : -1;
+        }
+        __syncthreads();
+        // columns: A <- A J, Q <- Q J
+        for (long long e = threadIdx.x; e < (long long)d * (dp / 2); e += blockDim.x) {
+          const int k = (int)(e / d), r = (int)(e % d);
+          if (qq[k] < 0 || sn[k] == 0.0) continue;
+          const int p = pp[k], q = qq[k];
+          const double c = cs[k], s = sn[k];
+          const double arp = A[(long long)r * d + p], arq = A[(long long)r * d + q];
+          A[(long long)r * d + p] = c * arp - s * arq;
+          A[(long long)r * d + q] = s * arp + c * arq;
+          const double qrp = Q[(long long)r * d + p], qrq = Q[(long long)r * d + q];
+          Q[(long long)r * d + p] = c * qrp - s * qrq;
+          Q[(long long)r * d + q] = s * qrp + c * qrq;
+        }
+        __syncthreads();
+        // rows: A <- J^T A
+        for (long long e = threadIdx.x; e < (long long)d * (dp / 2); e += blockDim.x) {
+          const int k = (int)(e / d), col = (int)(e % d);
+          if (qq[k] < 0 || sn[k] == 0.0) continue;
+          const int p = pp[k], q = qq[k];
+          const double c = cs[k], s = sn[k];
+          const double apc = A[(long long)p * d + col], aqc = A[(long long)q * d + col];
+          A[(long long)p * d + col] = c * apc - s * aqc;
+          A[(long long)q * d + col] = s * apc + c * aqc;
+        }
+        __syncthreads();
+      }
+    }
+    // eigenvalues = diagonal; sort descending with columns of Q (selection on thread 0)
+    if (threadIdx.x == 0) {
+      for (int i = 0; i < d; ++i) w[i] = A[(long long)i * d + i];
+    }
+    __syncthreads();
+    for (int i = 0; i < d - 1; ++i) {
+      __shared__ int best;
+      if (threadIdx.x == 0) {
+        int m = i;
+        for (int j = i + 1; j < d; ++j)
+          if (w[j] > w[m]) m = j;
+        best = m;
+        const double t = w[i];
+        w[i] = w[m];
+        w[m] = t;
+      }
+      __syncthreads();
+      const int m = best;
+      if (m != i)
+        for (int r = threadIdx.x; r < d; r += blockDim.x) {
+          const double t = Q[(long long)r * d + i];
+          Q[(long long)r * d + i] = Q[(long long)r * d + m];
+          Q[(long long)r * d + m] = t;
+        }
+      __syncthreads();
+    }
+    __syncthreads();
+  }
+}
+
+// Orthonormalise the columns of each d x m block (row-major, in place) by
+// classical Gram-Schmidt applied twice per column.
+__global__ void orthonormalize_kernel(double* __restrict__ store, const GramBlock* __restrict__ gb, int nb) {
+  __shared__ double coef[1024];
+  __shared__ double red[256];
+  for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+    const GramBlock g = gb[b];
+    double* G = store + g.g_off;
+    const int d = g.d, m = g.m;
+    for (int j = 0; j < m; ++j) {
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int i = threadIdx.x; i < j; i += blockDim.x) {
+          double s = 0.0;
+          for (int r = 0; r < d; ++r) s = fma(G[(long long)r * m + i], G[(long long)r * m + j], s);
+          coef[i] = s;
+        }
+        __syncthreads();
+        for (int r = threadIdx.x; r < d; r += blockDim.x) {
+          double s = 0.0;
+          for (int i = 0; i < j; ++i) s = fma(coef[i], G[(long long)r * m + i], s);
+          G[(long long)r * m + j] -= s;
+        }
+        __syncthreads();
+      }
+      double s = 0.0;
+      for (int r = threadIdx.x; r < d; r += blockDim.x) s = fma(G[(long long)r * m + j], G[(long long)r * m + j], s);
+      red[threadIdx.x] = s;
+      __syncthreads();
+      for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+      }
+      const double inv = red[0] > 0.0 ? 1.0 / sqrt(red[0]) : 0.0;
+      __syncthreads();
+      for (int r = threadIdx.x; r < d; r += blockDim.x) G[(long long)r * m + j] *= inv;
+      __syncthreads();
+    }
+  }
+}
+
+// dst[b] (d x k, row-major) = first k columns of Q[b] (d x d)
+__global__ void take_columns_kernel(const double* __restrict__ Qall, const TakeBlock* __restrict__ tb, int nb,
+                                    double* __restrict__ dst) {
+  for (int b = blockIdx.y; b < nb; b += gridDim.y) {
+    const TakeBlock t = tb[b];
+    const long long ne = (long long)t.d * t.k;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x) {
+      const int r = (int)(e / t.k), c = (int)(e % t.k);
+      dst[t.dst_off + e] = Qall[t.q_off + (long long)r * t.d + c];
+    }
+  }
+}
+
+}  // namespace
+
+void launch_blocking(double* dst_store, const double* src_store, const BlockJob* jobs, const DstBlock* dsts, int ndst,
+                     cudaStream_t st) {
+  if (ndst <= 0) return;
+  const int grid = ndst < 65535 ? ndst : 65535;
+  blocking_kernel<<<grid, 256, 0, st>>>(dst_store, src_store, jobs, dsts, ndst);
+}
+
+void launch_gram(const double* psi, const GramBlock* gb, int nb, double* G, bool left, cudaStream_t st) {
+  if (nb <= 0) return;
+  dim3 grid(32, nb < 65535 ? nb : 65535);
+  gram_kernel<<<grid, 256, 0, st>>>(psi, gb, nb, G, left ? 1 : 0);
+}
+
+void launch_jacobi_blocks(double* A, double* Q, double* w, const GramBlock* gb, int nb, cudaStream_t st) {
+  if (nb <= 0) return;
+  jacobi_blocks_kernel<<<nb < 65535 ? nb : 65535, 256, 0, st>>>(A, Q, w, gb, nb, 40);
+}
+
+void launch_orthonormalize(double* store, const GramBlock* gb, int nb, cudaStream_t st) {
+  if (nb <= 0) return;
+  orthonormalize_kernel<<<nb < 65535 ? nb : 65535, 256, 0, st>>>(store, gb, nb);
+}
+
+void launch_take_columns(const double* Q, const TakeBlock* tb, int nb, double* dst, cudaStream_t st) {
+  if (nb <= 0) return;
+  dim3 grid(16, nb < 65535 ? nb : 65535);
+  take_columns_kernel<<<grid, 256, 0, st>>>(Q, tb, nb, dst);
+}
+
+}  // namespace dmrg

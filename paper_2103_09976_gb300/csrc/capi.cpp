@@ -54,6 +54,11 @@ Basis parse_sectors(int n, const int* s) {
 }
 
 Problem& need_problem(Context& c, int site) {
+  if (c.sweep) {
+    if (site < 0) throw Error(DMRG_EINVAL, "site must be a bond index (0 .. K-2) for a context built from integrals");
+    sweep_problem(c, site);
+    return *c.prob;
+  }
   if (!c.prob) throw Error(DMRG_ESTATE, "no operators loaded (call dmrg_load_synthetic or dmrg_build_blocks)");
   if (site != -1) throw Error(DMRG_EINVAL, "site must be -1 for a synthetic context");
   return *c.prob;
@@ -374,6 +379,7 @@ dmrg_status dmrg_load_synthetic(dmrg_ctx* ctx, int n_left_modes, int n_modes, in
       throw Error(DMRG_ENOMEM, "operator store (" + std::to_string(elems * 8.0 / 1e9) +
                                    " GB) does not fit in free device memory");
     c.prob.reset();
+    c.sweep.reset();
     p->store.alloc((size_t)elems * sizeof(double));
     // generate every stored block on the device
     std::vector<GenBlock> gb;
@@ -495,13 +501,54 @@ dmrg_status dmrg_davidson(dmrg_ctx* ctx, int site, const double* psi0, double to
 dmrg_status dmrg_build_blocks(dmrg_ctx* ctx, const double* t, const double* v, int K, int N,
                               int two_sz, int M_init) {
   if (!ctx) return DMRG_EINVAL;
-  return guarded(ctx, [&] { throw Error(DMRG_ESTATE, "dmrg_build_blocks: not available yet"); });
+  return guarded(ctx, [&] {
+    if (!t || !v) throw Error(DMRG_EINVAL, "t and v must not be NULL");
+    DMRG_CUDA(cudaSetDevice(ctx->c.device));
+    ctx->c.prob.reset();
+    ctx->c.sweep.reset();
+    sweep_build_blocks(ctx->c, t, v, K, N, two_sz, M_init);
+  });
 }
 
 dmrg_status dmrg_sweep(dmrg_ctx* ctx, const int* M_schedule, int n_sweeps, double tol,
                        double* energies, double* max_discard) {
   if (!ctx) return DMRG_EINVAL;
-  return guarded(ctx, [&] { throw Error(DMRG_ESTATE, "dmrg_sweep: not available yet"); });
+  return guarded(ctx, [&] {
+    if (!M_schedule || n_sweeps < 1) throw Error(DMRG_EINVAL, "empty M schedule");
+    if (!(tol > 0.0)) throw Error(DMRG_EINVAL, "tol must be positive");
+    if (ctx->c.opts.dav_max_space > 32) throw Error(DMRG_EINVAL, "dav_max_space must be <= 32");
+    DMRG_CUDA(cudaSetDevice(ctx->c.device));
+    sweep_run(ctx->c, M_schedule, n_sweeps, tol, energies, max_discard);
+  });
+}
+
+dmrg_status dmrg_block_info(dmrg_ctx* ctx, int side, int j, int* n_sectors, int* q, int* dims, int* n_ops) {
+  if (!ctx) return DMRG_EINVAL;
+  return guarded(ctx, [&] {
+    if (!n_sectors) throw Error(DMRG_EINVAL, "n_sectors must not be NULL");
+    sweep_block_info(ctx->c, side, j, n_sectors, q, dims, n_ops);
+  });
+}
+
+dmrg_status dmrg_block_read(dmrg_ctx* ctx, int side, int j, int op, double* dense) {
+  if (!ctx) return DMRG_EINVAL;
+  return guarded(ctx, [&] {
+    if (!dense) throw Error(DMRG_EINVAL, "dense must not be NULL");
+    DMRG_CUDA(cudaSetDevice(ctx->c.device));
+    sweep_block_read(ctx->c, side, j, op, dense);
+  });
+}
+
+dmrg_status dmrg_sweep_log(dmrg_ctx* ctx, dmrg_step_log* out, int max_steps, int* n_steps) {
+  if (!ctx) return DMRG_EINVAL;
+  return guarded(ctx, [&] {
+    if (!n_steps) throw Error(DMRG_EINVAL, "n_steps must not be NULL");
+    if (max_steps < 0 || (max_steps > 0 && !out)) throw Error(DMRG_EINVAL, "out must hold max_steps records");
+    const std::vector<dmrg_step_log>& log = sweep_log(ctx->c);
+    const int n = (int)log.size();
+    for (int k = 0; k < n && k < max_steps; ++k) out[k] = log[k];
+    *n_steps = n;
+  });
 }
 
 dmrg_status dmrg_sync(dmrg_ctx* ctx) {

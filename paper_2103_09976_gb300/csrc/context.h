@@ -107,6 +107,8 @@ struct ProfScope {
   }
 };
 
+struct SweepState;
+
 struct Context {
   dmrg_opts opts;
   int device = 0;
@@ -114,6 +116,7 @@ struct Context {
   cudaStream_t stream = nullptr;
   std::string err;
   std::unique_ptr<Problem> prob;   // synthetic or current sweep step
+  std::shared_ptr<SweepState> sweep;  // blocks of a problem built from integrals
   DevBuf d_psi, d_sigma;           // staging for host psi / sigma
   Profiler prof;
   DevBuf d_wait_prof;              // tensor-core kernel wait accounting (profiling only)
@@ -123,6 +126,12 @@ void prepare_worklist(Context& c, Problem& p);
 void prepare_tc(Context& c, Problem& p);
 void check_device_error(Context& c, Problem& p);
 void sigma_noalloc(Context& c, Problem& p, const double* psi, double* sigma);
+void sweep_problem(Context& c, int site);
+void sweep_build_blocks(Context& c, const double* t, const double* v, int K, int N, int two_sz, int M_init);
+void sweep_run(Context& c, const int* Ms, int n_sweeps, double tol, double* energies, double* max_discard);
+const std::vector<dmrg_step_log>& sweep_log(const Context& c);
+void sweep_block_info(const Context& c, int side, int j, int* n_sectors, int* q, int* dims, int* n_ops);
+void sweep_block_read(Context& c, int side, int j, int op, double* dense);
 // Davidson on the device: x0 (device, may be null = seeded random) -> energy,
 // eigenvector in x_out (device, may be null). Returns false if not converged.
 bool run_davidson(Context& c, Problem& p, const double* x0, double tol, double* energy, double* x_out,

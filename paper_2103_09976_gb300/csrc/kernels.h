@@ -72,6 +72,34 @@ void launch_split_psi(const double* psi, const PsiBlock* blocks, const TcPsiBloc
                       cudaStream_t st);
 void launch_sigma_tc(const TcDev& a, int n_sm, cudaStream_t st);
 
+// ------------------------------------------------------------------- sweep
+// dst_block[r0 + i, c0 + j] += coef * src(i, j); src(i, j) = S[i, j] or S[j, i]
+// (trans) of a stored row-major block with row length src_ld, or the
+// identity when src < 0.
+struct BlockJob {
+  long long src;
+  int src_ld, rows, cols, r0, c0, trans;
+  double coef;
+};
+struct DstBlock {       // one destination block and the range of its jobs
+  long long off, n;
+  int ld, j0, j1, pad;
+};
+struct GramBlock {      // one psi block for decimation / one block to orthonormalise
+  long long psi_off, g_off, w_off;
+  int d, m;             // Gram dimension and contracted dimension (or d x m columns)
+};
+struct TakeBlock {      // dst (d x k) = first k columns of Q (d x d)
+  long long q_off, dst_off;
+  int d, k;
+};
+void launch_blocking(double* dst_store, const double* src_store, const BlockJob* jobs, const DstBlock* dsts, int ndst,
+                     cudaStream_t st);
+void launch_gram(const double* psi, const GramBlock* gb, int nb, double* G, bool left, cudaStream_t st);
+void launch_jacobi_blocks(double* A, double* Q, double* w, const GramBlock* gb, int nb, cudaStream_t st);
+void launch_orthonormalize(double* store, const GramBlock* gb, int nb, cudaStream_t st);
+void launch_take_columns(const double* Q, const TakeBlock* tb, int nb, double* dst, cudaStream_t st);
+
 // ---------------------------------------------------------------- Davidson
 // out[i*out_stride] = V[i] . w for i < k (V rows of length n, leading dim ld);
 // partial: k * 256 doubles of workspace. Fixed-order two-stage reduction.

@@ -188,17 +188,19 @@ static double tile_cost(const Task& k, const PsiBlock& in, int nr, int nc) {
 }
 
 void build_items(const std::vector<PsiBlock>& blocks, WorkList& wl, const TileShape& ts,
-                 int want_items) {
+                 int want_items, int n_out) {
+  // output blocks are blocks[0, n_out); inputs may follow them
+  const size_t nb = n_out < 0 ? blocks.size() : (size_t)n_out;
   wl.items.clear();
   wl.groups.clear();
   wl.scratch_elems = 0;
   double total = 0;
-  for (size_t b = 0; b < blocks.size(); ++b)
+  for (size_t b = 0; b < nb; ++b)
     for (int t = wl.out_start[b]; t < wl.out_start[b + 1]; ++t)
       total += tile_cost(wl.tasks[t], blocks[wl.tasks[t].in_blk], blocks[b].mL, blocks[b].mR);
   double target = std::max(ts.target, total / std::max(1, want_items));
   std::vector<double> cost;
-  for (size_t b = 0; b < blocks.size(); ++b) {
+  for (size_t b = 0; b < nb; ++b) {
     const PsiBlock& ob = blocks[b];
     int t0 = wl.out_start[b], t1 = wl.out_start[b + 1];
     if (t0 == t1) {

@@ -151,7 +151,7 @@ void build_tasks(const std::vector<PsiBlock>& blocks, const OpSet& L, const OpSe
 // Split every output block into tm x tn tiles and each tile's task list into
 // items of about max(ts.target, total / want_items) flops.
 void build_items(const std::vector<PsiBlock>& blocks, WorkList& wl, const TileShape& ts,
-                 int want_items);
+                 int want_items, int n_out = -1);
 
 }  // namespace dmrg
 

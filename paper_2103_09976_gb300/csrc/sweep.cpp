@@ -1,0 +1,898 @@
+// Two-site DMRG sweeps on the device (Appendix A): blocking (Eq.
+// blocked-ops), solving (Eq. eff-eigsh, device Davidson over the NC sigma),
+// decimation (per-sector Gram matrix + Jacobi, global truncation) and
+// transformation (Eq. op-trans). The host decides which blocks to add and
+// which states to keep; every floating-point step runs in CUDA kernels.
+//
+// Operators of a block are an NC set in canonical order (model.h NCIndex):
+// a left block holding modes [0, nL) keeps H, a+_p (p < nL), R^L_p (p >= nL),
+// A_pr and B_pq (p, q, r < nL); a right block holding modes [nL, n) keeps
+// H, a_p (p >= nL), R^R_p, P_pr, Q_pq (p, q, r < nL). The enlarged blocks
+// L x site and site x R are NC sets of the same kind one site larger, so the
+// sigma work list applies to them directly.
+//
+// Blocking: each enlarged operator is a sum of terms (block operator or 1)
+// (x) (4x4 site matrix) derived by splitting every second-quantized string
+// into its block part and its site part (the formulas below). Every nonzero
+// site-matrix element of a term becomes a scaled copy of one block-operator
+// block into one chunk of one enlarged block; a kernel applies the copies of
+// each destination block in a fixed order.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "context.h"
+
+namespace dmrg {
+
+namespace {
+
+constexpr uint64_t KEY_MPS = 0x4D50535F494E4954ull;    // "MPS_INIT"
+const QN SITE_Q[4] = {{0, 0}, {1, 1}, {1, -1}, {2, 0}};  // |0>, |a>, |b>, |ab>
+const int SITE_N[4] = {0, 1, 1, 2};
+
+using Mat4 = std::array<std::array<double, 4>, 4>;
+
+Mat4 zero4() {
+  Mat4 m{};
+  return m;
+}
+Mat4 eye4() {
+  Mat4 m{};
+  for (int i = 0; i < 4; ++i) m[i][i] = 1.0;
+  return m;
+}
+Mat4 mul(const Mat4& a, const Mat4& b) {
+  Mat4 c{};
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j)
+      for (int k = 0; k < 4; ++k) c[i][j] += a[i][k] * b[k][j];
+  return c;
+}
+Mat4 tr(const Mat4& a) {
+  Mat4 c{};
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) c[i][j] = a[j][i];
+  return c;
+}
+void axpy(Mat4& y, double c, const Mat4& x) {
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) y[i][j] += c * x[i][j];
+}
+// a+ of spin sigma on one spatial orbital; local states: bit0 = alpha, bit1 = beta
+Mat4 site_cre(int sigma) {
+  Mat4 m{};
+  for (int s = 0; s < 4; ++s)
+    if (!((s >> sigma) & 1)) m[s | (1 << sigma)][s] = (sigma == 1 && (s & 1)) ? -1.0 : 1.0;
+  return m;
+}
+const Mat4 SC[2] = {site_cre(0), site_cre(1)};
+const Mat4 SA[2] = {tr(SC[0]), tr(SC[1])};
+
+struct Ints {
+  int K = 0;
+  std::vector<double> t, v;
+  double tso(int p, int q) const { return (p & 1) == (q & 1) ? t[(p / 2) * K + q / 2] : 0.0; }
+  double vso(int p, int q, int r, int s) const {
+    if ((p & 1) != (q & 1) || (r & 1) != (s & 1)) return 0.0;
+    return v[(((size_t)(p / 2) * K + q / 2) * K + r / 2) * K + s / 2];
+  }
+};
+
+// site operators built from the integrals; x(p) = local a+ / a of mode p of the site
+struct Site {
+  const Ints& I;
+  int s;  // spatial orbital
+  int m0() const { return 2 * s; }
+  const Mat4& cre(int p) const { return SC[p - 2 * s]; }
+  const Mat4& ann(int p) const { return SA[p - 2 * s]; }
+  Mat4 R(int p, bool one_body) const {  // [sum t_pq a_q] + sum v_pqrs a+_r a_s a_q over site modes
+    Mat4 m = zero4();
+    const int a = 2 * s, b = 2 * s + 1;
+    if (one_body)
+      for (int q = a; q <= b; ++q) axpy(m, I.tso(p, q), ann(q));
+    for (int q = a; q <= b; ++q)
+      for (int r = a; r <= b; ++r)
+        for (int w = a; w <= b; ++w) {
+          const double x = I.vso(p, q, r, w);
+          if (x != 0.0) axpy(m, x, mul(mul(cre(r), ann(w)), ann(q)));
+        }
+    return m;
+  }
+  Mat4 P(int p, int r) const {  // sum v_pqrs a_s a_q
+    Mat4 m = zero4();
+    for (int q = 2 * s; q <= 2 * s + 1; ++q)
+      for (int w = 2 * s; w <= 2 * s + 1; ++w) {
+        const double x = I.vso(p, q, r, w);
+        if (x != 0.0) axpy(m, x, mul(ann(w), ann(q)));
+      }
+    return m;
+  }
+  Mat4 Q(int p, int q) const {  // sum (v_pqrs - v_psrq) a+_r a_s
+    Mat4 m = zero4();
+    for (int r = 2 * s; r <= 2 * s + 1; ++r)
+      for (int w = 2 * s; w <= 2 * s + 1; ++w) {
+        const double x = I.vso(p, q, r, w) - I.vso(p, w, r, q);
+        if (x != 0.0) axpy(m, x, mul(cre(r), ann(w)));
+      }
+    return m;
+  }
+  Mat4 H() const {
+    Mat4 m = zero4();
+    const int a = 2 * s, b = 2 * s + 1;
+    for (int p = a; p <= b; ++p)
+      for (int q = a; q <= b; ++q) axpy(m, I.tso(p, q), mul(cre(p), ann(q)));
+    for (int p = a; p <= b; ++p)
+      for (int q = a; q <= b; ++q)
+        for (int r = a; r <= b; ++r)
+          for (int w = a; w <= b; ++w) {
+            const double x = I.vso(p, q, r, w);
+            if (x != 0.0) axpy(m, 0.5 * x, mul(mul(mul(cre(p), cre(r)), ann(w)), ann(q)));
+          }
+    return m;
+  }
+};
+
+// One term of an enlarged operator: (block op src, maybe transposed) (x) E_{nout,nin}
+struct ETerm {
+  int src;  // op index in the block's NC set, -1 = identity
+  bool trans;
+  double coef;
+  int nout, nin;
+};
+using ETerms = std::vector<ETerm>;
+
+void add(ETerms& e, int src, bool trans, double c, const Mat4& m) {
+  if (c == 0.0) return;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j)
+      if (m[i][j] != 0.0) e.push_back({src, trans, c * m[i][j], i, j});
+}
+
+// Enlarged basis: sector Q = q_block + q_site; chunks in ascending block sector.
+struct Enlarged {
+  Basis basis;
+  std::vector<std::vector<int>> chunk_off;  // [Q index][block sector index] -> offset in Q, or -1
+};
+
+Enlarged enlarge(const Basis& b) {
+  std::map<std::pair<int, int>, int> dims;
+  for (int i = 0; i < b.size(); ++i)
+    for (int n = 0; n < 4; ++n) {
+      QN Q = b.q[i] + SITE_Q[n];
+      dims[{Q.n, Q.s}] += b.dim[i];
+    }
+  Enlarged E;
+  for (auto& kv : dims) {
+    E.basis.q.push_back({kv.first.first, kv.first.second});
+    E.basis.dim.push_back(kv.second);
+  }
+  E.basis.finish();
+  E.chunk_off.assign(E.basis.size(), std::vector<int>(b.size(), -1));
+  std::vector<int> fill(E.basis.size(), 0);
+  for (int i = 0; i < b.size(); ++i)  // ascending block sector
+    for (int n = 0; n < 4; ++n) {
+      const int Qi = E.basis.find(b.q[i] + SITE_Q[n]);
+      E.chunk_off[Qi][i] = fill[Qi];
+      fill[Qi] += b.dim[i];
+    }
+  return E;
+}
+
+// Jobs that build the dense blocks of the enlarged operators E from the
+// operators of block B. left: L x site (sign from the site part's parity and
+// N of the block state); right: site x R (sign from the block op's parity and
+// N of the site state).
+void make_jobs(const OpSet& B, const Enlarged& E, const OpSet& EO, const std::vector<ETerms>& terms, bool left,
+               std::vector<BlockJob>& jobs, std::vector<DstBlock>& dsts) {
+  std::vector<std::vector<BlockJob>> per;  // per destination block
+  std::vector<long long> doff;
+  std::vector<int> dld;
+  std::vector<long long> dn;
+  std::vector<std::vector<int>> dst_index(EO.ops.size());
+  for (size_t k = 0; k < EO.ops.size(); ++k) {
+    dst_index[k].assign(E.basis.size(), -1);
+    for (const OpBlock& ob : EO.ops[k].blocks) {
+      dst_index[k][ob.qin] = (int)per.size();
+      per.emplace_back();
+      doff.push_back(ob.off);
+      dld.push_back(ob.cols);
+      dn.push_back((long long)ob.rows * ob.cols);
+    }
+  }
+  for (size_t k = 0; k < EO.ops.size(); ++k) {
+    const QN dqk = EO.ops[k].dq;
+    for (const ETerm& e : terms[k]) {
+      for (int ib = 0; ib < B.basis.size(); ++ib) {
+        int ob;
+        long long src = -1;
+        int src_ld = 0, par = 0;
+        if (e.src < 0) {
+          ob = ib;
+        } else {
+          const OpDesc& S = B.ops[e.src];
+          par = S.parity;
+          if (!e.trans) {
+            const int kb = S.by_qin[ib];
+            if (kb < 0) continue;
+            ob = S.blocks[kb].qout;
+            src = S.blocks[kb].off;
+            src_ld = S.blocks[kb].cols;
+          } else {
+            ob = B.basis.find(B.basis.q[ib] - S.dq);
+            if (ob < 0) continue;
+            const int kb = S.by_qin[ob];
+            if (kb < 0) continue;
+            src = S.blocks[kb].off;
+            src_ld = S.blocks[kb].cols;
+          }
+        }
+        const int Qin = E.basis.find(B.basis.q[ib] + SITE_Q[e.nin]);
+        const int Qout = E.basis.find(B.basis.q[ob] + SITE_Q[e.nout]);
+        if (Qin < 0 || Qout < 0) continue;
+        if (!(E.basis.q[Qout] == E.basis.q[Qin] + dqk)) throw Error(DMRG_EINVAL, "internal: blocking shift");
+        const int d = dst_index[k][Qin];
+        if (d < 0) continue;
+        double sign = 1.0;
+        if (left) {
+          const int ps = (SITE_N[e.nout] - SITE_N[e.nin]) & 1;
+          if (ps && (B.basis.q[ib].n & 1)) sign = -1.0;
+        } else {
+          if (par && (SITE_N[e.nin] & 1)) sign = -1.0;
+        }
+        BlockJob j;
+        j.src = src;
+        j.src_ld = src_ld;
+        j.rows = B.basis.dim[ob];
+        j.cols = B.basis.dim[ib];
+        j.r0 = E.chunk_off[Qout][ob];
+        j.c0 = E.chunk_off[Qin][ib];
+        j.trans = e.trans ? 1 : 0;
+        j.coef = e.coef * sign;
+        per[d].push_back(j);
+      }
+    }
+  }
+  jobs.clear();
+  dsts.clear();
+  for (size_t d = 0; d < per.size(); ++d) {
+    DstBlock db{doff[d], dn[d], dld[d], (int)jobs.size(), 0, 0};
+    jobs.insert(jobs.end(), per[d].begin(), per[d].end());
+    db.j1 = (int)jobs.size();
+    dsts.push_back(db);
+  }
+}
+
+// ----------------------------------------------------- blocking formulas
+// Left: block L holds modes [0, 2s); site s; enlarged NC set nL' = 2s + 2.
+std::vector<ETerms> left_terms(const Ints& I, int s) {
+  const int n = 2 * I.K, nL = 2 * s, nE = 2 * s + 2;
+  NCIndex bx{nL, n}, ex{nE, n};
+  Site st{I, s};
+  std::vector<ETerms> T(ex.count());
+  const int S0 = 2 * s, S1 = 2 * s + 1;
+  auto B = [&](int p, int q, bool& t) {  // B_pq = B_pq or B_qp^T
+    t = p > q;
+    return p <= q ? bx.B(p, q) : bx.B(q, p);
+  };
+  // H
+  {
+    ETerms& e = T[ex.H()];
+    add(e, bx.H(), false, 1.0, eye4());
+    add(e, -1, false, 1.0, st.H());
+    for (int p = 0; p < nL; ++p) {
+      const Mat4 Rs = st.R(p, true);
+      add(e, bx.cd(p), false, 1.0, Rs);
+      add(e, bx.cd(p), true, -1.0, tr(Rs));
+    }
+    for (int p = S0; p <= S1; ++p) {
+      add(e, bx.RL(p), true, 1.0, st.ann(p));
+      add(e, bx.RL(p), false, -1.0, st.cre(p));
+    }
+    for (int p = 0; p < nL; ++p)
+      for (int r = p + 1; r < nL; ++r) {
+        const Mat4 Ps = st.P(p, r);
+        add(e, bx.A(p, r), false, 1.0, Ps);
+        add(e, bx.A(p, r), true, 1.0, tr(Ps));
+      }
+    for (int p = 0; p < nL; ++p)
+      for (int q = 0; q < nL; ++q) {
+        bool t;
+        const int k = B(p, q, t);
+        add(e, k, t, 1.0, st.Q(p, q));
+      }
+  }
+  // a+_p
+  for (int p = 0; p < nL; ++p) add(T[ex.cd(p)], bx.cd(p), false, 1.0, eye4());
+  for (int p = S0; p <= S1; ++p) add(T[ex.cd(p)], -1, false, 1.0, st.cre(p));
+  // A_pr, B_pq
+  for (int p = 0; p < nE; ++p)
+    for (int r = p; r < nE; ++r) {
+      if (p < r) {
+        ETerms& e = T[ex.A(p, r)];
+        if (r < nL) add(e, bx.A(p, r), false, 1.0, eye4());
+        else if (p < nL) add(e, bx.cd(p), false, 1.0, st.cre(r));
+        else add(e, -1, false, 1.0, mul(st.cre(p), st.cre(r)));
+      }
+      ETerms& e = T[ex.B(p, r)];
+      if (r < nL) add(e, bx.B(p, r), false, 1.0, eye4());
+      else if (p < nL) add(e, bx.cd(p), false, 1.0, st.ann(r));
+      else add(e, -1, false, 1.0, mul(st.cre(p), st.ann(r)));
+    }
+  // R^L_p for p right of the enlarged block
+  for (int p = nE; p < n; ++p) {
+    ETerms& e = T[ex.RL(p)];
+    add(e, bx.RL(p), false, 1.0, eye4());
+    add(e, -1, false, 1.0, st.R(p, false));
+    for (int x = S0; x <= S1; ++x)  // (sum_{r,y} (v_pxry - v_pyrx) B_ry) (x) a_x
+      for (int r = 0; r < nL; ++r)
+        for (int y = 0; y < nL; ++y) {
+          const double c = I.vso(p, x, r, y) - I.vso(p, y, r, x);
+          if (c == 0.0) continue;
+          bool t;
+          const int k = B(r, y, t);
+          add(e, k, t, c, st.ann(x));
+        }
+    for (int r = S0; r <= S1; ++r)  // (sum_{q,w} v_pqrw a_w a_q) (x) a+_r
+      for (int q = 0; q < nL; ++q)
+        for (int w = 0; w < nL; ++w) {
+          const double c = I.vso(p, q, r, w);
+          if (c == 0.0 || q == w) continue;
+          if (q < w) add(e, bx.A(q, w), true, c, st.cre(r));   // a_w a_q = A_qw^T
+          else add(e, bx.A(w, q), true, -c, st.cre(r));        // = -A_wq^T
+        }
+    for (int w = 0; w < nL; ++w) {  // -a_w (x) sum v_pqrw a+_r a_q  (q, r on the site)
+      Mat4 m = zero4();
+      for (int q = S0; q <= S1; ++q)
+        for (int r = S0; r <= S1; ++r) axpy(m, I.vso(p, q, r, w), mul(st.cre(r), st.ann(q)));
+      add(e, bx.cd(w), true, -1.0, m);
+    }
+    for (int r = 0; r < nL; ++r) {  // a+_r (x) sum v_pqrw a_w a_q  (q, w on the site)
+      Mat4 m = zero4();
+      for (int q = S0; q <= S1; ++q)
+        for (int w = S0; w <= S1; ++w) axpy(m, I.vso(p, q, r, w), mul(st.ann(w), st.ann(q)));
+      add(e, bx.cd(r), false, 1.0, m);
+    }
+    for (int q = 0; q < nL; ++q) {  // a_q (x) sum v_pqrw a+_r a_w  (r, w on the site)
+      Mat4 m = zero4();
+      for (int r = S0; r <= S1; ++r)
+        for (int w = S0; w <= S1; ++w) axpy(m, I.vso(p, q, r, w), mul(st.cre(r), st.ann(w)));
+      add(e, bx.cd(q), true, 1.0, m);
+    }
+  }
+  return T;
+}
+
+// Right: block R holds modes [2s+2, n) (complementary indices p < 2s+2);
+// site s; enlarged NC set (right kind) nL' = 2s. Terms read site (x) block.
+std::vector<ETerms> right_terms(const Ints& I, int s) {
+  const int n = 2 * I.K, nLb = 2 * s + 2, nE = 2 * s;
+  NCIndex bx{nLb, n}, ex{nE, n};
+  Site st{I, s};
+  std::vector<ETerms> T(ex.count());
+  const int S0 = 2 * s, S1 = 2 * s + 1;
+  auto Qk = [&](int p, int q, bool& t) {
+    t = p > q;
+    return p <= q ? bx.B(p, q) : bx.B(q, p);
+  };
+  for (int p = S0; p <= S1; ++p) add(T[ex.d(p)], -1, false, 1.0, st.ann(p));
+  for (int p = nLb; p < n; ++p) add(T[ex.d(p)], bx.d(p), false, 1.0, eye4());
+  {  // H of site x R: NC decomposition over (site | R)
+    ETerms& e = T[ex.H()];
+    add(e, -1, false, 1.0, st.H());
+    add(e, bx.H(), false, 1.0, eye4());
+    for (int p = S0; p <= S1; ++p) {
+      add(e, bx.RR(p), false, 1.0, st.cre(p));
+      add(e, bx.RR(p), true, -1.0, st.ann(p));
+    }
+    for (int p = nLb; p < n; ++p) {
+      const Mat4 Rs = st.R(p, false);
+      add(e, bx.d(p), false, 1.0, tr(Rs));
+      add(e, bx.d(p), true, -1.0, Rs);
+    }
+    const Mat4 A = mul(st.cre(S0), st.cre(S1));
+    add(e, bx.A(S0, S1), false, 1.0, A);
+    add(e, bx.A(S0, S1), true, 1.0, tr(A));
+    for (int p = S0; p <= S1; ++p)
+      for (int q = S0; q <= S1; ++q) {
+        bool t;
+        const int k = Qk(p, q, t);
+        add(e, k, t, 1.0, mul(st.cre(p), st.ann(q)));
+      }
+  }
+  for (int p = 0; p < nE; ++p) {  // R^R_p
+    ETerms& e = T[ex.RR(p)];
+    add(e, bx.RR(p), false, 1.0, eye4());
+    add(e, -1, false, 1.0, st.R(p, true));
+    for (int x = S0; x <= S1; ++x) {
+      add(e, bx.B(p, x), false, 1.0, st.ann(x));  // a_x (x) Q_px
+      add(e, bx.A(p, x), false, 1.0, st.cre(x));  // a+_x (x) P_px
+    }
+    for (int y = nLb; y < n; ++y) {
+      Mat4 m1 = zero4(), m2 = zero4(), m3 = zero4();
+      for (int u = S0; u <= S1; ++u)
+        for (int w = S0; w <= S1; ++w) {
+          axpy(m1, I.vso(p, u, w, y), mul(st.cre(w), st.ann(u)));
+          axpy(m2, I.vso(p, u, y, w), mul(st.ann(w), st.ann(u)));
+          axpy(m3, I.vso(p, y, u, w), mul(st.cre(u), st.ann(w)));
+        }
+      add(e, bx.d(y), false, -1.0, m1);
+      add(e, bx.d(y), true, 1.0, m2);
+      add(e, bx.d(y), false, 1.0, m3);
+    }
+  }
+  for (int p = 0; p < nE; ++p)
+    for (int r = p; r < nE; ++r) {
+      if (p < r) {  // P_pr
+        ETerms& e = T[ex.A(p, r)];
+        add(e, bx.A(p, r), false, 1.0, eye4());
+        add(e, -1, false, 1.0, st.P(p, r));
+        for (int x = S0; x <= S1; ++x)
+          for (int y = nLb; y < n; ++y) add(e, bx.d(y), false, I.vso(p, y, r, x) - I.vso(p, x, r, y), st.ann(x));
+      }
+      {  // Q_pr
+        ETerms& e = T[ex.B(p, r)];
+        const int q = r;
+        add(e, bx.B(p, q), false, 1.0, eye4());
+        add(e, -1, false, 1.0, st.Q(p, q));
+        for (int x = S0; x <= S1; ++x)
+          for (int y = nLb; y < n; ++y) {
+            add(e, bx.d(y), false, I.vso(p, q, x, y) - I.vso(p, y, x, q), st.cre(x));
+            add(e, bx.d(y), true, -(I.vso(p, q, y, x) - I.vso(p, x, y, q)), st.ann(x));
+          }
+      }
+    }
+  return T;
+}
+
+bool can_hold(int n_modes, QN q) {
+  return q.n >= 0 && q.n <= n_modes && ((q.s - q.n) % 2 == 0) && std::abs(q.s) <= std::min(q.n, n_modes - q.n);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ state
+struct DevBlock {
+  OpSet set;
+  int nL = 0;
+  bool left = true;
+  DevBuf store;
+};
+
+struct SweepState {
+  Ints I;
+  QN Q;
+  int K = 0;
+  std::vector<std::unique_ptr<DevBlock>> L, R;  // L[i]: modes [0, 2i); R[j]: modes [2j, 2K)
+  int prob_site = -1;
+  Enlarged EL, ER;
+  std::vector<dmrg_step_log> log;
+};
+
+void sweep_block_info(const Context& c, int side, int j, int* n_sectors, int* q, int* dims, int* n_ops) {
+  if (!c.sweep) throw Error(DMRG_ESTATE, "call dmrg_build_blocks first");
+  const SweepState& S = *c.sweep;
+  if (side != 0 && side != 1) throw Error(DMRG_EINVAL, "side must be 0 (left) or 1 (right)");
+  if (j < 0 || j > S.K) throw Error(DMRG_EINVAL, "block index out of range (0 .. K)");
+  const auto& blk = side == 0 ? S.L[j] : S.R[j];
+  if (!blk) throw Error(DMRG_ESTATE, "this block is not built");
+  const Basis& b = blk->set.basis;
+  *n_sectors = b.size();
+  for (int i = 0; i < b.size(); ++i) {
+    if (q) {
+      q[2 * i] = b.q[i].n;
+      q[2 * i + 1] = b.q[i].s;
+    }
+    if (dims) dims[i] = b.dim[i];
+  }
+  if (n_ops) *n_ops = (int)blk->set.ops.size();
+}
+
+void sweep_block_read(Context& c, int side, int j, int op, double* dense) {
+  int ns = 0, nops = 0;
+  sweep_block_info(c, side, j, &ns, nullptr, nullptr, &nops);
+  if (op < 0 || op >= nops) throw Error(DMRG_EINVAL, "operator index out of range");
+  const DevBlock& B = side == 0 ? *c.sweep->L[j] : *c.sweep->R[j];
+  const Basis& b = B.set.basis;
+  const long long tot = b.total;
+  std::fill(dense, dense + tot * tot, 0.0);
+  std::vector<double> tmp;
+  for (const OpBlock& ob : B.set.ops[op].blocks) {
+    tmp.resize((size_t)ob.rows * ob.cols);
+    if (tmp.empty()) continue;
+    DMRG_CUDA(cudaMemcpyAsync(tmp.data(), B.store.as<double>() + ob.off, tmp.size() * sizeof(double),
+                              cudaMemcpyDeviceToHost, c.stream));
+    DMRG_CUDA(cudaStreamSynchronize(c.stream));
+    const long long r0 = b.off[ob.qout], c0 = b.off[ob.qin];
+    for (int r = 0; r < ob.rows; ++r)
+      for (int k = 0; k < ob.cols; ++k) dense[(r0 + r) * tot + c0 + k] = tmp[(size_t)r * ob.cols + k];
+  }
+}
+
+const std::vector<dmrg_step_log>& sweep_log(const Context& c) {
+  static const std::vector<dmrg_step_log> none;
+  return c.sweep ? c.sweep->log : none;
+}
+
+namespace {
+
+std::unique_ptr<DevBlock> vacuum(const Ints& I, bool left, cudaStream_t st) {
+  auto b = std::make_unique<DevBlock>();
+  Basis v;
+  v.q.push_back({0, 0});
+  v.dim.push_back(1);
+  v.finish();
+  b->left = left;
+  b->nL = left ? 0 : 2 * I.K;
+  build_nc_opset(b->set, v, b->nL, 2 * I.K, left, 0);
+  b->store.alloc(std::max<long long>(1, b->set.elements) * sizeof(double));
+  DMRG_CUDA(cudaMemsetAsync(b->store.p, 0, std::max<long long>(1, b->set.elements) * sizeof(double), st));
+  return b;
+}
+
+// enlarged operators of one side into `store` at element offset base
+void build_enlarged(Context& c, const Ints& I, const DevBlock& B, int site, bool left, const Enlarged& E,
+                    OpSet& EO, double* store) {
+  std::vector<ETerms> terms = left ? left_terms(I, site) : right_terms(I, site);
+  std::vector<BlockJob> jobs;
+  std::vector<DstBlock> dsts;
+  make_jobs(B.set, E, EO, terms, left, jobs, dsts);
+  DevBuf dj, dd;
+  dj.upload(jobs, c.stream);
+  dd.upload(dsts, c.stream);
+  {
+    ProfScope ps(c.prof, 3, c.stream);
+    launch_blocking(store, B.store.as<double>(), dj.as<BlockJob>(), dd.as<DstBlock>(), (int)dsts.size(), c.stream);
+  }
+  DMRG_CUDA(cudaGetLastError());
+  DMRG_CUDA(cudaStreamSynchronize(c.stream));  // job buffers are freed on return
+}
+
+// Transformation O_new[Q' <- Q] = U_Q'^T O[Q' <- Q] U_Q of every operator of
+// the enlarged set EO (values at `enl_store`) onto the kept basis `nb`
+// (U blocks per enlarged sector in `u_store`, d x k row-major, offsets uoff).
+void transform(Context& c, const OpSet& EO, const double* enl_store, const Basis& nb,
+               const std::vector<int>& esec_of_new, const std::vector<long long>& uoff, const double* u_store,
+               DevBlock& out, int nL, int n, bool left) {
+  build_nc_opset(out.set, nb, nL, n, left, 0);
+  out.nL = nL;
+  out.left = left;
+  out.store.alloc(std::max<long long>(1, out.set.elements) * sizeof(double));
+  if ((int)out.set.ops.size() != (int)EO.ops.size()) throw Error(DMRG_EINVAL, "internal: transform op count");
+  std::vector<PsiBlock> blocks;
+  std::vector<std::pair<int, int>> in_ref;  // (op, enlarged block) per output block
+  WorkList wl;
+  std::vector<Task> tasks;
+  for (size_t k = 0; k < out.set.ops.size(); ++k)
+    for (const OpBlock& ob : out.set.ops[k].blocks) {
+      const int eq_in = esec_of_new[ob.qin], eq_out = esec_of_new[ob.qout];
+      const int kb = EO.ops[k].by_qin[eq_in];
+      if (kb < 0 || EO.ops[k].blocks[kb].qout != eq_out) throw Error(DMRG_EINVAL, "internal: transform block");
+      blocks.push_back({0, 0, ob.rows, ob.cols, ob.off});
+      in_ref.push_back({(int)k, kb});
+    }
+  const int nout = (int)blocks.size();
+  wl.out_start.assign(nout + 1, 0);
+  {
+    // one task per output block: rows side U_Q'^T, columns side U_Q^T (both
+    // stored d x k row-major, used transposed), input = the enlarged block
+    int b = 0;
+    for (size_t k = 0; k < out.set.ops.size(); ++k)
+      for (const OpBlock& ob : out.set.ops[k].blocks) {
+        const OpBlock& eb = EO.ops[in_ref[b].first].blocks[in_ref[b].second];
+        Task t;
+        t.aoff = uoff[ob.qout];
+        t.boff = uoff[ob.qin];
+        t.in_blk = (int)blocks.size();
+        t.flags = 3;
+        t.scale = 1.0;
+        blocks.push_back({0, 0, eb.rows, eb.cols, eb.off});
+        tasks.push_back(t);
+        wl.out_start[b + 1] = b + 1;
+        ++b;
+      }
+  }
+  wl.tasks = tasks;
+  build_items(blocks, wl, TileShape{F64_TM, F64_TN, 2e6}, c.n_sm * 8, nout);
+  DevBuf d_tasks, d_items, d_groups, d_sched, d_blocks, d_scratch, d_counter;
+  cudaStream_t st = c.stream;
+  d_tasks.upload(wl.tasks, st);
+  d_items.upload(wl.items, st);
+  d_groups.upload(wl.groups, st);
+  d_sched.upload(wl.schedule, st);
+  d_blocks.upload(blocks, st);
+  d_scratch.alloc(std::max<long long>(1, wl.scratch_elems) * sizeof(double));
+  d_counter.alloc(16);
+  DMRG_CUDA(cudaMemsetAsync(d_counter.p, 0, sizeof(unsigned int), st));
+  SigmaDev a;
+  a.store = u_store;
+  a.psi = enl_store;
+  a.sigma = out.store.as<double>();
+  a.tasks = d_tasks.as<Task>();
+  a.items = d_items.as<Item>();
+  a.schedule = d_sched.as<int>();
+  a.n_items = (int)wl.items.size();
+  a.groups = d_groups.as<Group>();
+  a.n_groups = (int)wl.groups.size();
+  a.blocks = d_blocks.as<PsiBlock>();
+  a.scratch = d_scratch.as<double>();
+  a.counter = d_counter.as<unsigned int>();
+  if (a.n_items > 0) {
+    ProfScope ps(c.prof, 3, st);
+    launch_sigma_f64(a, c.n_sm, st);
+    launch_reduce(a, st);
+  }
+  DMRG_CUDA(cudaGetLastError());
+  DMRG_CUDA(cudaStreamSynchronize(st));
+}
+
+}  // namespace
+
+// Build (if needed) the two-site problem at bond `site`: enlarged blocks
+// L[site] x s_site and s_{site+1} x R[site+2], NC terms, sigma work list.
+void sweep_problem(Context& c, int site) {
+  SweepState& S = *c.sweep;
+  if (site < 0 || site > S.K - 2) throw Error(DMRG_EINVAL, "site out of range (0 .. K-2)");
+  if (S.prob_site == site && c.prob) return;
+  if (!S.L[site] || !S.R[site + 2]) throw Error(DMRG_ESTATE, "blocks for this bond are not built");
+  const DevBlock& Lb = *S.L[site];
+  const DevBlock& Rb = *S.R[site + 2];
+  auto p = std::make_unique<Problem>();
+  p->nL = 2 * (site + 1);
+  p->n = 2 * S.K;
+  p->Q = S.Q;
+  S.EL = enlarge(Lb.set.basis);
+  S.ER = enlarge(Rb.set.basis);
+  build_nc_opset(p->L, S.EL.basis, p->nL, p->n, true, 0);
+  build_nc_opset(p->R, S.ER.basis, p->nL, p->n, false, p->L.elements);
+  p->terms = nc_terms(p->nL, p->n);
+  p->blocks = psi_layout(S.EL.basis, S.ER.basis, p->Q, &p->psi_size);
+  if (p->blocks.empty()) throw Error(DMRG_EINVAL, "no psi block at this bond");
+  const long long elems = p->L.elements + p->R.elements;
+  c.prob.reset();
+  p->store.alloc(std::max<long long>(1, elems) * sizeof(double));
+  build_enlarged(c, S.I, Lb, site, true, S.EL, p->L, p->store.as<double>());
+  build_enlarged(c, S.I, Rb, site + 1, false, S.ER, p->R, p->store.as<double>());
+  prepare_worklist(c, *p);
+  c.prob = std::move(p);
+  S.prob_site = site;
+}
+
+namespace {
+
+struct Decim {
+  Basis nb;                      // kept sectors (of the growing side's enlarged basis)
+  std::vector<int> esec_of_new;  // new sector -> enlarged sector index
+  std::vector<long long> uoff;   // new sector -> offset of its U block
+  DevBuf u;                      // U blocks (d x k row-major)
+  double discarded = 0.0;
+};
+
+// Decimation of psi (device, problem layout) keeping at most M states
+// (Appendix A step iii): per-sector Gram matrix, Jacobi eigenpairs, global
+// sort by (s desc, q_L asc, index asc), kept count min(M, sum min(mL, mR)).
+void decimate(Context& c, Problem& p, const Enlarged& E, const double* psi, int M, bool forward, Decim& D) {
+  cudaStream_t st = c.stream;
+  const int nb = (int)p.blocks.size();
+  std::vector<GramBlock> gb(nb);
+  long long goff = 0, woff = 0;
+  for (int b = 0; b < nb; ++b) {
+    const PsiBlock& pb = p.blocks[b];
+    const int d = forward ? pb.mL : pb.mR;
+    if (d > 1024) throw Error(DMRG_EINVAL, "sector dimension above 1024 in decimation");
+    gb[b] = {pb.off, goff, woff, d, forward ? pb.mR : pb.mL};
+    goff += (long long)d * d;
+    woff += d;
+  }
+  DevBuf dgb, G, Q, W;
+  dgb.upload(gb, st);
+  G.alloc(std::max<long long>(1, goff) * sizeof(double));
+  Q.alloc(std::max<long long>(1, goff) * sizeof(double));
+  W.alloc(std::max<long long>(1, woff) * sizeof(double));
+  {
+    ProfScope ps(c.prof, 3, st);
+    launch_gram(psi, dgb.as<GramBlock>(), nb, G.as<double>(), forward, st);
+    launch_jacobi_blocks(G.as<double>(), Q.as<double>(), W.as<double>(), dgb.as<GramBlock>(), nb, st);
+  }
+  DMRG_CUDA(cudaGetLastError());
+  std::vector<double> w(woff);
+  DMRG_CUDA(cudaMemcpyAsync(w.data(), W.p, woff * sizeof(double), cudaMemcpyDeviceToHost, st));
+  DMRG_CUDA(cudaStreamSynchronize(st));
+  struct Cand {
+    double s;
+    QN qL;
+    int idx, b;
+  };
+  std::vector<Cand> cand;
+  for (int b = 0; b < nb; ++b) {
+    const PsiBlock& pb = p.blocks[b];
+    const int r = std::min(pb.mL, pb.mR);
+    for (int i = 0; i < r; ++i)
+      cand.push_back({std::sqrt(std::max(0.0, w[gb[b].w_off + i])), p.L.basis.q[pb.qL], i, b});
+  }
+  std::stable_sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) {
+    if (a.s != b.s) return a.s > b.s;
+    if (!(a.qL == b.qL)) return a.qL < b.qL;
+    return a.idx < b.idx;
+  });
+  const size_t keep = std::min<size_t>((size_t)M, cand.size());
+  std::vector<int> kept(nb, 0);
+  D.discarded = 0.0;
+  for (size_t i = 0; i < cand.size(); ++i) {
+    if (i < keep) kept[cand[i].b]++;
+    else D.discarded += cand[i].s * cand[i].s;
+  }
+  // new basis: sectors of the growing side in ascending order
+  std::vector<std::pair<QN, int>> secs;  // (q, block)
+  for (int b = 0; b < nb; ++b)
+    if (kept[b] > 0) secs.push_back({forward ? p.L.basis.q[p.blocks[b].qL] : p.R.basis.q[p.blocks[b].qR], b});
+  std::sort(secs.begin(), secs.end(), [](const std::pair<QN, int>& a, const std::pair<QN, int>& b) {
+    return a.first < b.first;
+  });
+  D.nb = Basis();
+  D.esec_of_new.clear();
+  D.uoff.clear();
+  std::vector<TakeBlock> tb;
+  long long uo = 0;
+  for (auto& sb : secs) {
+    const int b = sb.second;
+    D.nb.q.push_back(sb.first);
+    D.nb.dim.push_back(kept[b]);
+    D.esec_of_new.push_back(forward ? p.blocks[b].qL : p.blocks[b].qR);
+    D.uoff.push_back(uo);
+    tb.push_back({gb[b].g_off, uo, gb[b].d, kept[b]});
+    uo += (long long)gb[b].d * kept[b];
+  }
+  D.nb.finish();
+  (void)E;
+  D.u.alloc(std::max<long long>(1, uo) * sizeof(double));
+  DevBuf dtb;
+  dtb.upload(tb, st);
+  launch_take_columns(Q.as<double>(), dtb.as<TakeBlock>(), (int)tb.size(), D.u.as<double>(), st);
+  DMRG_CUDA(cudaGetLastError());
+  DMRG_CUDA(cudaStreamSynchronize(st));
+}
+
+}  // namespace
+
+void sweep_build_blocks(Context& c, const double* t, const double* v, int K, int N, int two_sz, int M_init) {
+  if (K < 2 || K > 256) throw Error(DMRG_EINVAL, "K must be in [2, 256]");
+  if (M_init < 1) throw Error(DMRG_EINVAL, "M_init must be >= 1");
+  if (!can_hold(2 * K, {N, two_sz})) throw Error(DMRG_EINVAL, "N, 2Sz not reachable with K orbitals");
+  auto S = std::make_unique<SweepState>();
+  S->K = K;
+  S->Q = {N, two_sz};
+  S->I.K = K;
+  S->I.t.assign(t, t + (size_t)K * K);
+  S->I.v.assign(v, v + (size_t)K * K * K * K);
+  for (double x : S->I.t)
+    if (!std::isfinite(x)) throw Error(DMRG_EINVAL, "non-finite one-electron integral");
+  for (double x : S->I.v)
+    if (!std::isfinite(x)) throw Error(DMRG_EINVAL, "non-finite two-electron integral");
+  c.prob.reset();
+  cudaStream_t st = c.stream;
+  S->L.resize(K + 1);
+  S->R.resize(K + 1);
+  S->R[K] = vacuum(S->I, false, st);
+  S->L[0] = vacuum(S->I, true, st);
+  const uint64_t key = c.opts.seed ^ KEY_MPS;
+  unsigned long long counter = 0;
+  for (int j = K - 1; j >= 1; --j) {
+    const DevBlock& Rb = *S->R[j + 1];
+    Enlarged E = enlarge(Rb.set.basis);
+    OpSet EO;
+    build_nc_opset(EO, E.basis, 2 * j, 2 * K, false, 0);
+    DevBuf est;
+    est.alloc(std::max<long long>(1, EO.elements) * sizeof(double));
+    build_enlarged(c, S->I, Rb, j, false, E, EO, est.as<double>());
+    // kept sectors: those the left part (2j modes) can complement to the target
+    std::vector<int> comp;
+    long long D = 0;
+    for (int i = 0; i < E.basis.size(); ++i)
+      if (can_hold(2 * j, S->Q - E.basis.q[i])) {
+        comp.push_back(i);
+        D += E.basis.dim[i];
+      }
+    std::vector<int> m(comp.size());
+    if (D <= M_init) {
+      for (size_t a = 0; a < comp.size(); ++a) m[a] = E.basis.dim[comp[a]];
+    } else {
+      std::vector<double> exact(comp.size());
+      std::vector<long long> base(comp.size());
+      long long sum = 0;
+      for (size_t a = 0; a < comp.size(); ++a) {
+        exact[a] = (double)M_init * (double)E.basis.dim[comp[a]] / (double)D;
+        base[a] = (long long)std::floor(exact[a]);
+        sum += base[a];
+      }
+      std::vector<int> order(comp.size());
+      std::iota(order.begin(), order.end(), 0);
+      std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const double rx = exact[x] - (double)base[x], ry = exact[y] - (double)base[y];
+        if (rx != ry) return rx > ry;
+        return x < y;
+      });
+      for (long long a = 0; a < M_init - sum; ++a) base[order[a]] += 1;
+      for (size_t a = 0; a < comp.size(); ++a) m[a] = (int)base[a];
+    }
+    // random bases: counter-based normals, orthonormalised per sector
+    Decim Dm;
+    std::vector<GramBlock> gb;
+    long long uo = 0;
+    for (size_t a = 0; a < comp.size(); ++a) {
+      if (m[a] <= 0) continue;
+      const int d = E.basis.dim[comp[a]];
+      if (m[a] > 1024) throw Error(DMRG_EINVAL, "sector dimension above 1024 in the initial MPS");
+      Dm.nb.q.push_back(E.basis.q[comp[a]]);
+      Dm.nb.dim.push_back(m[a]);
+      Dm.esec_of_new.push_back(comp[a]);
+      Dm.uoff.push_back(uo);
+      gb.push_back({0, uo, 0, d, m[a]});
+      uo += (long long)d * m[a];
+    }
+    Dm.nb.finish();
+    Dm.u.alloc(std::max<long long>(1, uo) * sizeof(double));
+    launch_gen_vector(Dm.u.as<double>(), uo, key, counter, st);
+    counter += (unsigned long long)uo;
+    DevBuf dgb;
+    dgb.upload(gb, st);
+    {
+      ProfScope ps(c.prof, 3, st);
+      launch_orthonormalize(Dm.u.as<double>(), dgb.as<GramBlock>(), (int)gb.size(), st);
+    }
+    DMRG_CUDA(cudaGetLastError());
+    auto nbk = std::make_unique<DevBlock>();
+    transform(c, EO, est.as<double>(), Dm.nb, Dm.esec_of_new, Dm.uoff, Dm.u.as<double>(), *nbk, 2 * j, 2 * K, false);
+    S->R[j] = std::move(nbk);
+  }
+  c.sweep = std::move(S);
+}
+
+void sweep_run(Context& c, const int* Ms, int n_sweeps, double tol, double* energies, double* max_discard) {
+  if (!c.sweep) throw Error(DMRG_ESTATE, "call dmrg_build_blocks first");
+  SweepState& S = *c.sweep;
+  const int K = S.K;
+  S.log.clear();
+  for (int s = 0; s < n_sweeps; ++s) {
+    if (Ms[s] < 1) throw Error(DMRG_EINVAL, "bond dimension must be >= 1");
+    const bool fwd = (s % 2) == 0;
+    double emin = 1e300, dmax = 0.0;
+    for (int k = 0; k < K - 1; ++k) {
+      const int i = fwd ? k : K - 2 - k;
+      S.prob_site = -1;
+      sweep_problem(c, i);
+      Problem& p = *c.prob;
+      DevBuf x;
+      x.alloc(p.psi_size * sizeof(double));
+      double e = 0.0;
+      int it = 0;
+      const unsigned long long step_id = (unsigned long long)s * K + i;
+      const bool conv = run_davidson(c, p, nullptr, tol, &e, x.as<double>(), &it, step_id << 32);
+      emin = std::min(emin, e);
+      Decim D;
+      decimate(c, p, fwd ? S.EL : S.ER, x.as<double>(), Ms[s], fwd, D);
+      dmax = std::max(dmax, D.discarded);
+      int kept = 0;
+      for (int d : D.nb.dim) kept += d;
+      S.log.push_back({s, i, fwd ? 1 : 0, it, conv ? 1 : 0, kept, p.psi_size, e, D.discarded});
+      auto nbk = std::make_unique<DevBlock>();
+      if (fwd) {
+        transform(c, p.L, p.store.as<double>(), D.nb, D.esec_of_new, D.uoff, D.u.as<double>(), *nbk, 2 * (i + 1),
+                  2 * K, true);
+        S.L[i + 1] = std::move(nbk);
+      } else {
+        transform(c, p.R, p.store.as<double>(), D.nb, D.esec_of_new, D.uoff, D.u.as<double>(), *nbk, 2 * (i + 1),
+                  2 * K, false);
+        S.R[i + 1] = std::move(nbk);
+      }
+      c.prob.reset();
+      S.prob_site = -1;
+    }
+    if (energies) energies[s] = emin;
+    if (max_discard) max_discard[s] = dmax;
+  }
+}
+
+}  // namespace dmrg
