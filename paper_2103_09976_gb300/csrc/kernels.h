@@ -25,7 +25,7 @@ void launch_gen_vector(double* x, long long n, uint64_t key, unsigned long long 
 
 // ---------------------------------------------------------------- FP64 sigma
 constexpr int F64_TM = 32;    // output rows per tile
-constexpr int F64_TN = 320;   // output columns per tile (10 warp-wide groups)
+constexpr int F64_TN = 256;   // output columns per tile (32 groups of 8)
 
 struct SigmaDev {
   const double* store;        // operator store (FP64)

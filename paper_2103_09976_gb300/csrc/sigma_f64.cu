@@ -12,26 +12,37 @@
 // (Sec. II.D's final reduction), so sigma is bitwise deterministic whatever
 // the schedule of the items.
 //
-// The FP64 path is bound by the FP64 FMA rate, so the kernel keeps the
-// operands in shared memory and uses register micro-tiles (2x4 for the first
-// product, 4x10 for the second).
+// The FP64 path is bound by the FP64 multiply-add rate, which on this GPU
+// is the same for the FP64 tensor instruction (mma.sync m8n8k4 .f64: 256
+// multiply-adds per warp instruction) and for scalar FMAs. The tensor form
+// is used because its 8x8x4 granularity keeps padding small: every output
+// tile, intermediate chunk and contraction is padded only to multiples of 8
+// (rows, columns) and 4 (k), instead of to whole register micro-tiles.
+// Each warp owns a set of 8x8 sub-tiles of the output tile and of the
+// intermediate chunk; fragments come from shared memory.
 #include "kernels.h"
 
 namespace dmrg {
 
 namespace {
 
-constexpr int TM = F64_TM;    // 32 output rows
-constexpr int TN = F64_TN;    // up to 320 output columns
+constexpr int TM = F64_TM;    // 32 output rows (4 row groups of 8)
+constexpr int TN = F64_TN;    // up to 256 output columns (32 column groups)
 constexpr int NCH = 64;       // intermediate columns per chunk
-constexpr int KC = 16;        // k staging depth
-constexpr int NT = 256;       // threads
+constexpr int KC = 32;        // k staging depth of the first product
+constexpr int KC2 = 16;       // k staging depth of the second product
+constexpr int NT = 256;       // threads (8 warps)
+constexpr int NW = NT / 32;
+constexpr int XS = (TM / 8) * (NCH / 8) / NW;  // intermediate sub-tiles per warp (4)
+constexpr int SS = (TM / 8) * (TN / 8) / NW;   // output sub-tiles per warp (16)
 
+// Row strides = 4 (mod 16) doubles: a fragment load (8 rows x 4 k, or 4 k x
+// 8 columns) then touches every bank pair exactly twice.
 struct Smem {
-  double A[TM][KC + 1];       // left operator tile (rows x k)
-  double B[KC][NCH + 1];      // psi tile (k x chunk)
-  double X[TM][NCH + 1];      // intermediate chunk
-  double C[KC][TN + 1];       // right operator tile, k-major: C[k][j] = X_R(c0 + j, k)
+  double A[TM][KC + 4];       // left operator rows x k
+  double B[KC][NCH + 4];      // psi k x chunk columns
+  double X[TM][NCH + 4];      // intermediate rows x chunk columns
+  double C[KC2][TN + 4];      // right operator, k-major: C[k][j] = X_R(c0 + j, k)
   int item;
 };
 
@@ -41,14 +52,24 @@ __device__ __forceinline__ double ld_op(const double* __restrict__ base, long lo
   return trans ? base[aoff + (long long)k * rows + i] : base[aoff + (long long)i * cols + k];
 }
 
-__global__ void __launch_bounds__(NT, 1)
+// D = A(8x4) B(4x8) + D; lane (g = lane/4, c = lane%4) holds A[g][c],
+// B[c][g] and D[g][2c], D[g][2c+1].
+__device__ __forceinline__ void dmma(double (&d)[2], double a, double b) {
+  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+               : "+d"(d[0]), "+d"(d[1])
+               : "d"(a), "d"(b));
+}
+
+__device__ __forceinline__ int up8(int x) { return (x + 7) & ~7; }
+__device__ __forceinline__ int up4(int x) { return (x + 3) & ~3; }
+
+__global__ void __launch_bounds__(NT, 2)
 sigma_f64_kernel(SigmaDev a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  // step-1 micro-tile: rows 2*rp, 2*rp+1; cols cg + 16*j (j < 4)
-  const int rp = tid >> 4, cg = tid & 15;
+  const int g = lane >> 2, c = lane & 3;
 
   for (;;) {
     if (tid == 0) {
@@ -62,13 +83,12 @@ sigma_f64_kernel(SigmaDev a) {
     const Item it = a.items[it_idx];
     const PsiBlock ob = a.blocks[it.out];
     const int nr = it.nrows, ncol = it.ncols;
-    const int nj = (ncol + 31) >> 5;
+    const int nr8 = up8(nr), nrg = nr8 >> 3, ncg = up8(ncol) >> 3;
+    const int n_s = nrg * ncg;  // output sub-tiles of this item
 
-    double s[4][10];
+    double s[SS][2];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 10; ++j) s[i][j] = 0.0;
+    for (int q = 0; q < SS; ++q) s[q][0] = s[q][1] = 0.0;
 
     for (int t = it.t_begin; t < it.t_end; ++t) {
       const Task tk = a.tasks[t];
@@ -79,98 +99,102 @@ sigma_f64_kernel(SigmaDev a) {
       const double* __restrict__ psib = a.psi + ib.off;
 
       for (int nc0 = 0; nc0 < n; nc0 += NCH) {
-        // ---- step 1: X = scale * X_L[r0:r0+nr, :] * psi_b[:, nc0:nc0+NCH]
+        const int nch = min(NCH, n - nc0), nch8 = up8(nch), nch4 = up4(nch);
+        const int xcg = nch8 >> 3, n_x = nrg * xcg;
+        // ---- step 1: X = scale * X_L[r0:r0+nr, :] psi_b[:, nc0:nc0+nch]
         if (tk.aoff < 0) {
-          for (int e = tid; e < TM * NCH; e += NT) {
-            int i = e / NCH, j = e % NCH;
+          for (int e = tid; e < nr8 * nch8; e += NT) {
+            const int i = e / nch8, j = e % nch8;
             double v = 0.0;
-            if (i < nr && nc0 + j < n) v = psib[(long long)(it.r0 + i) * n + nc0 + j];
+            if (i < nr && j < nch) v = psib[(long long)(it.r0 + i) * n + nc0 + j];
             sm.X[i][j] = tk.scale * v;
           }
         } else {
-          double x[2][4];
+          double x[XS][2];
 #pragma unroll
-          for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) x[i][j] = 0.0;
+          for (int p = 0; p < XS; ++p) x[p][0] = x[p][1] = 0.0;
           for (int k0 = 0; k0 < m; k0 += KC) {
+            const int kc = min(KC, m - k0), kc4 = up4(kc);
             if (!tA) {
-              for (int e = tid; e < TM * KC; e += NT) {
-                int i = e / KC, kk = e % KC;
-                sm.A[i][kk] = (i < nr && k0 + kk < m)
-                                  ? ld_op(a.store, tk.aoff, false, mo, m, it.r0 + i, k0 + kk) : 0.0;
+              for (int e = tid; e < nr8 * kc4; e += NT) {
+                const int i = e / kc4, kk = e % kc4;
+                sm.A[i][kk] = (i < nr && kk < kc) ? ld_op(a.store, tk.aoff, false, mo, m, it.r0 + i, k0 + kk) : 0.0;
               }
             } else {
-              for (int e = tid; e < TM * KC; e += NT) {
-                int kk = e / TM, i = e % TM;
-                sm.A[i][kk] = (i < nr && k0 + kk < m)
-                                  ? ld_op(a.store, tk.aoff, true, mo, m, it.r0 + i, k0 + kk) : 0.0;
+              for (int e = tid; e < nr8 * kc4; e += NT) {
+                const int kk = e / nr8, i = e % nr8;
+                sm.A[i][kk] = (i < nr && kk < kc) ? ld_op(a.store, tk.aoff, true, mo, m, it.r0 + i, k0 + kk) : 0.0;
               }
             }
-            for (int e = tid; e < KC * NCH; e += NT) {
-              int kk = e / NCH, j = e % NCH;
-              sm.B[kk][j] = (k0 + kk < m && nc0 + j < n) ? psib[(long long)(k0 + kk) * n + nc0 + j] : 0.0;
+            for (int e = tid; e < kc4 * nch8; e += NT) {
+              const int kk = e / nch8, j = e % nch8;
+              sm.B[kk][j] = (kk < kc && j < nch) ? psib[(long long)(k0 + kk) * n + nc0 + j] : 0.0;
             }
             __syncthreads();
+            for (int kk = 0; kk < kc4; kk += 4) {
 #pragma unroll
-            for (int kk = 0; kk < KC; ++kk) {
-              double a0 = sm.A[2 * rp][kk], a1 = sm.A[2 * rp + 1][kk];
-#pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                double b = sm.B[kk][cg + 16 * j];
-                x[0][j] = fma(a0, b, x[0][j]);
-                x[1][j] = fma(a1, b, x[1][j]);
+              for (int p = 0; p < XS; ++p) {
+                const int sx = warp + NW * p;
+                if (sx < n_x) {
+                  const int rg = sx / xcg, cg = sx - rg * xcg;
+                  dmma(x[p], sm.A[rg * 8 + g][kk + c], sm.B[kk + c][cg * 8 + g]);
+                }
               }
             }
             __syncthreads();
           }
 #pragma unroll
-          for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) sm.X[2 * rp + i][cg + 16 * j] = tk.scale * x[i][j];
+          for (int p = 0; p < XS; ++p) {
+            const int sx = warp + NW * p;
+            if (sx < n_x) {
+              const int rg = sx / xcg, cg = sx - rg * xcg;
+              sm.X[rg * 8 + g][cg * 8 + 2 * c] = tk.scale * x[p][0];
+              sm.X[rg * 8 + g][cg * 8 + 2 * c + 1] = tk.scale * x[p][1];
+            }
+          }
         }
         __syncthreads();
 
-        // ---- step 2: S += X * X_R[c0:c0+ncol, nc0:nc0+NCH]^T
+        // ---- step 2: S += X X_R[c0:c0+ncol, nc0:nc0+nch]^T
         if (tk.boff < 0) {
-          // identity on the right: output columns = input columns
+          // identity on the right: output column j reads intermediate column j
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
+          for (int q = 0; q < SS; ++q) {
+            const int ss = warp + NW * q;
+            if (ss < n_s) {
+              const int rg = ss / ncg, cg = ss - rg * ncg;
 #pragma unroll
-            for (int j = 0; j < 10; ++j) {
-              int col = it.c0 + lane + 32 * j - nc0;
-              if (j < nj && col >= 0 && col < NCH) s[i][j] += sm.X[4 * warp + i][col];
+              for (int h = 0; h < 2; ++h) {
+                const int col = it.c0 + cg * 8 + 2 * c + h - nc0;
+                if (col >= 0 && col < nch) s[q][h] += sm.X[rg * 8 + g][col];
+              }
             }
+          }
         } else {
-          const int kend = min(NCH, n - nc0);
-          for (int kk0 = 0; kk0 < kend; kk0 += KC) {
+          const int nc8 = ncg * 8;
+          for (int k0 = 0; k0 < nch4; k0 += KC2) {
+            const int kc4 = min(KC2, nch4 - k0);
             if (!tB) {
-              for (int e = tid; e < TN * KC; e += NT) {
-                int j = e / KC, kk = e % KC;
-                int k = nc0 + kk0 + kk;
-                sm.C[kk][j] = (j < ncol && kk0 + kk < kend)
-                                  ? ld_op(a.store, tk.boff, false, no, n, it.c0 + j, k) : 0.0;
+              for (int e = tid; e < nc8 * kc4; e += NT) {
+                const int j = e / kc4, kk = e % kc4;
+                const int k = nc0 + k0 + kk;
+                sm.C[kk][j] = (j < ncol && k0 + kk < nch) ? ld_op(a.store, tk.boff, false, no, n, it.c0 + j, k) : 0.0;
               }
             } else {
-              for (int e = tid; e < TN * KC; e += NT) {
-                int kk = e / TN, j = e % TN;
-                int k = nc0 + kk0 + kk;
-                sm.C[kk][j] = (j < ncol && kk0 + kk < kend)
-                                  ? ld_op(a.store, tk.boff, true, no, n, it.c0 + j, k) : 0.0;
+              for (int e = tid; e < nc8 * kc4; e += NT) {
+                const int kk = e / nc8, j = e % nc8;
+                const int k = nc0 + k0 + kk;
+                sm.C[kk][j] = (j < ncol && k0 + kk < nch) ? ld_op(a.store, tk.boff, true, no, n, it.c0 + j, k) : 0.0;
               }
             }
             __syncthreads();
+            for (int kk = 0; kk < kc4; kk += 4) {
 #pragma unroll
-            for (int kk = 0; kk < KC; ++kk) {
-              double xa[4];
-#pragma unroll
-              for (int i = 0; i < 4; ++i) xa[i] = sm.X[4 * warp + i][kk0 + kk];
-#pragma unroll
-              for (int j = 0; j < 10; ++j) {
-                if (j < nj) {
-                  double c = sm.C[kk][lane + 32 * j];
-#pragma unroll
-                  for (int i = 0; i < 4; ++i) s[i][j] = fma(xa[i], c, s[i][j]);
+              for (int q = 0; q < SS; ++q) {
+                const int ss = warp + NW * q;
+                if (ss < n_s) {
+                  const int rg = ss / ncg, cg = ss - rg * ncg;
+                  dmma(s[q], sm.X[rg * 8 + g][k0 + kk + c], sm.C[kk + c][cg * 8 + g]);
                 }
               }
             }
@@ -183,12 +207,18 @@ sigma_f64_kernel(SigmaDev a) {
     // partial tile -> private scratch slot
     double* out = a.scratch + it.slot;
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int q = 0; q < SS; ++q) {
+      const int ss = warp + NW * q;
+      if (ss < n_s) {
+        const int rg = ss / ncg, cg = ss - rg * ncg;
+        const int r = rg * 8 + g;
 #pragma unroll
-      for (int j = 0; j < 10; ++j) {
-        int r = 4 * warp + i, c = lane + 32 * j;
-        if (r < nr && c < ncol) out[(long long)r * ncol + c] = s[i][j];
+        for (int h = 0; h < 2; ++h) {
+          const int col = cg * 8 + 2 * c + h;
+          if (r < nr && col < ncol) out[(long long)r * ncol + col] = s[q][h];
+        }
       }
+    }
   }
 }
 
@@ -215,7 +245,7 @@ void launch_sigma_f64(const SigmaDev& a, int n_sm, cudaStream_t st) {
     cudaFuncSetAttribute(sigma_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     attr = true;
   }
-  int grid = n_sm;
+  int grid = 2 * n_sm;  // two resident CTAs per SM overlap one's loads with the other's products
   if (grid > a.n_items) grid = a.n_items;
   if (grid < 1) grid = 1;
   sigma_f64_kernel<<<grid, NT, smem, st>>>(a);
