@@ -180,11 +180,21 @@ void build_tasks(const std::vector<PsiBlock>& blocks, const OpSet& L, const OpSe
   wl.schedule.clear();
 }
 
+// Cost of one task on one output tile as the FP64 kernel executes it: the
+// multiply-adds of its 8x8x4 tensor instructions (rows and columns padded to
+// 8, contractions to 4, the intermediate in 64-column chunks) plus a fixed
+// per-task latency term. Items are split and ordered (largest first) by it.
 static double tile_cost(const Task& k, const PsiBlock& in, int nr, int nc) {
-  double m = in.mL, n = in.mR;
-  if (k.aoff < 0) return 2.0 * nr * n * nc;
-  if (k.boff < 0) return 2.0 * nr * m * n;
-  return 2.0 * nr * m * n + 2.0 * nr * n * nc;
+  auto up8 = [](int x) { return (double)((x + 7) & ~7); };
+  auto up4 = [](int x) { return (double)((x + 3) & ~3); };
+  const double per_task = 16384.0;
+  double c = per_task;
+  for (int nc0 = 0; nc0 < in.mR; nc0 += 64) {
+    const int nch = std::min(64, in.mR - nc0);
+    if (k.aoff >= 0) c += 2.0 * up8(nr) * up4(in.mL) * up8(nch);
+    if (k.boff >= 0) c += 2.0 * up8(nr) * up4(nch) * up8(nc);
+  }
+  return c;
 }
 
 void build_items(const std::vector<PsiBlock>& blocks, WorkList& wl, const TileShape& ts,
