@@ -169,12 +169,29 @@ dmrg_status dmrg_sigma(dmrg_ctx* ctx, int site, const double* psi, double* sigma
 dmrg_status dmrg_sigma_noalloc(dmrg_ctx* ctx, int site, const double* psi, double* sigma);
 
 /*
+ * One sub-Hamiltonian's share of sigma (Sec. II.B, Eqs. sum-h, sub-h,
+ * proc-def, proc-def-nc): the terms of the NC sum are assigned to n_ranks
+ * ranks by their left-block spin-orbital indices: one index p -> p mod
+ * n_ranks; a pair p <= r -> (r(r+1)/2 + p) mod n_ranks (so O_pr and O_rp,
+ * and every conjugate pair, share a rank); H_L x 1 and 1 x H_R -> rank 0.
+ * sigma receives the FP64 sigma of rank `rank`'s terms only; the sum over
+ * ranks is the full sigma (one all-reduce of sigma in a multi-GPU setting,
+ * which this library does not perform). Arguments as dmrg_sigma.
+ * DMRG_EINVAL unless 0 <= rank < n_ranks.
+ */
+dmrg_status dmrg_sigma_part(dmrg_ctx* ctx, int site, int rank, int n_ranks, const double* psi, double* sigma);
+
+/*
  * Lowest eigenpair of H_eff at bond `site` by Davidson (Appendix A solving
  * step; details: diagonal preconditioner clamped at 1e-8, thick restart
  * from the two lowest Ritz vectors, converged when ||H x - E x||_2^2 < tol).
  * psi0 (may be NULL = seeded random guess) and psi_out (may be NULL): host
  * or device, psi_size doubles. *iters receives the number of sigma calls.
  * DMRG_ENOCONV when dav_max_iter is reached (energy and vector still set).
+ * With a mixed-precision sigma (DMRG_BF16X3 / DMRG_BF16X2) the iteration and
+ * its residual use that sigma, and the returned energy is the Rayleigh
+ * quotient of the final vector with one extra FP64 sigma (error second
+ * order in the vector's error instead of first order in the sigma's).
  */
 dmrg_status dmrg_davidson(dmrg_ctx* ctx, int site, const double* psi0, double tol, double* energy,
                           double* psi_out, int* iters);

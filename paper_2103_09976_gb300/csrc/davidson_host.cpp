@@ -146,6 +146,17 @@ bool run_davidson(Context& c, Problem& p, const double* x0, double tol, double* 
     ++k;
     update_H(k);
   }
+  if (c.opts.sigma_prec != DMRG_FP64) {
+    // The mixed-precision operator differs from H by a relative 1e-5 or so,
+    // which moves its eigenvalue at first order. The Rayleigh quotient of
+    // the final vector with the FP64 sigma is off only at second order in
+    // the vector's error, so it is the energy returned.
+    run_sigma_f64(c, p, x, ax);
+    dav_dots(x, n, 1, ax, n, part, s + 43, 1, st);
+    dav_dots(x, n, 1, x, n, part, s + 44, 1, st);
+    read2(s + 43, s + 44);
+    theta = host[0] / host[1];
+  }
   if (x_out) DMRG_CUDA(cudaMemcpyAsync(x_out, x, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
   DMRG_CUDA(cudaStreamSynchronize(st));
   check_device_error(c, p);
