@@ -85,6 +85,40 @@ def sigma_blocks(psi_vec, layout, terms, opsL, opsR, term_range=None):
     return blocks_to_psi(sig, layout, sum(m * n for _, _, m, n, _ in layout))
 
 
+# ------------------------------------------------- sub-Hamiltonian split
+def proc_one(i, P):
+    """Eq. proc-def, one index (0-based ranks and indices): i mod P."""
+    return i % P
+
+
+def proc_two(i, j, P):
+    """Eq. proc-def, two indices: the rank of the pair depends only on the
+    unordered pair {i, j}; with i <= j (1-based) it is (j-1)j/2 + i mod P,
+    i.e. j(j+1)/2 + i mod P for 0-based i <= j."""
+    lo, hi = min(i, j), max(i, j)
+    return (hi * (hi + 1) // 2 + lo) % P
+
+
+def nc_term_rank(term, P):
+    """Rank of one NC term under the NC partition of Eq. proc-def-nc, in
+    spin-orbital indices: a term's rank follows the left-block indices of its
+    left operator (a+_p, R^L_p: one index; A_pr, B_pq: the pair); the terms
+    H_L x 1 and 1 x H_R, which carry no pair, go to rank 0."""
+    kl = term[0]
+    if kl is None or kl == "H":
+        return 0
+    if kl[0] in ("cd", "RL"):
+        return proc_one(kl[1], P)
+    return proc_two(kl[1], kl[2], P)
+
+
+def sigma_part(psi_vec, layout, terms, opsL, opsR, rank, P):
+    """sigma of sub-Hamiltonian `rank` of P (Sec. II.B, Eq. sum-h): the terms
+    that nc_term_rank assigns to it."""
+    mine = [t for t in terms if nc_term_rank(t, P) == rank]
+    return sigma_blocks(psi_vec, layout, mine, opsL, opsR)
+
+
 def heff_diagonal(layout, terms, opsL, opsR):
     """Diagonal of H_eff (terms whose left and right shifts are both zero)."""
     size = sum(m * n for _, _, m, n, _ in layout)

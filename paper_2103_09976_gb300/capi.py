@@ -58,6 +58,7 @@ SIGNATURES = {
     "dmrg_build_blocks": (_I, [_P, _P, _P, _I, _I, _I, _I]),
     "dmrg_sweep": (_I, [_P, _P, _I, _D, _P, _P]),
     "dmrg_sweep_log": (_I, [_P, _P, _I, _P]),
+    "dmrg_sigma_part": (_I, [_P, _I, _I, _I, _P, _P]),
     "dmrg_block_info": (_I, [_P, _I, _I, _P, _P, _P, _P]),
     "dmrg_block_read": (_I, [_P, _I, _I, _I, _P]),
     "dmrg_sync": (_I, [_P]),
@@ -176,6 +177,11 @@ def dmrg_get_sigma_info(ctx, site=-1):
 
 def dmrg_sigma(ctx, site, psi, sigma):
     _check(ctx, lib().dmrg_sigma(ctx, site, _ptr(psi), _ptr(sigma)))
+
+
+def dmrg_sigma_part(ctx, site, rank, n_ranks, psi, sigma):
+    """FP64 sigma of the NC terms owned by sub-Hamiltonian `rank` of `n_ranks`."""
+    _check(ctx, lib().dmrg_sigma_part(ctx, site, rank, n_ranks, _ptr(psi), _ptr(sigma)))
 
 
 def dmrg_sigma_noalloc(ctx, site, psi, sigma):

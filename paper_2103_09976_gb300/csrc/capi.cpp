@@ -189,10 +189,13 @@ static void run_sigma_tc(Context& c, Problem& p, const double* d_psi, double* d_
 }
 
 void run_sigma(Context& c, Problem& p, const double* d_psi, double* d_sigma) {
-  if (c.opts.sigma_prec != DMRG_FP64) {
+  if (c.opts.sigma_prec != DMRG_FP64)
     run_sigma_tc(c, p, d_psi, d_sigma);
-    return;
-  }
+  else
+    run_sigma_f64(c, p, d_psi, d_sigma);
+}
+
+void run_sigma_f64(Context& c, Problem& p, const double* d_psi, double* d_sigma) {
   SigmaDev a;
   a.store = p.store.as<double>();
   a.psi = d_psi;
@@ -215,6 +218,53 @@ void run_sigma(Context& c, Problem& p, const double* d_psi, double* d_sigma) {
   {
     ProfScope ps(c.prof, 1, c.stream);
     launch_reduce(a, c.stream);
+  }
+  DMRG_CUDA(cudaGetLastError());
+}
+
+void run_sigma_part(Context& c, Problem& p, int rank, int n_ranks, const double* d_psi, double* d_sigma) {
+  auto& slot = p.parts[{n_ranks, rank}];
+  cudaStream_t st = c.stream;
+  if (!slot) {
+    auto w = std::make_unique<DevWork>();
+    const std::vector<int> ranks = nc_term_ranks(p.nL, p.n, n_ranks);
+    std::vector<Term> mine;
+    for (size_t t = 0; t < p.terms.size(); ++t)
+      if (ranks[t] == rank) mine.push_back(p.terms[t]);
+    build_tasks(p.blocks, p.L, p.R, mine, w->wl);
+    build_items(p.blocks, w->wl, TileShape{F64_TM, F64_TN, 2e6}, c.n_sm * 8);
+    w->d_tasks.upload(w->wl.tasks, st);
+    w->d_items.upload(w->wl.items, st);
+    w->d_groups.upload(w->wl.groups, st);
+    w->d_sched.upload(w->wl.schedule, st);
+    w->d_scratch.alloc(std::max<long long>(1, w->wl.scratch_elems) * sizeof(double));
+    w->d_counter.alloc(16);
+    DMRG_CUDA(cudaStreamSynchronize(st));
+    slot = std::move(w);
+  }
+  DevWork& w = *slot;
+  SigmaDev a;
+  a.store = p.store.as<double>();
+  a.psi = d_psi;
+  a.sigma = d_sigma;
+  a.tasks = w.d_tasks.as<Task>();
+  a.items = w.d_items.as<Item>();
+  a.schedule = w.d_sched.as<int>();
+  a.n_items = (int)w.wl.items.size();
+  a.groups = w.d_groups.as<Group>();
+  a.n_groups = (int)w.wl.groups.size();
+  a.blocks = p.d_blocks.as<PsiBlock>();
+  a.scratch = w.d_scratch.as<double>();
+  a.counter = w.d_counter.as<unsigned int>();
+  DMRG_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), st));
+  {
+    ProfScope ps(c.prof, 0, st);
+    launch_sigma_f64(a, c.n_sm, st);
+  }
+  DMRG_CUDA(cudaGetLastError());
+  {
+    ProfScope ps(c.prof, 1, st);
+    launch_reduce(a, st);
   }
   DMRG_CUDA(cudaGetLastError());
 }
@@ -273,6 +323,38 @@ Profiler::~Profiler() {
   for (auto e : pool) cudaEventDestroy(e);
 }
 
+}  // namespace dmrg
+
+namespace dmrg {
+namespace {
+// Host/device marshalling shared by the sigma entry points: stage host
+// buffers through the context's device copies around `compute`.
+template <class F>
+void sigma_call(Context& c, Problem& p, const double* psi, double* sigma, F compute) {
+  if (!psi || !sigma) throw Error(DMRG_EINVAL, "psi and sigma must not be NULL");
+  const size_t bytes = (size_t)p.psi_size * sizeof(double);
+  const char* a0 = (const char*)psi;
+  const char* b0 = (const char*)sigma;
+  if (a0 < b0 + bytes && b0 < a0 + bytes) throw Error(DMRG_EINVAL, "psi and sigma overlap");
+  bool dpsi = is_device_ptr(psi), dsig = is_device_ptr(sigma);
+  const double* xin = psi;
+  double* yout = sigma;
+  if (!dpsi) {
+    c.d_psi.alloc(bytes);
+    DMRG_CUDA(cudaMemcpyAsync(c.d_psi.p, psi, bytes, cudaMemcpyHostToDevice, c.stream));
+    xin = c.d_psi.as<double>();
+  }
+  if (!dsig) {
+    c.d_sigma.alloc(bytes);
+    yout = c.d_sigma.as<double>();
+  }
+  compute(xin, yout);
+  if (!dsig) {
+    DMRG_CUDA(cudaMemcpyAsync(sigma, yout, bytes, cudaMemcpyDeviceToHost, c.stream));
+    check_device_error(c, p);
+  }
+}
+}  // namespace
 }  // namespace dmrg
 
 extern "C" {
@@ -430,34 +512,25 @@ dmrg_status dmrg_get_sigma_info(dmrg_ctx* ctx, int site, dmrg_sigma_info* info) 
   });
 }
 
+
 dmrg_status dmrg_sigma(dmrg_ctx* ctx, int site, const double* psi, double* sigma) {
   if (!ctx) return DMRG_EINVAL;
   return guarded(ctx, [&] {
     Context& c = ctx->c;
     DMRG_CUDA(cudaSetDevice(c.device));
     Problem& p = need_problem(c, site);
-    if (!psi || !sigma) throw Error(DMRG_EINVAL, "psi and sigma must not be NULL");
-    const size_t bytes = (size_t)p.psi_size * sizeof(double);
-    const char* a0 = (const char*)psi;
-    const char* b0 = (const char*)sigma;
-    if (a0 < b0 + bytes && b0 < a0 + bytes) throw Error(DMRG_EINVAL, "psi and sigma overlap");
-    bool dpsi = is_device_ptr(psi), dsig = is_device_ptr(sigma);
-    const double* xin = psi;
-    double* yout = sigma;
-    if (!dpsi) {
-      c.d_psi.alloc(bytes);
-      DMRG_CUDA(cudaMemcpyAsync(c.d_psi.p, psi, bytes, cudaMemcpyHostToDevice, c.stream));
-      xin = c.d_psi.as<double>();
-    }
-    if (!dsig) {
-      c.d_sigma.alloc(bytes);
-      yout = c.d_sigma.as<double>();
-    }
-    run_sigma(c, p, xin, yout);
-    if (!dsig) {
-      DMRG_CUDA(cudaMemcpyAsync(sigma, yout, bytes, cudaMemcpyDeviceToHost, c.stream));
-      check_device_error(c, p);
-    }
+    sigma_call(c, p, psi, sigma, [&](const double* x, double* y) { run_sigma(c, p, x, y); });
+  });
+}
+
+dmrg_status dmrg_sigma_part(dmrg_ctx* ctx, int site, int rank, int n_ranks, const double* psi, double* sigma) {
+  if (!ctx) return DMRG_EINVAL;
+  return guarded(ctx, [&] {
+    Context& c = ctx->c;
+    if (n_ranks < 1 || rank < 0 || rank >= n_ranks) throw Error(DMRG_EINVAL, "need 0 <= rank < n_ranks");
+    DMRG_CUDA(cudaSetDevice(c.device));
+    Problem& p = need_problem(c, site);
+    sigma_call(c, p, psi, sigma, [&](const double* x, double* y) { run_sigma_part(c, p, rank, n_ranks, x, y); });
   });
 }
 

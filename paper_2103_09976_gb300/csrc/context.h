@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <map>
 #include <memory>
 #include <string>
 #include <vector>
@@ -54,6 +55,12 @@ struct DevBuf {
 
 // A two-site problem: left/right operator tables over one FP64 store
 // (left ops first), the psi layout, NC terms and the sigma work list.
+// A work list and its device copies (the full sigma, or one sub-Hamiltonian part).
+struct DevWork {
+  WorkList wl;
+  DevBuf d_tasks, d_items, d_groups, d_sched, d_scratch, d_counter;
+};
+
 struct Problem {
   int nL = 0, n = 0;
   QN Q;
@@ -75,6 +82,8 @@ struct Problem {
   DevBuf d_dstart, d_dtask;
   DevBuf split, psi_split;         // slice-interleaved bf16 tiles of the operators / of psi
   DevBuf d_tc_recs, d_tc_item_rec, d_tc_items, d_tc_groups, d_tc_sched, d_tc_pblk, d_tc_scratch, d_err;
+  // sub-Hamiltonian parts: (n_ranks, rank) -> work list of that rank's terms
+  std::map<std::pair<int, int>, std::unique_ptr<DevWork>> parts;
 };
 
 // CUDA-event timing of kernel launches (dmrg_profile).
@@ -136,7 +145,10 @@ void sweep_block_read(Context& c, int side, int j, int op, double* dense);
 // eigenvector in x_out (device, may be null). Returns false if not converged.
 bool run_davidson(Context& c, Problem& p, const double* x0, double tol, double* energy, double* x_out,
                   int* iters, unsigned long long guess_counter_base);
-void run_sigma(Context& c, Problem& p, const double* d_psi, double* d_sigma);
+void run_sigma(Context& c, Problem& p, const double* d_psi, double* d_sigma);      // context precision
+void run_sigma_f64(Context& c, Problem& p, const double* d_psi, double* d_sigma);  // always FP64
+// FP64 sigma of the terms that sub-Hamiltonian rank `rank` of n_ranks owns
+void run_sigma_part(Context& c, Problem& p, int rank, int n_ranks, const double* d_psi, double* d_sigma);
 
 }  // namespace dmrg
 

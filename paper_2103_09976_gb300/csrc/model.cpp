@@ -94,6 +94,25 @@ std::vector<Term> nc_terms(int nL, int n) {
   return T;
 }
 
+std::vector<int> nc_term_ranks(int nL, int n, int n_ranks) {
+  // same enumeration order as nc_terms
+  std::vector<int> r;
+  auto one = [&](int p) { return p % n_ranks; };
+  auto two = [&](int p, int q) {
+    const int i = std::min(p, q), j = std::max(p, q);
+    return (int)(((long long)j * (j + 1) / 2 + i) % n_ranks);
+  };
+  r.push_back(0);
+  r.push_back(0);
+  for (int p = 0; p < nL; ++p) r.insert(r.end(), 2, one(p));
+  for (int p = nL; p < n; ++p) r.insert(r.end(), 2, one(p));
+  for (int p = 0; p < nL; ++p)
+    for (int q = p + 1; q < nL; ++q) r.insert(r.end(), 2, two(p, q));
+  for (int p = 0; p < nL; ++p)
+    for (int q = 0; q < nL; ++q) r.push_back(two(p, q));
+  return r;
+}
+
 std::vector<PsiBlock> psi_layout(const Basis& L, const Basis& R, QN Qtot, long long* size) {
   std::vector<PsiBlock> out;
   long long off = 0;

@@ -100,6 +100,12 @@ struct Term {
   int parR;         // fermion parity of the right operator
 };
 std::vector<Term> nc_terms(int nL, int n);
+// Sub-Hamiltonian rank of every term of nc_terms(nL, n) among n_ranks
+// (Sec. II.B, Eqs. proc-def and proc-def-nc in spin-orbital indices): terms
+// with one left index p go to p mod P; terms with a left pair p <= r to
+// (r(r+1)/2 + p) mod P, so O_pr and O_rp always share a rank; H_L x 1 and
+// 1 x H_R go to rank 0.
+std::vector<int> nc_term_ranks(int nL, int n, int n_ranks);
 
 struct PsiBlock {
   int qL, qR;       // sector indices in the left / right basis

@@ -41,7 +41,7 @@ def _layout_matches(lay_gpu, lay_oracle):
     (24, 3, 6, 1),        # tiny: single tile per block
     (120, 4, 8, 2),       # 25 sectors, blocks up to 9
     (1200, 3, 6, 3),      # blocks up to 107: several 32-row tiles and 64-column chunks, ragged tails
-    (4000, 3, 6, 4),      # blocks up to 355: several 320-column tiles
+    (4000, 3, 6, 4),      # blocks up to 355: several 256-column tiles
 ])
 def test_sigma_fp64_matches_oracle(capi, M, nsp, ntot, seed):
     from synth import gaussian_sector_dims, mirrored_sectors, random_unit_vector
