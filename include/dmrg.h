@@ -249,6 +249,53 @@ typedef struct dmrg_step_log {
 dmrg_status dmrg_sweep_log(dmrg_ctx* ctx, dmrg_step_log* out, int max_steps, int* n_steps);
 
 /*
+ * Serving: continuous batching of Davidson solves on one GPU (the paper
+ * has no serving layer; this runs many independent Eq. eff-eigsh solves).
+ * A request is a middle-bond problem with synthetic operator blocks (as
+ * dmrg_load_synthetic: spin-orbital counts, target N / 2Sz, (N, 2Sz, dim)
+ * sector triples, seed) plus precision, Davidson tolerance and sigma-call
+ * limit. dmrg_server_submit copies the request, estimates its device
+ * footprint and queues it (DMRG_ENOMEM if the footprint exceeds the
+ * budget, DMRG_EINVAL for a malformed request). n_slots worker threads,
+ * each with its own context and stream, admit the oldest queued request
+ * whose footprint fits in the unused budget (a request passed over four
+ * times blocks later ones until it fits), build its operators on the
+ * device, solve, free them and post a result. dmrg_server_poll moves up to
+ * max_results finished results to `out` (host), waiting up to wait_ms for
+ * the first, and returns how many. Times are seconds since creation.
+ * dmrg_server_destroy drops queued requests, waits for running ones and
+ * frees everything. One thread at a time may call submit/poll/destroy on a
+ * server.
+ */
+typedef struct dmrg_server dmrg_server;
+typedef struct dmrg_request {
+  long long id;                          /* caller's tag, copied to the result */
+  int n_left_modes, n_modes, N, two_sz;  /* as dmrg_load_synthetic */
+  int n_sec_left;
+  const int* sec_left;
+  int n_sec_right;
+  const int* sec_right;
+  unsigned long long seed;               /* operator blocks and Davidson guess */
+  int sigma_prec;                        /* dmrg_prec */
+  int max_iter;                          /* Davidson sigma-call limit */
+  double tol;                            /* Davidson tolerance on ||r||^2 */
+} dmrg_request;
+typedef struct dmrg_result {
+  long long id;
+  int status;                            /* dmrg_status of the solve */
+  int iters, converged, slot;
+  double energy;
+  double t_submit, t_admit, t_done;
+  long long bytes;                       /* admitted footprint */
+} dmrg_result;
+dmrg_status dmrg_server_create(dmrg_server** out, int device, int n_slots, long long budget_bytes);
+dmrg_status dmrg_server_submit(dmrg_server* s, const dmrg_request* r);
+int dmrg_server_poll(dmrg_server* s, dmrg_result* out, int max_results, int wait_ms);
+dmrg_status dmrg_server_pending(dmrg_server* s, int* queued, int* running, long long* bytes_in_use);
+const char* dmrg_server_last_error(dmrg_server* s);
+void dmrg_server_destroy(dmrg_server* s);
+
+/*
  * Per-kernel timing with CUDA events recorded on the context's stream
  * around each launch of the library's kernels (tracing aid; off by default).
  * dmrg_profile(ctx, 1) clears the counters and starts recording; 0 stops.

@@ -27,6 +27,7 @@ SOURCES = [
     "davidson_host.cpp",
     "blocking.cu",
     "sweep.cpp",
+    "server.cpp",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

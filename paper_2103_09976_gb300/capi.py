@@ -38,6 +38,21 @@ class DMRGError(RuntimeError):
         self.status = status
 
 
+class dmrg_request(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_longlong), ("n_left_modes", ctypes.c_int), ("n_modes", ctypes.c_int),
+                ("N", ctypes.c_int), ("two_sz", ctypes.c_int), ("n_sec_left", ctypes.c_int),
+                ("sec_left", ctypes.c_void_p), ("n_sec_right", ctypes.c_int), ("sec_right", ctypes.c_void_p),
+                ("seed", ctypes.c_ulonglong), ("sigma_prec", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("tol", ctypes.c_double)]
+
+
+class dmrg_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_longlong), ("status", ctypes.c_int), ("iters", ctypes.c_int),
+                ("converged", ctypes.c_int), ("slot", ctypes.c_int), ("energy", ctypes.c_double),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("bytes", ctypes.c_longlong)]
+
+
 _lib = None
 
 # C signatures: name -> (restype, argtypes)
@@ -65,6 +80,12 @@ SIGNATURES = {
     "dmrg_profile": (_I, [_P, _I]),
     "dmrg_profile_read": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_LL)]),
     "dmrg_profile_waits": (_I, [_P, _P, _I]),
+    "dmrg_server_create": (_I, [ctypes.POINTER(_P), _I, _I, _LL]),
+    "dmrg_server_submit": (_I, [_P, ctypes.POINTER(dmrg_request)]),
+    "dmrg_server_poll": (_I, [_P, _P, _I, _I]),
+    "dmrg_server_pending": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_LL)]),
+    "dmrg_server_last_error": (ctypes.c_char_p, [_P]),
+    "dmrg_server_destroy": (None, [_P]),
 }
 
 
@@ -273,3 +294,48 @@ def dmrg_profile_waits(ctx):
     buf = np.zeros(17)
     _check(ctx, lib().dmrg_profile_waits(ctx, _ptr(buf), 17))
     return buf
+
+
+# ------------------------------------------------------------------ serving
+def _scheck(srv, st):
+    if st != DMRG_OK:
+        raise DMRGError(st, lib().dmrg_server_last_error(srv).decode())
+
+
+def dmrg_server_create(device=0, n_slots=4, budget_bytes=200 << 30):
+    h = ctypes.c_void_p()
+    st = lib().dmrg_server_create(ctypes.byref(h), device, n_slots, int(budget_bytes))
+    if st != DMRG_OK:
+        raise DMRGError(st, "dmrg_server_create failed")
+    return h.value
+
+
+def dmrg_server_submit(srv, req_id, n_left_modes, n_modes, N, two_sz, left, right, seed,
+                       sigma_prec=DMRG_FP64, max_iter=200, tol=1e-8):
+    """Queue one Davidson solve; left/right are (N, 2Sz, dim) sector lists."""
+    L = np.ascontiguousarray(np.array(left, dtype=np.int32).reshape(-1, 3))
+    R = np.ascontiguousarray(np.array(right, dtype=np.int32).reshape(-1, 3))
+    r = dmrg_request(req_id, n_left_modes, n_modes, N, two_sz, len(L), L.ctypes.data, len(R), R.ctypes.data,
+                     seed, sigma_prec, max_iter, float(tol))
+    _scheck(srv, lib().dmrg_server_submit(srv, ctypes.byref(r)))
+
+
+def dmrg_server_poll(srv, max_results=64, wait_ms=0):
+    """Finished results as a list of dicts."""
+    buf = (dmrg_result * max_results)()
+    n = lib().dmrg_server_poll(srv, buf, max_results, int(wait_ms))
+    return [{f: getattr(buf[k], f) for f, _ in dmrg_result._fields_} for k in range(n)]
+
+
+def dmrg_server_pending(srv):
+    q, r, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+    _scheck(srv, lib().dmrg_server_pending(srv, ctypes.byref(q), ctypes.byref(r), ctypes.byref(b)))
+    return q.value, r.value, b.value
+
+
+def dmrg_server_last_error(srv):
+    return lib().dmrg_server_last_error(srv).decode()
+
+
+def dmrg_server_destroy(srv):
+    lib().dmrg_server_destroy(srv)

@@ -10,6 +10,19 @@
 
 using namespace dmrg;
 
+Basis dmrg::parse_sectors(int n, const int* s) {
+  if (n <= 0 || !s) throw Error(DMRG_EINVAL, "empty sector list");
+  Basis b;
+  for (int i = 0; i < n; ++i) {
+    b.q.push_back({s[3 * i], s[3 * i + 1]});
+    b.dim.push_back(s[3 * i + 2]);
+    if ((s[3 * i + 1] - s[3 * i]) % 2 != 0) throw Error(DMRG_EINVAL, "2Sz parity must match N");
+  }
+  b.finish();
+  return b;
+}
+
+
 namespace {
 
 thread_local std::string g_noctx_err = "no error";
@@ -41,17 +54,6 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-Basis parse_sectors(int n, const int* s) {
-  if (n <= 0 || !s) throw Error(DMRG_EINVAL, "empty sector list");
-  Basis b;
-  for (int i = 0; i < n; ++i) {
-    b.q.push_back({s[3 * i], s[3 * i + 1]});
-    b.dim.push_back(s[3 * i + 2]);
-    if ((s[3 * i + 1] - s[3 * i]) % 2 != 0) throw Error(DMRG_EINVAL, "2Sz parity must match N");
-  }
-  b.finish();
-  return b;
-}
 
 Problem& need_problem(Context& c, int site) {
   if (c.sweep) {
@@ -357,6 +359,69 @@ void sigma_call(Context& c, Problem& p, const double* psi, double* sigma, F comp
 }  // namespace
 }  // namespace dmrg
 
+namespace dmrg {
+
+// Middle-bond problem with synthetic operators: sector tables, NC operator
+// tables and terms on the host, every stored block drawn on the device.
+static void build_synthetic_tables(Problem& p, int nL, int n, int N, int two_sz, const Basis& bL,
+                                   const Basis& bR) {
+  if (nL <= 0 || n <= nL || nL % 2 || n % 2)
+    throw Error(DMRG_EINVAL, "mode counts must be even with 0 < n_left_modes < n_modes");
+  p.nL = nL;
+  p.n = n;
+  p.Q = {N, two_sz};
+  build_nc_opset(p.L, bL, nL, n, true, 0);
+  build_nc_opset(p.R, bR, nL, n, false, p.L.elements);
+  p.terms = nc_terms(nL, n);
+  p.blocks = psi_layout(bL, bR, p.Q, &p.psi_size);
+  if (p.blocks.empty()) throw Error(DMRG_EINVAL, "no psi block: sectors cannot form the target");
+  for (auto& b : p.blocks)
+    if (b.mR > F64_TN * 64 || b.mL > (1 << 20)) throw Error(DMRG_EINVAL, "block too large");
+}
+
+void load_synthetic(Context& c, int nL, int n, int N, int two_sz, const Basis& bL, const Basis& bR,
+                    unsigned long long seed) {
+  auto p = std::make_unique<Problem>();
+  build_synthetic_tables(*p, nL, n, N, two_sz, bL, bR);
+  long long elems = p->L.elements + p->R.elements;
+  size_t freeb = 0, totb = 0;
+  DMRG_CUDA(cudaMemGetInfo(&freeb, &totb));
+  if ((double)elems * 8.0 > 0.92 * (double)freeb)
+    throw Error(DMRG_ENOMEM, "operator store (" + std::to_string(elems * 8.0 / 1e9) +
+                                 " GB) does not fit in free device memory");
+  c.prob.reset();
+  c.sweep.reset();
+  p->store.alloc((size_t)elems * sizeof(double));
+  // generate every stored block on the device
+  std::vector<GenBlock> gb;
+  for (const OpSet* s : {&p->L, &p->R})
+    for (const OpDesc& o : s->ops)
+      for (const OpBlock& b : o.blocks) gb.push_back({b.off, b.rows, b.cols, o.sym ? 1 : 0, 0});
+  DevBuf d_gb;
+  d_gb.upload(gb, c.stream);
+  launch_gen_blocks(p->store.as<double>(), d_gb.as<GenBlock>(), (long long)gb.size(), (uint64_t)seed, c.stream);
+  DMRG_CUDA(cudaGetLastError());
+  DMRG_CUDA(cudaStreamSynchronize(c.stream));
+  prepare_worklist(c, *p);
+  c.prob = std::move(p);
+}
+
+long long synthetic_footprint(int nL, int n, int N, int two_sz, const Basis& bL, const Basis& bR, int prec,
+                              int dav_space, int n_sm) {
+  Problem p;
+  build_synthetic_tables(p, nL, n, N, two_sz, bL, bR);
+  const double elems = (double)(p.L.elements + p.R.elements);
+  const double psi = (double)p.psi_size;
+  double bytes = 8.0 * elems;                                  // FP64 store
+  bytes += 8.0 * (2.0 * psi + (double)F64_TM * F64_TN * n_sm * 8);  // partial-tile scratch (bound)
+  bytes += 8.0 * psi * (2.0 * dav_space + 8.0);               // Davidson vectors and staging
+  if (prec != DMRG_FP64) bytes += 6.0 * elems * 1.5 + 6.0 * psi * 2.0 + 8.0 * psi * 4.0;  // bf16 slices
+  bytes += 64.0 * (1 << 20);                                   // tables, work lists, slack
+  return (long long)bytes;
+}
+
+}  // namespace dmrg
+
 extern "C" {
 
 void dmrg_default_opts(dmrg_opts* o) {
@@ -439,43 +504,8 @@ dmrg_status dmrg_load_synthetic(dmrg_ctx* ctx, int n_left_modes, int n_modes, in
   return guarded(ctx, [&] {
     Context& c = ctx->c;
     DMRG_CUDA(cudaSetDevice(c.device));
-    if (n_left_modes <= 0 || n_modes <= n_left_modes || n_left_modes % 2 || n_modes % 2)
-      throw Error(DMRG_EINVAL, "mode counts must be even with 0 < n_left_modes < n_modes");
-    auto p = std::make_unique<Problem>();
-    p->nL = n_left_modes;
-    p->n = n_modes;
-    p->Q = {N, two_sz};
-    Basis bL = parse_sectors(n_sec_left, sec_left);
-    Basis bR = parse_sectors(n_sec_right, sec_right);
-    build_nc_opset(p->L, bL, n_left_modes, n_modes, true, 0);
-    build_nc_opset(p->R, bR, n_left_modes, n_modes, false, p->L.elements);
-    p->terms = nc_terms(n_left_modes, n_modes);
-    p->blocks = psi_layout(bL, bR, p->Q, &p->psi_size);
-    if (p->blocks.empty()) throw Error(DMRG_EINVAL, "no psi block: sectors cannot form the target");
-    for (auto& b : p->blocks)
-      if (b.mR > F64_TN * 64 || b.mL > (1 << 20)) throw Error(DMRG_EINVAL, "block too large");
-    long long elems = p->L.elements + p->R.elements;
-    size_t freeb = 0, totb = 0;
-    DMRG_CUDA(cudaMemGetInfo(&freeb, &totb));
-    if ((double)elems * 8.0 > 0.92 * (double)freeb)
-      throw Error(DMRG_ENOMEM, "operator store (" + std::to_string(elems * 8.0 / 1e9) +
-                                   " GB) does not fit in free device memory");
-    c.prob.reset();
-    c.sweep.reset();
-    p->store.alloc((size_t)elems * sizeof(double));
-    // generate every stored block on the device
-    std::vector<GenBlock> gb;
-    for (const OpSet* s : {&p->L, &p->R})
-      for (const OpDesc& o : s->ops)
-        for (const OpBlock& b : o.blocks) gb.push_back({b.off, b.rows, b.cols, o.sym ? 1 : 0, 0});
-    DevBuf d_gb;
-    d_gb.upload(gb, c.stream);
-    launch_gen_blocks(p->store.as<double>(), d_gb.as<GenBlock>(), (long long)gb.size(),
-                      (uint64_t)seed, c.stream);
-    DMRG_CUDA(cudaGetLastError());
-    DMRG_CUDA(cudaStreamSynchronize(c.stream));
-    prepare_worklist(c, *p);
-    c.prob = std::move(p);
+    load_synthetic(c, n_left_modes, n_modes, N, two_sz, parse_sectors(n_sec_left, sec_left),
+                   parse_sectors(n_sec_right, sec_right), seed);
   });
 }
 

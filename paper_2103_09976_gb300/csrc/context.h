@@ -132,6 +132,12 @@ struct Context {
 };
 
 void prepare_worklist(Context& c, Problem& p);
+Basis parse_sectors(int n, const int* s);
+void load_synthetic(Context& c, int nL, int n, int N, int two_sz, const Basis& bL, const Basis& bR,
+                    unsigned long long seed);
+// Device bytes a synthetic problem needs for one Davidson solve (an upper estimate).
+long long synthetic_footprint(int nL, int n, int N, int two_sz, const Basis& bL, const Basis& bR, int prec,
+                              int dav_space, int n_sm);
 void prepare_tc(Context& c, Problem& p);
 void check_device_error(Context& c, Problem& p);
 void sigma_noalloc(Context& c, Problem& p, const double* psi, double* sigma);

@@ -57,6 +57,15 @@ def test_create_without_gpu_fails_cleanly(libpath):
     assert e.value.status in (capi.DMRG_ECUDA, capi.DMRG_EINVAL)
 
 
+def test_server_create_without_gpu_fails_cleanly(libpath):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2103_09976_gb300 import capi
+    with pytest.raises(capi.DMRGError):
+        capi.dmrg_server_create(0, 2, 1 << 30)
+
+
 def test_default_opts(libpath):
     from paper_2103_09976_gb300 import capi
     o = capi.dmrg_default_opts()
