@@ -66,9 +66,13 @@ typedef struct {
   double noise;                /* reserved, must be 0 */
   unsigned long long seed;     /* seed of the counter-based random streams (initial MPS, guesses) */
   int device;                  /* CUDA device ordinal */
+  int graphs;                  /* 1: replay each sigma's launches (counter reset, product kernel,
+                                  reduction; psi split for the tensor-core path) as a CUDA graph
+                                  captured on the second call with the same psi / sigma pointers;
+                                  0: launch them one by one. Profiling always launches directly. */
 } dmrg_opts;
 
-/* Fill *o with defaults: FP64, 24, 200, 0, 0.0, seed 0, device 0. */
+/* Fill *o with defaults: FP64, 24, 200, 0, 0.0, seed 0, device 0, graphs 1. */
 void dmrg_default_opts(dmrg_opts* o);
 
 /* Create a context on opts->device (NULL opts = defaults). *out is NULL on failure. */
@@ -167,6 +171,20 @@ dmrg_status dmrg_sigma(dmrg_ctx* ctx, int site, const double* psi, double* sigma
  * The call is stream-ordered on dmrg_stream(ctx) and does not synchronize.
  */
 dmrg_status dmrg_sigma_noalloc(dmrg_ctx* ctx, int site, const double* psi, double* sigma);
+
+/*
+ * Autotuner of the FP64 sigma work list: times one sigma (after one warm-up)
+ * for every combination of items per SM {8, 16, 32} and per-task latency
+ * cost {4096, 16384, 65536} (the item split and largest-first order of the
+ * persistent kernel's work items, Sec. II.D-E collapsed into one list) on a
+ * seeded psi, keeps the fastest and reports it (any output may be NULL;
+ * best_ms = its time). Results stay bitwise deterministic for the chosen
+ * setting; they can differ in the last bits from another setting because
+ * items sum their tasks in another grouping. A tuned work list may need more
+ * scratch than dmrg_sigma_noalloc holds. The default without tuning is
+ * 8 items per SM and cost 16384.
+ */
+dmrg_status dmrg_autotune(dmrg_ctx* ctx, int site, int* items_per_sm, double* per_task_cost, double* best_ms);
 
 /*
  * One sub-Hamiltonian's share of sigma (Sec. II.B, Eqs. sum-h, sub-h,

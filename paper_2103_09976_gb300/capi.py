@@ -23,7 +23,8 @@ DMRG_FP64, DMRG_BF16X2, DMRG_BF16X3 = 0, 1, 2
 class dmrg_opts(ctypes.Structure):
     _fields_ = [("sigma_prec", ctypes.c_int), ("dav_max_space", ctypes.c_int),
                 ("dav_max_iter", ctypes.c_int), ("keep_one_per_q", ctypes.c_int),
-                ("noise", ctypes.c_double), ("seed", ctypes.c_ulonglong), ("device", ctypes.c_int)]
+                ("noise", ctypes.c_double), ("seed", ctypes.c_ulonglong), ("device", ctypes.c_int),
+                ("graphs", ctypes.c_int)]
 
 
 class dmrg_sigma_info(ctypes.Structure):
@@ -74,6 +75,7 @@ SIGNATURES = {
     "dmrg_sweep": (_I, [_P, _P, _I, _D, _P, _P]),
     "dmrg_sweep_log": (_I, [_P, _P, _I, _P]),
     "dmrg_sigma_part": (_I, [_P, _I, _I, _I, _P, _P]),
+    "dmrg_autotune": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "dmrg_block_info": (_I, [_P, _I, _I, _P, _P, _P, _P]),
     "dmrg_block_read": (_I, [_P, _I, _I, _I, _P]),
     "dmrg_sync": (_I, [_P]),
@@ -203,6 +205,13 @@ def dmrg_sigma(ctx, site, psi, sigma):
 def dmrg_sigma_part(ctx, site, rank, n_ranks, psi, sigma):
     """FP64 sigma of the NC terms owned by sub-Hamiltonian `rank` of `n_ranks`."""
     _check(ctx, lib().dmrg_sigma_part(ctx, site, rank, n_ranks, _ptr(psi), _ptr(sigma)))
+
+
+def dmrg_autotune(ctx, site=-1):
+    """Tune the FP64 sigma work list; returns (items_per_sm, per_task_cost, best_ms)."""
+    w, c, ms = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+    _check(ctx, lib().dmrg_autotune(ctx, site, ctypes.byref(w), ctypes.byref(c), ctypes.byref(ms)))
+    return w.value, c.value, ms.value
 
 
 def dmrg_sigma_noalloc(ctx, site, psi, sigma):

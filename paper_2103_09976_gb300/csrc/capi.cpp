@@ -70,10 +70,23 @@ Problem& need_problem(Context& c, int site) {
 
 namespace dmrg {
 
+// Items, groups and scratch of the FP64 work list for the problem's tuning.
+static void prepare_items(Context& c, Problem& p) {
+  TileShape ts{F64_TM, F64_TN, 2e6, p.per_task_cost};
+  build_items(p.blocks, p.wl, ts, c.n_sm * p.items_per_sm);
+  cudaStream_t st = c.stream;
+  p.d_items.upload(p.wl.items, st);
+  p.d_groups.upload(p.wl.groups, st);
+  p.d_sched.upload(p.wl.schedule, st);
+  p.d_scratch.alloc(std::max<long long>(1, p.wl.scratch_elems) * sizeof(double));
+  DMRG_CUDA(cudaStreamSynchronize(st));
+  p.graphs.clear();
+}
+
 void prepare_worklist(Context& c, Problem& p) {
   build_tasks(p.blocks, p.L, p.R, p.terms, p.wl);
-  TileShape ts{F64_TM, F64_TN, 2e6};
-  build_items(p.blocks, p.wl, ts, c.n_sm * 8);
+  TileShape ts{F64_TM, F64_TN, 2e6, p.per_task_cost};
+  build_items(p.blocks, p.wl, ts, c.n_sm * p.items_per_sm);
   cudaStream_t st = c.stream;
   p.d_tasks.upload(p.wl.tasks, st);
   p.d_items.upload(p.wl.items, st);
@@ -190,11 +203,48 @@ static void run_sigma_tc(Context& c, Problem& p, const double* d_psi, double* d_
   DMRG_CUDA(cudaGetLastError());
 }
 
+// One sigma at the context's precision. With graphs on, the launch sequence
+// for a given (precision, psi, sigma) is captured once (on its second use;
+// the first runs directly so that one-time setup such as kernel attributes
+// happens outside a capture) and replayed as one graph launch afterwards.
 void run_sigma(Context& c, Problem& p, const double* d_psi, double* d_sigma) {
-  if (c.opts.sigma_prec != DMRG_FP64)
-    run_sigma_tc(c, p, d_psi, d_sigma);
-  else
-    run_sigma_f64(c, p, d_psi, d_sigma);
+  const int prec = c.opts.sigma_prec;
+  auto direct = [&] {
+    if (prec != DMRG_FP64)
+      run_sigma_tc(c, p, d_psi, d_sigma);
+    else
+      run_sigma_f64(c, p, d_psi, d_sigma);
+  };
+  if (!c.opts.graphs || c.prof.on) {
+    direct();
+    return;
+  }
+  if (prec != DMRG_FP64 && !p.tc_ready) prepare_tc(c, p);  // allocations stay outside any capture
+  const GraphKey key{prec, d_psi, d_sigma};
+  auto it = p.graphs.m.find(key);
+  if (it == p.graphs.m.end()) {
+    if (!(p.graphs.warm & (1u << prec))) {
+      direct();
+      p.graphs.warm |= 1u << prec;
+      return;
+    }
+    cudaGraph_t g = nullptr;
+    DMRG_CUDA(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
+    try {
+      direct();
+    } catch (...) {
+      cudaStreamEndCapture(c.stream, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
+    DMRG_CUDA(cudaStreamEndCapture(c.stream, &g));
+    cudaGraphExec_t e = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&e, g, 0);
+    cudaGraphDestroy(g);
+    DMRG_CUDA(ie);
+    it = p.graphs.m.emplace(key, e).first;
+  }
+  DMRG_CUDA(cudaGraphLaunch(it->second, c.stream));
 }
 
 void run_sigma_f64(Context& c, Problem& p, const double* d_psi, double* d_sigma) {
@@ -434,6 +484,7 @@ void dmrg_default_opts(dmrg_opts* o) {
   o->noise = 0.0;
   o->seed = 0;
   o->device = 0;
+  o->graphs = 1;
 }
 
 dmrg_status dmrg_create(dmrg_ctx** out, const dmrg_opts* opts) {
@@ -550,6 +601,60 @@ dmrg_status dmrg_sigma(dmrg_ctx* ctx, int site, const double* psi, double* sigma
     DMRG_CUDA(cudaSetDevice(c.device));
     Problem& p = need_problem(c, site);
     sigma_call(c, p, psi, sigma, [&](const double* x, double* y) { run_sigma(c, p, x, y); });
+  });
+}
+
+dmrg_status dmrg_autotune(dmrg_ctx* ctx, int site, int* items_per_sm, double* per_task_cost, double* best_ms) {
+  if (!ctx) return DMRG_EINVAL;
+  return guarded(ctx, [&] {
+    Context& c = ctx->c;
+    DMRG_CUDA(cudaSetDevice(c.device));
+    Problem& p = need_problem(c, site);
+    const size_t bytes = (size_t)p.psi_size * sizeof(double);
+    c.d_psi.alloc(bytes);
+    c.d_sigma.alloc(bytes);
+    launch_gen_vector(c.d_psi.as<double>(), p.psi_size, 0x54554E45ull ^ c.opts.seed, 0ull, c.stream);
+    DMRG_CUDA(cudaGetLastError());
+    const int cand_items[3] = {8, 16, 32};
+    const double cand_cost[3] = {4096.0, 16384.0, 65536.0};
+    cudaEvent_t e0, e1;
+    DMRG_CUDA(cudaEventCreate(&e0));
+    DMRG_CUDA(cudaEventCreate(&e1));
+    double best = 1e300;
+    int bi = p.items_per_sm;
+    double bc = p.per_task_cost;
+    try {
+      for (int wi : cand_items)
+        for (double cc : cand_cost) {
+          p.items_per_sm = wi;
+          p.per_task_cost = cc;
+          prepare_items(c, p);
+          run_sigma_f64(c, p, c.d_psi.as<double>(), c.d_sigma.as<double>());  // warm-up
+          DMRG_CUDA(cudaEventRecord(e0, c.stream));
+          run_sigma_f64(c, p, c.d_psi.as<double>(), c.d_sigma.as<double>());
+          DMRG_CUDA(cudaEventRecord(e1, c.stream));
+          DMRG_CUDA(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          DMRG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          if (ms < best) {
+            best = ms;
+            bi = wi;
+            bc = cc;
+          }
+        }
+    } catch (...) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p.items_per_sm = bi;
+    p.per_task_cost = bc;
+    prepare_items(c, p);
+    if (items_per_sm) *items_per_sm = bi;
+    if (per_task_cost) *per_task_cost = bc;
+    if (best_ms) *best_ms = best;
   });
 }
 

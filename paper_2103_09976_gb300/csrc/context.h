@@ -55,6 +55,30 @@ struct DevBuf {
 
 // A two-site problem: left/right operator tables over one FP64 store
 // (left ops first), the psi layout, NC terms and the sigma work list.
+// Instantiated sigma graphs of a problem, keyed by (precision, psi, sigma).
+struct GraphKey {
+  int prec;
+  const void* psi;
+  const void* sigma;
+  bool operator<(const GraphKey& o) const {
+    if (prec != o.prec) return prec < o.prec;
+    if (psi != o.psi) return psi < o.psi;
+    return sigma < o.sigma;
+  }
+};
+struct GraphCache {
+  std::map<GraphKey, cudaGraphExec_t> m;
+  unsigned warm = 0;  // bit p: precision p has run once directly
+  GraphCache() = default;
+  GraphCache(const GraphCache&) = delete;
+  GraphCache& operator=(const GraphCache&) = delete;
+  void clear() {
+    for (auto& kv : m) cudaGraphExecDestroy(kv.second);
+    m.clear();
+  }
+  ~GraphCache() { clear(); }
+};
+
 // A work list and its device copies (the full sigma, or one sub-Hamiltonian part).
 struct DevWork {
   WorkList wl;
@@ -82,6 +106,10 @@ struct Problem {
   DevBuf d_dstart, d_dtask;
   DevBuf split, psi_split;         // slice-interleaved bf16 tiles of the operators / of psi
   DevBuf d_tc_recs, d_tc_item_rec, d_tc_items, d_tc_groups, d_tc_sched, d_tc_pblk, d_tc_scratch, d_err;
+  GraphCache graphs;
+  // FP64 work-list tuning (dmrg_autotune): items per SM and per-task cost term
+  int items_per_sm = 8;
+  double per_task_cost = 16384.0;
   // sub-Hamiltonian parts: (n_ranks, rank) -> work list of that rank's terms
   std::map<std::pair<int, int>, std::unique_ptr<DevWork>> parts;
 };

@@ -203,10 +203,9 @@ void build_tasks(const std::vector<PsiBlock>& blocks, const OpSet& L, const OpSe
 // multiply-adds of its 8x8x4 tensor instructions (rows and columns padded to
 // 8, contractions to 4, the intermediate in 64-column chunks) plus a fixed
 // per-task latency term. Items are split and ordered (largest first) by it.
-static double tile_cost(const Task& k, const PsiBlock& in, int nr, int nc) {
+static double tile_cost(const Task& k, const PsiBlock& in, int nr, int nc, double per_task) {
   auto up8 = [](int x) { return (double)((x + 7) & ~7); };
   auto up4 = [](int x) { return (double)((x + 3) & ~3); };
-  const double per_task = 16384.0;
   double c = per_task;
   for (int nc0 = 0; nc0 < in.mR; nc0 += 64) {
     const int nch = std::min(64, in.mR - nc0);
@@ -226,7 +225,7 @@ void build_items(const std::vector<PsiBlock>& blocks, WorkList& wl, const TileSh
   double total = 0;
   for (size_t b = 0; b < nb; ++b)
     for (int t = wl.out_start[b]; t < wl.out_start[b + 1]; ++t)
-      total += tile_cost(wl.tasks[t], blocks[wl.tasks[t].in_blk], blocks[b].mL, blocks[b].mR);
+      total += tile_cost(wl.tasks[t], blocks[wl.tasks[t].in_blk], blocks[b].mL, blocks[b].mR, ts.per_task);
   double target = std::max(ts.target, total / std::max(1, want_items));
   std::vector<double> cost;
   for (size_t b = 0; b < nb; ++b) {
@@ -254,7 +253,7 @@ void build_items(const std::vector<PsiBlock>& blocks, WorkList& wl, const TileSh
         int start = t0;
         double acc = 0;
         for (int t = t0; t < t1; ++t) {
-          double c = tile_cost(wl.tasks[t], blocks[wl.tasks[t].in_blk], nr, nc);
+          double c = tile_cost(wl.tasks[t], blocks[wl.tasks[t].in_blk], nr, nc, ts.per_task);
           if (acc > 0 && acc + c > target) {
             wl.items.push_back({(int)b, r0, nr, c0, nc, start, t, 0, wl.scratch_elems});
             wl.scratch_elems += (long long)nr * nc;

@@ -149,7 +149,8 @@ struct WorkList {
 struct TileShape {
   int tm;          // rows per tile
   int tn;          // max cols per tile
-  double target;   // flops per item
+  double target;   // minimum cost per item
+  double per_task = 16384.0;  // fixed latency term of one task in the item cost
 };
 
 void build_tasks(const std::vector<PsiBlock>& blocks, const OpSet& L, const OpSet& R,
