@@ -133,17 +133,20 @@ def test_invalid_inputs_rejected(capi):
         capi.dmrg_destroy(ctx)
 
 
-def test_sigma_middle_bond_m2000_sampled_blocks(capi):
-    """K=108 (54|54), N=30, Sz=0, M=2000: the benchmark workload at full size,
-    checked on 3x3 sampled entries of three output blocks (largest, median,
-    smallest)."""
+@pytest.mark.parametrize("M,size,nblk", [(2000, 106004, 104), (4000, 424716, 116), (6000, 956036, 120)])
+def test_sigma_middle_bond_sampled_blocks(capi, M, size, nblk):
+    """K=108 (54|54), N=30, Sz=0 at the benchmark's bond dimensions: checked on
+    3x3 sampled entries of three output blocks (largest, median, smallest).
+    At M=2000 the work list is autotuned first, as bench.py times it."""
     from synth import gaussian_sector_dims, mirrored_sectors, random_unit_vector
     from oracle.sigma import synthetic_sigma_sampled
-    left = gaussian_sector_dims(2000)
+    left = gaussian_sector_dims(M)
     right = mirrored_sectors(left)
     ctx = capi.dmrg_create(device=0)
     try:
         capi.dmrg_load_synthetic(ctx, 108, 216, 30, 0, left, right, 1)
+        if M == 2000:
+            capi.dmrg_autotune(ctx, -1)
         lay = capi.dmrg_psi_layout(ctx)
         info = capi.dmrg_get_sigma_info(ctx)
         x = random_unit_vector(lay["size"], 1)
@@ -151,10 +154,11 @@ def test_sigma_middle_bond_m2000_sampled_blocks(capi):
         capi.dmrg_sigma(ctx, -1, x, y)
     finally:
         capi.dmrg_destroy(ctx)
-    assert lay["size"] == 106004 and len(lay["m_l"]) == 104
+    assert lay["size"] == size and len(lay["m_l"]) == nblk
     assert info["n_terms"] == 23654
-    assert info["op_elements"] == 2130976408
-    assert abs(info["flops"] - 0.568442744e12) < 1e3
+    if M == 2000:
+        assert info["op_elements"] == 2130976408
+        assert abs(info["flops"] - 0.568442744e12) < 1e3
     order = np.argsort(lay["m_l"] * lay["m_r"])
     pick = [order[-1], order[len(order) // 2], order[0]]
     samples = []
