@@ -53,6 +53,11 @@ def config(M, prec="fp64"):
             "l2": "inputs larger than L2 (operator store >> 129 MB), no flush"}
 
 
+# DRAM bytes per launch of the FP64 sigma kernel on the default workload,
+# from ncu (dram__bytes_read.sum + dram__bytes_write.sum), recorded in
+# profiles/sigma_f64_middle_bond_m2000_dram.md; valid for M=2000 only.
+F64_TRAFFIC_M2000 = 57.05e9
+
 # ------------------------------------------------------------------ clocks
 class Clocks:
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -325,7 +330,10 @@ def main():
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": config(args.M),
            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
-                        "frac": achieved / peak64, "traffic": None,
+                        "frac": achieved / peak64,
+                        "traffic": F64_TRAFFIC_M2000 if args.M == 2000 else None,
+                        "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
+                                          "profiles/sigma_f64_middle_bond_m2000_dram.md",
                         "kernel": "sigma_f64_kernel",
                         "peak_source": "cuBLAS DGEMM 4096^3 measured in this run (no FP64 entry in MEASURED_PEAKS.json)",
                         "kernel_ms": kern_s * 1e3, "reduce_ms": r_ms / max(1, r_n),
