@@ -335,7 +335,9 @@ def main():
                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
                                           "profiles/sigma_f64_middle_bond_m2000_dram.md",
                         "kernel": "sigma_f64_kernel",
-                        "peak_source": "cuBLAS DGEMM 4096^3 measured in this run (no FP64 entry in MEASURED_PEAKS.json)",
+                        "peak_source": "cuBLAS DGEMM 4096^3 measured in this run (no FP64 entry in MEASURED_PEAKS.json); "
+                                       "cross-check: measured bf16 x nominal FP64/bf16 ratio = "
+                                       f"{bf16 * 1.25 / 2250.0:.3f} TFLOP/s",
                         "kernel_ms": kern_s * 1e3, "reduce_ms": r_ms / max(1, r_n),
                         "autotuned": {"items_per_sm": tuned[0], "per_task_cost": tuned[1], "tune_ms": tuned[2]}},
            "e2e": {"value": flops / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 8 * n,
