@@ -119,6 +119,12 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
 }
 
+// Bits of two floats rounded to bf16 (round to nearest even), lo in bits 0-15.
+__device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
+  const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&p);
+}
+
 __device__ __forceinline__ void mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
   asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
@@ -530,21 +536,17 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
         uint32_t hw[4], mw[4], lw[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          uint32_t hp = 0, mp = 0, lp = 0;
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            const float x = v[g * 8 + 2 * q + e];
-            const __nv_bfloat16 h0 = __float2bfloat16_rn(x);
-            const float r1 = x - __bfloat162float(h0);
-            const __nv_bfloat16 m0 = __float2bfloat16_rn(r1);
-            const __nv_bfloat16 l0 = __float2bfloat16_rn(r1 - __bfloat162float(m0));
-            hp |= (uint32_t)__bfloat16_as_ushort(h0) << (16 * e);
-            mp |= (uint32_t)__bfloat16_as_ushort(m0) << (16 * e);
-            lp |= (uint32_t)__bfloat16_as_ushort(l0) << (16 * e);
-          }
+          // two columns at a time: one paired round-to-nearest conversion per
+          // slice; a bf16 value is the upper half of its float, so the
+          // residuals need only a mask or a shift and a subtraction
+          const float x0 = v[g * 8 + 2 * q], x1 = v[g * 8 + 2 * q + 1];
+          const uint32_t hp = bf16x2_bits(x0, x1);
+          const float r0 = x0 - __uint_as_float(hp << 16), r1 = x1 - __uint_as_float(hp & 0xFFFF0000u);
+          const uint32_t mp = bf16x2_bits(r0, r1);
+          const float s0 = r0 - __uint_as_float(mp << 16), s1 = r1 - __uint_as_float(mp & 0xFFFF0000u);
           hw[q] = hp;
           mw[q] = mp;
-          lw[q] = lp;
+          lw[q] = bf16x2_bits(s0, s1);
         }
         const int off = (((row >> 3) * 8 + half * 4 + g) * 64 + (row & 7) * 8);
         *reinterpret_cast<uint4*>(a2 + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
