@@ -263,6 +263,7 @@ typedef struct dmrg_step_log {
   int sweep, site, forward, iters, converged, kept;
   long long psi_size;
   double energy, discarded;
+  double t_block, t_solve, t_decimate, t_transform;  /* seconds (host clock, device work included) */
 } dmrg_step_log;
 dmrg_status dmrg_sweep_log(dmrg_ctx* ctx, dmrg_step_log* out, int max_steps, int* n_steps);
 

@@ -267,7 +267,8 @@ class dmrg_step_log(ctypes.Structure):
     _fields_ = [("sweep", ctypes.c_int), ("site", ctypes.c_int), ("forward", ctypes.c_int),
                 ("iters", ctypes.c_int), ("converged", ctypes.c_int), ("kept", ctypes.c_int),
                 ("psi_size", ctypes.c_longlong), ("energy", ctypes.c_double),
-                ("discarded", ctypes.c_double)]
+                ("discarded", ctypes.c_double), ("t_block", ctypes.c_double), ("t_solve", ctypes.c_double),
+                ("t_decimate", ctypes.c_double), ("t_transform", ctypes.c_double)]
 
 
 def dmrg_sweep_log(ctx):

@@ -18,6 +18,7 @@
 // block into one chunk of one enlarged block; a kernel applies the copies of
 // each destination block in a fixed order.
 #include <algorithm>
+#include <chrono>
 #include <array>
 #include <cmath>
 #include <cstring>
@@ -861,9 +862,12 @@ void sweep_run(Context& c, const int* Ms, int n_sweeps, double tol, double* ener
     double emin = 1e300, dmax = 0.0;
     for (int k = 0; k < K - 1; ++k) {
       const int i = fwd ? k : K - 2 - k;
+      auto clk = [] { return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count(); };
+      const double t0 = clk();
       S.prob_site = -1;
       sweep_problem(c, i);
       Problem& p = *c.prob;
+      const double t1 = clk();
       DevBuf x;
       x.alloc(p.psi_size * sizeof(double));
       double e = 0.0;
@@ -871,12 +875,13 @@ void sweep_run(Context& c, const int* Ms, int n_sweeps, double tol, double* ener
       const unsigned long long step_id = (unsigned long long)s * K + i;
       const bool conv = run_davidson(c, p, nullptr, tol, &e, x.as<double>(), &it, step_id << 32);
       emin = std::min(emin, e);
+      const double t2 = clk();
       Decim D;
       decimate(c, p, fwd ? S.EL : S.ER, x.as<double>(), Ms[s], fwd, D);
       dmax = std::max(dmax, D.discarded);
       int kept = 0;
       for (int d : D.nb.dim) kept += d;
-      S.log.push_back({s, i, fwd ? 1 : 0, it, conv ? 1 : 0, kept, p.psi_size, e, D.discarded});
+      const double t3 = clk();
       auto nbk = std::make_unique<DevBlock>();
       if (fwd) {
         transform(c, p.L, p.store.as<double>(), D.nb, D.esec_of_new, D.uoff, D.u.as<double>(), *nbk, 2 * (i + 1),
@@ -887,6 +892,9 @@ void sweep_run(Context& c, const int* Ms, int n_sweeps, double tol, double* ener
                   2 * K, false);
         S.R[i + 1] = std::move(nbk);
       }
+      const double t4 = clk();
+      S.log.push_back({s, i, fwd ? 1 : 0, it, conv ? 1 : 0, kept, p.psi_size, e, D.discarded, t1 - t0, t2 - t1,
+                       t3 - t2, t4 - t3});
       c.prob.reset();
       S.prob_site = -1;
     }
