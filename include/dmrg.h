@@ -330,7 +330,8 @@ dmrg_status dmrg_profile(dmrg_ctx* ctx, int enable);
  * spent blocked on barrier kind k (1 stage free, 2 sigma tile free, 3 X tile
  * free, 4 stage loaded, 5 second-product operand written, 6 X tile computed,
  * 7 second-product operand free, 8 sigma tile computed, 9-13 unit-record
- * ring), cycles[16] = total CTA cycles. Fills min(n, 17) entries. */
+ * ring; 14 and 15 are not waits: cycles the MMA-issuing thread spends
+ * issuing MMAs and committing them), cycles[16] = total CTA cycles. Fills min(n, 17) entries. */
 dmrg_status dmrg_profile_waits(dmrg_ctx* ctx, double* cycles, int n);
 dmrg_status dmrg_profile_read(dmrg_ctx* ctx, int kernel, double* total_ms, long long* launches);
 

@@ -297,7 +297,8 @@ def dmrg_profile_read(ctx, kernel):
 WAIT_KINDS = {1: "stage free", 2: "sigma tile free", 3: "X tile free", 4: "stage loaded",
               5: "second operand written", 6: "X tile computed", 7: "second operand free",
               8: "sigma tile computed", 9: "record slot free", 10: "record loaded (producer)",
-              11: "terminator slot", 12: "record loaded (MMA)", 13: "record loaded (epilogue)"}
+              11: "terminator slot", 12: "record loaded (MMA)", 13: "record loaded (epilogue)",
+              14: "MMA thread issuing MMAs", 15: "MMA thread committing"}
 
 
 def dmrg_profile_waits(ctx):

@@ -396,6 +396,13 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
   } else if (warp == 1) {
     // --------------------------------------------------------------- MMA
     if (lane == 0) {
+      // with profiling on, slots 14 / 15 of the wait accounting receive the
+      // cycles this thread spends issuing MMAs / committing them
+      const bool prof = a.wait_prof != nullptr;
+      auto tick = [&]() -> long long { return prof ? clock64() : 0ll; };
+      auto tock = [&](int slot, long long t0) {
+        if (prof) s_wait[slot] += (unsigned long long)(clock64() - t0);
+      };
       uint32_t stage = 0, phase = 0;
       uint32_t xcnt = 0, xph_empty = 3u;   // bit b: expected parity of X-empty[b]
       uint32_t a2_full_ph = 0;
@@ -407,7 +414,9 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
         return sbase + stage * STAGE_BYTES;
       };
       auto release = [&]() {
+        const long long t0 = tick();
         commit(bar(B_EMPTY + stage));
+        tock(15, t0);
         if (++stage == STAGES) { stage = 0; phase ^= 1; }
       };
       auto mma_k1 = [&](const TcRec& u) {
@@ -428,9 +437,11 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
             const uint32_t a_lbo = tA ? (uint32_t)min(16, aC8 - rg0) * TILE3 : TILE3;
             const uint32_t a_sbo = tA ? TILE3 : (uint32_t)aC8 * TILE3;
             const uint32_t b_lbo = (uint32_t)pC8 * TILE3;
+            const long long t0 = tick();
             mma_chain<NPROD>(tmem_x + tk.xcol, sdesc(sst + tk.k1a * TILE3, a_lbo, a_sbo),
                              sdesc(sst + tk.k1b * TILE3, b_lbo, TILE3), 128u, 128u, 2 * a_lbo, 2 * b_lbo,
                              tk.pR8 / 2, idesc_bf16(n16, tA, 1), false);
+            tock(14, t0);
           }
           release();
         } else {
@@ -442,12 +453,18 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
           for (int k = 0; k < nk && ok; ++k) {
             const uint32_t sst = acquire();
             if (!ok) return;
+            const long long t0 = tick();
             mma_chain<NPROD>(tmem_x, sdesc(sst, a_lbo, a_sbo), sdesc(sst + PSI_TILE * TILE3, 16u * TILE3, TILE3),
                              128u, 128u, 2 * a_lbo, 2 * 16u * TILE3, min(4, pR8 - 4 * k) / 2, id1, k > 0);
+            tock(14, t0);
             release();
           }
         }
-        commit(bar(B_XFULL + xb));
+        {
+          const long long t0 = tick();
+          commit(bar(B_XFULL + xb));
+          tock(15, t0);
+        }
         ++xcnt;
       };
       auto mma_k2 = [&](const TcRec& u) {
@@ -478,11 +495,15 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
             b_sbo = tB ? TILE3 : 8u * TILE3;
             nks = (min(64, u.width - h * 64) + 15) / 16;
           }
+          const long long t0 = tick();
           mma_chain<NPROD>(tmem_s, sdesc(a2, 128u, 1024u), sdesc(sst, b_lbo, b_sbo), A2_SLICE, 128u, 2 * 128u,
                            2 * b_lbo, nks, id2, seg_open);
+          tock(14, t0);
           seg_open = true;
           release();
+          const long long t1 = tick();
           commit(bar(B_A2EMPTY));
+          tock(15, t1);
         }
         if (ok && (u.flags & UNIT_ENDS_SEGMENT)) {
           commit(bar(B_SFULL + sb));
