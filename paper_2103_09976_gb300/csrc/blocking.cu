@@ -8,26 +8,85 @@ namespace dmrg {
 
 namespace {
 
-// One destination block per CTA: zero it, then apply its jobs in order
-// (dst[i, j] += coef * src(i, j)), so the sum is deterministic.
-__global__ void blocking_kernel(double* __restrict__ dst_store, const double* __restrict__ src_store,
-                                const BlockJob* __restrict__ jobs, const DstBlock* __restrict__ dsts, int ndst) {
-  for (int d = blockIdx.x; d < ndst; d += gridDim.x) {
-    const DstBlock db = dsts[d];
-    double* dst = dst_store + db.off;
-    for (long long e = threadIdx.x; e < db.n; e += blockDim.x) dst[e] = 0.0;
-    __syncthreads();
-    for (int q = db.j0; q < db.j1; ++q) {
-      const BlockJob jb = jobs[q];
-      const long long ne = (long long)jb.rows * jb.cols;
-      for (long long e = threadIdx.x; e < ne; e += blockDim.x) {
-        const int i = (int)(e / jb.cols), j = (int)(e % jb.cols);
-        double v;
-        if (jb.src < 0) v = (i == j) ? 1.0 : 0.0;
-        else v = jb.trans ? src_store[jb.src + (long long)j * jb.src_ld + i] : src_store[jb.src + (long long)i * jb.src_ld + j];
-        dst[(long long)(jb.r0 + i) * db.ld + jb.c0 + j] += jb.coef * v;
+__constant__ int c_site_n[4] = {0, 1, 1, 2};
+__constant__ int c_site_s[4] = {0, 1, -1, 0};
+
+// index of sector (n, s) in a basis sorted by (n, s), or -1
+__device__ __forceinline__ int find_sector(const int* q, int nq, int n, int s) {
+  int lo = 0, hi = nq - 1;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    const int mn = q[2 * mid], ms = q[2 * mid + 1];
+    if (mn == n && ms == s) return mid;
+    if (mn < n || (mn == n && ms < s)) lo = mid + 1;
+    else hi = mid - 1;
+  }
+  return -1;
+}
+
+// One destination block per CTA (grid-stride): for every term of its
+// operator, in order, find the block sector ib the term reads (enlarged
+// input sector minus the site state's quantum numbers), the source block
+// and its output sector ob, and add coef * sign * source into the chunk
+// (rows of ob within Qout, columns of ib within Qin). Each destination
+// element is owned by one thread (index mod blockDim) for the zeroing and
+// every update, so terms are applied in order without barriers and the
+// sums are deterministic. Signs: block x site takes (-1)^{N(block in)} when
+// the site part is odd; site x block takes (-1)^{N(site in)} when the block
+// operator is odd.
+__global__ void blocking_kernel(BlockingDev d) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int bi = blockIdx.x; bi < d.ndst; bi += gridDim.x) {
+    const BDst db = d.dsts[bi];
+    double* dst = d.dst_store + db.off;
+    const long long ne = (long long)db.rows * db.cols;
+    for (long long e = tid; e < ne; e += nt) dst[e] = 0.0;
+    const int qin_n = d.eq[2 * db.Qin], qin_s = d.eq[2 * db.Qin + 1];
+    const int qout_n = d.eq[2 * db.Qout], qout_s = d.eq[2 * db.Qout + 1];
+    for (int t = d.term_start[db.k]; t < d.term_start[db.k + 1]; ++t) {
+      const BTerm tm = d.terms[t];
+      const int ib = find_sector(d.bq, d.nb, qin_n - c_site_n[tm.nin], qin_s - c_site_s[tm.nin]);
+      if (ib < 0) continue;
+      const int c0 = d.chunk_off[db.Qin * d.nb + ib];
+      if (c0 < 0) continue;
+      int ob = ib, par = 0;
+      long long soff = -1;
+      if (tm.src >= 0) {
+        const int dn = d.src_dq[2 * tm.src], ds = d.src_dq[2 * tm.src + 1];
+        par = d.src_par[tm.src];
+        if (!tm.trans) {
+          soff = d.srcblk[(long long)tm.src * d.nb + ib];
+          if (soff < 0) continue;
+          ob = find_sector(d.bq, d.nb, d.bq[2 * ib] + dn, d.bq[2 * ib + 1] + ds);
+        } else {
+          ob = find_sector(d.bq, d.nb, d.bq[2 * ib] - dn, d.bq[2 * ib + 1] - ds);
+          if (ob >= 0) soff = d.srcblk[(long long)tm.src * d.nb + ob];
+          if (soff < 0) continue;
+        }
+        if (ob < 0) continue;
       }
-      __syncthreads();
+      if (d.bq[2 * ob] + c_site_n[tm.nout] != qout_n || d.bq[2 * ob + 1] + c_site_s[tm.nout] != qout_s) {
+        if (tid == 0) atomicExch(d.err, 1);
+        continue;
+      }
+      const int r0 = d.chunk_off[db.Qout * d.nb + ob];
+      if (r0 < 0) continue;
+      const int rows = d.bdim[ob], cols = d.bdim[ib];
+      bool neg;
+      if (d.left) neg = ((c_site_n[tm.nout] - c_site_n[tm.nin]) & 1) && (d.bq[2 * ib] & 1);
+      else neg = par && (c_site_n[tm.nin] & 1);
+      const double w = neg ? -tm.coef : tm.coef;
+      for (int i = 0; i < rows; ++i) {
+        const long long base = (long long)(r0 + i) * db.cols + c0;
+        int j = (int)(((long long)tid - base % nt + nt) % nt);  // first column this thread owns
+        for (; j < cols; j += nt) {
+          double v;
+          if (tm.src < 0) v = (i == j) ? 1.0 : 0.0;
+          else if (!tm.trans) v = d.src_store[soff + (long long)i * cols + j];
+          else v = d.src_store[soff + (long long)j * rows + i];
+          dst[base + j] += w * v;
+        }
+      }
     }
   }
 }
@@ -222,11 +281,10 @@ __global__ void take_columns_kernel(const double* __restrict__ Qall, const TakeB
 
 }  // namespace
 
-void launch_blocking(double* dst_store, const double* src_store, const BlockJob* jobs, const DstBlock* dsts, int ndst,
-                     cudaStream_t st) {
-  if (ndst <= 0) return;
-  const int grid = ndst < 65535 ? ndst : 65535;
-  blocking_kernel<<<grid, 256, 0, st>>>(dst_store, src_store, jobs, dsts, ndst);
+void launch_blocking(const BlockingDev& d, cudaStream_t st) {
+  if (d.ndst <= 0) return;
+  const int grid = d.ndst < 152 * 64 ? d.ndst : 152 * 64;
+  blocking_kernel<<<grid, 256, 0, st>>>(d);
 }
 
 void launch_gram(const double* psi, const GramBlock* gb, int nb, double* G, bool left, cudaStream_t st) {

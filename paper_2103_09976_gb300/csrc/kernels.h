@@ -73,17 +73,35 @@ void launch_split_psi(const double* psi, const PsiBlock* blocks, const TcPsiBloc
 void launch_sigma_tc(const TcDev& a, int n_sm, cudaStream_t st);
 
 // ------------------------------------------------------------------- sweep
-// dst_block[r0 + i, c0 + j] += coef * src(i, j); src(i, j) = S[i, j] or S[j, i]
-// (trans) of a stored row-major block with row length src_ld, or the
-// identity when src < 0.
-struct BlockJob {
-  long long src;
-  int src_ld, rows, cols, r0, c0, trans;
+// One term of an enlarged operator: coef * (source op `src`, transposed when
+// trans; -1 = identity) (x) |nout><nin| on the site.
+struct BTerm {
+  int src, trans, nout, nin;
   double coef;
 };
-struct DstBlock {       // one destination block and the range of its jobs
-  long long off, n;
-  int ld, j0, j1, pad;
+// One destination block of the enlarged operator set: op k, sectors Qin -> Qout.
+struct BDst {
+  long long off;
+  int k, Qin, Qout, rows, cols, pad;
+};
+// Everything the blocking kernel needs to expand terms into sector blocks.
+struct BlockingDev {
+  double* dst_store;
+  const double* src_store;
+  const BDst* dsts;
+  int ndst;
+  const int* term_start;        // per destination op, CSR into terms
+  const BTerm* terms;
+  const int* bq;                // block basis: (N, 2Sz) per sector, ascending
+  const int* bdim;
+  int nb;
+  const int* eq;                // enlarged basis (N, 2Sz) per sector
+  const int* chunk_off;         // [enlarged sector][block sector]: row offset of the chunk, or -1
+  const long long* srcblk;      // [source op][input sector]: offset of its block, or -1
+  const int* src_dq;            // (dN, d2Sz) per source op
+  const int* src_par;           // fermion parity per source op
+  int left;                     // 1: block x site, 0: site x block
+  int* err;                     // set to 1 on an inconsistent term
 };
 struct GramBlock {      // one psi block for decimation / one block to orthonormalise
   long long psi_off, g_off, w_off;
@@ -93,8 +111,7 @@ struct TakeBlock {      // dst (d x k) = first k columns of Q (d x d)
   long long q_off, dst_off;
   int d, k;
 };
-void launch_blocking(double* dst_store, const double* src_store, const BlockJob* jobs, const DstBlock* dsts, int ndst,
-                     cudaStream_t st);
+void launch_blocking(const BlockingDev& d, cudaStream_t st);
 void launch_gram(const double* psi, const GramBlock* gb, int nb, double* G, bool left, cudaStream_t st);
 void launch_jacobi_blocks(double* A, double* Q, double* w, const GramBlock* gb, int nb, cudaStream_t st);
 void launch_orthonormalize(double* store, const GramBlock* gb, int nb, cudaStream_t st);

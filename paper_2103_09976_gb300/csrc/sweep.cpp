@@ -182,90 +182,6 @@ Enlarged enlarge(const Basis& b) {
   return E;
 }
 
-// Jobs that build the dense blocks of the enlarged operators E from the
-// operators of block B. left: L x site (sign from the site part's parity and
-// N of the block state); right: site x R (sign from the block op's parity and
-// N of the site state).
-void make_jobs(const OpSet& B, const Enlarged& E, const OpSet& EO, const std::vector<ETerms>& terms, bool left,
-               std::vector<BlockJob>& jobs, std::vector<DstBlock>& dsts) {
-  std::vector<std::vector<BlockJob>> per;  // per destination block
-  std::vector<long long> doff;
-  std::vector<int> dld;
-  std::vector<long long> dn;
-  std::vector<std::vector<int>> dst_index(EO.ops.size());
-  for (size_t k = 0; k < EO.ops.size(); ++k) {
-    dst_index[k].assign(E.basis.size(), -1);
-    for (const OpBlock& ob : EO.ops[k].blocks) {
-      dst_index[k][ob.qin] = (int)per.size();
-      per.emplace_back();
-      doff.push_back(ob.off);
-      dld.push_back(ob.cols);
-      dn.push_back((long long)ob.rows * ob.cols);
-    }
-  }
-  for (size_t k = 0; k < EO.ops.size(); ++k) {
-    const QN dqk = EO.ops[k].dq;
-    for (const ETerm& e : terms[k]) {
-      for (int ib = 0; ib < B.basis.size(); ++ib) {
-        int ob;
-        long long src = -1;
-        int src_ld = 0, par = 0;
-        if (e.src < 0) {
-          ob = ib;
-        } else {
-          const OpDesc& S = B.ops[e.src];
-          par = S.parity;
-          if (!e.trans) {
-            const int kb = S.by_qin[ib];
-            if (kb < 0) continue;
-            ob = S.blocks[kb].qout;
-            src = S.blocks[kb].off;
-            src_ld = S.blocks[kb].cols;
-          } else {
-            ob = B.basis.find(B.basis.q[ib] - S.dq);
-            if (ob < 0) continue;
-            const int kb = S.by_qin[ob];
-            if (kb < 0) continue;
-            src = S.blocks[kb].off;
-            src_ld = S.blocks[kb].cols;
-          }
-        }
-        const int Qin = E.basis.find(B.basis.q[ib] + SITE_Q[e.nin]);
-        const int Qout = E.basis.find(B.basis.q[ob] + SITE_Q[e.nout]);
-        if (Qin < 0 || Qout < 0) continue;
-        if (!(E.basis.q[Qout] == E.basis.q[Qin] + dqk)) throw Error(DMRG_EINVAL, "internal: blocking shift");
-        const int d = dst_index[k][Qin];
-        if (d < 0) continue;
-        double sign = 1.0;
-        if (left) {
-          const int ps = (SITE_N[e.nout] - SITE_N[e.nin]) & 1;
-          if (ps && (B.basis.q[ib].n & 1)) sign = -1.0;
-        } else {
-          if (par && (SITE_N[e.nin] & 1)) sign = -1.0;
-        }
-        BlockJob j;
-        j.src = src;
-        j.src_ld = src_ld;
-        j.rows = B.basis.dim[ob];
-        j.cols = B.basis.dim[ib];
-        j.r0 = E.chunk_off[Qout][ob];
-        j.c0 = E.chunk_off[Qin][ib];
-        j.trans = e.trans ? 1 : 0;
-        j.coef = e.coef * sign;
-        per[d].push_back(j);
-      }
-    }
-  }
-  jobs.clear();
-  dsts.clear();
-  for (size_t d = 0; d < per.size(); ++d) {
-    DstBlock db{doff[d], dn[d], dld[d], (int)jobs.size(), 0, 0};
-    jobs.insert(jobs.end(), per[d].begin(), per[d].end());
-    db.j1 = (int)jobs.size();
-    dsts.push_back(db);
-  }
-}
-
 // ----------------------------------------------------- blocking formulas
 // Left: block L holds modes [0, 2s); site s; enlarged NC set nL' = 2s + 2.
 std::vector<ETerms> left_terms(const Ints& I, int s) {
@@ -533,22 +449,87 @@ std::unique_ptr<DevBlock> vacuum(const Ints& I, bool left, cudaStream_t st) {
   return b;
 }
 
-// enlarged operators of one side into `store` at element offset base
+// Enlarged operators of one side into `store`: the host lists each enlarged
+// operator's terms (block op or identity, transposed or not, coefficient,
+// site matrix element); the blocking kernel expands them over the sectors.
 void build_enlarged(Context& c, const Ints& I, const DevBlock& B, int site, bool left, const Enlarged& E,
                     OpSet& EO, double* store) {
-  std::vector<ETerms> terms = left ? left_terms(I, site) : right_terms(I, site);
-  std::vector<BlockJob> jobs;
-  std::vector<DstBlock> dsts;
-  make_jobs(B.set, E, EO, terms, left, jobs, dsts);
-  DevBuf dj, dd;
-  dj.upload(jobs, c.stream);
-  dd.upload(dsts, c.stream);
+  const std::vector<ETerms> terms = left ? left_terms(I, site) : right_terms(I, site);
+  std::vector<int> term_start(EO.ops.size() + 1, 0);
+  std::vector<BTerm> flat;
+  size_t total = 0;
+  for (const ETerms& t : terms) total += t.size();
+  flat.reserve(total);
+  for (size_t k = 0; k < EO.ops.size(); ++k) {
+    for (const ETerm& e : terms[k]) flat.push_back({e.src, e.trans ? 1 : 0, e.nout, e.nin, e.coef});
+    term_start[k + 1] = (int)flat.size();
+  }
+  const Basis& bb = B.set.basis;
+  const int nb = bb.size(), ne = E.basis.size();
+  std::vector<int> bq(2 * nb), eq(2 * ne), chunk((size_t)ne * nb, -1);
+  for (int i = 0; i < nb; ++i) {
+    bq[2 * i] = bb.q[i].n;
+    bq[2 * i + 1] = bb.q[i].s;
+  }
+  for (int i = 0; i < ne; ++i) {
+    eq[2 * i] = E.basis.q[i].n;
+    eq[2 * i + 1] = E.basis.q[i].s;
+    for (int j = 0; j < nb; ++j) chunk[(size_t)i * nb + j] = E.chunk_off[i][j];
+  }
+  const size_t nsrc = B.set.ops.size();
+  std::vector<long long> srcblk(std::max<size_t>(1, nsrc * nb), -1);
+  std::vector<int> src_dq(std::max<size_t>(2, 2 * nsrc)), src_par(std::max<size_t>(1, nsrc));
+  for (size_t j = 0; j < nsrc; ++j) {
+    const OpDesc& o = B.set.ops[j];
+    for (const OpBlock& ob : o.blocks) srcblk[j * nb + ob.qin] = ob.off;
+    src_dq[2 * j] = o.dq.n;
+    src_dq[2 * j + 1] = o.dq.s;
+    src_par[j] = o.parity;
+  }
+  std::vector<BDst> dsts;
+  for (size_t k = 0; k < EO.ops.size(); ++k)
+    for (const OpBlock& ob : EO.ops[k].blocks)
+      dsts.push_back({ob.off, (int)k, ob.qin, ob.qout, ob.rows, ob.cols, 0});
+  cudaStream_t st = c.stream;
+  DevBuf d_ts, d_terms, d_bq, d_bdim, d_eq, d_chunk, d_srcblk, d_dq, d_par, d_dsts, d_err;
+  d_ts.upload(term_start, st);
+  d_terms.upload(flat, st);
+  d_bq.upload(bq, st);
+  d_bdim.upload(bb.dim, st);
+  d_eq.upload(eq, st);
+  d_chunk.upload(chunk, st);
+  d_srcblk.upload(srcblk, st);
+  d_dq.upload(src_dq, st);
+  d_par.upload(src_par, st);
+  d_dsts.upload(dsts, st);
+  d_err.alloc(sizeof(int));
+  DMRG_CUDA(cudaMemsetAsync(d_err.p, 0, sizeof(int), st));
+  BlockingDev d;
+  d.dst_store = store;
+  d.src_store = B.store.as<double>();
+  d.dsts = d_dsts.as<BDst>();
+  d.ndst = (int)dsts.size();
+  d.term_start = d_ts.as<int>();
+  d.terms = d_terms.as<BTerm>();
+  d.bq = d_bq.as<int>();
+  d.bdim = d_bdim.as<int>();
+  d.nb = nb;
+  d.eq = d_eq.as<int>();
+  d.chunk_off = d_chunk.as<int>();
+  d.srcblk = d_srcblk.as<long long>();
+  d.src_dq = d_dq.as<int>();
+  d.src_par = d_par.as<int>();
+  d.left = left ? 1 : 0;
+  d.err = d_err.as<int>();
   {
-    ProfScope ps(c.prof, 3, c.stream);
-    launch_blocking(store, B.store.as<double>(), dj.as<BlockJob>(), dd.as<DstBlock>(), (int)dsts.size(), c.stream);
+    ProfScope ps(c.prof, 3, st);
+    launch_blocking(d, st);
   }
   DMRG_CUDA(cudaGetLastError());
-  DMRG_CUDA(cudaStreamSynchronize(c.stream));  // job buffers are freed on return
+  int herr = 0;
+  DMRG_CUDA(cudaMemcpyAsync(&herr, d_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DMRG_CUDA(cudaStreamSynchronize(st));  // tables are freed on return
+  if (herr) throw Error(DMRG_EINVAL, "internal: blocking term shifts a sector inconsistently");
 }
 
 // Transformation O_new[Q' <- Q] = U_Q'^T O[Q' <- Q] U_Q of every operator of
