@@ -301,7 +301,9 @@ int tc_k2_tiles(const TcTask& t, int c0) {  // tiles of the right operand for on
 void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const OpSet& R,
                    const WorkList& wl, TcPlan& plan, int want_items, int seg_tasks) {
   plan = TcPlan();
-  std::map<long long, TcBlock> by_off;  // element offset -> tiled block
+  // element offset -> tiled block: offsets grow in store order, so a sorted
+  // array and binary search map them
+  std::vector<long long> offs;
   long long tile = 0;
   for (const OpSet* s : {&L, &R})
     for (const OpDesc& o : s->ops) {
@@ -310,9 +312,15 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
         TcBlock t{tile, ceil8(b.rows), ceil8(b.cols)};
         tile += (long long)t.R8 * t.C8;
         plan.opblocks.push_back(t);
-        by_off[b.off] = t;
+        offs.push_back(b.off);
       }
     }
+  if (!std::is_sorted(offs.begin(), offs.end())) throw Error(1, "internal: operator blocks out of store order");
+  auto block_at = [&](long long off) -> const TcBlock& {
+    const auto it = std::lower_bound(offs.begin(), offs.end(), off);
+    if (it == offs.end() || *it != off) throw Error(1, "internal: task names no stored block");
+    return plan.opblocks[it - offs.begin()];
+  };
   for (int i = 0; i < L.basis.size(); ++i) {
     TcBlock t{tile, ceil8(L.basis.dim[i]), ceil8(L.basis.dim[i])};
     tile += (long long)t.R8 * t.C8;
@@ -336,8 +344,8 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
   for (size_t t = 0; t < wl.tasks.size(); ++t) {
     const Task& k = wl.tasks[t];
     const PsiBlock& in = blocks[k.in_blk];
-    TcBlock a = k.aoff >= 0 ? by_off.at(k.aoff) : plan.identL[in.qL];
-    TcBlock b = k.boff >= 0 ? by_off.at(k.boff) : plan.identR[in.qR];
+    TcBlock a = k.aoff >= 0 ? block_at(k.aoff) : plan.identL[in.qL];
+    TcBlock b = k.boff >= 0 ? block_at(k.boff) : plan.identR[in.qR];
     TcTask x{};
     x.a_tile = a.tile;
     x.aR8 = a.R8;
@@ -473,6 +481,9 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
   // records
   static_assert(sizeof(TcTaskRec) == 64 && sizeof(TcRec) == 304, "record layout");
   plan.recs.clear();
+  size_t nrec = 0;
+  for (const TcItem& it : plan.items) nrec += std::max(1, it.u_end - it.u_begin);
+  plan.recs.reserve(nrec);
   plan.item_rec.assign(plan.items.size() + 1, 0);
   for (size_t i = 0; i < plan.items.size(); ++i) {
     const TcItem& it = plan.items[i];
