@@ -47,3 +47,25 @@ def test_davidson_lowest_eigenvalue(prec, bar):
     assert abs(np.linalg.norm(x) - 1.0) < 1e-10
     if w[1] - w[0] > 1e-6:
         assert abs(V[:, 0] @ x) > 1.0 - (1e-8 if prec == 0 else 1e-3)
+
+
+def test_davidson_iteration_limit_reports_enoconv():
+    """dav_max_iter reached: DMRG_ENOCONV, with the best Ritz pair still
+    returned; a Ritz value of a symmetric matrix is an upper bound of its
+    lowest eigenvalue."""
+    from paper_2103_09976_gb300 import capi
+    from synth import gaussian_sector_dims, mirrored_sectors
+    left = gaussian_sector_dims(60, n_spatial=4, n_tot=8)
+    right = mirrored_sectors(left, n_tot=8)
+    w, _ = _exact(left, right, 8, 16, (8, 0), 3)
+    ctx = capi.dmrg_create(device=0, dav_max_iter=3)
+    try:
+        capi.dmrg_load_synthetic(ctx, 8, 16, 8, 0, left, right, 3)
+        n = capi.dmrg_psi_layout(ctx)["size"]
+        x = np.zeros(n)
+        e, it, conv = capi.dmrg_davidson(ctx, -1, None, 1e-20, x)
+    finally:
+        capi.dmrg_destroy(ctx)
+    assert not conv and it == 3
+    assert np.isfinite(e) and e >= w[0] - 1e-9 * abs(w[0])
+    assert abs(np.linalg.norm(x) - 1.0) < 1e-10
