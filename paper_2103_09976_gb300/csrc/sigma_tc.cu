@@ -92,13 +92,22 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 // Per-CTA wait-time accounting (profiling only): cycles spent blocked on
 // each kind of barrier, summed in shared memory, flushed to global memory.
 __shared__ unsigned long long s_wait[16];
+__shared__ int s_prof;  // 1 when the launch records wait accounting
+
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+               : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+  return ok != 0;
+}
 
 // Bounded wait; returns false (and raises the abort flag) on timeout or if
 // another role already aborted. `code` names the barrier kind (wait
-// accounting and the error report).
+// accounting and the error report). When profiling, the first probe does
+// not block (test_wait), so every cycle spent waiting is counted.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
                                           int* err, int code) {
-  if (mbar_try(bar, parity)) return true;
+  if (s_prof ? mbar_test(bar, parity) : mbar_try(bar, parity)) return true;
   long long t0 = clock64();
   for (;;) {
     if (mbar_try(bar, parity)) {
@@ -261,6 +270,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
 
   const long long t_start = clock64();
   if (tid < 16) s_wait[tid] = 0ull;
+  if (tid == 0) s_prof = a.wait_prof != nullptr ? 1 : 0;
   // zero all operand buffers once: afterwards shared memory only ever holds
   // finite operand data or zeros, so padded K positions multiply to 0 and
   // padded rows stay finite.
