@@ -5,7 +5,12 @@ dimension M=2000 per side (104 sectors, |psi| = 106,004), 23,654 NC terms,
 synthetic N(0,1) operator blocks (seed 1), FP64 arithmetic. One step = one
 sigma call with psi and the operators resident in HBM.
 
-Prints one JSON line (rank 0). See the design doc for the roofline accounting.
+Prints one JSON line (rank 0). Roofline of the FP64 kernel: algorithmic
+FLOPs per launch (sum over terms and blocks of the cheaper contraction
+order) over its CUDA-event duration, against cuBLAS DGEMM measured in the
+same run; mixed precision: algorithmic bytes (every stored operator element
+once as three bf16 slices, psi, sigma) over the kernel duration, against the
+measured HBM bandwidth.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--M 2000] [--impl ours|reference]
 """
 

@@ -12,9 +12,9 @@
 // read from TMEM, scaled, re-split into bf16 slices and written to shared
 // memory as the A operand of the second product.
 //
-// Warp roles (192 threads): warp 0 streams operator and psi tiles with
-// cp.async.bulk into a 3-stage ring; warp 1 issues the MMAs; warps 2-5 are
-// the epilogue. Operands are stored in 8x8 core-matrix tiles, so one stored
+// Warp roles (320 threads): warp 0 streams operator and psi tiles with
+// cp.async.bulk into a 3-stage ring; warp 1 issues the MMAs; warps 2-9 are
+// the epilogue (two warps per TMEM lane quarter, 32 columns each). Operands are stored in 8x8 core-matrix tiles, so one stored
 // block serves as a K-major operand (S) or an MN-major one (S^T) with no
 // copy: transposed terms only change the shared-memory descriptors.
 //
