@@ -304,7 +304,7 @@ typedef struct dmrg_result {
   int status;                            /* dmrg_status of the solve */
   int iters, converged, slot;
   double energy;
-  double t_submit, t_admit, t_done;
+  double t_submit, t_admit, t_loaded, t_done;  /* t_loaded: operators built, solve starts */
   long long bytes;                       /* admitted footprint */
 } dmrg_result;
 dmrg_status dmrg_server_create(dmrg_server** out, int device, int n_slots, long long budget_bytes);

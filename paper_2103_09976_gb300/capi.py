@@ -50,7 +50,8 @@ class dmrg_request(ctypes.Structure):
 class dmrg_result(ctypes.Structure):
     _fields_ = [("id", ctypes.c_longlong), ("status", ctypes.c_int), ("iters", ctypes.c_int),
                 ("converged", ctypes.c_int), ("slot", ctypes.c_int), ("energy", ctypes.c_double),
-                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_loaded", ctypes.c_double),
+                ("t_done", ctypes.c_double),
                 ("bytes", ctypes.c_longlong)]
 
 

@@ -30,6 +30,7 @@ thread_local std::string g_noctx_err = "no error";
 template <class F>
 dmrg_status guarded(dmrg_ctx* ctx, F&& f) {
   try {
+    AllocStreamScope scope(ctx ? ctx->c.stream : nullptr);
     f();
     if (ctx) ctx->c.err.clear();
     return DMRG_OK;
@@ -472,6 +473,20 @@ long long synthetic_footprint(int nL, int n, int N, int two_sz, const Basis& bL,
 
 }  // namespace dmrg
 
+namespace dmrg {
+thread_local cudaStream_t t_alloc_stream = nullptr;
+
+void release_context_buffers(Context& c) {
+  if (c.stream) cudaStreamSynchronize(c.stream);
+  c.prob.reset();
+  c.sweep.reset();
+  c.d_psi.reset();
+  c.d_sigma.reset();
+  c.d_wait_prof.reset();
+  if (c.stream) cudaStreamSynchronize(c.stream);
+}
+}  // namespace dmrg
+
 extern "C" {
 
 void dmrg_default_opts(dmrg_opts* o) {
@@ -525,11 +540,9 @@ dmrg_status dmrg_create(dmrg_ctx** out, const dmrg_opts* opts) {
 void dmrg_destroy(dmrg_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->c.device);
-  if (ctx->c.stream) cudaStreamSynchronize(ctx->c.stream);
-  ctx->c.prob.reset();
-  ctx->c.d_psi.reset();
-  ctx->c.d_sigma.reset();
+  release_context_buffers(ctx->c);
   if (ctx->c.stream) cudaStreamDestroy(ctx->c.stream);
+  ctx->c.stream = nullptr;
   delete ctx;
 }
 

@@ -23,33 +23,64 @@ namespace dmrg {
                           std::string(#call) + ": " + cudaGetErrorString(e_));             \
   } while (0)
 
-// Owning device allocation.
+// Stream that this thread's device allocations are ordered on: set by the
+// library's entry points (the context's stream) and by serving workers.
+// With a stream set, DevBuf uses the stream-ordered allocator
+// (cudaMallocAsync / cudaFreeAsync on that stream), so allocating or freeing
+// never synchronizes the device with work on other streams; without one it
+// falls back to cudaMalloc / cudaFree.
+extern thread_local cudaStream_t t_alloc_stream;
+struct AllocStreamScope {
+  cudaStream_t prev;
+  explicit AllocStreamScope(cudaStream_t s) : prev(t_alloc_stream) { t_alloc_stream = s; }
+  ~AllocStreamScope() { t_alloc_stream = prev; }
+  AllocStreamScope(const AllocStreamScope&) = delete;
+  AllocStreamScope& operator=(const AllocStreamScope&) = delete;
+};
+
+// Owning device allocation. A stream-ordered buffer is freed on the stream
+// it was allocated on, which must outlive it (contexts free their buffers
+// before destroying their stream).
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  cudaStream_t st = nullptr;
+  bool async = false;
   DevBuf() = default;
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
   ~DevBuf() { reset(); }
   void reset() {
-    if (p) cudaFree(p);
+    if (p) {
+      if (async)
+        cudaFreeAsync(p, st);
+      else
+        cudaFree(p);
+    }
     p = nullptr;
     bytes = 0;
+    async = false;
   }
   void alloc(size_t n) {
     if (n <= bytes && p) return;
     reset();
     if (n == 0) n = 16;
-    DMRG_CUDA(cudaMalloc(&p, n));
+    if (t_alloc_stream) {
+      DMRG_CUDA(cudaMallocAsync(&p, n, t_alloc_stream));
+      st = t_alloc_stream;
+      async = true;
+    } else {
+      DMRG_CUDA(cudaMalloc(&p, n));
+    }
     bytes = n;
   }
   template <class T>
   T* as() const { return reinterpret_cast<T*>(p); }
   template <class T>
-  void upload(const std::vector<T>& v, cudaStream_t st) {
+  void upload(const std::vector<T>& v, cudaStream_t s) {
     alloc(v.size() * sizeof(T));
     if (!v.empty())
-      DMRG_CUDA(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+      DMRG_CUDA(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
   }
 };
 
@@ -159,6 +190,9 @@ struct Context {
   DevBuf d_wait_prof;              // tensor-core kernel wait accounting (profiling only)
 };
 
+// Free every device buffer of the context (in stream order) and wait for the
+// frees; the stream itself stays.
+void release_context_buffers(Context& c);
 void prepare_worklist(Context& c, Problem& p);
 Basis parse_sectors(int n, const int* s);
 void load_synthetic(Context& c, int nL, int n, int N, int two_sz, const Basis& bL, const Basis& bR,

@@ -72,6 +72,7 @@ struct dmrg_server {
     c.device = device;
     c.n_sm = n_sm;
     if (cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking) != cudaSuccess) return;
+    AllocStreamScope scope(c.stream);
     for (;;) {
       Job job;
       {
@@ -98,6 +99,7 @@ struct dmrg_server {
         load_synthetic(c, job.r.n_left_modes, job.r.n_modes, job.r.N, job.r.two_sz,
                        parse_sectors((int)job.left.size() / 3, job.left.data()),
                        parse_sectors((int)job.right.size() / 3, job.right.data()), job.r.seed);
+        res.t_loaded = now();
         double e = 0.0;
         int it = 0;
         const bool conv = run_davidson(c, *c.prob, nullptr, job.r.tol, &e, nullptr, &it, 0ull);
@@ -126,7 +128,7 @@ struct dmrg_server {
       cv_work.notify_all();
       cv_done.notify_all();
     }
-    c.prob.reset();
+    release_context_buffers(c);
     cudaStreamDestroy(c.stream);
     c.stream = nullptr;
   }

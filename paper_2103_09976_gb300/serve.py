@@ -62,6 +62,8 @@ def summarize(results, requests):
             "solves_per_s": len(results) / span if span > 0 else None,
             "ok": sum(1 for r in results.values() if r["status"] == capi.DMRG_OK),
             "converged": sum(1 for r in results.values() if r["converged"]),
+            "mean_load_s": float(np.mean([r["t_loaded"] - r["t_admit"] for r in results.values()])),
+            "mean_solve_s": float(np.mean([r["t_done"] - r["t_loaded"] for r in results.values()])),
             "mix": sorted({(by_id[i]["K"], by_id[i]["M"]) for i in results})}
 
 
