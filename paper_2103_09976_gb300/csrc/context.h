@@ -188,6 +188,21 @@ struct Context {
   DevBuf d_psi, d_sigma;           // staging for host psi / sigma
   Profiler prof;
   DevBuf d_wait_prof;              // tensor-core kernel wait accounting (profiling only)
+  // Pinned host scalars for the few device-to-host reads of the Davidson
+  // loop (a pageable destination would stage every copy).
+  struct PinnedScalars {
+    double* p = nullptr;
+    PinnedScalars() = default;
+    PinnedScalars(const PinnedScalars&) = delete;
+    PinnedScalars& operator=(const PinnedScalars&) = delete;
+    double* get() {
+      if (!p && cudaMallocHost(&p, 8 * sizeof(double)) != cudaSuccess) p = nullptr;
+      return p;
+    }
+    ~PinnedScalars() {
+      if (p) cudaFreeHost(p);
+    }
+  } h_scalars;
 };
 
 // Free every device buffer of the context (in stream order) and wait for the

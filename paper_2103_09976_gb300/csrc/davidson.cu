@@ -16,38 +16,51 @@ namespace {
 constexpr int RED_BLOCKS = 256;   // partial sums per dot product
 constexpr int RED_THREADS = 256;
 
-// partial[i * RED_BLOCKS + b] = sum over block b's elements of V[i][e] * w[e]
+constexpr int KMAX = 32;           // vectors per dot-product call (subspace size limit)
+
+// partial[i * RED_BLOCKS + b] = sum over block b's elements of V[i][e] * w[e],
+// for all i < k in one pass: each thread keeps k running sums, then the block
+// reduces them (warp shuffles, then across warps) in a fixed order.
 __global__ void dots_partial(const double* __restrict__ V, long long ld, int k, const double* __restrict__ w,
                              long long n, double* __restrict__ partial) {
-  __shared__ double red[RED_THREADS];
-  for (int i = 0; i < k; ++i) {
-    double s = 0.0;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-      s = fma(V[i * ld + e], w[e], s);
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-      if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
-      __syncthreads();
+  __shared__ double red[RED_THREADS / 32][KMAX];
+  double s[KMAX];
+#pragma unroll
+  for (int i = 0; i < KMAX; ++i) s[i] = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const double we = w[e];
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i)
+      if (i < k) s[i] = fma(V[i * ld + e], we, s[i]);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < KMAX; ++i) {
+    if (i < k) {
+      double v = s[i];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[wid][i] = v;
     }
-    if (threadIdx.x == 0) partial[i * RED_BLOCKS + blockIdx.x] = red[0];
-    __syncthreads();
+  }
+  __syncthreads();
+  if (threadIdx.x < k) {
+    double v = 0.0;
+    for (int j = 0; j < RED_THREADS / 32; ++j) v += red[j][threadIdx.x];
+    partial[threadIdx.x * RED_BLOCKS + blockIdx.x] = v;
   }
 }
 
-// out[i * out_stride] = sum_b partial[i * RED_BLOCKS + b] (fixed order)
+// out[i * out_stride] = sum_b partial[i * RED_BLOCKS + b] (fixed order); one block per i
 __global__ void dots_final(const double* __restrict__ partial, int k, double* __restrict__ out, int out_stride) {
   __shared__ double red[RED_BLOCKS];
-  for (int i = 0; i < k; ++i) {
-    red[threadIdx.x] = partial[i * RED_BLOCKS + threadIdx.x];
-    __syncthreads();
-    for (int h = RED_BLOCKS / 2; h > 0; h >>= 1) {
-      if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) out[(long long)i * out_stride] = red[0];
+  const int i = blockIdx.x;
+  red[threadIdx.x] = partial[i * RED_BLOCKS + threadIdx.x];
+  __syncthreads();
+  for (int h = RED_BLOCKS / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
     __syncthreads();
   }
+  if (threadIdx.x == 0) out[(long long)i * out_stride] = red[0];
 }
 
 // out = sum_i c[i*cs] V[i] (+ beta * out when add)
@@ -81,12 +94,17 @@ __global__ void scale_kernel(double* __restrict__ x, const double* __restrict__ 
 }
 
 // Eigenpairs of the symmetric part of the k x k matrix H (row-major, leading
-// dimension ldh) by cyclic Jacobi rotations; w ascending, Y columns = vectors
-// (Y row-major k x ldh). One warp; lane r owns row/column r.
+// dimension ldh) by cyclic Jacobi in round-robin order (Brent-Luk): each
+// round rotates up to 16 disjoint index pairs at once, lane i computing the
+// rotation of pair i, then every lane applies all of them to its row (and
+// its column). w ascending, Y columns = vectors (Y row-major k x ldh). One
+// warp; k <= 32.
 __global__ void jacobi_eigh(const double* __restrict__ H, int k, int ldh, double* __restrict__ w,
                             double* __restrict__ Y) {
   __shared__ double A[32][33];
   __shared__ double Q[32][33];
+  __shared__ double cs[16], sn[16];
+  __shared__ int pp[16], qq[16];
   const int r = threadIdx.x;
   for (int c = 0; c < k; ++c)
     if (r < k) {
@@ -94,7 +112,9 @@ __global__ void jacobi_eigh(const double* __restrict__ H, int k, int ldh, double
       Q[r][c] = (r == c) ? 1.0 : 0.0;
     }
   __syncwarp();
-  for (int sweep = 0; sweep < 60; ++sweep) {
+  const int kp = k + (k & 1);            // players, one dummy when k is odd
+  const int npairs = kp / 2;
+  for (int sweep = 0; sweep < 60 && k > 1; ++sweep) {
     double off = 0.0, tot = 0.0;
     if (r < k)
       for (int c = 0; c < k; ++c) {
@@ -106,38 +126,55 @@ __global__ void jacobi_eigh(const double* __restrict__ H, int k, int ldh, double
       tot += __shfl_xor_sync(0xffffffffu, tot, o);
     }
     if (off <= 1e-30 * tot || off == 0.0) break;
-    for (int p = 0; p < k - 1; ++p)
-      for (int q = p + 1; q < k; ++q) {
-        const double apq = A[p][q];
-        if (apq == 0.0) continue;
-        const double app = A[p][p], aqq = A[q][q];
-        const double th = (aqq - app) / (2.0 * apq);
-        const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-        const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
-        __syncwarp();
-        if (r < k && r != p && r != q) {
-          const double arp = A[r][p], arq = A[r][q];
-          A[r][p] = cs * arp - sn * arq;
-          A[r][q] = sn * arp + cs * arq;
+    for (int round = 0; round < kp - 1; ++round) {
+      if (r < npairs) {
+        auto player = [&](int i) { return i == 0 ? 0 : 1 + (i - 1 + round) % (kp - 1); };
+        int p = player(r), q = player(kp - 1 - r);
+        if (p > q) { const int t = p; p = q; q = t; }
+        double c = 1.0, sv = 0.0;
+        if (q < k) {
+          const double apq = A[p][q];
+          if (apq != 0.0) {
+            const double th = (A[q][q] - A[p][p]) / (2.0 * apq);
+            const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            sv = t * c;
+          }
         }
-        if (r < k) {
-          const double qp = Q[r][p], qq = Q[r][q];
-          Q[r][p] = cs * qp - sn * qq;
-          Q[r][q] = sn * qp + cs * qq;
-        }
-        __syncwarp();
-        if (r < k && r != p && r != q) {
-          A[p][r] = A[r][p];
-          A[q][r] = A[r][q];
-        }
-        if (r == 0) {
-          A[p][p] = app - t * apq;
-          A[q][q] = aqq + t * apq;
-          A[p][q] = 0.0;
-          A[q][p] = 0.0;
-        }
-        __syncwarp();
+        cs[r] = c;
+        sn[r] = sv;
+        pp[r] = p;
+        qq[r] = q < k ? q : -1;
       }
+      __syncwarp();
+      // columns: A <- A J, Q <- Q J (lane r owns row r)
+      if (r < k)
+        for (int i = 0; i < npairs; ++i) {
+          const int q = qq[i];
+          if (q < 0 || sn[i] == 0.0) continue;
+          const int p = pp[i];
+          const double c = cs[i], sv = sn[i];
+          const double arp = A[r][p], arq = A[r][q];
+          A[r][p] = c * arp - sv * arq;
+          A[r][q] = sv * arp + c * arq;
+          const double qp = Q[r][p], qv = Q[r][q];
+          Q[r][p] = c * qp - sv * qv;
+          Q[r][q] = sv * qp + c * qv;
+        }
+      __syncwarp();
+      // rows: A <- J^T A (lane r owns column r)
+      if (r < k)
+        for (int i = 0; i < npairs; ++i) {
+          const int q = qq[i];
+          if (q < 0 || sn[i] == 0.0) continue;
+          const int p = pp[i];
+          const double c = cs[i], sv = sn[i];
+          const double apc = A[p][r], aqc = A[q][r];
+          A[p][r] = c * apc - sv * aqc;
+          A[q][r] = sv * apc + c * aqc;
+        }
+      __syncwarp();
+    }
   }
   // sort ascending (selection sort on lane 0, columns of Q follow)
   if (r == 0) {
@@ -151,10 +188,9 @@ __global__ void jacobi_eigh(const double* __restrict__ H, int k, int ldh, double
       idx[i] = idx[m];
       idx[m] = tmp;
     }
-    for (int i = 0; i < k; ++i) {
-      w[i] = A[idx[i]][idx[i]];
+    for (int i = 0; i < k; ++i) w[i] = A[idx[i]][idx[i]];
+    for (int i = 0; i < k; ++i)
       for (int rr = 0; rr < k; ++rr) Y[rr * ldh + i] = Q[rr][idx[i]];
-    }
   }
 }
 
@@ -163,8 +199,9 @@ __global__ void jacobi_eigh(const double* __restrict__ H, int k, int ldh, double
 void dav_dots(const double* V, long long ld, int k, const double* w, long long n, double* partial, double* out,
               int out_stride, cudaStream_t st) {
   if (k <= 0) return;
+  if (k > KMAX) k = KMAX;  // the subspace size is checked against this limit on the host
   dots_partial<<<RED_BLOCKS, RED_THREADS, 0, st>>>(V, ld, k, w, n, partial);
-  dots_final<<<1, RED_BLOCKS, 0, st>>>(partial, k, out, out_stride);
+  dots_final<<<k, RED_BLOCKS, 0, st>>>(partial, k, out, out_stride);
 }
 
 void dav_lincomb(const double* V, long long ld, int k, const double* c, int cs, double sign, double* out,

@@ -79,10 +79,14 @@ bool run_davidson(Context& c, Problem& p, const double* x0, double tol, double* 
   double host[2];
 
   auto sigma = [&](const double* in, double* out) { run_sigma(c, p, in, out); };
+  double* pinned = c.h_scalars.get();
   auto read2 = [&](const double* a, const double* b) {
-    DMRG_CUDA(cudaMemcpyAsync(&host[0], a, sizeof(double), cudaMemcpyDeviceToHost, st));
-    DMRG_CUDA(cudaMemcpyAsync(&host[1], b, sizeof(double), cudaMemcpyDeviceToHost, st));
+    double* dst = pinned ? pinned : host;
+    DMRG_CUDA(cudaMemcpyAsync(&dst[0], a, sizeof(double), cudaMemcpyDeviceToHost, st));
+    DMRG_CUDA(cudaMemcpyAsync(&dst[1], b, sizeof(double), cudaMemcpyDeviceToHost, st));
     DMRG_CUDA(cudaStreamSynchronize(st));
+    host[0] = dst[0];
+    host[1] = dst[1];
   };
   // projected-matrix entries of the newest vector j: H[i][j] = V_i . AV_j, H[j][i] = V_j . AV_i
   auto update_H = [&](int k) {
