@@ -95,41 +95,95 @@ __global__ void scale_kernel(double* __restrict__ x, const double* __restrict__ 
 
 // Eigenpairs of the symmetric part of the k x k matrix H (row-major, leading
 // dimension ldh) by cyclic Jacobi in round-robin order (Brent-Luk): each
-// round rotates up to 16 disjoint index pairs at once, lane i computing the
-// rotation of pair i, then every lane applies all of them to its row (and
-// its column). w ascending, Y columns = vectors (Y row-major k x ldh). One
-// warp; k <= 32.
+// round rotates up to 16 disjoint index pairs at once. Four warps share the
+// work (the FP64 rate of one SM sub-partition would otherwise bound it):
+// pair i's rotation is computed by warp i % 4, and every thread applies the
+// rotations of its warp's pairs to its row (and its column). w ascending,
+// Y columns = vectors (Y row-major k x ldh). k <= 32; 128 threads.
+//
+// Warm start (k0 > 0): the leading k0 x k0 block of H is the previous
+// projected matrix and Y holds its eigenvectors, so Q starts as
+// diag(Y[:k0, :k0], 1) and A as Q^T H Q, which is diagonal except for the
+// rows and columns added since; Jacobi then needs fewer sweeps.
+constexpr int EIGH_WARPS = 4;
 __global__ void jacobi_eigh(const double* __restrict__ H, int k, int ldh, double* __restrict__ w,
-                            double* __restrict__ Y) {
+                            double* __restrict__ Y, int k0) {
   __shared__ double A[32][33];
   __shared__ double Q[32][33];
+  __shared__ double T[32][33];
   __shared__ double cs[16], sn[16];
   __shared__ int pp[16], qq[16];
-  const int r = threadIdx.x;
-  for (int c = 0; c < k; ++c)
-    if (r < k) {
-      A[r][c] = 0.5 * (H[r * ldh + c] + H[c * ldh + r]);
-      Q[r][c] = (r == c) ? 1.0 : 0.0;
+  __shared__ double red[2][EIGH_WARPS];
+  __shared__ int stop;
+  const int tid = threadIdx.x, r = tid & 31, wid = tid >> 5;
+  for (int e = tid; e < k * k; e += blockDim.x) {
+    const int i = e / k, c = e % k;
+    A[i][c] = 0.5 * (H[i * ldh + c] + H[c * ldh + i]);
+    Q[i][c] = (i < k0 && c < k0) ? Y[i * ldh + c] : (i == c ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  if (k0 > 0) {
+    for (int e = tid; e < k * k; e += blockDim.x) {  // T = A Q
+      const int i = e / k, c = e % k;
+      double s = 0.0;
+      for (int j = 0; j < k; ++j) s = fma(A[i][j], Q[j][c], s);
+      T[i][c] = s;
     }
-  __syncwarp();
+    __syncthreads();
+    for (int e = tid; e < k * k; e += blockDim.x) {  // A = Q^T T, symmetrized below
+      const int i = e / k, c = e % k;
+      double s = 0.0;
+      for (int j = 0; j < k; ++j) s = fma(Q[j][i], T[j][c], s);
+      A[i][c] = s;
+    }
+    __syncthreads();
+    for (int e = tid; e < k * k; e += blockDim.x) {
+      const int i = e / k, c = e % k;
+      if (c < i) T[i][c] = 0.5 * (A[i][c] + A[c][i]);
+    }
+    __syncthreads();
+    for (int e = tid; e < k * k; e += blockDim.x) {
+      const int i = e / k, c = e % k;
+      if (c < i) A[i][c] = T[i][c];
+      else if (c > i) A[i][c] = T[c][i];
+    }
+    __syncthreads();
+  }
   const int kp = k + (k & 1);            // players, one dummy when k is odd
   const int npairs = kp / 2;
   for (int sweep = 0; sweep < 60 && k > 1; ++sweep) {
     double off = 0.0, tot = 0.0;
-    if (r < k)
-      for (int c = 0; c < k; ++c) {
-        tot += A[r][c] * A[r][c];
-        if (c != r) off += A[r][c] * A[r][c];
-      }
+    for (int e = tid; e < k * k; e += blockDim.x) {
+      const int i = e / k, c = e % k;
+      const double a = A[i][c];
+      tot += a * a;
+      if (c != i) off += a * a;
+    }
     for (int o = 16; o > 0; o >>= 1) {
       off += __shfl_xor_sync(0xffffffffu, off, o);
       tot += __shfl_xor_sync(0xffffffffu, tot, o);
     }
-    if (off <= 1e-30 * tot || off == 0.0) break;
+    if (r == 0) {
+      red[0][wid] = off;
+      red[1][wid] = tot;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double o2 = 0.0, t2 = 0.0;
+      for (int j = 0; j < EIGH_WARPS; ++j) {
+        o2 += red[0][j];
+        t2 += red[1][j];
+      }
+      stop = (o2 <= 1e-30 * t2 || o2 == 0.0) ? 1 : 0;
+    }
+    __syncthreads();
+    if (stop) break;
     for (int round = 0; round < kp - 1; ++round) {
-      if (r < npairs) {
-        auto player = [&](int i) { return i == 0 ? 0 : 1 + (i - 1 + round) % (kp - 1); };
-        int p = player(r), q = player(kp - 1 - r);
+      // pair i = r * EIGH_WARPS + wid: lane r of warp wid
+      const int i = r * EIGH_WARPS + wid;
+      if (r < 4 && i < npairs) {
+        auto player = [&](int x) { return x == 0 ? 0 : 1 + (x - 1 + round) % (kp - 1); };
+        int p = player(i), q = player(kp - 1 - i);
         if (p > q) { const int t = p; p = q; q = t; }
         double c = 1.0, sv = 0.0;
         if (q < k) {
@@ -141,19 +195,19 @@ __global__ void jacobi_eigh(const double* __restrict__ H, int k, int ldh, double
             sv = t * c;
           }
         }
-        cs[r] = c;
-        sn[r] = sv;
-        pp[r] = p;
-        qq[r] = q < k ? q : -1;
+        cs[i] = c;
+        sn[i] = sv;
+        pp[i] = p;
+        qq[i] = q < k ? q : -1;
       }
-      __syncwarp();
-      // columns: A <- A J, Q <- Q J (lane r owns row r)
+      __syncthreads();
+      // columns: A <- A J, Q <- Q J (thread (r, wid): row r, pairs wid, wid + 4, ...)
       if (r < k)
-        for (int i = 0; i < npairs; ++i) {
-          const int q = qq[i];
-          if (q < 0 || sn[i] == 0.0) continue;
-          const int p = pp[i];
-          const double c = cs[i], sv = sn[i];
+        for (int j = wid; j < npairs; j += EIGH_WARPS) {
+          const int q = qq[j];
+          if (q < 0 || sn[j] == 0.0) continue;
+          const int p = pp[j];
+          const double c = cs[j], sv = sn[j];
           const double arp = A[r][p], arq = A[r][q];
           A[r][p] = c * arp - sv * arq;
           A[r][q] = sv * arp + c * arq;
@@ -161,36 +215,31 @@ __global__ void jacobi_eigh(const double* __restrict__ H, int k, int ldh, double
           Q[r][p] = c * qp - sv * qv;
           Q[r][q] = sv * qp + c * qv;
         }
-      __syncwarp();
-      // rows: A <- J^T A (lane r owns column r)
+      __syncthreads();
+      // rows: A <- J^T A (thread (r, wid): column r, pairs wid, wid + 4, ...)
       if (r < k)
-        for (int i = 0; i < npairs; ++i) {
-          const int q = qq[i];
-          if (q < 0 || sn[i] == 0.0) continue;
-          const int p = pp[i];
-          const double c = cs[i], sv = sn[i];
+        for (int j = wid; j < npairs; j += EIGH_WARPS) {
+          const int q = qq[j];
+          if (q < 0 || sn[j] == 0.0) continue;
+          const int p = pp[j];
+          const double c = cs[j], sv = sn[j];
           const double apc = A[p][r], aqc = A[q][r];
           A[p][r] = c * apc - sv * aqc;
           A[q][r] = sv * apc + c * aqc;
         }
-      __syncwarp();
+      __syncthreads();
     }
   }
-  // sort ascending (selection sort on lane 0, columns of Q follow)
-  if (r == 0) {
-    int idx[32];
-    for (int i = 0; i < k; ++i) idx[i] = i;
-    for (int i = 0; i < k; ++i) {
-      int m = i;
-      for (int j = i + 1; j < k; ++j)
-        if (A[idx[j]][idx[j]] < A[idx[m]][idx[m]]) m = j;
-      const int tmp = idx[i];
-      idx[i] = idx[m];
-      idx[m] = tmp;
+  // sort ascending: rank of each eigenvalue (ties by index), then scatter
+  if (tid < k) {
+    const double v = A[tid][tid];
+    int rank = 0;
+    for (int j = 0; j < k; ++j) {
+      const double u = A[j][j];
+      rank += (u < v) || (u == v && j < tid);
     }
-    for (int i = 0; i < k; ++i) w[i] = A[idx[i]][idx[i]];
-    for (int i = 0; i < k; ++i)
-      for (int rr = 0; rr < k; ++rr) Y[rr * ldh + i] = Q[rr][idx[i]];
+    w[rank] = v;
+    for (int rr = 0; rr < k; ++rr) Y[rr * ldh + rank] = Q[rr][tid];
   }
 }
 
@@ -227,8 +276,8 @@ void dav_scale(double* x, const double* nrm2, long long n, cudaStream_t st) {
   scale_kernel<<<(unsigned)grid, 256, 0, st>>>(x, nrm2, n);
 }
 
-void dav_eigh(const double* H, int k, int ldh, double* w, double* Y, cudaStream_t st) {
-  jacobi_eigh<<<1, 32, 0, st>>>(H, k, ldh, w, Y);
+void dav_eigh(const double* H, int k, int ldh, double* w, double* Y, int k0, cudaStream_t st) {
+  jacobi_eigh<<<1, 32 * EIGH_WARPS, 0, st>>>(H, k, ldh, w, Y, k0 < k ? k0 : 0);
 }
 
 }  // namespace dmrg

@@ -108,8 +108,10 @@ bool run_davidson(Context& c, Problem& p, const double* x0, double tol, double* 
   update_H(k);
   bool converged = false;
   double theta = 0.0;
+  int warm = 0;  // size of the projected matrix whose eigenvectors Y holds
   for (;;) {
-    dav_eigh(H, k, LDH, w, Y, st);
+    dav_eigh(H, k, LDH, w, Y, warm, st);
+    warm = k;
     dav_lincomb(V, n, k, Y, LDH, 1.0, x, n, false, st);
     dav_lincomb(AV, n, k, Y, LDH, 1.0, ax, n, false, st);
     dav_residual(x, ax, p.dav_diag.as<double>(), w, r, t, n, st);
@@ -131,6 +133,7 @@ bool run_davidson(Context& c, Problem& p, const double* x0, double tol, double* 
       DMRG_CUDA(cudaMemcpyAsync(row(AV, 0), ax, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
       DMRG_CUDA(cudaMemcpyAsync(row(AV, 1), r, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
       k = 2;
+      warm = 0;
       update_H(1);
       update_H(2);
     }
