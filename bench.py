@@ -310,16 +310,19 @@ def main():
         for _ in range(max(3, args.warmup)):
             capi.dmrg_sigma(ctx, -1, x, y)
         capi.dmrg_sync(ctx)
-        capi.dmrg_profile(ctx, True)
         e0.record(stream)
         for _ in range(args.steps):
             capi.dmrg_sigma(ctx, -1, x, y)
         e1.record(stream)
         e1.synchronize()
         capi.dmrg_sync(ctx)
+        step = e0.elapsed_time(e1) / 1e3 / args.steps
+        capi.dmrg_profile(ctx, True)          # kernel durations, launched directly
+        for _ in range(args.steps):
+            capi.dmrg_sigma(ctx, -1, x, y)
+        capi.dmrg_sync(ctx)
         tms, tn = capi.dmrg_profile_read(ctx, capi.KERNEL_SIGMA)
         capi.dmrg_profile(ctx, False)
-        step = e0.elapsed_time(e1) / 1e3 / args.steps
         kern = tms / 1e3 / max(1, tn)
         d = (y - y64).abs().max().item() / y64.abs().max().item()
         rq = abs(float(x @ y) - float(x @ y64)) / abs(float(x @ y64))

@@ -317,7 +317,9 @@ void dmrg_server_destroy(dmrg_server* s);
 /*
  * Per-kernel timing with CUDA events recorded on the context's stream
  * around each launch of the library's kernels (tracing aid; off by default).
- * dmrg_profile(ctx, 1) clears the counters and starts recording; 0 stops.
+ * dmrg_profile(ctx, 1) clears the counters and starts recording; 2 does the
+ * same and also runs the tensor-core kernel's wait accounting (which slows
+ * that kernel; see dmrg_profile_waits); 0 stops.
  * dmrg_profile_read synchronizes the stream and returns, for kernel id
  * `kernel` (0 = sigma product kernel, 1 = sigma reduction, 2 = Davidson
  * vector kernels, 3 = blocking / transformation kernels), the summed
@@ -326,7 +328,7 @@ void dmrg_server_destroy(dmrg_server* s);
 dmrg_status dmrg_profile(dmrg_ctx* ctx, int enable);
 
 /* Wait accounting of the tensor-core sigma kernel, summed over its CTAs and
- * launches since dmrg_profile(ctx, 1): cycles[k] for k < 16 = clock cycles
+ * launches since dmrg_profile(ctx, 2): cycles[k] for k < 16 = clock cycles
  * spent blocked on barrier kind k (1 stage free, 2 sigma tile free, 3 X tile
  * free, 4 stage loaded, 5 second-product operand written, 6 X tile computed,
  * 7 second-product operand free, 8 sigma tile computed, 9-13 unit-record

@@ -284,8 +284,10 @@ def dmrg_sweep_log(ctx):
 KERNEL_SIGMA, KERNEL_REDUCE, KERNEL_DAVIDSON, KERNEL_BLOCKING = 0, 1, 2, 3
 
 
-def dmrg_profile(ctx, enable):
-    _check(ctx, lib().dmrg_profile(ctx, 1 if enable else 0))
+def dmrg_profile(ctx, enable, waits=False):
+    """Per-kernel CUDA-event timing on (enable) / off; waits=True also runs the
+    tensor-core kernel's wait accounting (slower kernel)."""
+    _check(ctx, lib().dmrg_profile(ctx, (2 if waits else 1) if enable else 0))
 
 
 def dmrg_profile_read(ctx, kernel):

@@ -177,7 +177,7 @@ static void run_sigma_tc(Context& c, Problem& p, const double* d_psi, double* d_
   t.err = p.d_err.as<int>();
   t.nprod = c.opts.sigma_prec == DMRG_BF16X3 ? 6 : 3;
   t.wait_prof = nullptr;
-  if (c.prof.on) {
+  if (c.prof.on && c.prof.waits) {
     if (!c.d_wait_prof.p) {
       c.d_wait_prof.alloc(32 * sizeof(unsigned long long));
       DMRG_CUDA(cudaMemsetAsync(c.d_wait_prof.p, 0, 32 * sizeof(unsigned long long), c.stream));
@@ -799,8 +799,10 @@ dmrg_status dmrg_profile(dmrg_ctx* ctx, int enable) {
     DMRG_CUDA(cudaSetDevice(ctx->c.device));
     if (enable && ctx->c.d_wait_prof.p)
       DMRG_CUDA(cudaMemsetAsync(ctx->c.d_wait_prof.p, 0, 32 * sizeof(unsigned long long), ctx->c.stream));
+    if (enable < 0 || enable > 2) throw Error(DMRG_EINVAL, "enable must be 0, 1 or 2");
     if (enable) ctx->c.prof.clear();
     ctx->c.prof.on = enable != 0;
+    ctx->c.prof.waits = enable == 2;
   });
 }
 

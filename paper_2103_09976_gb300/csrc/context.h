@@ -149,6 +149,7 @@ struct Problem {
 struct Profiler {
   static constexpr int kKinds = 4;
   bool on = false;
+  bool waits = false;   // also run the tensor-core kernel's wait accounting
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[kKinds];
   std::vector<cudaEvent_t> pool;
   double ms[kKinds] = {0, 0, 0, 0};

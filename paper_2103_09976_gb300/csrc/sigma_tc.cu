@@ -92,7 +92,6 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 // Per-CTA wait-time accounting (profiling only): cycles spent blocked on
 // each kind of barrier, summed in shared memory, flushed to global memory.
 __shared__ unsigned long long s_wait[16];
-__shared__ int s_prof;  // 1 when the launch records wait accounting
 
 __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
   uint32_t ok;
@@ -103,15 +102,16 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
 
 // Bounded wait; returns false (and raises the abort flag) on timeout or if
 // another role already aborted. `code` names the barrier kind (wait
-// accounting and the error report). When profiling, the first probe does
-// not block (test_wait), so every cycle spent waiting is counted.
+// accounting and the error report). With wait accounting (PROF) the first
+// probe does not block (test_wait), so every cycle spent waiting is counted.
+template <bool PROF>
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
                                           int* err, int code) {
-  if (s_prof ? mbar_test(bar, parity) : mbar_try(bar, parity)) return true;
+  if (PROF ? mbar_test(bar, parity) : mbar_try(bar, parity)) return true;
   long long t0 = clock64();
   for (;;) {
     if (mbar_try(bar, parity)) {
-      atomicAdd(&s_wait[code & 15], (unsigned long long)(clock64() - t0));
+      if (PROF) atomicAdd(&s_wait[code & 15], (unsigned long long)(clock64() - t0));
       return true;
     }
     if (*abort_flag) return false;
@@ -257,7 +257,8 @@ __device__ __forceinline__ void mma_chain(uint32_t tmem_d, uint64_t ad0, uint64_
   }
 }
 
-template <int NPROD>
+// PROF: record wait accounting and MMA-thread cycles into a.wait_prof.
+template <int NPROD, bool PROF>
 __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -270,7 +271,6 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
 
   const long long t_start = clock64();
   if (tid < 16) s_wait[tid] = 0ull;
-  if (tid == 0) s_prof = a.wait_prof != nullptr ? 1 : 0;
   // zero all operand buffers once: afterwards shared memory only ever holds
   // finite operand data or zeros, so padded K positions multiply to 0 and
   // padded rows stay finite.
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
     const char* const ps = (const char*)a.psi;
     auto produce = [&](const TcRec& u, int k1, int k2) {
       if (!ok) return;
-      if (!mbar_wait(bar(B_EMPTY + stage), phase, abort_flag, a.err, 1)) { ok = false; return; }
+      if (!mbar_wait<PROF>(bar(B_EMPTY + stage), phase, abort_flag, a.err, 1)) { ok = false; return; }
       uint32_t tiles = 0;
       lane_copies(u, k1, k2, lane, [&](long long, int, int, int n) { tiles += (uint32_t)n; });
       tiles = __reduce_add_sync(0xffffffffu, tiles);
@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
       }
       const int slot = (int)(pf_s % NMETA);
       const uint32_t par = (uint32_t)(((pf_s / NMETA) & 1) ^ 1);
-      if (!mbar_wait(bar(B_MEMPTY + slot), par, abort_flag, a.err, 9)) { ok = false; return false; }
+      if (!mbar_wait<PROF>(bar(B_MEMPTY + slot), par, abort_flag, a.err, 9)) { ok = false; return false; }
       if (lane == 0) {
         mbar_expect_tx(bar(B_MFULL + slot), (uint32_t)sizeof(TcRec));
         bulk_g2s(smem_u32(ring + slot), a.recs + pf_r, (uint32_t)sizeof(TcRec), bar(B_MFULL + slot));
@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
       if (!ok) break;
       if (s == pf_s) break;  // nothing left
       const int slot = (int)(s % NMETA);
-      if (!mbar_wait(bar(B_MFULL + slot), (uint32_t)((s / NMETA) & 1), abort_flag, a.err, 10)) { ok = false; break; }
+      if (!mbar_wait<PROF>(bar(B_MFULL + slot), (uint32_t)((s / NMETA) & 1), abort_flag, a.err, 10)) { ok = false; break; }
       const TcRec& u = ring[slot];
       if (!(u.flags & REC_ZERO))
         for (int k = 0; k < rec_k1(u); ++k) produce(u, k, -1);
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
     if (ok) {
       const int slot = (int)(s % NMETA);
       const uint32_t par = (uint32_t)(((s / NMETA) & 1) ^ 1);
-      if (mbar_wait(bar(B_MEMPTY + slot), par, abort_flag, a.err, 11)) {
+      if (mbar_wait<PROF>(bar(B_MEMPTY + slot), par, abort_flag, a.err, 11)) {
         if (lane == 0) {
           ring[slot].flags = REC_DONE;
           mbar_arrive(bar(B_MFULL + slot));
@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
     __syncwarp();
     // drain: wait (bounded) until the MMA side released every stage we filled
     for (int k = 0; k < STAGES; ++k) {
-      mbar_wait(bar(B_EMPTY + stage), phase, abort_flag, a.err, 0);
+      mbar_wait<PROF>(bar(B_EMPTY + stage), phase, abort_flag, a.err, 0);
       if (++stage == STAGES) { stage = 0; phase ^= 1; }
     }
   } else if (warp == 1) {
@@ -408,7 +408,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
     if (lane == 0) {
       // with profiling on, slots 14 / 15 of the wait accounting receive the
       // cycles this thread spends issuing MMAs / committing them
-      const bool prof = a.wait_prof != nullptr;
+      constexpr bool prof = PROF;
       auto tick = [&]() -> long long { return prof ? clock64() : 0ll; };
       auto tock = [&](int slot, long long t0) {
         if (prof) s_wait[slot] += (unsigned long long)(clock64() - t0);
@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
       uint32_t sb = 0, sph_empty = 3u;     // bit b: expected parity of S-empty[b]
       bool seg_open = false, ok = true;
       auto acquire = [&]() -> uint32_t {
-        if (!mbar_wait(bar(B_FULL + stage), phase, abort_flag, a.err, 4)) { ok = false; return 0; }
+        if (!mbar_wait<PROF>(bar(B_FULL + stage), phase, abort_flag, a.err, 4)) { ok = false; return 0; }
         asm volatile("tcgen05.fence::after_thread_sync;\n");
         return sbase + stage * STAGE_BYTES;
       };
@@ -431,7 +431,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
       };
       auto mma_k1 = [&](const TcRec& u) {
         const uint32_t xb = xcnt & 1;
-        if (!mbar_wait(bar(B_XEMPTY + xb), (xph_empty >> xb) & 1u, abort_flag, a.err, 3)) { ok = false; return; }
+        if (!mbar_wait<PROF>(bar(B_XEMPTY + xb), (xph_empty >> xb) & 1u, abort_flag, a.err, 3)) { ok = false; return; }
         xph_empty ^= 1u << xb;
         asm volatile("tcgen05.fence::after_thread_sync;\n");
         const uint32_t tmem_x = tmem + xb * 128;
@@ -482,10 +482,10 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
         const uint32_t a2 = sbase + A2_OFF;
         const int nk2 = rec_k2(u);
         for (int h = 0; h < nk2 && ok; ++h) {
-          if (!mbar_wait(bar(B_A2FULL), a2_full_ph, abort_flag, a.err, 5)) { ok = false; return; }
+          if (!mbar_wait<PROF>(bar(B_A2FULL), a2_full_ph, abort_flag, a.err, 5)) { ok = false; return; }
           a2_full_ph ^= 1;
           if (!seg_open) {
-            if (!mbar_wait(bar(B_SEMPTY + sb), (sph_empty >> sb) & 1u, abort_flag, a.err, 2)) { ok = false; return; }
+            if (!mbar_wait<PROF>(bar(B_SEMPTY + sb), (sph_empty >> sb) & 1u, abort_flag, a.err, 2)) { ok = false; return; }
             sph_empty ^= 1u << sb;
           }
           const uint32_t sst = acquire();
@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
       int prev_slot = -1;
       while (ok) {
         const int slot = (int)(s % NMETA);
-        if (!mbar_wait(bar(B_MFULL + slot), (uint32_t)((s / NMETA) & 1), abort_flag, a.err, 12)) { ok = false; break; }
+        if (!mbar_wait<PROF>(bar(B_MFULL + slot), (uint32_t)((s / NMETA) & 1), abort_flag, a.err, 12)) { ok = false; break; }
         const TcRec& u = ring[slot];
         const int fl = u.flags;
         if (fl & REC_DONE) break;
@@ -591,7 +591,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
     long long s = 0;
     while (ok) {
       const int slot = (int)(s % NMETA);
-      if (!mbar_wait(bar(B_MFULL + slot), (uint32_t)((s / NMETA) & 1), abort_flag, a.err, 13)) { ok = false; break; }
+      if (!mbar_wait<PROF>(bar(B_MFULL + slot), (uint32_t)((s / NMETA) & 1), abort_flag, a.err, 13)) { ok = false; break; }
       const TcRec& u = ring[slot];
       const int fl = u.flags;
       if (fl & REC_DONE) break;
@@ -601,7 +601,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
           for (int c = half * 64; c < min(u.ncols, half * 64 + 64); ++c) out[(long long)row * u.ncols + c] = 0.0;
       } else {
         const uint32_t xb = xcnt & 1;
-        if (!mbar_wait(bar(B_XFULL + xb), (xph_full >> xb) & 1u, abort_flag, a.err, 6)) { ok = false; break; }
+        if (!mbar_wait<PROF>(bar(B_XFULL + xb), (xph_full >> xb) & 1u, abort_flag, a.err, 6)) { ok = false; break; }
         xph_full ^= 1u << xb;
         asm volatile("tcgen05.fence::after_thread_sync;\n");
         const uint32_t xaddr = tmem + lane_off + xb * 128;
@@ -635,7 +635,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
 #pragma unroll
             for (int j = 0; j < 32; ++j) v[j] = j < valid ? v[j] * sc : 0.0f;
           }
-          if (!mbar_wait(bar(B_A2EMPTY), a2_empty_ph, abort_flag, a.err, 7)) { ok = false; break; }
+          if (!mbar_wait<PROF>(bar(B_A2EMPTY), a2_empty_ph, abort_flag, a.err, 7)) { ok = false; break; }
           a2_empty_ph ^= 1;
           write_a2(v);
         }
@@ -643,7 +643,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
         if (!ok) break;
         if (fl & UNIT_ENDS_SEGMENT) {
           // segment's FP32 sigma tile -> FP64 slot (store on the first segment, add after)
-          if (!mbar_wait(bar(B_SFULL + sb), (sph_full >> sb) & 1u, abort_flag, a.err, 8)) { ok = false; break; }
+          if (!mbar_wait<PROF>(bar(B_SFULL + sb), (sph_full >> sb) & 1u, abort_flag, a.err, 8)) { ok = false; break; }
           sph_full ^= 1u << sb;
           asm volatile("tcgen05.fence::after_thread_sync;\n");
           const bool first = fl & UNIT_FIRST_SEGMENT;
@@ -675,7 +675,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
     asm volatile("tcgen05.fence::after_thread_sync;\n");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem));
   }
-  if (a.wait_prof && tid < 16) {
+  if (PROF && a.wait_prof && tid < 16) {
     atomicAdd(a.wait_prof + tid, s_wait[tid]);
     if (tid == 0) atomicAdd(a.wait_prof + 16, (unsigned long long)(clock64() - t_start));
   }
@@ -747,16 +747,26 @@ void launch_split_psi(const double* psi, const PsiBlock* blocks, const TcPsiBloc
 void launch_sigma_tc(const TcDev& a, int n_sm, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(sigma_tc_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    cudaFuncSetAttribute(sigma_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaFuncSetAttribute(sigma_tc_kernel<6, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaFuncSetAttribute(sigma_tc_kernel<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaFuncSetAttribute(sigma_tc_kernel<6, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaFuncSetAttribute(sigma_tc_kernel<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     attr = true;
   }
   int grid = n_sm < a.n_items ? n_sm : a.n_items;
   if (grid < 1) grid = 1;
-  if (a.nprod == 6)
-    sigma_tc_kernel<6><<<grid, NTHR, SMEM_BYTES, st>>>(a);
-  else
-    sigma_tc_kernel<3><<<grid, NTHR, SMEM_BYTES, st>>>(a);
+  const bool prof = a.wait_prof != nullptr;
+  if (a.nprod == 6) {
+    if (prof)
+      sigma_tc_kernel<6, true><<<grid, NTHR, SMEM_BYTES, st>>>(a);
+    else
+      sigma_tc_kernel<6, false><<<grid, NTHR, SMEM_BYTES, st>>>(a);
+  } else {
+    if (prof)
+      sigma_tc_kernel<3, true><<<grid, NTHR, SMEM_BYTES, st>>>(a);
+    else
+      sigma_tc_kernel<3, false><<<grid, NTHR, SMEM_BYTES, st>>>(a);
+  }
 }
 
 }  // namespace dmrg
