@@ -57,6 +57,18 @@ def largest_remainder(total, weights):
     return base
 
 
+def fix_sign(U):
+    """Columns with the sign that makes each column's entry of largest
+    magnitude positive (the first such entry on ties): singular vectors have
+    an arbitrary sign, and this fixes the gauge of the kept states."""
+    U = np.array(U, dtype=np.float64)
+    for j in range(U.shape[1]):
+        i = int(np.argmax(np.abs(U[:, j])))
+        if U[i, j] < 0.0:
+            U[:, j] = -U[:, j]
+    return U
+
+
 def orthonormal_columns(G):
     """Orthonormal basis of the columns of G in Gram-Schmidt orientation:
     the unique thin QR with a positive diagonal of R, so the basis (and every
@@ -68,12 +80,14 @@ def orthonormal_columns(G):
 
 class PlainDMRG:
     def __init__(self, t, v, N, two_sz, seed=0, dav_tol=1e-10, dav_max_space=24,
-                 dav_max_iter=200):
+                 dav_max_iter=200, noise=0.0, keep_one_per_q=False):
         self.ints = Integrals(t, v)
         self.K = self.ints.K
         self.Q = (N, two_sz)
         self.seed = seed
         self.dav = dict(tol=dav_tol, max_space=dav_max_space, max_iter=dav_max_iter)
+        self.noise = float(noise)
+        self.keep_one_per_q = bool(keep_one_per_q)
         self.L = {}
         self.R = {}
         self.UL = {}  # i -> {sector of L[i-1] x site: kept columns}, for inspection
@@ -124,9 +138,27 @@ class PlainDMRG:
         th, x, nmv, conv = davidson(mv, diag, g, **self.dav)
         return th, x, layout, nmv, conv
 
+    def perturb(self, x, step_id):
+        """Perturbative noise (the paper runs two-site DMRG with noise, Sec. III):
+        the wavefunction handed to decimation is s x + noise * z / |z|, renormalized,
+        with s = sign(x . z) (the solver's sign of x is arbitrary)
+        with z seeded N(0,1) numbers (noise stream, counter (step_id << 32) + i),
+        so that states the current wavefunction does not reach can enter the
+        kept basis."""
+        if self.noise == 0.0:
+            return x
+        key = splitmix.stream_key(self.seed, splitmix.KEY_NOISE)
+        z = splitmix.normal(key, (np.uint64(step_id) << np.uint64(32)) + np.arange(len(x), dtype=np.uint64))
+        sgn = -1.0 if x @ z < 0.0 else 1.0   # eigenvector sign is arbitrary: align x with z first
+        y = sgn * x + self.noise * z / np.linalg.norm(z)
+        return y / np.linalg.norm(y)
+
     @staticmethod
-    def decimate(x, layout, M):
-        """Per-block SVD and global truncation. Returns (kept per q_L, U, V, discarded weight, svals)."""
+    def decimate(x, layout, M, keep_one_per_q=False):
+        """Per-block SVD and global truncation. Returns (kept per q_L, U, V, discarded weight).
+        keep_one_per_q: a block none of whose states made the global cut keeps its
+        largest one as well (the paper keeps at least one state per quantum
+        number, Sec. III), so the kept count may exceed M."""
         blocks = psi_to_blocks(x, layout)
         svd, cand = {}, []
         for qL, qR, mL, mR, off in layout:
@@ -139,14 +171,19 @@ class PlainDMRG:
         for _, qL, k in cand[:keep]:
             kept[qL] = kept.get(qL, 0) + 1
         disc = sum(c[0] ** 2 for c in cand[keep:])
+        if keep_one_per_q:
+            for qL, qR, mL, mR, off in layout:
+                if kept.get(qL, 0) == 0 and min(mL, mR) > 0:
+                    kept[qL] = 1
+                    disc -= float(svd[qL][1][0]) ** 2
         return kept, svd, disc
 
     def step(self, i, forward, M, step_id):
         EL, oL, ER, oR = self.enlarged(i)
         th, x, layout, nmv, conv = self.solve(i, step_id, EL, oL, ER, oR)
-        kept, svd, disc = self.decimate(x, layout, M)
+        kept, svd, disc = self.decimate(self.perturb(x, step_id), layout, M, self.keep_one_per_q)
         if forward:
-            U = {qL: svd[qL][0][:, :m] for qL, m in kept.items()}
+            U = {qL: fix_sign(svd[qL][0][:, :m]) for qL, m in kept.items()}
             nb = Basis(list(kept.items()))
             self.L[i + 1] = (nb, {k: transform(o, U, nb) for k, o in oL.items()})
             self.UL[i + 1] = U
@@ -154,13 +191,13 @@ class PlainDMRG:
             V, secs = {}, []
             for qL, m in kept.items():
                 qR = svd[qL][3]
-                V[qR] = svd[qL][2][:m, :].T
+                V[qR] = fix_sign(svd[qL][2][:m, :].T)
                 secs.append((qR, m))
             nb = Basis(secs)
             self.R[i + 1] = (nb, {k: transform(o, V, nb) for k, o in oR.items()})
             self.UR[i + 1] = V
         self.log.append(dict(i=i, forward=forward, M=M, energy=th, nmv=nmv,
-                             converged=conv, discarded=disc, dim=len(x)))
+                             converged=conv, discarded=disc, dim=len(x), kept=sum(kept.values())))
         return th, disc
 
     def sweep(self, M_schedule):

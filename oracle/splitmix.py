@@ -60,6 +60,7 @@ def normal(key, g):
 KEY_OPS = 0x0000000000000000
 KEY_MPS = 0x4D50535F494E4954  # "MPS_INIT"
 KEY_GUESS = 0x4755455353505349  # "GUESSPSI"
+KEY_NOISE = 0x4E4F495345505349  # "NOISEPSI"
 
 
 def stream_key(seed, which):

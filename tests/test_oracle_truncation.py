@@ -131,3 +131,38 @@ def test_step_energy_is_projected_fock_ground_state():
     EL, oL, ER, oR = d.enlarged(0)
     th = d.solve(0, 0, EL, oL, ER, oR)[0]
     assert abs(th - e_ref) < 1e-10, (th, e_ref)
+
+
+def test_noise_and_keep_one_per_q_keep_blocks_exact_projections():
+    """With perturbative noise and one kept state per quantum number, the
+    renormalized operators are still exact projections on orthonormal states,
+    every psi block's left sector survives each forward step, and energies stay
+    variational."""
+    from oracle.fock import fci_energy
+    t, v = random_integrals(K, 7)
+    d = PlainDMRG(t, v, N, TWO_SZ, seed=1, dav_tol=1e-12, noise=1e-2, keep_one_per_q=True)
+    d.build_blocks(6)
+    e, disc = d.sweep([6, 6])
+    assert all(x > fci_energy(t, v, N, TWO_SZ) - 1e-9 for x in e)
+    _check_block(d, _left_states(d), d.L, lambda i: list(range(0, 2 * i)), "L")
+    _check_block(d, _right_states(d), d.R, lambda j: list(range(2 * j, 2 * K)), "R")
+    # one step with M=1: every left sector of the two-site psi still keeps a state
+    d2 = PlainDMRG(t, v, N, TWO_SZ, seed=1, dav_tol=1e-12, noise=1e-2, keep_one_per_q=True)
+    d2.build_blocks(6)
+    EL, oL, ER, oR = d2.enlarged(0)
+    th, x, layout, nmv, conv = d2.solve(0, 0, EL, oL, ER, oR)
+    kept, svd, disc = d2.decimate(d2.perturb(x, 0), layout, 1, True)
+    assert set(kept) == {qL for qL, qR, mL, mR, off in layout if min(mL, mR) > 0}
+
+
+def test_perturb_is_seeded_unit_norm_and_off_without_noise():
+    t, v = random_integrals(K, 7)
+    d = PlainDMRG(t, v, N, TWO_SZ, seed=1, noise=1e-3)
+    x = np.random.default_rng(0).standard_normal(50)
+    x /= np.linalg.norm(x)
+    y1, y2 = d.perturb(x, 7), d.perturb(x, 7)
+    assert np.array_equal(y1, y2) and abs(np.linalg.norm(y1) - 1.0) < 1e-14
+    assert 0 < min(np.linalg.norm(y1 - x), np.linalg.norm(y1 + x)) < 3e-3   # up to the sign of x
+    assert not np.array_equal(d.perturb(x, 8), y1)
+    d0 = PlainDMRG(t, v, N, TWO_SZ, seed=1)
+    assert d0.perturb(x, 7) is x
