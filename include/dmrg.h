@@ -62,8 +62,12 @@ typedef struct {
   int sigma_prec;              /* dmrg_prec */
   int dav_max_space;           /* Davidson subspace size (default 24, >= 3) */
   int dav_max_iter;            /* Davidson matrix-vector products per solve (default 200) */
-  int keep_one_per_q;          /* reserved, must be 0 */
-  double noise;                /* reserved, must be 0 */
+  int keep_one_per_q;          /* 1: in sweeps, a quantum number of psi none of whose states makes
+                                  the bond-dimension cut keeps its largest one too (the kept count
+                                  may exceed M; Sec. III keeps one state per quantum number) */
+  double noise;                /* sweeps: decimate s psi + noise * z / |z| (renormalized), z seeded
+                                  N(0,1) numbers, s = sign(psi . z); 0 = off (Sec. III runs with
+                                  perturbative noise) */
   unsigned long long seed;     /* seed of the counter-based random streams (initial MPS, guesses) */
   int device;                  /* CUDA device ordinal */
   int graphs;                  /* 1: replay each sigma's launches (counter reset, product kernel,

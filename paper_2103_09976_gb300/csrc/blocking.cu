@@ -266,15 +266,40 @@ __global__ void orthonormalize_kernel(double* __restrict__ store, const GramBloc
   }
 }
 
-// dst[b] (d x k, row-major) = first k columns of Q[b] (d x d)
+// dst[b] (d x k, row-major) = first k columns of Q[b] (d x d), each column
+// with the sign that makes its entry of largest magnitude positive (first
+// such entry on ties). Eigenvectors carry an arbitrary sign; this fixes the
+// gauge of the kept states, so a basis is a function of the wavefunction
+// alone. One warp per column.
 __global__ void take_columns_kernel(const double* __restrict__ Qall, const TakeBlock* __restrict__ tb, int nb,
                                     double* __restrict__ dst) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int b = blockIdx.y; b < nb; b += gridDim.y) {
     const TakeBlock t = tb[b];
-    const long long ne = (long long)t.d * t.k;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x) {
-      const int r = (int)(e / t.k), c = (int)(e % t.k);
-      dst[t.dst_off + e] = Qall[t.q_off + (long long)r * t.d + c];
+    for (int c = blockIdx.x * nw + wid; c < t.k; c += gridDim.x * nw) {
+      double best = -1.0, val = 0.0;
+      int bi = 0x7fffffff;
+      for (int r = lane; r < t.d; r += 32) {
+        const double v = Qall[t.q_off + (long long)r * t.d + c];
+        if (fabs(v) > best) {  // r ascends per lane, so ties keep the first
+          best = fabs(v);
+          bi = r;
+          val = v;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        const double ov = __shfl_xor_sync(0xffffffffu, val, o);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+          val = ov;
+        }
+      }
+      const double sg = val < 0.0 ? -1.0 : 1.0;
+      for (int r = lane; r < t.d; r += 32)
+        dst[t.dst_off + (long long)r * t.k + c] = sg * Qall[t.q_off + (long long)r * t.d + c];
     }
   }
 }
@@ -305,7 +330,7 @@ void launch_orthonormalize(double* store, const GramBlock* gb, int nb, cudaStrea
 
 void launch_take_columns(const double* Q, const TakeBlock* tb, int nb, double* dst, cudaStream_t st) {
   if (nb <= 0) return;
-  dim3 grid(16, nb < 65535 ? nb : 65535);
+  dim3 grid(8, nb < 65535 ? nb : 65535);
   take_columns_kernel<<<grid, 256, 0, st>>>(Q, tb, nb, dst);
 }
 

@@ -6,6 +6,8 @@
 #include <cstring>
 #include <new>
 
+#include <cmath>
+
 #include "context.h"
 
 using namespace dmrg;
@@ -515,8 +517,8 @@ dmrg_status dmrg_create(dmrg_ctx** out, const dmrg_opts* opts) {
     if (opts) o = *opts;
     if (o.dav_max_space < 3) throw Error(DMRG_EINVAL, "dav_max_space must be >= 3");
     if (o.dav_max_iter < 1) throw Error(DMRG_EINVAL, "dav_max_iter must be >= 1");
-    if (o.keep_one_per_q != 0 || o.noise != 0.0)
-      throw Error(DMRG_EINVAL, "keep_one_per_q and noise are reserved and must be 0");
+    if (o.keep_one_per_q != 0 && o.keep_one_per_q != 1) throw Error(DMRG_EINVAL, "keep_one_per_q must be 0 or 1");
+    if (!(o.noise >= 0.0) || !std::isfinite(o.noise)) throw Error(DMRG_EINVAL, "noise must be finite and >= 0");
     if (o.sigma_prec < DMRG_FP64 || o.sigma_prec > DMRG_BF16X3)
       throw Error(DMRG_EINVAL, "unknown sigma precision");
     int ndev = 0;

@@ -87,6 +87,15 @@ __global__ void residual_precond(const double* __restrict__ x, const double* __r
   }
 }
 
+// x <- sign(x . z) x + a z / sqrt(z . z); xz_zz = {x . z, z . z}
+__global__ void axpy_unit_kernel(double* __restrict__ x, const double* __restrict__ z,
+                                 const double* __restrict__ xz_zz, double a, long long n) {
+  const double sg = xz_zz[0] < 0.0 ? -1.0 : 1.0;
+  const double s = a / sqrt(xz_zz[1]);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    x[e] = fma(s, z[e], sg * x[e]);
+}
+
 __global__ void scale_kernel(double* __restrict__ x, const double* __restrict__ nrm2, long long n) {
   const double s = 1.0 / sqrt(*nrm2);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
@@ -274,6 +283,13 @@ void dav_scale(double* x, const double* nrm2, long long n, cudaStream_t st) {
   if (grid > 152 * 8) grid = 152 * 8;
   if (grid < 1) grid = 1;
   scale_kernel<<<(unsigned)grid, 256, 0, st>>>(x, nrm2, n);
+}
+
+void dav_axpy_unit(double* x, const double* z, const double* xz_zz, double a, long long n, cudaStream_t st) {
+  long long grid = (n + 255) / 256;
+  if (grid > 152 * 8) grid = 152 * 8;
+  if (grid < 1) grid = 1;
+  axpy_unit_kernel<<<(unsigned)grid, 256, 0, st>>>(x, z, xz_zz, a, n);
 }
 
 void dav_eigh(const double* H, int k, int ldh, double* w, double* Y, int k0, cudaStream_t st) {

@@ -132,6 +132,8 @@ void dav_residual(const double* x, const double* ax, const double* diag, const d
 void dav_scale(double* x, const double* nrm2, long long n, cudaStream_t st);
 // eigenpairs (ascending) of the symmetric part of a k x k matrix, k <= 32
 void dav_eigh(const double* H, int k, int ldh, double* w, double* Y, int k0, cudaStream_t st);
+// x <- sign(x . z) x + a z / sqrt(z . z), with xz_zz = {x . z, z . z} on the device
+void dav_axpy_unit(double* x, const double* z, const double* xz_zz, double a, long long n, cudaStream_t st);
 // diagonal of H_eff from the diagonal tasks (output block = input block)
 void launch_heff_diag(const double* store, const Task* tasks, const int* dstart, const int* dtask,
                       const PsiBlock* blocks, int nblk, double* diag, cudaStream_t st);

@@ -31,6 +31,7 @@ namespace dmrg {
 namespace {
 
 constexpr uint64_t KEY_MPS = 0x4D50535F494E4954ull;    // "MPS_INIT"
+constexpr uint64_t KEY_NOISE = 0x4E4F495345505349ull;  // "NOISEPSI"
 const QN SITE_Q[4] = {{0, 0}, {1, 1}, {1, -1}, {2, 0}};  // |0>, |a>, |b>, |ab>
 const int SITE_N[4] = {0, 1, 1, 2};
 
@@ -706,6 +707,13 @@ void decimate(Context& c, Problem& p, const Enlarged& E, const double* psi, int 
     if (i < keep) kept[cand[i].b]++;
     else D.discarded += cand[i].s * cand[i].s;
   }
+  if (c.opts.keep_one_per_q)  // every quantum number of psi keeps its largest state
+    for (int b = 0; b < nb; ++b)
+      if (kept[b] == 0 && std::min(p.blocks[b].mL, p.blocks[b].mR) > 0) {
+        kept[b] = 1;
+        const double s0 = std::sqrt(std::max(0.0, w[gb[b].w_off]));
+        D.discarded -= s0 * s0;
+      }
   // new basis: sectors of the growing side in ascending order
   std::vector<std::pair<QN, int>> secs;  // (q, block)
   for (int b = 0; b < nb; ++b)
@@ -855,6 +863,22 @@ void sweep_run(Context& c, const int* Ms, int n_sweeps, double tol, double* ener
       int it = 0;
       const unsigned long long step_id = (unsigned long long)s * K + i;
       const bool conv = run_davidson(c, p, nullptr, tol, &e, x.as<double>(), &it, step_id << 32);
+      if (c.opts.noise > 0.0) {
+        // perturbative noise: decimate s x + noise z / |z|, renormalized, with
+        // z seeded N(0,1) numbers of the noise stream and s = sign(x . z)
+        // (the solver's sign of x is arbitrary)
+        DevBuf z;
+        z.alloc(p.psi_size * sizeof(double));
+        launch_gen_vector(z.as<double>(), p.psi_size, (uint64_t)(c.opts.seed ^ KEY_NOISE), step_id << 32, c.stream);
+        double* sc = p.dav_s.as<double>() + 50;
+        double* part = p.dav_partial.as<double>();
+        dav_dots(x.as<double>(), p.psi_size, 1, z.as<double>(), p.psi_size, part, sc, 1, c.stream);
+        dav_dots(z.as<double>(), p.psi_size, 1, z.as<double>(), p.psi_size, part, sc + 1, 1, c.stream);
+        dav_axpy_unit(x.as<double>(), z.as<double>(), sc, c.opts.noise, p.psi_size, c.stream);
+        dav_dots(x.as<double>(), p.psi_size, 1, x.as<double>(), p.psi_size, part, sc + 2, 1, c.stream);
+        dav_scale(x.as<double>(), sc + 2, p.psi_size, c.stream);
+        DMRG_CUDA(cudaGetLastError());
+      }
       emin = std::min(emin, e);
       const double t2 = clk();
       Decim D;
