@@ -2,6 +2,8 @@
 // matrix and Jacobi eigensolver), orthonormal bases for the initial MPS.
 // The transformation of Eq. op-trans runs on the FP64 sigma kernel with a
 // dedicated work list (see sweep.cpp).
+#include <cooperative_groups.h>
+
 #include "kernels.h"
 
 namespace dmrg {
@@ -91,141 +93,6 @@ __global__ void blocking_kernel(BlockingDev d) {
   }
 }
 
-// G[b] = X_b X_b^T (rows) or X_b^T X_b (cols) for every block b of psi.
-__global__ void gram_kernel(const double* __restrict__ psi, const GramBlock* __restrict__ gb, int nb,
-                            double* __restrict__ G, int left) {
-  for (int b = blockIdx.y; b < nb; b += gridDim.y) {
-    const GramBlock g = gb[b];
-    const long long ne = (long long)g.d * g.d;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x) {
-      const int i = (int)(e / g.d), j = (int)(e % g.d);
-      double s = 0.0;
-      if (left)
-        for (int k = 0; k < g.m; ++k) s = fma(psi[g.psi_off + (long long)i * g.m + k], psi[g.psi_off + (long long)j * g.m + k], s);
-      else
-        for (int k = 0; k < g.m; ++k) s = fma(psi[g.psi_off + (long long)k * g.d + i], psi[g.psi_off + (long long)k * g.d + j], s);
-      G[g.g_off + e] = s;
-    }
-  }
-}
-
-// Symmetric eigenproblem of each d x d matrix A (row-major, in place) by
-// cyclic Jacobi in round-robin order: each round rotates d/2 disjoint index
-// pairs at once. Q receives the eigenvectors (columns), w the eigenvalues,
-// both sorted by descending eigenvalue (ties by index).
-__global__ void jacobi_blocks_kernel(double* __restrict__ Aall, double* __restrict__ Qall, double* __restrict__ wall,
-                                     const GramBlock* __restrict__ gb, int nb, int max_sweeps) {
-  __shared__ double cs[512], sn[512];
-  __shared__ int pp[512], qq[512];
-  __shared__ double red[2][256];
-  __shared__ int stop;
-  for (int b = blockIdx.x; b < nb; b += gridDim.x) {
-    const GramBlock g = gb[b];
-    const int d = g.d;
-    double* A = Aall + g.g_off;
-    double* Q = Qall + g.g_off;
-    double* w = wall + g.w_off;
-    for (long long e = threadIdx.x; e < (long long)d * d; e += blockDim.x) Q[e] = (e / d == e % d) ? 1.0 : 0.0;
-    __syncthreads();
-    const int dp = d + (d & 1);  // players (one dummy when d is odd)
-    for (int sweep = 0; sweep < max_sweeps && d > 1; ++sweep) {
-      double off = 0.0, tot = 0.0;
-      for (long long e = threadIdx.x; e < (long long)d * d; e += blockDim.x) {
-        const double a = A[e];
-        tot += a * a;
-        if (e / d != e % d) off += a * a;
-      }
-      red[0][threadIdx.x] = off;
-      red[1][threadIdx.x] = tot;
-      __syncthreads();
-      for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h) {
-          red[0][threadIdx.x] += red[0][threadIdx.x + h];
-          red[1][threadIdx.x] += red[1][threadIdx.x + h];
-        }
-        __syncthreads();
-      }
-      if (threadIdx.x == 0) stop = (red[0][0] <= 1e-30 * red[1][0]) ? 1 : 0;
-      __syncthreads();
-      if (stop) break;
-      for (int round = 0; round < dp - 1; ++round) {
-        for (int k = threadIdx.x; k < dp / 2; k += blockDim.x) {
-          auto player = [&](int i) { return i == 0 ? 0 : 1 + (i - 1 + round) % (dp - 1); };
-          int p = player(k), q = player(dp - 1 - k);
-          if (p > q) { const int t = p; p = q; q = t; }
-          double c = 1.0, s = 0.0;
-          if (q < d) {
-            const double apq = A[(long long)p * d + q];
-            if (apq != 0.0) {
-              const double th = (A[(long long)q * d + q] - A[(long long)p * d + p]) / (2.0 * apq);
-              const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-              c = 1.0 / sqrt(t * t + 1.0);
-              s = t * c;
-            }
-          }
-          cs[k] = c;
-          sn[k] = s;
-          pp[k] = p;
-          qq[k] = q < d ? q : -1;
-        }
-        __syncthreads();
-        // columns: A <- A J, Q <- Q J
-        for (long long e = threadIdx.x; e < (long long)d * (dp / 2); e += blockDim.x) {
-          const int k = (int)(e / d), r = (int)(e % d);
-          if (qq[k] < 0 || sn[k] == 0.0) continue;
-          const int p = pp[k], q = qq[k];
-          const double c = cs[k], s = sn[k];
-          const double arp = A[(long long)r * d + p], arq = A[(long long)r * d + q];
-          A[(long long)r * d + p] = c * arp - s * arq;
-          A[(long long)r * d + q] = s * arp + c * arq;
-          const double qrp = Q[(long long)r * d + p], qrq = Q[(long long)r * d + q];
-          Q[(long long)r * d + p] = c * qrp - s * qrq;
-          Q[(long long)r * d + q] = s * qrp + c * qrq;
-        }
-        __syncthreads();
-        // rows: A <- J^T A
-        for (long long e = threadIdx.x; e < (long long)d * (dp / 2); e += blockDim.x) {
-          const int k = (int)(e / d), col = (int)(e % d);
-          if (qq[k] < 0 || sn[k] == 0.0) continue;
-          const int p = pp[k], q = qq[k];
-          const double c = cs[k], s = sn[k];
-          const double apc = A[(long long)p * d + col], aqc = A[(long long)q * d + col];
-          A[(long long)p * d + col] = c * apc - s * aqc;
-          A[(long long)q * d + col] = s * apc + c * aqc;
-        }
-        __syncthreads();
-      }
-    }
-    // eigenvalues = diagonal; sort descending with columns of Q (selection on thread 0)
-    if (threadIdx.x == 0) {
-      for (int i = 0; i < d; ++i) w[i] = A[(long long)i * d + i];
-    }
-    __syncthreads();
-    for (int i = 0; i < d - 1; ++i) {
-      __shared__ int best;
-      if (threadIdx.x == 0) {
-        int m = i;
-        for (int j = i + 1; j < d; ++j)
-          if (w[j] > w[m]) m = j;
-        best = m;
-        const double t = w[i];
-        w[i] = w[m];
-        w[m] = t;
-      }
-      __syncthreads();
-      const int m = best;
-      if (m != i)
-        for (int r = threadIdx.x; r < d; r += blockDim.x) {
-          const double t = Q[(long long)r * d + i];
-          Q[(long long)r * d + i] = Q[(long long)r * d + m];
-          Q[(long long)r * d + m] = t;
-        }
-      __syncthreads();
-    }
-    __syncthreads();
-  }
-}
-
 // Orthonormalise the columns of each d x m block (row-major, in place) by
 // classical Gram-Schmidt applied twice per column.
 __global__ void orthonormalize_kernel(double* __restrict__ store, const GramBlock* __restrict__ gb, int nb) {
@@ -304,23 +171,137 @@ __global__ void take_columns_kernel(const double* __restrict__ Qall, const TakeB
   }
 }
 
+// ---------------------------------------------------------------- SVD
+// One-sided (Hestenes) Jacobi: the d columns of A (d x m data, each column a
+// contiguous vector of length m) are rotated in pairs until mutually
+// orthogonal; the rotations, accumulated in V (d x d), are the singular
+// vectors of the psi block's d-dimensional side, and the final column norms
+// are the singular values. Pairs of one round are disjoint (round-robin
+// order), so every warp of the grid takes pairs of any block, and the grid
+// synchronizes between rounds.
+__global__ void svd_setup_kernel(const double* __restrict__ psi, const SvdBlock* __restrict__ sb, int nb,
+                                 double* __restrict__ work, int left) {
+  for (int b = blockIdx.y; b < nb; b += gridDim.y) {
+    const SvdBlock s = sb[b];
+    const long long na = (long long)s.d * s.m;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < na; e += (long long)gridDim.x * blockDim.x) {
+      const int c = (int)(e / s.m), i = (int)(e % s.m);
+      // left: column c = row c of X (d = rows, m = cols); right: column c = column c of X (d = cols, m = rows)
+      work[s.a_off + e] = left ? psi[s.psi_off + (long long)c * s.m + i] : psi[s.psi_off + (long long)i * s.d + c];
+    }
+    const long long nv = (long long)s.d * s.d;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nv; e += (long long)gridDim.x * blockDim.x)
+      work[s.v_off + e] = (e / s.d == e % s.d) ? 1.0 : 0.0;
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void svd_jacobi_kernel(const SvdBlock* __restrict__ sb, int nb, int total_pairs, int max_rounds,
+                                  double* __restrict__ work, unsigned long long* __restrict__ off_max) {
+  namespace cgp = cooperative_groups;
+  cgp::grid_group grid = cgp::this_grid();
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    const int slot = sweep & 1;
+    double local = 0.0;
+    for (int round = 0; round < max_rounds; ++round) {
+      for (long long pid = warp; pid < total_pairs; pid += nwarps) {
+        int lo = 0, hi = nb - 1;  // block of pair pid: last b with pair0 <= pid
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (sb[mid].pair0 <= pid) lo = mid;
+          else hi = mid - 1;
+        }
+        const SvdBlock s = sb[lo];
+        const int i = (int)(pid - s.pair0);
+        if (i >= s.npairs || s.rounds <= 0) continue;
+        const int dp = s.d + (s.d & 1), r = round % s.rounds;
+        auto player = [&](int x) { return x == 0 ? 0 : 1 + (x - 1 + r) % (dp - 1); };
+        int p = player(i), q = player(dp - 1 - i);
+        if (p > q) { const int t = p; p = q; q = t; }
+        if (q >= s.d) continue;
+        double* ap = work + s.a_off + (long long)p * s.m;
+        double* aq = work + s.a_off + (long long)q * s.m;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int e = lane; e < s.m; e += 32) {
+          const double x = ap[e], y = aq[e];
+          al = fma(x, x, al);
+          be = fma(y, y, be);
+          ga = fma(x, y, ga);
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (ga == 0.0 || al == 0.0 || be == 0.0) continue;
+        const double cosv = fabs(ga) / sqrt(al * be);
+        local = fmax(local, cosv);
+        if (cosv < 1e-15) continue;
+        const double zeta = (be - al) / (2.0 * ga);
+        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+        for (int e = lane; e < s.m; e += 32) {
+          const double x = ap[e], y = aq[e];
+          ap[e] = c * x - sn * y;
+          aq[e] = sn * x + c * y;
+        }
+        double* vp = work + s.v_off + (long long)p * s.d;
+        double* vq = work + s.v_off + (long long)q * s.d;
+        for (int e = lane; e < s.d; e += 32) {
+          const double x = vp[e], y = vq[e];
+          vp[e] = c * x - sn * y;
+          vq[e] = sn * x + c * y;
+        }
+      }
+      grid.sync();
+    }
+    if (lane == 0 && local > 0.0) atomicMax(off_max + slot, (unsigned long long)__double_as_longlong(local));
+    grid.sync();
+    const double worst = __longlong_as_double((long long)off_max[slot]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) off_max[slot ^ 1] = 0ull;
+    grid.sync();
+    if (worst < 1e-15) break;
+  }
+}
+
+// singular values (column norms) sorted descending (ties by index); Q row r,
+// column rank(c) = V[c][r]
+__global__ void svd_finish_kernel(const SvdBlock* __restrict__ sb, int nb, const double* __restrict__ work,
+                                  double* __restrict__ Q, double* __restrict__ w) {
+  extern __shared__ double sig[];
+  for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+    const SvdBlock s = sb[b];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c = wid; c < s.d; c += nw) {
+      const double* a = work + s.a_off + (long long)c * s.m;
+      double v = 0.0;
+      for (int e = lane; e < s.m; e += 32) v = fma(a[e], a[e], v);
+      v = warp_sum(v);
+      if (lane == 0) sig[c] = v;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < s.d; c += blockDim.x) {
+      const double v = sig[c];
+      int rank = 0;
+      for (int j = 0; j < s.d; ++j) rank += (sig[j] > v) || (sig[j] == v && j < c);
+      w[s.w_off + rank] = v;
+      for (int r = 0; r < s.d; ++r) Q[s.q_off + (long long)r * s.d + rank] = work[s.v_off + (long long)c * s.d + r];
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 void launch_blocking(const BlockingDev& d, cudaStream_t st) {
   if (d.ndst <= 0) return;
   const int grid = d.ndst < 152 * 64 ? d.ndst : 152 * 64;
   blocking_kernel<<<grid, 256, 0, st>>>(d);
-}
-
-void launch_gram(const double* psi, const GramBlock* gb, int nb, double* G, bool left, cudaStream_t st) {
-  if (nb <= 0) return;
-  dim3 grid(32, nb < 65535 ? nb : 65535);
-  gram_kernel<<<grid, 256, 0, st>>>(psi, gb, nb, G, left ? 1 : 0);
-}
-
-void launch_jacobi_blocks(double* A, double* Q, double* w, const GramBlock* gb, int nb, cudaStream_t st) {
-  if (nb <= 0) return;
-  jacobi_blocks_kernel<<<nb < 65535 ? nb : 65535, 256, 0, st>>>(A, Q, w, gb, nb, 40);
 }
 
 void launch_orthonormalize(double* store, const GramBlock* gb, int nb, cudaStream_t st) {
@@ -332,6 +313,35 @@ void launch_take_columns(const double* Q, const TakeBlock* tb, int nb, double* d
   if (nb <= 0) return;
   dim3 grid(8, nb < 65535 ? nb : 65535);
   take_columns_kernel<<<grid, 256, 0, st>>>(Q, tb, nb, dst);
+}
+
+}  // namespace dmrg
+
+namespace dmrg {
+
+void launch_svd_blocks(const double* psi, const SvdBlock* sb, int nb, int total_pairs, int max_rounds, int max_d_hint,
+                       double* Q, double* w, double* work, bool left, int n_sm, cudaStream_t st) {
+  if (nb <= 0) return;
+  if ((size_t)max_d_hint * sizeof(double) > 48 * 1024)
+    cudaFuncSetAttribute(svd_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)((size_t)max_d_hint * sizeof(double)));
+  {
+    dim3 grid(32, nb < 65535 ? nb : 65535);
+    svd_setup_kernel<<<grid, 256, 0, st>>>(psi, sb, nb, work, left ? 1 : 0);
+  }
+  if (total_pairs > 0 && max_rounds > 0) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, svd_jacobi_kernel, 256, 0);
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 4) per_sm = 4;
+    int grid = n_sm * per_sm;
+    unsigned long long* off_max = reinterpret_cast<unsigned long long*>(work);  // first 2 words of work
+    cudaMemsetAsync(off_max, 0, 2 * sizeof(unsigned long long), st);
+    void* args[] = {(void*)&sb, (void*)&nb, (void*)&total_pairs, (void*)&max_rounds, (void*)&work, (void*)&off_max};
+    const cudaError_t e = cudaLaunchCooperativeKernel((void*)svd_jacobi_kernel, dim3(grid), dim3(256), args, 0, st);
+    if (e != cudaSuccess) return;  // the caller's cudaGetLastError reports it
+  }
+  svd_finish_kernel<<<nb < 65535 ? nb : 65535, 256, (size_t)max_d_hint * sizeof(double), st>>>(sb, nb, work, Q, w);
 }
 
 }  // namespace dmrg

@@ -112,8 +112,18 @@ struct TakeBlock {      // dst (d x k) = first k columns of Q (d x d)
   int d, k;
 };
 void launch_blocking(const BlockingDev& d, cudaStream_t st);
-void launch_gram(const double* psi, const GramBlock* gb, int nb, double* G, bool left, cudaStream_t st);
-void launch_jacobi_blocks(double* A, double* Q, double* w, const GramBlock* gb, int nb, cudaStream_t st);
+// Per psi block: singular vectors of its d-dimensional side (rows when left,
+// columns otherwise) and squared singular values, by one-sided Jacobi over
+// the whole GPU (one cooperative launch for all blocks): Q (d x d row-major,
+// columns = vectors) and w (d values), by descending singular value. Work
+// space: 64 doubles, then A (d x m) and V (d x d) of every block at a_off /
+// v_off. max_d_hint >= every d (shared memory of the final sort).
+struct SvdBlock {
+  long long psi_off, q_off, w_off, a_off, v_off;
+  int d, m, pair0, npairs, rounds, pad;
+};
+void launch_svd_blocks(const double* psi, const SvdBlock* sb, int nb, int total_pairs, int max_rounds, int max_d_hint,
+                       double* Q, double* w, double* work, bool left, int n_sm, cudaStream_t st);
 void launch_orthonormalize(double* store, const GramBlock* gb, int nb, cudaStream_t st);
 void launch_take_columns(const double* Q, const TakeBlock* tb, int nb, double* dst, cudaStream_t st);
 

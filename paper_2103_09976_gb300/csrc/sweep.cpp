@@ -659,25 +659,32 @@ struct Decim {
 void decimate(Context& c, Problem& p, const Enlarged& E, const double* psi, int M, bool forward, Decim& D) {
   cudaStream_t st = c.stream;
   const int nb = (int)p.blocks.size();
-  std::vector<GramBlock> gb(nb);
-  long long goff = 0, woff = 0;
+  std::vector<GramBlock> gb(nb);   // Q / w offsets and the two dimensions of every block
+  std::vector<SvdBlock> sb(nb);
+  long long goff = 0, woff = 0, aoff = 64;
+  int pairs = 0, max_rounds = 0, max_d = 1;
   for (int b = 0; b < nb; ++b) {
     const PsiBlock& pb = p.blocks[b];
-    const int d = forward ? pb.mL : pb.mR;
-    if (d > 1024) throw Error(DMRG_EINVAL, "sector dimension above 1024 in decimation");
-    gb[b] = {pb.off, goff, woff, d, forward ? pb.mR : pb.mL};
+    const int d = forward ? pb.mL : pb.mR, m = forward ? pb.mR : pb.mL;
+    gb[b] = {pb.off, goff, woff, d, m};
+    const int dp = d + (d & 1);
+    sb[b] = {pb.off, goff, woff, aoff, aoff + (long long)d * m, d, m, pairs, dp / 2, dp - 1, 0};
+    pairs += dp / 2;
+    max_rounds = std::max(max_rounds, dp - 1);
+    max_d = std::max(max_d, d);
+    aoff += (long long)d * m + (long long)d * d;
     goff += (long long)d * d;
     woff += d;
   }
-  DevBuf dgb, G, Q, W;
-  dgb.upload(gb, st);
-  G.alloc(std::max<long long>(1, goff) * sizeof(double));
+  DevBuf dsb, Q, W, work;
+  dsb.upload(sb, st);
   Q.alloc(std::max<long long>(1, goff) * sizeof(double));
   W.alloc(std::max<long long>(1, woff) * sizeof(double));
+  work.alloc((size_t)aoff * sizeof(double));
   {
     ProfScope ps(c.prof, 3, st);
-    launch_gram(psi, dgb.as<GramBlock>(), nb, G.as<double>(), forward, st);
-    launch_jacobi_blocks(G.as<double>(), Q.as<double>(), W.as<double>(), dgb.as<GramBlock>(), nb, st);
+    launch_svd_blocks(psi, dsb.as<SvdBlock>(), nb, pairs, max_rounds, max_d, Q.as<double>(), W.as<double>(),
+                      work.as<double>(), forward, c.n_sm, st);
   }
   DMRG_CUDA(cudaGetLastError());
   std::vector<double> w(woff);
