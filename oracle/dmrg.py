@@ -2,7 +2,8 @@
 
 Follows Appendix A: for each sweep iteration at sites (i, i+1),
   (i)  blocking: enlarged blocks L_i x s_i and s_{i+1} x R_{i+2}
-       (Eq. blocked-ops; formulas in nc.blocking_left / blocking_right);
+       (Eq. blocked-ops; formulas in nc.blocking_left / blocking_right and,
+       for the CN form, cn.blocking_left_cn / blocking_right_cn);
   (ii) solving: lowest eigenpair of H_eff (Eq. eff-eigsh) by Davidson, with
        the NC sigma of sigma.sigma_blocks;
   (iii) decimation by SVD of psi per sector block and truncation to M, then
@@ -25,6 +26,10 @@ Fixed readings of points the paper leaves open:
   * Davidson guess at each step: SplitMix64 normals (key = seed ^ KEY_GUESS,
     counter = step_id * 2^32 + element index, step_id = sweep * K + i).
   * Sweep energy: the lowest Davidson eigenvalue of the sweep.
+  * Mixed NC/CN (Sec. III.A, cn.py): with cut c, blocks of at most c left
+    orbitals / starting at orbital c or before are in NC form, the others in
+    CN form; the step whose enlarged left block holds e orbitals uses the NC
+    terms when e <= c, the CN terms otherwise. cut=None is NC everywhere.
 
 Parity status: pinned (tests/test_oracle_dmrg.py): at full bond dimension
 every sweep energy equals the FCI energy; blocked operators equal their
@@ -36,8 +41,8 @@ import numpy as np
 from . import splitmix
 from .blocks import Basis, BlockOp, qadd, qsub
 from .davidson import davidson
-from .nc import (Integrals, assemble_all, blocking_left, blocking_right, nc_terms,
-                 transform, vacuum_left, vacuum_right)
+from .cn import blocking_left_mixed, blocking_right_mixed, mixed_terms, vacuum_right_cn
+from .nc import Integrals, assemble_all, transform, vacuum_left, vacuum_right
 from .sigma import heff_diagonal, psi_layout, psi_to_blocks, sigma_blocks
 
 
@@ -80,9 +85,10 @@ def orthonormal_columns(G):
 
 class PlainDMRG:
     def __init__(self, t, v, N, two_sz, seed=0, dav_tol=1e-10, dav_max_space=24,
-                 dav_max_iter=200, noise=0.0, keep_one_per_q=False):
+                 dav_max_iter=200, noise=0.0, keep_one_per_q=False, cut=None):
         self.ints = Integrals(t, v)
         self.K = self.ints.K
+        self.cut = self.K if cut is None else int(cut)
         self.Q = (N, two_sz)
         self.seed = seed
         self.dav = dict(tol=dav_tol, max_space=dav_max_space, max_iter=dav_max_iter)
@@ -97,12 +103,12 @@ class PlainDMRG:
     # ------------------------------------------------------ initial blocks
     def build_blocks(self, M_init):
         K = self.K
-        self.R[K] = vacuum_right(self.ints)
+        self.R[K] = vacuum_right(self.ints) if K <= self.cut else vacuum_right_cn(self.ints)
         key = splitmix.stream_key(self.seed, splitmix.KEY_MPS)
         off = 0
         for j in range(K - 1, 0, -1):
             bR, opsR = self.R[j + 1]
-            E, chunks, enl = blocking_right(self.ints, bR, opsR, j)
+            E, chunks, enl = blocking_right_mixed(self.ints, bR, opsR, j, self.cut)
             comp = [(Q, E.dim(Q)) for Q in E.qs if can_hold(2 * j, qsub(self.Q, Q))]
             D = sum(d for _, d in comp)
             dims = [d for _, d in comp] if D <= M_init else list(largest_remainder(M_init, [d for _, d in comp]))
@@ -124,12 +130,12 @@ class PlainDMRG:
     def enlarged(self, i):
         bL, opsL = self.L[i]
         bR, opsR = self.R[i + 2]
-        EL, chL, enlL = blocking_left(self.ints, bL, opsL, i)
-        ER, chR, enlR = blocking_right(self.ints, bR, opsR, i + 1)
+        EL, chL, enlL = blocking_left_mixed(self.ints, bL, opsL, i, self.cut)
+        ER, chR, enlR = blocking_right_mixed(self.ints, bR, opsR, i + 1, self.cut)
         return EL, assemble_all(enlL, EL, chL), ER, assemble_all(enlR, ER, chR)
 
     def solve(self, i, step_id, EL, oL, ER, oR):
-        terms = nc_terms(2 * (i + 1), self.ints.n)
+        terms = mixed_terms(i + 1, self.K, self.cut)
         layout, size = psi_layout(EL, ER, self.Q)
         diag = heff_diagonal(layout, terms, oL, oR)
         key = splitmix.stream_key(self.seed, splitmix.KEY_GUESS)

@@ -127,13 +127,16 @@ def fock_block_basis(modes):
     return Basis(list(secs.items())), perm
 
 
-def fock_ops_exact(ints, modes, side):
-    """Exact matrices of all NC operators of a block holding `modes`, in its
-    sector-ordered full Fock basis (for pins; small blocks only)."""
+def fock_ops_exact(ints, modes, side, kind="nc"):
+    """Exact matrices of all operators of a block holding `modes`, in its
+    sector-ordered full Fock basis (for pins; small blocks only). side 'L'
+    keeps a+_p (p in modes) and R^L_p (p outside), side 'R' keeps a_p and
+    R^R_p; the two-index operators are the normal A, B over `modes` for a
+    left NC or right CN block, else the complementary P, Q over the modes
+    outside (kind 'nc' or 'cn', see cn.py)."""
     nm = len(modes)
     m0 = modes[0]
     basis, perm = fock_block_basis(modes)
-    inv = np.argsort(perm)
     c = [cre_fock(nm, k).toarray()[np.ix_(perm, perm)] for k in range(nm)]
     a = [x.T for x in c]
     loc = lambda p: p - m0
@@ -157,12 +160,6 @@ def fock_ops_exact(ints, modes, side):
     if side == "L":
         for p in modes:
             ops[("cd", p)] = op(c[loc(p)], (1, spin(p)))
-        for p in modes:
-            for r in modes:
-                if p < r:
-                    ops[("A", p, r)] = op(c[loc(p)] @ c[loc(r)], (2, spin(p) + spin(r)))
-                if p <= r:
-                    ops[("B", p, r)] = op(c[loc(p)] @ a[loc(r)], (0, spin(p) - spin(r)))
         for p in others:
             R = np.zeros_like(H)
             for q, r, s in itertools.product(modes, repeat=3):
@@ -182,6 +179,14 @@ def fock_ops_exact(ints, modes, side):
                 if x != 0.0:
                     R += x * c[loc(r)] @ a[loc(s)] @ a[loc(q)]
             ops[("RR", p)] = op(R, (-1, -spin(p)))
+    if (side, kind) in (("L", "nc"), ("R", "cn")):
+        for p in modes:
+            for r in modes:
+                if p < r:
+                    ops[("A", p, r)] = op(c[loc(p)] @ c[loc(r)], (2, spin(p) + spin(r)))
+                if p <= r:
+                    ops[("B", p, r)] = op(c[loc(p)] @ a[loc(r)], (0, spin(p) - spin(r)))
+    else:
         for p in others:
             for r in others:
                 if p < r:

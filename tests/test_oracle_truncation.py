@@ -79,7 +79,8 @@ def _check_block(d, vecs, blocks, modes_of, side):
             continue
         basis, ops = blocks[j]
         assert np.abs(V.T @ V - np.eye(V.shape[1])).max() < 1e-12
-        _, perm, exact = fock_ops_exact(d.ints, modes_of(j), side)
+        kind = "nc" if j <= d.cut else "cn"   # block of j left orbitals / starting at orbital j
+        _, perm, exact = fock_ops_exact(d.ints, modes_of(j), side, kind)
         assert set(ops) == set(exact)
         for key, op in ops.items():
             ref = V.T @ _raw(exact[key].to_dense(), perm) @ V
@@ -102,6 +103,21 @@ def test_swept_blocks_are_projections():
     d = PlainDMRG(t, v, N, TWO_SZ, seed=1, dav_tol=1e-12)
     d.build_blocks(M)
     d.sweep([M, M])
+    _check_block(d, _left_states(d), d.L, lambda i: list(range(0, 2 * i)), "L")
+    _check_block(d, _right_states(d), d.R, lambda j: list(range(2 * j, 2 * K)), "R")
+
+
+def test_mixed_nc_cn_blocks_are_projections():
+    """Mixed NC/CN (cut after orbital 2): blocks on both sides of the cut,
+    including the ones made by the normal-to-complementary transformation,
+    are exact projections of their Fock-space operators."""
+    t, v = random_integrals(K, 7)
+    d = PlainDMRG(t, v, N, TWO_SZ, seed=1, dav_tol=1e-12, cut=2)
+    d.build_blocks(M)
+    _check_block(d, _right_states(d), d.R, lambda j: list(range(2 * j, 2 * K)), "R")
+    d.sweep([M, M])
+    assert {k[0] for k in d.L[4][1] if isinstance(k, tuple)} == {"cd", "RL", "P", "Q"}
+    assert {k[0] for k in d.R[4][1] if isinstance(k, tuple)} == {"d", "RR", "A", "B"}
     _check_block(d, _left_states(d), d.L, lambda i: list(range(0, 2 * i)), "L")
     _check_block(d, _right_states(d), d.R, lambda j: list(range(2 * j, 2 * K)), "R")
 
