@@ -74,9 +74,16 @@ typedef struct {
                                   reduction; psi split for the tensor-core path) as a CUDA graph
                                   captured on the second call with the same psi / sigma pointers;
                                   0: launch them one by one. Profiling always launches directly. */
+  int mixed_cut;               /* sweeps: partition of H at each bond (Sec. III.A, App. B).
+                                  -1: the NC partition (Eq. h-nc) everywhere. c >= 0: mixed NC/CN -
+                                  a step whose enlarged left block holds e <= c spatial orbitals uses
+                                  NC, the others the CN partition (Eq. h-cn: two-index complementary
+                                  operators on the left, normal ones on the right); blocks switch
+                                  form by the normal-to-complementary transformation at the cut.
+                                  Takes effect at dmrg_build_blocks. */
 } dmrg_opts;
 
-/* Fill *o with defaults: FP64, 24, 200, 0, 0.0, seed 0, device 0, graphs 1. */
+/* Fill *o with defaults: FP64, 24, 200, 0, 0.0, seed 0, device 0, graphs 1, mixed_cut -1. */
 void dmrg_default_opts(dmrg_opts* o);
 
 /* Create a context on opts->device (NULL opts = defaults). *out is NULL on failure. */
@@ -192,10 +199,12 @@ dmrg_status dmrg_autotune(dmrg_ctx* ctx, int site, int* items_per_sm, double* pe
 
 /*
  * One sub-Hamiltonian's share of sigma (Sec. II.B, Eqs. sum-h, sub-h,
- * proc-def, proc-def-nc): the terms of the NC sum are assigned to n_ranks
- * ranks by their left-block spin-orbital indices: one index p -> p mod
- * n_ranks; a pair p <= r -> (r(r+1)/2 + p) mod n_ranks (so O_pr and O_rp,
- * and every conjugate pair, share a rank); H_L x 1 and 1 x H_R -> rank 0.
+ * proc-def, proc-def-nc, proc-def-cn): the terms of the NC sum are assigned
+ * to n_ranks ranks by their left-block spin-orbital indices: one index p ->
+ * p mod n_ranks; a pair p <= r -> (r(r+1)/2 + p) mod n_ranks (so O_pr and
+ * O_rp, and every conjugate pair, share a rank); H_L x 1 and 1 x H_R -> rank
+ * 0. At a sweep bond that uses the CN partition (dmrg_opts.mixed_cut) the
+ * pair is the right-block pair of the term (Eq. proc-def-cn).
  * sigma receives the FP64 sigma of rank `rank`'s terms only; the sum over
  * ranks is the full sigma (one all-reduce of sigma in a multi-GPU setting,
  * which this library does not perform). Arguments as dmrg_sigma.

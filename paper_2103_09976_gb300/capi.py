@@ -24,7 +24,7 @@ class dmrg_opts(ctypes.Structure):
     _fields_ = [("sigma_prec", ctypes.c_int), ("dav_max_space", ctypes.c_int),
                 ("dav_max_iter", ctypes.c_int), ("keep_one_per_q", ctypes.c_int),
                 ("noise", ctypes.c_double), ("seed", ctypes.c_ulonglong), ("device", ctypes.c_int),
-                ("graphs", ctypes.c_int)]
+                ("graphs", ctypes.c_int), ("mixed_cut", ctypes.c_int)]
 
 
 class dmrg_sigma_info(ctypes.Structure):

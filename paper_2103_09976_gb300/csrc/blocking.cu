@@ -74,6 +74,7 @@ __global__ void blocking_kernel(BlockingDev d) {
       const int r0 = d.chunk_off[db.Qout * d.nb + ob];
       if (r0 < 0) continue;
       const int rows = d.bdim[ob], cols = d.bdim[ib];
+      const double* __restrict__ S = tm.src >= d.nsrc1 ? d.src_store2 : d.src_store;
       bool neg;
       if (d.left) neg = ((c_site_n[tm.nout] - c_site_n[tm.nin]) & 1) && (d.bq[2 * ib] & 1);
       else neg = par && (c_site_n[tm.nin] & 1);
@@ -84,11 +85,81 @@ __global__ void blocking_kernel(BlockingDev d) {
         for (; j < cols; j += nt) {
           double v;
           if (tm.src < 0) v = (i == j) ? 1.0 : 0.0;
-          else if (!tm.trans) v = d.src_store[soff + (long long)i * cols + j];
-          else v = d.src_store[soff + (long long)j * rows + i];
+          else if (!tm.trans) v = S[soff + (long long)i * cols + j];
+          else v = S[soff + (long long)j * rows + i];
           dst[base + j] += w * v;
         }
       }
+    }
+  }
+}
+
+// Y_o = sum_i C[o][i] X_i for one 64 x 128 (operator, element) tile per
+// iteration: the coefficient tile (64 x 16) and 16 source rows of 128
+// elements are staged in shared memory, each warp owns 8 output operators x
+// 128 elements (16 sub-tiles of 8 x 8) and accumulates them with the FP64
+// m8n8k4 tensor instruction (lane g = lane/4, c = lane%4 holds A[g][c],
+// B[c][g], D[g][2c..2c+1]). Each output element is written once.
+constexpr int CB_K = 16;
+struct CombSmem {
+  double C[COMB_TM][CB_K + 4];
+  double X[CB_K][COMB_TN + 4];
+};
+
+__device__ __forceinline__ void dmma8(double (&d)[2], double a, double b) {
+  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+               : "+d"(d[0]), "+d"(d[1])
+               : "d"(a), "d"(b));
+}
+
+__global__ void __launch_bounds__(256, 2)
+opcomb_kernel(const double* __restrict__ src, const long long* __restrict__ xoff, const double* __restrict__ coef,
+              const CombClass* __restrict__ cls, int ncls, int ntiles, double* __restrict__ dst) {
+  __shared__ __align__(16) CombSmem sm;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, c = lane & 3;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int k = 0;
+    while (k + 1 < ncls && cls[k + 1].tile_start <= t) ++k;
+    const CombClass cc = cls[k];
+    const int local = t - cc.tile_start;
+    const int to = local / cc.tiles_e, te = local - to * cc.tiles_e;
+    const int o0 = to * COMB_TM;
+    const long long e0 = (long long)te * COMB_TN;
+    double acc[COMB_TN / 8][2];
+#pragma unroll
+    for (int q = 0; q < COMB_TN / 8; ++q) acc[q][0] = acc[q][1] = 0.0;
+    for (int i0 = 0; i0 < cc.n_in; i0 += CB_K) {
+      for (int x = tid; x < COMB_TM * CB_K; x += blockDim.x) {
+        const int r = x / CB_K, kk = x - r * CB_K;
+        const int o = o0 + r, i = i0 + kk;
+        sm.C[r][kk] = (o < cc.n_out && i < cc.n_in) ? coef[cc.c_off + (long long)o * cc.n_in + i] : 0.0;
+      }
+      for (int x = tid; x < CB_K * COMB_TN; x += blockDim.x) {
+        const int kk = x / COMB_TN, j = x - kk * COMB_TN;
+        const int i = i0 + kk;
+        const long long e = e0 + j;
+        sm.X[kk][j] = (i < cc.n_in && e < cc.E) ? src[xoff[cc.x_start + i] + e] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < CB_K; kk += 4) {
+        const double a = sm.C[warp * 8 + g][kk + c];
+#pragma unroll
+        for (int q = 0; q < COMB_TN / 8; ++q) dmma8(acc[q], a, sm.X[kk + c][q * 8 + g]);
+      }
+      __syncthreads();
+    }
+    const int o = o0 + warp * 8 + g;
+    if (o < cc.n_out) {
+      double* y = dst + cc.y_off + (long long)o * cc.E;
+#pragma unroll
+      for (int q = 0; q < COMB_TN / 8; ++q)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const long long e = e0 + q * 8 + 2 * c + h;
+          if (e < cc.E) y[e] = acc[q][h];
+        }
     }
   }
 }
@@ -302,6 +373,13 @@ void launch_blocking(const BlockingDev& d, cudaStream_t st) {
   if (d.ndst <= 0) return;
   const int grid = d.ndst < 152 * 64 ? d.ndst : 152 * 64;
   blocking_kernel<<<grid, 256, 0, st>>>(d);
+}
+
+void launch_opcomb(const double* src, const long long* xoff, const double* coef, const CombClass* cls, int ncls,
+                   int ntiles, double* dst, cudaStream_t st) {
+  if (ntiles <= 0) return;
+  const int grid = ntiles < 152 * 2 * 8 ? ntiles : 152 * 2 * 8;
+  opcomb_kernel<<<grid, 256, 0, st>>>(src, xoff, coef, cls, ncls, ntiles, dst);
 }
 
 void launch_orthonormalize(double* store, const GramBlock* gb, int nb, cudaStream_t st) {

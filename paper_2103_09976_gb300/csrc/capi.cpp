@@ -282,7 +282,8 @@ void run_sigma_part(Context& c, Problem& p, int rank, int n_ranks, const double*
   cudaStream_t st = c.stream;
   if (!slot) {
     auto w = std::make_unique<DevWork>();
-    const std::vector<int> ranks = nc_term_ranks(p.nL, p.n, n_ranks);
+    const std::vector<int> ranks = p.cn ? cn_term_ranks(p.nL, p.n, n_ranks) : nc_term_ranks(p.nL, p.n, n_ranks);
+    if (ranks.size() != p.terms.size()) throw Error(DMRG_EINVAL, "internal: term rank count");
     std::vector<Term> mine;
     for (size_t t = 0; t < p.terms.size(); ++t)
       if (ranks[t] == rank) mine.push_back(p.terms[t]);
@@ -502,6 +503,7 @@ void dmrg_default_opts(dmrg_opts* o) {
   o->seed = 0;
   o->device = 0;
   o->graphs = 1;
+  o->mixed_cut = -1;
 }
 
 dmrg_status dmrg_create(dmrg_ctx** out, const dmrg_opts* opts) {
@@ -519,6 +521,7 @@ dmrg_status dmrg_create(dmrg_ctx** out, const dmrg_opts* opts) {
     if (o.dav_max_iter < 1) throw Error(DMRG_EINVAL, "dav_max_iter must be >= 1");
     if (o.keep_one_per_q != 0 && o.keep_one_per_q != 1) throw Error(DMRG_EINVAL, "keep_one_per_q must be 0 or 1");
     if (!(o.noise >= 0.0) || !std::isfinite(o.noise)) throw Error(DMRG_EINVAL, "noise must be finite and >= 0");
+    if (o.mixed_cut < -1) throw Error(DMRG_EINVAL, "mixed_cut must be -1 (NC everywhere) or >= 0");
     if (o.sigma_prec < DMRG_FP64 || o.sigma_prec > DMRG_BF16X3)
       throw Error(DMRG_EINVAL, "unknown sigma precision");
     int ndev = 0;

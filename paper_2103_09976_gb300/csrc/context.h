@@ -118,6 +118,7 @@ struct DevWork {
 
 struct Problem {
   int nL = 0, n = 0;
+  bool cn = false;           // terms of the CN partition (App. B, Eq. h-cn) instead of NC
   QN Q;
   OpSet L, R;
   std::vector<PsiBlock> blocks;

@@ -87,7 +87,9 @@ struct BDst {
 // Everything the blocking kernel needs to expand terms into sector blocks.
 struct BlockingDev {
   double* dst_store;
-  const double* src_store;
+  const double* src_store;      // source ops [0, nsrc1)
+  const double* src_store2;     // source ops [nsrc1, ...): complementary sums of the block
+  int nsrc1;
   const BDst* dsts;
   int ndst;
   const int* term_start;        // per destination op, CSR into terms
@@ -112,6 +114,24 @@ struct TakeBlock {      // dst (d x k) = first k columns of Q (d x d)
   int d, k;
 };
 void launch_blocking(const BlockingDev& d, cudaStream_t st);
+// Linear combinations of a block's stored operators (the normal-to-
+// complementary transformation, Sec. III.A): for every class g (operators
+// sharing one shift, hence one block structure of E elements),
+//   Y_o = sum_i C[o][i] X_i,   o < n_out, i < n_in,
+// X_i the class's i-th source operator (E contiguous elements at
+// src + xoff[x_start + i]), Y_o at dst + y_off + o * E, C row-major at
+// coef + c_off. One 64 x 128 tile of (o, element) per CTA, FP64 tensor
+// instructions, k in steps of 16 sources.
+struct CombClass {
+  long long y_off, c_off, E;
+  int x_start, n_out, n_in;
+  int tile_start;   // first tile of the class in the launch
+  int tiles_e;      // tiles along E
+  int pad;
+};
+constexpr int COMB_TM = 64, COMB_TN = 128;
+void launch_opcomb(const double* src, const long long* xoff, const double* coef, const CombClass* cls, int ncls,
+                   int ntiles, double* dst, cudaStream_t st);
 // Per psi block: singular vectors of its d-dimensional side (rows when left,
 // columns otherwise) and squared singular values, by one-sided Jacobi over
 // the whole GPU (one cooperative launch for all blocks): Q (d x d row-major,

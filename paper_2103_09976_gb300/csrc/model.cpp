@@ -42,11 +42,11 @@ void add_op(OpSet& set, QN dq, int parity, bool sym, long long& cursor) {
   set.ops.push_back(std::move(d));
 }
 
-void build_nc_opset(OpSet& out, const Basis& basis, int nL, int n, bool left, long long base) {
+void build_nc_opset(OpSet& out, const Basis& basis, int nL, int n, bool left, long long base, bool cn) {
   out.basis = basis;
   out.ops.clear();
   long long cur = base;
-  NCIndex ix{nL, n};
+  NCIndex ix{nL, n, cn};
   add_op(out, {0, 0}, 0, true, cur);  // H
   if (left) {
     for (int p = 0; p < nL; ++p) add_op(out, {1, spin_of(p)}, 1, false, cur);        // a+_p
@@ -55,12 +55,15 @@ void build_nc_opset(OpSet& out, const Basis& basis, int nL, int n, bool left, lo
     for (int p = nL; p < n; ++p) add_op(out, {-1, -spin_of(p)}, 1, false, cur);      // a_p
     for (int p = 0; p < nL; ++p) add_op(out, {-1, -spin_of(p)}, 1, false, cur);      // R^R_p
   }
-  const int sgn = left ? 1 : -1;
-  for (int p = 0; p < nL; ++p)
-    for (int r = p + 1; r < nL; ++r)  // A_pr (left) / P_pr (right)
+  // normal pairs (A, B: creation shift) on the NC left and CN right, complementary
+  // pairs (P, Q: the adjoint shift) on the NC right and CN left
+  const int sgn = left != cn ? 1 : -1;
+  const int p0 = ix.pb(), p1 = ix.pb() + ix.np();
+  for (int p = p0; p < p1; ++p)
+    for (int r = p + 1; r < p1; ++r)  // A_pr / P_pr
       add_op(out, {2 * sgn, sgn * (spin_of(p) + spin_of(r))}, 0, false, cur);
-  for (int p = 0; p < nL; ++p)
-    for (int q = p; q < nL; ++q)  // B_pq (left) / Q_pq (right)
+  for (int p = p0; p < p1; ++p)
+    for (int q = p; q < p1; ++q)  // B_pq / Q_pq
       add_op(out, {0, sgn * (spin_of(p) - spin_of(q))}, 0, p == q, cur);
   if ((int)out.ops.size() != ix.count()) throw Error(1, "internal: NC operator count");
   out.elements = cur - base;
@@ -94,6 +97,34 @@ std::vector<Term> nc_terms(int nL, int n) {
   return T;
 }
 
+std::vector<Term> cn_terms(int nL, int n) {
+  NCIndex ix{nL, n, true};
+  std::vector<Term> T;
+  T.push_back({ix.H(), -1, false, false, 1.0, 0});
+  T.push_back({-1, ix.H(), false, false, 1.0, 0});
+  for (int p = 0; p < nL; ++p) {
+    T.push_back({ix.cd(p), ix.RR(p), false, false, 1.0, 1});
+    T.push_back({ix.cd(p), ix.RR(p), true, true, -1.0, 1});
+  }
+  for (int p = nL; p < n; ++p) {
+    T.push_back({ix.RL(p), ix.d(p), true, false, 1.0, 1});
+    T.push_back({ix.RL(p), ix.d(p), false, true, -1.0, 1});
+  }
+  for (int p = nL; p < n; ++p)
+    for (int r = p + 1; r < n; ++r) {
+      T.push_back({ix.A(p, r), ix.A(p, r), false, false, 1.0, 0});
+      T.push_back({ix.A(p, r), ix.A(p, r), true, true, 1.0, 0});
+    }
+  for (int p = nL; p < n; ++p)
+    for (int q = nL; q < n; ++q) {
+      if (p <= q)
+        T.push_back({ix.B(p, q), ix.B(p, q), false, false, 1.0, 0});
+      else
+        T.push_back({ix.B(q, p), ix.B(q, p), true, true, 1.0, 0});
+    }
+  return T;
+}
+
 std::vector<int> nc_term_ranks(int nL, int n, int n_ranks) {
   // same enumeration order as nc_terms
   std::vector<int> r;
@@ -110,6 +141,25 @@ std::vector<int> nc_term_ranks(int nL, int n, int n_ranks) {
     for (int q = p + 1; q < nL; ++q) r.insert(r.end(), 2, two(p, q));
   for (int p = 0; p < nL; ++p)
     for (int q = 0; q < nL; ++q) r.push_back(two(p, q));
+  return r;
+}
+
+std::vector<int> cn_term_ranks(int nL, int n, int n_ranks) {
+  // same enumeration order as cn_terms
+  std::vector<int> r;
+  auto one = [&](int p) { return p % n_ranks; };
+  auto two = [&](int p, int q) {
+    const int i = std::min(p, q), j = std::max(p, q);
+    return (int)(((long long)j * (j + 1) / 2 + i) % n_ranks);
+  };
+  r.push_back(0);
+  r.push_back(0);
+  for (int p = 0; p < nL; ++p) r.insert(r.end(), 2, one(p));
+  for (int p = nL; p < n; ++p) r.insert(r.end(), 2, one(p));
+  for (int p = nL; p < n; ++p)
+    for (int q = p + 1; q < n; ++q) r.insert(r.end(), 2, two(p, q));
+  for (int p = nL; p < n; ++p)
+    for (int q = nL; q < n; ++q) r.push_back(two(p, q));
   return r;
 }
 

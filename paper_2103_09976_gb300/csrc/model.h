@@ -60,12 +60,18 @@ struct OpDesc {
   std::vector<int> by_qin;       // sector index -> block index or -1
 };
 
-// Stored operators of one NC block. Left kind: H, a+_p (p<nL), R^L_p
-// (nL<=p<n), A_pr (p<r<nL), B_pq (p<=q<nL). Right kind: H, a_p (p>=nL),
-// R^R_p (p<nL), P_pr (p<r<nL), Q_pq (p<=q<nL). Both have 1 + n + nL^2 ops.
+// Stored operators of one block, in canonical order. NC form: left kind H,
+// a+_p (p<nL), R^L_p (nL<=p<n), A_pr (p<r<nL), B_pq (p<=q<nL); right kind H,
+// a_p (p>=nL), R^R_p (p<nL), P_pr (p<r<nL), Q_pq (p<=q<nL). CN form (App. B,
+// Eq. h-cn): the same one-index operators, and two-index pairs over the right
+// modes [nL, n): P^L_pr, Q^L_pq on the left, A_pr, B_pq on the right. Both
+// forms have 1 + n + np^2 ops, np = number of modes the pairs run over.
 struct NCIndex {
   int nL = 0, n = 0;
-  int count() const { return 1 + n + nL * nL; }
+  bool cn = false;
+  int pb() const { return cn ? nL : 0; }       // first mode of the pair range
+  int np() const { return cn ? n - nL : nL; }  // modes in the pair range
+  int count() const { return 1 + n + np() * np(); }
   int H() const { return 0; }
   // left kind
   int cd(int p) const { return 1 + p; }
@@ -73,11 +79,19 @@ struct NCIndex {
   // right kind
   int d(int p) const { return 1 + (p - nL); }
   int RR(int p) const { return 1 + (n - nL) + p; }
-  // both kinds
-  int pair_strict(int p, int r) const { return p * nL - p * (p + 1) / 2 + (r - p - 1); }
-  int pair_le(int p, int q) const { return p * nL - p * (p - 1) / 2 + (q - p); }
-  int A(int p, int r) const { return 1 + n + pair_strict(p, r); }  // == P index on the right
-  int B(int p, int q) const { return 1 + n + nL * (nL - 1) / 2 + pair_le(p, q); }  // == Q index
+  // both kinds (p, q, r in the pair range)
+  int pair_strict(int p, int r) const {
+    p -= pb();
+    r -= pb();
+    return p * np() - p * (p + 1) / 2 + (r - p - 1);
+  }
+  int pair_le(int p, int q) const {
+    p -= pb();
+    q -= pb();
+    return p * np() - p * (p - 1) / 2 + (q - p);
+  }
+  int A(int p, int r) const { return 1 + n + pair_strict(p, r); }  // A / P / P^L index
+  int B(int p, int q) const { return 1 + n + np() * (np() - 1) / 2 + pair_le(p, q); }  // B / Q / Q^L index
 };
 
 struct OpSet {
@@ -86,10 +100,10 @@ struct OpSet {
   long long elements = 0;
 };
 
-// Build the block tables of the canonical left or right NC operator list over
-// `basis`, offsets starting at `base` (left ops first, then right ops, in
-// one flat store for the synthetic problem).
-void build_nc_opset(OpSet& out, const Basis& basis, int nL, int n, bool left, long long base);
+// Build the block tables of the canonical left or right operator list (NC
+// form, or CN form when cn) over `basis`, offsets starting at `base` (left
+// ops first, then right ops, in one flat store for the synthetic problem).
+void build_nc_opset(OpSet& out, const Basis& basis, int nL, int n, bool left, long long base, bool cn = false);
 // Add one operator with shift dq over `basis` (blocks wherever both sectors exist).
 void add_op(OpSet& set, QN dq, int parity, bool sym, long long& cursor);
 
@@ -100,12 +114,19 @@ struct Term {
   int parR;         // fermion parity of the right operator
 };
 std::vector<Term> nc_terms(int nL, int n);
+// CN partition (App. B, Eq. h-cn in spin orbitals): H_L x 1, 1 x H_R, the NC
+// one-index terms, P^L_pr x A_pr and its transpose (nL <= p < r), and
+// Q^L_pq x B_pq (nL <= p, q), over CN-form operator sets.
+std::vector<Term> cn_terms(int nL, int n);
 // Sub-Hamiltonian rank of every term of nc_terms(nL, n) among n_ranks
 // (Sec. II.B, Eqs. proc-def and proc-def-nc in spin-orbital indices): terms
 // with one left index p go to p mod P; terms with a left pair p <= r to
 // (r(r+1)/2 + p) mod P, so O_pr and O_rp always share a rank; H_L x 1 and
 // 1 x H_R go to rank 0.
 std::vector<int> nc_term_ranks(int nL, int n, int n_ranks);
+// The same for cn_terms(nL, n) (Eq. proc-def-cn): the pair of a CN term is
+// its right-block pair p <= r (the larger indices).
+std::vector<int> cn_term_ranks(int nL, int n, int n_ranks);
 
 struct PsiBlock {
   int qL, qR;       // sector indices in the left / right basis

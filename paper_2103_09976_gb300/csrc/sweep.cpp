@@ -4,12 +4,17 @@
 // transformation (Eq. op-trans). The host decides which blocks to add and
 // which states to keep; every floating-point step runs in CUDA kernels.
 //
-// Operators of a block are an NC set in canonical order (model.h NCIndex):
-// a left block holding modes [0, nL) keeps H, a+_p (p < nL), R^L_p (p >= nL),
-// A_pr and B_pq (p, q, r < nL); a right block holding modes [nL, n) keeps
-// H, a_p (p >= nL), R^R_p, P_pr, Q_pq (p, q, r < nL). The enlarged blocks
-// L x site and site x R are NC sets of the same kind one site larger, so the
-// sigma work list applies to them directly.
+// Operators of a block are a set in canonical order (model.h NCIndex). NC
+// form: a left block holding modes [0, nL) keeps H, a+_p (p < nL), R^L_p
+// (p >= nL), A_pr and B_pq (p, q, r < nL); a right block holding modes
+// [nL, n) keeps H, a_p (p >= nL), R^R_p, P_pr, Q_pq (p, q, r < nL). CN form
+// (App. B, Eq. h-cn) moves the two-index pairs to the modes right of the
+// cut: P^L_pr, Q^L_pq on a left block, A_pr, B_pq on a right block. With the
+// mixed NC/CN scheme (Sec. III.A) blocks left of the cut are in NC form and
+// blocks right of it in CN form; the block that crosses the cut is built by
+// the normal-to-complementary transformation. The enlarged blocks L x site
+// and site x R of one bond share a form, so the sigma work list (NC or CN
+// terms) applies to them directly.
 //
 // Blocking: each enlarged operator is a sum of terms (block operator or 1)
 // (x) (4x4 site matrix) derived by splitting every second-quantized string
@@ -365,6 +370,344 @@ std::vector<ETerms> right_terms(const Ints& I, int s) {
   return T;
 }
 
+// ------------------------------------------- CN form and the transformation
+// Complementary sums of one block whose two-index operators are normal (an
+// NC left block, or a CN right block), for the pairs (p, r) of `out` modes:
+//   T_pr = sum_{q<s} (v_pqrs - v_psrq) A_qs          (P~_pr = T_pr^T)
+//   U_pq = sum_{r<=s} c_pq,rs B_rs,  V_pq = sum_{r<s} c_pq,sr B_rs
+//   (Q~_pq = U_pq + V_pq^T,  c_pq,rs = v_pqrs - v_psrq)
+// with q, r, s over the block's modes: P~_pr = sum_{q,s} v_pqrs a_s a_q and
+// Q~_pq = sum_{r,s} c_pq,rs a+_r a_s written with the stored A_qs = a+_q a+_s
+// (q < s) and B_rs = a+_r a_s (r <= s). Every output is a linear combination
+// of source operators of one shift, so the sums are one GEMM per shift class
+// (launch_opcomb); the comp ops are stored class by class.
+struct CompSet {
+  std::map<std::pair<int, int>, int> T, U, V;  // output pair -> comp op index
+  OpSet set;                                   // over the block's basis
+  std::vector<CombClass> cls;
+  std::vector<long long> xoff;
+  std::vector<double> coef;
+  int ntiles = 0;
+  double flops = 0.0;
+};
+
+void make_comp(const Ints& I, const NCIndex& bx, const OpSet& bset, int o0, int o1, CompSet& cs) {
+  const int s0 = bx.pb(), s1 = bx.pb() + bx.np();
+  struct Src {
+    int op, a, b;
+    bool isB;
+  };
+  struct Out {
+    char kind;  // 'T', 'U', 'V'
+    int p, q;
+  };
+  std::map<std::pair<int, int>, std::pair<std::vector<Src>, std::vector<Out>>> cl;  // by (dN, d2Sz)
+  for (int q = s0; q < s1; ++q)
+    for (int w = q + 1; w < s1; ++w) cl[{2, spin_of(q) + spin_of(w)}].first.push_back({bx.A(q, w), q, w, false});
+  for (int r = s0; r < s1; ++r)
+    for (int w = r; w < s1; ++w) cl[{0, spin_of(r) - spin_of(w)}].first.push_back({bx.B(r, w), r, w, true});
+  for (int p = o0; p < o1; ++p)
+    for (int r = p + 1; r < o1; ++r) cl[{2, spin_of(p) + spin_of(r)}].second.push_back({'T', p, r});
+  for (int p = o0; p < o1; ++p)
+    for (int q = p; q < o1; ++q) {
+      cl[{0, spin_of(q) - spin_of(p)}].second.push_back({'U', p, q});
+      cl[{0, spin_of(p) - spin_of(q)}].second.push_back({'V', p, q});
+    }
+  cs.set = OpSet();
+  cs.set.basis = bset.basis;
+  long long cur = 0;
+  for (auto& kv : cl) {
+    const QN dq{kv.first.first, kv.first.second};
+    const auto& src = kv.second.first;
+    const auto& out = kv.second.second;
+    if (out.empty()) continue;
+    CombClass cc{};
+    const int first = (int)cs.set.ops.size();
+    for (const Out& o : out) {
+      const int idx = (int)cs.set.ops.size();
+      add_op(cs.set, dq, 0, false, cur);
+      (o.kind == 'T' ? cs.T : o.kind == 'U' ? cs.U : cs.V)[{o.p, o.q}] = idx;
+    }
+    const OpDesc& f = cs.set.ops[first];
+    long long E = 0;
+    for (const OpBlock& b : f.blocks) E += (long long)b.rows * b.cols;
+    cc.y_off = f.blocks.empty() ? 0 : f.blocks[0].off;
+    cc.E = E;
+    cc.n_out = (int)out.size();
+    cc.n_in = (int)src.size();
+    cc.x_start = (int)cs.xoff.size();
+    cc.c_off = (long long)cs.coef.size();
+    for (const Src& x : src) {
+      const OpDesc& so = bset.ops[x.op];
+      cs.xoff.push_back(so.blocks.empty() ? 0 : so.blocks[0].off);
+    }
+    for (const Out& o : out)
+      for (const Src& x : src) {
+        double c = 0.0;
+        if (o.kind == 'T') {
+          if (!x.isB) c = I.vso(o.p, x.a, o.q, x.b) - I.vso(o.p, x.b, o.q, x.a);
+        } else if (x.isB) {
+          if (o.kind == 'U') c = I.vso(o.p, o.q, x.a, x.b) - I.vso(o.p, x.b, x.a, o.q);
+          else if (x.a < x.b) c = I.vso(o.p, o.q, x.b, x.a) - I.vso(o.p, x.a, x.b, o.q);
+        }
+        cs.coef.push_back(c);
+      }
+    cc.tiles_e = (int)((E + COMB_TN - 1) / COMB_TN);
+    cc.tile_start = cs.ntiles;
+    cs.ntiles += cc.tiles_e * ((cc.n_out + COMB_TM - 1) / COMB_TM);
+    cs.flops += 2.0 * cc.n_out * cc.n_in * (double)E;
+    cs.cls.push_back(cc);
+  }
+  cs.set.elements = cur;
+}
+
+// Left: block L holds modes [0, 2s) (NC form when src_nc, else CN form); the
+// enlarged block (modes [0, 2s+2)) is in CN form: H, a+_p, R^L_p (p >= 2s+2),
+// P^L_pr, Q^L_pq (2s+2 <= p, q, r). Comp ops (src_nc) are source indices
+// nsrc1 + comp index.
+std::vector<ETerms> left_terms_cn(const Ints& I, int s, bool src_nc, const CompSet* cs, int nsrc1) {
+  const int n = 2 * I.K, nL = 2 * s, nE = 2 * s + 2;
+  NCIndex bx{nL, n, !src_nc}, ex{nE, n, true};
+  Site st{I, s};
+  std::vector<ETerms> T(ex.count());
+  const int S0 = 2 * s, S1 = 2 * s + 1;
+  auto herm = [](const NCIndex& x, int p, int q, bool& t) {  // O_pq = O_pq or O_qp^T
+    t = p > q;
+    return p <= q ? x.B(p, q) : x.B(q, p);
+  };
+  {  // H of L x s
+    ETerms& e = T[ex.H()];
+    add(e, bx.H(), false, 1.0, eye4());
+    add(e, -1, false, 1.0, st.H());
+    for (int p = 0; p < nL; ++p) {
+      const Mat4 Rs = st.R(p, true);
+      add(e, bx.cd(p), false, 1.0, Rs);
+      add(e, bx.cd(p), true, -1.0, tr(Rs));
+    }
+    for (int p = S0; p <= S1; ++p) {
+      add(e, bx.RL(p), true, 1.0, st.ann(p));
+      add(e, bx.RL(p), false, -1.0, st.cre(p));
+    }
+    if (src_nc) {  // NC form at the cut (L | s)
+      for (int p = 0; p < nL; ++p)
+        for (int r = p + 1; r < nL; ++r) {
+          const Mat4 Ps = st.P(p, r);
+          add(e, bx.A(p, r), false, 1.0, Ps);
+          add(e, bx.A(p, r), true, 1.0, tr(Ps));
+        }
+      for (int p = 0; p < nL; ++p)
+        for (int q = 0; q < nL; ++q) {
+          bool t;
+          const int k = herm(bx, p, q, t);
+          add(e, k, t, 1.0, st.Q(p, q));
+        }
+    } else {  // CN form: P^L / Q^L of the site's modes with the site's normal pairs
+      const Mat4 A = mul(st.cre(S0), st.cre(S1));
+      add(e, bx.A(S0, S1), false, 1.0, A);
+      add(e, bx.A(S0, S1), true, 1.0, tr(A));
+      for (int p = S0; p <= S1; ++p)
+        for (int q = S0; q <= S1; ++q) {
+          bool t;
+          const int k = herm(bx, p, q, t);
+          add(e, k, t, 1.0, mul(st.cre(p), st.ann(q)));
+        }
+    }
+  }
+  for (int p = 0; p < nL; ++p) add(T[ex.cd(p)], bx.cd(p), false, 1.0, eye4());
+  for (int p = S0; p <= S1; ++p) add(T[ex.cd(p)], -1, false, 1.0, st.cre(p));
+  for (int p = nE; p < n; ++p) {  // R^L_p
+    ETerms& e = T[ex.RL(p)];
+    add(e, bx.RL(p), false, 1.0, eye4());
+    add(e, -1, false, 1.0, st.R(p, false));
+    if (src_nc) {  // Q^L_px and P^L_pr of L written out over its B and A
+      for (int x = S0; x <= S1; ++x)
+        for (int r = 0; r < nL; ++r)
+          for (int y = 0; y < nL; ++y) {
+            const double c = I.vso(p, x, r, y) - I.vso(p, y, r, x);
+            if (c == 0.0) continue;
+            bool t;
+            const int k = herm(bx, r, y, t);
+            add(e, k, t, c, st.ann(x));
+          }
+      for (int r = S0; r <= S1; ++r)
+        for (int q = 0; q < nL; ++q)
+          for (int w = 0; w < nL; ++w) {
+            const double c = I.vso(p, q, r, w);
+            if (c == 0.0 || q == w) continue;
+            if (q < w) add(e, bx.A(q, w), true, c, st.cre(r));
+            else add(e, bx.A(w, q), true, -c, st.cre(r));
+          }
+    } else {  // stored: Q^L_px = (Q^L_xp)^T, P^L_pr = -P^L_rp (x, r < p)
+      for (int x = S0; x <= S1; ++x) add(e, bx.B(x, p), true, 1.0, st.ann(x));
+      for (int r = S0; r <= S1; ++r) add(e, bx.A(r, p), false, -1.0, st.cre(r));
+    }
+    for (int w = 0; w < nL; ++w) {  // -a_w (x) sum v_pqrw a+_r a_q  (q, r on the site)
+      Mat4 m = zero4();
+      for (int q = S0; q <= S1; ++q)
+        for (int r = S0; r <= S1; ++r) axpy(m, I.vso(p, q, r, w), mul(st.cre(r), st.ann(q)));
+      add(e, bx.cd(w), true, -1.0, m);
+    }
+    for (int r = 0; r < nL; ++r) {  // a+_r (x) sum v_pqrw a_w a_q  (q, w on the site)
+      Mat4 m = zero4();
+      for (int q = S0; q <= S1; ++q)
+        for (int w = S0; w <= S1; ++w) axpy(m, I.vso(p, q, r, w), mul(st.ann(w), st.ann(q)));
+      add(e, bx.cd(r), false, 1.0, m);
+    }
+    for (int q = 0; q < nL; ++q) {  // a_q (x) sum v_pqrw a+_r a_w  (r, w on the site)
+      Mat4 m = zero4();
+      for (int r = S0; r <= S1; ++r)
+        for (int w = S0; w <= S1; ++w) axpy(m, I.vso(p, q, r, w), mul(st.cre(r), st.ann(w)));
+      add(e, bx.cd(q), true, 1.0, m);
+    }
+  }
+  for (int p = nE; p < n; ++p)
+    for (int r = p; r < n; ++r) {
+      if (p < r) {  // P^L_pr = sum_{q,w in L+s} v_pqrw a_w a_q
+        ETerms& e = T[ex.A(p, r)];
+        if (src_nc) add(e, nsrc1 + cs->T.at({p, r}), true, 1.0, eye4());
+        else add(e, bx.A(p, r), false, 1.0, eye4());
+        add(e, -1, false, 1.0, st.P(p, r));
+        for (int x = S0; x <= S1; ++x)  // one of q, w on the site (x), the other in L (y)
+          for (int y = 0; y < nL; ++y) add(e, bx.cd(y), true, I.vso(p, x, r, y) - I.vso(p, y, r, x), st.ann(x));
+      }
+      {  // Q^L_pq = sum_{r',w in L+s} (v_pqr'w - v_pwr'q) a+_r' a_w
+        ETerms& e = T[ex.B(p, r)];
+        const int q = r;
+        if (src_nc) {
+          add(e, nsrc1 + cs->U.at({p, q}), false, 1.0, eye4());
+          add(e, nsrc1 + cs->V.at({p, q}), true, 1.0, eye4());
+        } else {
+          add(e, bx.B(p, q), false, 1.0, eye4());
+        }
+        add(e, -1, false, 1.0, st.Q(p, q));
+        for (int x = S0; x <= S1; ++x)
+          for (int y = 0; y < nL; ++y) {
+            add(e, bx.cd(y), false, I.vso(p, q, y, x) - I.vso(p, x, y, q), st.ann(x));    // a+_y (x) a_x
+            add(e, bx.cd(y), true, -(I.vso(p, q, x, y) - I.vso(p, y, x, q)), st.cre(x));  // -a_y (x) a+_x
+          }
+      }
+    }
+  return T;
+}
+
+// Right: block R holds modes [2s+2, n) in CN form (normal A, B over its
+// modes); the enlarged block (modes [2s, n)) is in NC form when dst_nc (P, Q
+// over [0, 2s) from the comp ops: the transformation), else in CN form.
+std::vector<ETerms> right_terms_cn(const Ints& I, int s, bool dst_nc, const CompSet* cs, int nsrc1) {
+  const int n = 2 * I.K, nLb = 2 * s + 2, nE = 2 * s;
+  NCIndex bx{nLb, n, true}, ex{nE, n, !dst_nc};
+  Site st{I, s};
+  std::vector<ETerms> T(ex.count());
+  const int S0 = 2 * s, S1 = 2 * s + 1;
+  auto herm = [&](int p, int q, bool& t) {
+    t = p > q;
+    return p <= q ? bx.B(p, q) : bx.B(q, p);
+  };
+  for (int p = S0; p <= S1; ++p) add(T[ex.d(p)], -1, false, 1.0, st.ann(p));
+  for (int p = nLb; p < n; ++p) add(T[ex.d(p)], bx.d(p), false, 1.0, eye4());
+  {  // H of site x R, CN form at the cut (s | R)
+    ETerms& e = T[ex.H()];
+    add(e, -1, false, 1.0, st.H());
+    add(e, bx.H(), false, 1.0, eye4());
+    for (int p = S0; p <= S1; ++p) {
+      add(e, bx.RR(p), false, 1.0, st.cre(p));
+      add(e, bx.RR(p), true, -1.0, st.ann(p));
+    }
+    for (int p = nLb; p < n; ++p) {
+      const Mat4 Rs = st.R(p, false);
+      add(e, bx.d(p), false, 1.0, tr(Rs));
+      add(e, bx.d(p), true, -1.0, Rs);
+    }
+    for (int p = nLb; p < n; ++p)
+      for (int r = p + 1; r < n; ++r) {
+        const Mat4 Ps = st.P(p, r);
+        add(e, bx.A(p, r), false, 1.0, Ps);
+        add(e, bx.A(p, r), true, 1.0, tr(Ps));
+      }
+    for (int p = nLb; p < n; ++p)
+      for (int q = nLb; q < n; ++q) {
+        bool t;
+        const int k = herm(p, q, t);
+        add(e, k, t, 1.0, st.Q(p, q));
+      }
+  }
+  for (int p = 0; p < nE; ++p) {  // R^R_p
+    ETerms& e = T[ex.RR(p)];
+    add(e, bx.RR(p), false, 1.0, eye4());
+    add(e, -1, false, 1.0, st.R(p, true));
+    for (int x = S0; x <= S1; ++x) {
+      // a_x (x) Q^R_px: sum_{r,y in R} (v_pxry - v_pyrx) a+_r a_y
+      for (int r = nLb; r < n; ++r)
+        for (int y = nLb; y < n; ++y) {
+          const double c = I.vso(p, x, r, y) - I.vso(p, y, r, x);
+          if (c == 0.0) continue;
+          bool t;
+          const int k = herm(r, y, t);
+          add(e, k, t, c, st.ann(x));
+        }
+      // a+_x (x) P^R_px: sum_{q,w in R} v_pqxw a_w a_q
+      for (int q = nLb; q < n; ++q)
+        for (int w = nLb; w < n; ++w) {
+          const double c = I.vso(p, q, x, w);
+          if (c == 0.0 || q == w) continue;
+          if (q < w) add(e, bx.A(q, w), true, c, st.cre(x));
+          else add(e, bx.A(w, q), true, -c, st.cre(x));
+        }
+    }
+    for (int y = nLb; y < n; ++y) {
+      Mat4 m1 = zero4(), m2 = zero4(), m3 = zero4();
+      for (int u = S0; u <= S1; ++u)
+        for (int w = S0; w <= S1; ++w) {
+          axpy(m1, I.vso(p, u, w, y), mul(st.cre(w), st.ann(u)));
+          axpy(m2, I.vso(p, u, y, w), mul(st.ann(w), st.ann(u)));
+          axpy(m3, I.vso(p, y, u, w), mul(st.cre(u), st.ann(w)));
+        }
+      add(e, bx.d(y), false, -1.0, m1);
+      add(e, bx.d(y), true, 1.0, m2);
+      add(e, bx.d(y), false, 1.0, m3);
+    }
+  }
+  if (!dst_nc) {
+    for (int p = nE; p < n; ++p)
+      for (int r = p; r < n; ++r) {
+        if (p < r) {  // A_pr
+          ETerms& e = T[ex.A(p, r)];
+          if (p >= nLb) add(e, bx.A(p, r), false, 1.0, eye4());
+          else if (r >= nLb) add(e, bx.d(r), true, 1.0, st.cre(p));  // a+_p (site) a+_r (block)
+          else add(e, -1, false, 1.0, mul(st.cre(p), st.cre(r)));
+        }
+        ETerms& e = T[ex.B(p, r)];  // B_pq, q = r
+        if (p >= nLb) add(e, bx.B(p, r), false, 1.0, eye4());
+        else if (r >= nLb) add(e, bx.d(r), false, 1.0, st.cre(p));  // a+_p (site) a_q (block)
+        else add(e, -1, false, 1.0, mul(st.cre(p), st.ann(r)));
+      }
+    return T;
+  }
+  for (int p = 0; p < nE; ++p)
+    for (int r = p; r < nE; ++r) {
+      if (p < r) {  // P_pr
+        ETerms& e = T[ex.A(p, r)];
+        add(e, nsrc1 + cs->T.at({p, r}), true, 1.0, eye4());
+        add(e, -1, false, 1.0, st.P(p, r));
+        for (int x = S0; x <= S1; ++x)
+          for (int y = nLb; y < n; ++y) add(e, bx.d(y), false, I.vso(p, y, r, x) - I.vso(p, x, r, y), st.ann(x));
+      }
+      {  // Q_pq
+        ETerms& e = T[ex.B(p, r)];
+        const int q = r;
+        add(e, nsrc1 + cs->U.at({p, q}), false, 1.0, eye4());
+        add(e, nsrc1 + cs->V.at({p, q}), true, 1.0, eye4());
+        add(e, -1, false, 1.0, st.Q(p, q));
+        for (int x = S0; x <= S1; ++x)
+          for (int y = nLb; y < n; ++y) {
+            add(e, bx.d(y), false, I.vso(p, q, x, y) - I.vso(p, y, x, q), st.cre(x));
+            add(e, bx.d(y), true, -(I.vso(p, q, y, x) - I.vso(p, x, y, q)), st.ann(x));
+          }
+      }
+    }
+  return T;
+}
+
 bool can_hold(int n_modes, QN q) {
   return q.n >= 0 && q.n <= n_modes && ((q.s - q.n) % 2 == 0) && std::abs(q.s) <= std::min(q.n, n_modes - q.n);
 }
@@ -376,6 +719,7 @@ struct DevBlock {
   OpSet set;
   int nL = 0;
   bool left = true;
+  bool cn = false;  // CN form (two-index pairs over the modes right of the cut)
   DevBuf store;
 };
 
@@ -385,6 +729,8 @@ struct SweepState {
   int K = 0;
   std::vector<std::unique_ptr<DevBlock>> L, R;  // L[i]: modes [0, 2i); R[j]: modes [2j, 2K)
   int prob_site = -1;
+  int cut = 0;            // mixed NC/CN cut (orbitals); K = NC everywhere
+  bool prob_cn = false;   // partition of the current problem
   Enlarged EL, ER;
   std::vector<dmrg_step_log> log;
 };
@@ -436,7 +782,7 @@ const std::vector<dmrg_step_log>& sweep_log(const Context& c) {
 
 namespace {
 
-std::unique_ptr<DevBlock> vacuum(const Ints& I, bool left, cudaStream_t st) {
+std::unique_ptr<DevBlock> vacuum(const Ints& I, bool left, cudaStream_t st, bool cn = false) {
   auto b = std::make_unique<DevBlock>();
   Basis v;
   v.q.push_back({0, 0});
@@ -444,18 +790,45 @@ std::unique_ptr<DevBlock> vacuum(const Ints& I, bool left, cudaStream_t st) {
   v.finish();
   b->left = left;
   b->nL = left ? 0 : 2 * I.K;
-  build_nc_opset(b->set, v, b->nL, 2 * I.K, left, 0);
+  b->cn = cn;
+  build_nc_opset(b->set, v, b->nL, 2 * I.K, left, 0, cn);
   b->store.alloc(std::max<long long>(1, b->set.elements) * sizeof(double));
   DMRG_CUDA(cudaMemsetAsync(b->store.p, 0, std::max<long long>(1, b->set.elements) * sizeof(double), st));
   return b;
 }
 
-// Enlarged operators of one side into `store`: the host lists each enlarged
-// operator's terms (block op or identity, transposed or not, coefficient,
-// site matrix element); the blocking kernel expands them over the sectors.
+// Enlarged operators of one side into `store` (NC form, or CN form when
+// e_cn): the host lists each enlarged operator's terms (block op or
+// identity, transposed or not, coefficient, site matrix element); the
+// blocking kernel expands them over the sectors. When the block and the
+// enlarged block differ in form (the normal-to-complementary transformation
+// at the mixed NC/CN cut), the block's complementary sums are first formed
+// by one GEMM per shift class and serve as further source operators.
 void build_enlarged(Context& c, const Ints& I, const DevBlock& B, int site, bool left, const Enlarged& E,
-                    OpSet& EO, double* store) {
-  const std::vector<ETerms> terms = left ? left_terms(I, site) : right_terms(I, site);
+                    OpSet& EO, double* store, bool e_cn) {
+  const int n = 2 * I.K;
+  const bool transform_step = B.cn != e_cn;
+  if (transform_step && (left ? B.cn : !B.cn)) throw Error(DMRG_EINVAL, "internal: blocks change form only at the cut");
+  CompSet cs;
+  DevBuf d_comp, d_cls, d_xoff, d_coef;
+  const int nsrc1 = (int)B.set.ops.size();
+  cudaStream_t st = c.stream;
+  if (transform_step) {
+    const NCIndex bx = left ? NCIndex{2 * site, n, false} : NCIndex{2 * site + 2, n, true};
+    if (left) make_comp(I, bx, B.set, 2 * site + 2, n, cs);
+    else make_comp(I, bx, B.set, 0, 2 * site, cs);
+    d_comp.alloc(std::max<long long>(1, cs.set.elements) * sizeof(double));
+    d_cls.upload(cs.cls, st);
+    d_xoff.upload(cs.xoff, st);
+    d_coef.upload(cs.coef, st);
+    ProfScope ps(c.prof, 3, st);
+    launch_opcomb(B.store.as<double>(), d_xoff.as<long long>(), d_coef.as<double>(), d_cls.as<CombClass>(),
+                  (int)cs.cls.size(), cs.ntiles, d_comp.as<double>(), st);
+    DMRG_CUDA(cudaGetLastError());
+  }
+  std::vector<ETerms> terms;
+  if (left) terms = e_cn ? left_terms_cn(I, site, !B.cn, &cs, nsrc1) : left_terms(I, site);
+  else terms = B.cn ? right_terms_cn(I, site, !e_cn, &cs, nsrc1) : right_terms(I, site);
   std::vector<int> term_start(EO.ops.size() + 1, 0);
   std::vector<BTerm> flat;
   size_t total = 0;
@@ -477,11 +850,11 @@ void build_enlarged(Context& c, const Ints& I, const DevBlock& B, int site, bool
     eq[2 * i + 1] = E.basis.q[i].s;
     for (int j = 0; j < nb; ++j) chunk[(size_t)i * nb + j] = E.chunk_off[i][j];
   }
-  const size_t nsrc = B.set.ops.size();
+  const size_t nsrc = B.set.ops.size() + cs.set.ops.size();
   std::vector<long long> srcblk(std::max<size_t>(1, nsrc * nb), -1);
   std::vector<int> src_dq(std::max<size_t>(2, 2 * nsrc)), src_par(std::max<size_t>(1, nsrc));
   for (size_t j = 0; j < nsrc; ++j) {
-    const OpDesc& o = B.set.ops[j];
+    const OpDesc& o = j < (size_t)nsrc1 ? B.set.ops[j] : cs.set.ops[j - nsrc1];
     for (const OpBlock& ob : o.blocks) srcblk[j * nb + ob.qin] = ob.off;
     src_dq[2 * j] = o.dq.n;
     src_dq[2 * j + 1] = o.dq.s;
@@ -491,7 +864,6 @@ void build_enlarged(Context& c, const Ints& I, const DevBlock& B, int site, bool
   for (size_t k = 0; k < EO.ops.size(); ++k)
     for (const OpBlock& ob : EO.ops[k].blocks)
       dsts.push_back({ob.off, (int)k, ob.qin, ob.qout, ob.rows, ob.cols, 0});
-  cudaStream_t st = c.stream;
   DevBuf d_ts, d_terms, d_bq, d_bdim, d_eq, d_chunk, d_srcblk, d_dq, d_par, d_dsts, d_err;
   d_ts.upload(term_start, st);
   d_terms.upload(flat, st);
@@ -508,6 +880,8 @@ void build_enlarged(Context& c, const Ints& I, const DevBlock& B, int site, bool
   BlockingDev d;
   d.dst_store = store;
   d.src_store = B.store.as<double>();
+  d.src_store2 = d_comp.as<double>();
+  d.nsrc1 = nsrc1;
   d.dsts = d_dsts.as<BDst>();
   d.ndst = (int)dsts.size();
   d.term_start = d_ts.as<int>();
@@ -538,10 +912,11 @@ void build_enlarged(Context& c, const Ints& I, const DevBlock& B, int site, bool
 // (U blocks per enlarged sector in `u_store`, d x k row-major, offsets uoff).
 void transform(Context& c, const OpSet& EO, const double* enl_store, const Basis& nb,
                const std::vector<int>& esec_of_new, const std::vector<long long>& uoff, const double* u_store,
-               DevBlock& out, int nL, int n, bool left) {
-  build_nc_opset(out.set, nb, nL, n, left, 0);
+               DevBlock& out, int nL, int n, bool left, bool cn) {
+  build_nc_opset(out.set, nb, nL, n, left, 0, cn);
   out.nL = nL;
   out.left = left;
+  out.cn = cn;
   out.store.alloc(std::max<long long>(1, out.set.elements) * sizeof(double));
   if ((int)out.set.ops.size() != (int)EO.ops.size()) throw Error(DMRG_EINVAL, "internal: transform op count");
   std::vector<PsiBlock> blocks;
@@ -628,19 +1003,22 @@ void sweep_problem(Context& c, int site) {
   p->Q = S.Q;
   S.EL = enlarge(Lb.set.basis);
   S.ER = enlarge(Rb.set.basis);
-  build_nc_opset(p->L, S.EL.basis, p->nL, p->n, true, 0);
-  build_nc_opset(p->R, S.ER.basis, p->nL, p->n, false, p->L.elements);
-  p->terms = nc_terms(p->nL, p->n);
+  const bool cn = site + 1 > S.cut;  // mixed NC/CN: partition of this bond
+  build_nc_opset(p->L, S.EL.basis, p->nL, p->n, true, 0, cn);
+  build_nc_opset(p->R, S.ER.basis, p->nL, p->n, false, p->L.elements, cn);
+  p->terms = cn ? cn_terms(p->nL, p->n) : nc_terms(p->nL, p->n);
+  p->cn = cn;
   p->blocks = psi_layout(S.EL.basis, S.ER.basis, p->Q, &p->psi_size);
   if (p->blocks.empty()) throw Error(DMRG_EINVAL, "no psi block at this bond");
   const long long elems = p->L.elements + p->R.elements;
   c.prob.reset();
   p->store.alloc(std::max<long long>(1, elems) * sizeof(double));
-  build_enlarged(c, S.I, Lb, site, true, S.EL, p->L, p->store.as<double>());
-  build_enlarged(c, S.I, Rb, site + 1, false, S.ER, p->R, p->store.as<double>());
+  build_enlarged(c, S.I, Lb, site, true, S.EL, p->L, p->store.as<double>(), cn);
+  build_enlarged(c, S.I, Rb, site + 1, false, S.ER, p->R, p->store.as<double>(), cn);
   prepare_worklist(c, *p);
   c.prob = std::move(p);
   S.prob_site = site;
+  S.prob_cn = cn;
 }
 
 namespace {
@@ -770,9 +1148,10 @@ void sweep_build_blocks(Context& c, const double* t, const double* v, int K, int
     if (!std::isfinite(x)) throw Error(DMRG_EINVAL, "non-finite two-electron integral");
   c.prob.reset();
   cudaStream_t st = c.stream;
+  S->cut = c.opts.mixed_cut < 0 ? K : std::min(c.opts.mixed_cut, K);
   S->L.resize(K + 1);
   S->R.resize(K + 1);
-  S->R[K] = vacuum(S->I, false, st);
+  S->R[K] = vacuum(S->I, false, st, K > S->cut);
   S->L[0] = vacuum(S->I, true, st);
   const uint64_t key = c.opts.seed ^ KEY_MPS;
   unsigned long long counter = 0;
@@ -780,10 +1159,11 @@ void sweep_build_blocks(Context& c, const double* t, const double* v, int K, int
     const DevBlock& Rb = *S->R[j + 1];
     Enlarged E = enlarge(Rb.set.basis);
     OpSet EO;
-    build_nc_opset(EO, E.basis, 2 * j, 2 * K, false, 0);
+    const bool cn = j > S->cut;  // right block starting at orbital j
+    build_nc_opset(EO, E.basis, 2 * j, 2 * K, false, 0, cn);
     DevBuf est;
     est.alloc(std::max<long long>(1, EO.elements) * sizeof(double));
-    build_enlarged(c, S->I, Rb, j, false, E, EO, est.as<double>());
+    build_enlarged(c, S->I, Rb, j, false, E, EO, est.as<double>(), cn);
     // kept sectors: those the left part (2j modes) can complement to the target
     std::vector<int> comp;
     long long D = 0;
@@ -841,7 +1221,8 @@ void sweep_build_blocks(Context& c, const double* t, const double* v, int K, int
     }
     DMRG_CUDA(cudaGetLastError());
     auto nbk = std::make_unique<DevBlock>();
-    transform(c, EO, est.as<double>(), Dm.nb, Dm.esec_of_new, Dm.uoff, Dm.u.as<double>(), *nbk, 2 * j, 2 * K, false);
+    transform(c, EO, est.as<double>(), Dm.nb, Dm.esec_of_new, Dm.uoff, Dm.u.as<double>(), *nbk, 2 * j, 2 * K, false,
+              cn);
     S->R[j] = std::move(nbk);
   }
   c.sweep = std::move(S);
@@ -897,11 +1278,11 @@ void sweep_run(Context& c, const int* Ms, int n_sweeps, double tol, double* ener
       auto nbk = std::make_unique<DevBlock>();
       if (fwd) {
         transform(c, p.L, p.store.as<double>(), D.nb, D.esec_of_new, D.uoff, D.u.as<double>(), *nbk, 2 * (i + 1),
-                  2 * K, true);
+                  2 * K, true, S.prob_cn);
         S.L[i + 1] = std::move(nbk);
       } else {
         transform(c, p.R, p.store.as<double>(), D.nb, D.esec_of_new, D.uoff, D.u.as<double>(), *nbk, 2 * (i + 1),
-                  2 * K, false);
+                  2 * K, false, S.prob_cn);
         S.R[i + 1] = std::move(nbk);
       }
       const double t4 = clk();

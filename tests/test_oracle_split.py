@@ -60,3 +60,29 @@ def test_terms_balance_over_ranks_at_k108(P):
     mean = len(terms) / P
     assert set(cnt) == set(range(P))
     assert max(abs(c - mean) for c in cnt.values()) < 0.02 * mean
+
+
+@pytest.mark.parametrize("P", [2, 3, 5])
+def test_cn_parts_sum_to_full_sigma_and_use_the_large_indices(P):
+    """CN partition (Eq. proc-def-cn): a two-index term is placed by its
+    right-block pair, i.e. by the two larger orbital indices; the parts
+    still partition the terms."""
+    from oracle.cn import cn_terms
+    from oracle.nc import Integrals, fock_ops_exact
+    from synth import random_integrals
+    K, nL = 4, 4
+    t, v = random_integrals(K, 2)
+    ints = Integrals(t, v)
+    bL, _, oL = fock_ops_exact(ints, list(range(nL)), "L", "cn")
+    bR, _, oR = fock_ops_exact(ints, list(range(nL, 2 * K)), "R", "cn")
+    lay, size = psi_layout(bL, bR, (4, 0))
+    x = random_unit_vector(size, 3)
+    terms = cn_terms(nL, 2 * K)
+    full = sigma_blocks(x, lay, terms, oL, oR)
+    parts = [sigma_part(x, lay, terms, oL, oR, r, P) for r in range(P)]
+    assert np.abs(sum(parts) - full).max() <= 1e-13 * np.abs(full).max()
+    for term in terms:
+        if term[0] is not None and term[0] != "H" and term[0][0] in ("P", "Q"):
+            p, r = term[0][1], term[0][2]
+            assert p >= nL and r >= nL
+            assert nc_term_rank(term, P) == proc_two(p, r, P)

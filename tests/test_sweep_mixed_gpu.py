@@ -2,7 +2,11 @@
 control, decimation and transformation, bf16-slice sigma products. The
 energy of every step is the FP64 Rayleigh quotient of the converged vector,
 so at full bond dimension it reproduces FCI to far better than the mixed
-sigma's own relative error (about 1e-5): the bar is 1e-6 Ha."""
+sigma's own relative error: the bar is 1e-6 Ha. The Davidson tolerance on
+|r|^2 follows what each sigma can resolve: BF16X3 keeps 24 significant bits
+(relative error ~6e-8, |r|^2 floor far below 1e-10), BF16X2 16 bits
+(~1.5e-5, so |r|^2 of a vector of norm 1 with |H psi| ~ 10 cannot go much
+below ~1e-8); 1e-10 and 1e-8 respectively."""
 
 import json
 import os
@@ -15,8 +19,8 @@ pytestmark = pytest.mark.gpu
 GOLD = os.path.join(os.path.dirname(__file__), "golden", "fci_energies.json")
 
 
-@pytest.mark.parametrize("prec", ["BF16X3", "BF16X2"])
-def test_config1_mixed_sweeps_within_1e6_of_fci(prec):
+@pytest.mark.parametrize("prec,tol", [("BF16X3", 1e-10), ("BF16X2", 1e-8)])
+def test_config1_mixed_sweeps_within_1e6_of_fci(prec, tol):
     from paper_2103_09976_gb300 import capi
     from synth import random_integrals
     gold = json.load(open(GOLD))["cfg1"]["energy"]
@@ -24,9 +28,9 @@ def test_config1_mixed_sweeps_within_1e6_of_fci(prec):
     ctx = capi.dmrg_create(device=0, seed=0, dav_max_iter=400, sigma_prec=getattr(capi, "DMRG_" + prec))
     try:
         capi.dmrg_build_blocks(ctx, t, v, 8, 8, 0, 256)
-        e, _ = capi.dmrg_sweep(ctx, [256] * 4, 1e-10)
+        e, _ = capi.dmrg_sweep(ctx, [256] * 4, tol)
         log = capi.dmrg_sweep_log(ctx)
     finally:
         capi.dmrg_destroy(ctx)
     assert np.all(np.abs(e - gold) < 1e-6), (e, gold)
-    assert all(l["converged"] for l in log)
+    assert all(l["converged"] for l in log), [(l["site"], l["iters"]) for l in log if not l["converged"]]
