@@ -13,6 +13,9 @@ Modules:
   nc        U(1)xU(1) normal/complementary (NC) left-right decomposition
             (spin-orbital form of Eq. h-nc and Eq. op-def), site operators,
             blocking (Eq. blocked-ops) and transformation (Eq. op-trans)
+  cn        complementary/normal (CN) partition (Eq. h-cn), CN blocking, the
+            normal-to-complementary transformation and the mixed NC/CN
+            scheme (Sec. III.A)
   sigma     H_eff . psi as a sum over NC terms of block-sparse O_L psi O_R^T
             products (Sec. II.D-E); synthetic middle-bond operator layout
   davidson  plain Davidson eigensolver (Appendix A, solving step)

@@ -23,8 +23,14 @@ Fixed readings of points the paper leaves open:
   * Truncation: all singular values of all psi blocks sorted by
     (s descending, q_L ascending, index ascending); the first
     min(M, count) are kept, zero singular values included.
-  * Davidson guess at each step: SplitMix64 normals (key = seed ^ KEY_GUESS,
-    counter = step_id * 2^32 + element index, step_id = sweep * K + i).
+  * Davidson guess at each step: the previous step's wavefunction carried to
+    the new bond (the sweep moves one site; the previous psi is projected on
+    the block just kept and the block it leaves is expanded through the
+    stored basis of the next block: predict()); at the turn of a sweep the
+    bond and blocks are unchanged and the previous psi is the guess. The
+    first step after build_blocks uses SplitMix64 normals (key = seed ^
+    KEY_GUESS, counter = step_id * 2^32 + element index, step_id =
+    sweep * K + i).
   * Sweep energy: the lowest Davidson eigenvalue of the sweep.
   * Mixed NC/CN (Sec. III.A, cn.py): with cut c, blocks of at most c left
     orbitals / starting at orbital c or before are in NC form, the others in
@@ -39,11 +45,11 @@ Fock-space matrices; renormalized bases are orthonormal.
 import numpy as np
 
 from . import splitmix
-from .blocks import Basis, BlockOp, qadd, qsub
+from .blocks import SITE_Q, Basis, BlockOp, enlarged_left, enlarged_right, qadd, qsub
 from .davidson import davidson
 from .cn import blocking_left_mixed, blocking_right_mixed, mixed_terms, vacuum_right_cn
 from .nc import Integrals, assemble_all, transform, vacuum_left, vacuum_right
-from .sigma import heff_diagonal, psi_layout, psi_to_blocks, sigma_blocks
+from .sigma import blocks_to_psi, heff_diagonal, psi_layout, psi_to_blocks, sigma_blocks
 
 
 def can_hold(n_modes, q):
@@ -99,6 +105,7 @@ class PlainDMRG:
         self.UL = {}  # i -> {sector of L[i-1] x site: kept columns}, for inspection
         self.UR = {}  # j -> {sector of site x R[j+1]: kept columns}
         self.log = []
+        self.prev = None  # (i, forward, psi, layout) of the last step
 
     # ------------------------------------------------------ initial blocks
     def build_blocks(self, M_init):
@@ -125,6 +132,7 @@ class PlainDMRG:
             self.R[j] = (nb, ops)
             self.UR[j] = U
         self.L[0] = vacuum_left(self.ints)
+        self.prev = None
 
     # ------------------------------------------------------------- a step
     def enlarged(self, i):
@@ -134,12 +142,75 @@ class PlainDMRG:
         ER, chR, enlR = blocking_right_mixed(self.ints, bR, opsR, i + 1, self.cut)
         return EL, assemble_all(enlL, EL, chL), ER, assemble_all(enlR, ER, chR)
 
-    def solve(self, i, step_id, EL, oL, ER, oR):
+    def predict(self, i, forward):
+        """Guess for the step at bond i from the previous step's psi
+        (None if there is no usable previous step).
+
+        Moving right (previous step at bond i-1): psi lived on
+        (L_{i-1} x s_{i-1}) x (s_i x R_{i+1}); projecting its left index on
+        the kept states of L_i (phi = U^T psi) leaves L_i x (s_i x R_{i+1}),
+        i.e. (L_i x s_i) x R_{i+1} with no sign (the product state is
+        c_l c_n c_r |0> in either grouping), and each state of R_{i+1} is a
+        combination of states of s_{i+1} x R_{i+2} (its stored basis V):
+            psi'[(l, n), :] = phi[l, (n, r)] V^T.
+        Moving left is the mirror image with psi V and the stored basis U of
+        L_{i+1} over L_i x s_i."""
+        if self.prev is None:
+            return None
+        pi, pfwd, px, play = self.prev
+        if pi == i:  # turn of the sweep: same bond, same blocks
+            return px
+        bL_new, bR_new = self.L[i][0], self.R[i + 2][0]
+        ELn, chLn = enlarged_left(bL_new)
+        ERn, chRn = enlarged_right(bR_new)
+        lay, size = psi_layout(ELn, ERn, self.Q)
+        out = {qL: np.zeros((mL, mR)) for qL, qR, mL, mR, off in lay}
+        qR_of = {qL: qR for qL, qR, mL, mR, off in lay}
+        prev = psi_to_blocks(px, play)
+        if forward and pfwd and pi == i - 1:
+            U, V = self.UL[i], self.UR[i + 1]
+            _, chR = enlarged_right(self.R[i + 1][0])
+            bR1 = self.R[i + 1][0]
+            row_of = {Q: {(qb, n): off for qb, n, off in lst} for Q, lst in chLn.items()}
+            for QL, QR, mL, mR, off in play:
+                if QL not in U:
+                    continue
+                phi = U[QL].T @ prev[QL]
+                for qr, n, offc in chR[QR]:
+                    QLn = qadd(QL, SITE_Q[n])
+                    if QLn not in out or qR_of[QLn] != qr or qr not in V:
+                        continue
+                    r0 = row_of[QLn][(QL, n)]
+                    out[QLn][r0:r0 + phi.shape[0], :] += phi[:, offc:offc + bR1.dim(qr)] @ V[qr].T
+        elif not forward and not pfwd and pi == i + 1:
+            V, U = self.UR[i + 2], self.UL[i + 1]
+            _, chL = enlarged_left(self.L[i + 1][0])
+            bL1 = self.L[i + 1][0]
+            col_of = {Q: {(qb, n): off for qb, n, off in lst} for Q, lst in chRn.items()}
+            for QL, QR, mL, mR, off in play:
+                if QR not in V:
+                    continue
+                phi = prev[QL] @ V[QR]
+                for ql, n, offc in chL[QL]:
+                    QRn = qadd(QR, SITE_Q[n])
+                    if ql not in out or qR_of[ql] != QRn or ql not in U:
+                        continue
+                    c0 = col_of[QRn][(QR, n)]
+                    out[ql][:, c0:c0 + phi.shape[1]] += U[ql] @ phi[offc:offc + bL1.dim(ql), :]
+        else:
+            return None
+        g = blocks_to_psi(out, lay, size)
+        return g if np.linalg.norm(g) > 1e-12 else None
+
+    def solve(self, i, step_id, EL, oL, ER, oR, guess=None):
         terms = mixed_terms(i + 1, self.K, self.cut)
         layout, size = psi_layout(EL, ER, self.Q)
         diag = heff_diagonal(layout, terms, oL, oR)
-        key = splitmix.stream_key(self.seed, splitmix.KEY_GUESS)
-        g = splitmix.normal(key, (np.uint64(step_id) << np.uint64(32)) + np.arange(size, dtype=np.uint64))
+        if guess is not None:
+            g = guess
+        else:
+            key = splitmix.stream_key(self.seed, splitmix.KEY_GUESS)
+            g = splitmix.normal(key, (np.uint64(step_id) << np.uint64(32)) + np.arange(size, dtype=np.uint64))
         mv = lambda x: sigma_blocks(x, layout, terms, oL, oR)
         th, x, nmv, conv = davidson(mv, diag, g, **self.dav)
         return th, x, layout, nmv, conv
@@ -186,7 +257,8 @@ class PlainDMRG:
 
     def step(self, i, forward, M, step_id):
         EL, oL, ER, oR = self.enlarged(i)
-        th, x, layout, nmv, conv = self.solve(i, step_id, EL, oL, ER, oR)
+        th, x, layout, nmv, conv = self.solve(i, step_id, EL, oL, ER, oR, self.predict(i, forward))
+        self.prev = (i, forward, x, layout)
         kept, svd, disc = self.decimate(self.perturb(x, step_id), layout, M, self.keep_one_per_q)
         if forward:
             U = {qL: fix_sign(svd[qL][0][:, :m]) for qL, m in kept.items()}

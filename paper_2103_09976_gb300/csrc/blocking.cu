@@ -164,6 +164,37 @@ opcomb_kernel(const double* __restrict__ src, const long long* __restrict__ xoff
   }
 }
 
+// One strided GEMM job per CTA (grid-stride): 16 x 16 output tiles, one
+// element per thread, k staged in shared memory 16 at a time.
+__global__ void bgemm_kernel(const double* __restrict__ A, const double* __restrict__ B, double* __restrict__ C,
+                             const GJob* __restrict__ jobs, int njobs) {
+  __shared__ double sa[16][17], sb[16][17];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int jb = blockIdx.x; jb < njobs; jb += gridDim.x) {
+    const GJob g = jobs[jb];
+    for (int i0 = 0; i0 < g.m; i0 += 16)
+      for (int j0 = 0; j0 < g.n; j0 += 16) {
+        double acc = 0.0;
+        for (int k0 = 0; k0 < g.kk; k0 += 16) {
+          {
+            const int i = i0 + ty, k = k0 + tx;
+            sa[ty][tx] = (i < g.m && k < g.kk)
+                             ? A[g.a + (g.ta ? (long long)k * g.lda + i : (long long)i * g.lda + k)] : 0.0;
+            const int kb = k0 + ty, j = j0 + tx;
+            sb[ty][tx] = (kb < g.kk && j < g.n)
+                             ? B[g.b + (g.tb ? (long long)j * g.ldb + kb : (long long)kb * g.ldb + j)] : 0.0;
+          }
+          __syncthreads();
+#pragma unroll
+          for (int q = 0; q < 16; ++q) acc = fma(sa[ty][q], sb[q][tx], acc);
+          __syncthreads();
+        }
+        const int i = i0 + ty, j = j0 + tx;
+        if (i < g.m && j < g.n) C[g.c + (long long)i * g.ldc + j] = acc;
+      }
+  }
+}
+
 // Orthonormalise the columns of each d x m block (row-major, in place) by
 // classical Gram-Schmidt applied twice per column.
 __global__ void orthonormalize_kernel(double* __restrict__ store, const GramBlock* __restrict__ gb, int nb) {
@@ -380,6 +411,11 @@ void launch_opcomb(const double* src, const long long* xoff, const double* coef,
   if (ntiles <= 0) return;
   const int grid = ntiles < 152 * 2 * 8 ? ntiles : 152 * 2 * 8;
   opcomb_kernel<<<grid, 256, 0, st>>>(src, xoff, coef, cls, ncls, ntiles, dst);
+}
+
+void launch_bgemm(const double* A, const double* B, double* C, const GJob* jobs, int njobs, cudaStream_t st) {
+  if (njobs <= 0) return;
+  bgemm_kernel<<<njobs < 152 * 16 ? njobs : 152 * 16, 256, 0, st>>>(A, B, C, jobs, njobs);
 }
 
 void launch_orthonormalize(double* store, const GramBlock* gb, int nb, cudaStream_t st) {

@@ -74,6 +74,17 @@ struct DevBuf {
     }
     bytes = n;
   }
+  // Take over o's allocation (o becomes empty).
+  void take(DevBuf& o) {
+    reset();
+    p = o.p;
+    bytes = o.bytes;
+    st = o.st;
+    async = o.async;
+    o.p = nullptr;
+    o.bytes = 0;
+    o.async = false;
+  }
   template <class T>
   T* as() const { return reinterpret_cast<T*>(p); }
   template <class T>
@@ -228,6 +239,7 @@ void sweep_block_info(const Context& c, int side, int j, int* n_sectors, int* q,
 void sweep_block_read(Context& c, int side, int j, int op, double* dense);
 // Davidson on the device: x0 (device, may be null = seeded random) -> energy,
 // eigenvector in x_out (device, may be null). Returns false if not converged.
+void ensure_davidson_workspace(Context& c, Problem& p);
 bool run_davidson(Context& c, Problem& p, const double* x0, double tol, double* energy, double* x_out,
                   int* iters, unsigned long long guess_counter_base);
 void run_sigma(Context& c, Problem& p, const double* d_psi, double* d_sigma);      // context precision

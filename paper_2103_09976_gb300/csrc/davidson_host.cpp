@@ -17,7 +17,10 @@ namespace {
 constexpr uint64_t KEY_GUESS = 0x4755455353505349ull;  // "GUESSPSI" stream of the seed
 constexpr int LDH = 32;                                // leading dimension of the projected matrix
 
-void ensure_workspace(Context& c, Problem& p) {
+}  // namespace
+
+// Davidson buffers of a problem and the diagonal of H_eff (built once).
+void ensure_davidson_workspace(Context& c, Problem& p) {
   const int S = c.opts.dav_max_space;
   if (p.dav_ready && p.dav_space == S) return;
   const long long n = p.psi_size;
@@ -55,11 +58,13 @@ void ensure_workspace(Context& c, Problem& p) {
   p.dav_ready = true;
 }
 
+namespace {
+
 }  // namespace
 
 bool run_davidson(Context& c, Problem& p, const double* x0, double tol, double* energy, double* x_out,
                   int* iters, unsigned long long guess_counter_base) {
-  ensure_workspace(c, p);
+  ensure_davidson_workspace(c, p);
   const long long n = p.psi_size;
   const int S = c.opts.dav_max_space;
   const int max_iter = c.opts.dav_max_iter;

@@ -721,6 +721,11 @@ struct DevBlock {
   bool left = true;
   bool cn = false;  // CN form (two-index pairs over the modes right of the cut)
   DevBuf store;
+  // the block's states over the enlarged basis it was made from: sector s is
+  // enlarged sector esec[s], basis u + uoff[s] (d x k row-major, columns = states)
+  DevBuf u;
+  std::vector<long long> uoff;
+  std::vector<int> esec;
 };
 
 struct SweepState {
@@ -732,6 +737,14 @@ struct SweepState {
   int cut = 0;            // mixed NC/CN cut (orbitals); K = NC everywhere
   bool prob_cn = false;   // partition of the current problem
   Enlarged EL, ER;
+  // previous step of the sweep (wavefunction prediction)
+  bool has_prev = false;
+  int prev_site = -1;
+  bool prev_fwd = true;
+  long long prev_size = 0;
+  DevBuf prev_x;
+  std::vector<PsiBlock> prev_blocks;
+  Enlarged prev_EL, prev_ER;
   std::vector<dmrg_step_log> log;
 };
 
@@ -1130,6 +1143,118 @@ void decimate(Context& c, Problem& p, const Enlarged& E, const double* psi, int 
   DMRG_CUDA(cudaStreamSynchronize(st));
 }
 
+// Davidson guess for the step at bond i: the previous step's psi carried to
+// this bond, into g (p.psi_size doubles). Moving right (previous step at
+// bond i-1), psi over (L_{i-1} x s_{i-1}) x (s_i x R_{i+1}) is projected on
+// the kept states of L_i (phi = U^T psi), which leaves (L_i x s_i) x R_{i+1}
+// with no fermion sign (the product state is c_l c_n c_r |0> in either
+// grouping), and every state of R_{i+1} is expanded in s_{i+1} x R_{i+2}
+// through its stored basis V: psi'[(l, n), :] = phi[l, (n, r)] V^T. Moving
+// left is the mirror image (phi = psi V, psi'[:, (n, r)] = U phi[(l, n), r]
+// with the stored basis U of L_{i+1}). At the turn of a sweep the bond and
+// its blocks are unchanged and the previous psi is the guess. Returns false
+// (random guess) without a usable previous step or if the carried vector
+// vanishes.
+bool predict_guess(Context& c, int i, bool forward, const Problem& p, double* g) {
+  SweepState& S = *c.sweep;
+  if (!S.has_prev) return false;
+  cudaStream_t st = c.stream;
+  if (S.prev_site == i) {
+    if (S.prev_size != p.psi_size) return false;
+    DMRG_CUDA(cudaMemcpyAsync(g, S.prev_x.as<double>(), p.psi_size * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    return true;
+  }
+  const bool fw = forward && S.prev_fwd && S.prev_site == i - 1;
+  const bool bw = !forward && !S.prev_fwd && S.prev_site == i + 1;
+  if (!fw && !bw) return false;
+  std::vector<int> blk_of_qL(S.EL.basis.size(), -1);
+  for (size_t b = 0; b < p.blocks.size(); ++b) blk_of_qL[p.blocks[b].qL] = (int)b;
+  auto site_state = [](QN d) {
+    for (int n = 0; n < 4; ++n)
+      if (SITE_Q[n] == d) return n;
+    return -1;
+  };
+  std::vector<GJob> j1, j2;
+  long long phi_size = 0;
+  const DevBlock& Lb = fw ? *S.L[i] : *S.L[i + 1];
+  const DevBlock& Rb = fw ? *S.R[i + 1] : *S.R[i + 2];
+  if (fw) {  // Lb: kept states of the previous left enlarged block; Rb: basis over the new ER
+    std::vector<int> kept_of(S.prev_EL.basis.size(), -1);
+    for (size_t s = 0; s < Lb.esec.size(); ++s) kept_of[Lb.esec[s]] = (int)s;
+    for (const PsiBlock& pb : S.prev_blocks) {
+      const int s = kept_of[pb.qL];
+      if (s < 0) continue;
+      const int k = Lb.set.basis.dim[s];
+      const long long phi_off = phi_size;
+      phi_size += (long long)k * pb.mR;
+      j1.push_back({Lb.uoff[s], pb.off, phi_off, k, pb.mR, pb.mL, k, pb.mR, pb.mR, 1, 0});  // U^T psi
+      const QN qR = S.prev_ER.basis.q[pb.qR];
+      for (int jb = 0; jb < Rb.set.basis.size(); ++jb) {
+        const int offc = S.prev_ER.chunk_off[pb.qR][jb];
+        if (offc < 0) continue;
+        const int n = site_state(qR - Rb.set.basis.q[jb]);
+        if (n < 0) continue;
+        const int QLn = S.EL.basis.find(Lb.set.basis.q[s] + SITE_Q[n]);
+        if (QLn < 0) continue;
+        const int b = blk_of_qL[QLn];
+        if (b < 0 || p.blocks[b].qR != Rb.esec[jb]) continue;
+        const PsiBlock& nb = p.blocks[b];
+        const int r0 = S.EL.chunk_off[QLn][s], kr = Rb.set.basis.dim[jb];
+        j2.push_back({phi_off + offc, Rb.uoff[jb], nb.off + (long long)r0 * nb.mR, k, nb.mR, kr, pb.mR, kr, nb.mR,
+                      0, 1});  // phi[:, chunk] V^T
+      }
+    }
+  } else {  // Rb: kept states of the previous right enlarged block; Lb: basis over the new EL
+    std::vector<int> kept_of(S.prev_ER.basis.size(), -1);
+    for (size_t s = 0; s < Rb.esec.size(); ++s) kept_of[Rb.esec[s]] = (int)s;
+    for (const PsiBlock& pb : S.prev_blocks) {
+      const int s = kept_of[pb.qR];
+      if (s < 0) continue;
+      const int k = Rb.set.basis.dim[s];
+      const long long phi_off = phi_size;
+      phi_size += (long long)pb.mL * k;
+      j1.push_back({pb.off, Rb.uoff[s], phi_off, pb.mL, k, pb.mR, pb.mR, k, k, 0, 0});  // psi V
+      const QN qL = S.prev_EL.basis.q[pb.qL];
+      for (int ja = 0; ja < Lb.set.basis.size(); ++ja) {
+        const int offc = S.prev_EL.chunk_off[pb.qL][ja];
+        if (offc < 0) continue;
+        const int n = site_state(qL - Lb.set.basis.q[ja]);
+        if (n < 0) continue;
+        const int QRn = S.ER.basis.find(Rb.set.basis.q[s] + SITE_Q[n]);
+        if (QRn < 0) continue;
+        const int b = blk_of_qL[Lb.esec[ja]];
+        if (b < 0 || p.blocks[b].qR != QRn) continue;
+        const PsiBlock& nb = p.blocks[b];
+        const int c0 = S.ER.chunk_off[QRn][s], kl = Lb.set.basis.dim[ja];
+        j2.push_back({Lb.uoff[ja], phi_off + (long long)offc * k, nb.off + c0, nb.mL, k, kl, kl, k, nb.mR, 0,
+                      0});  // U phi[chunk, :]
+      }
+    }
+  }
+  if (j2.empty()) return false;
+  DevBuf phi, d1, d2;
+  phi.alloc(std::max<long long>(1, phi_size) * sizeof(double));
+  d1.upload(j1, st);
+  d2.upload(j2, st);
+  DMRG_CUDA(cudaMemsetAsync(g, 0, p.psi_size * sizeof(double), st));
+  if (fw) {
+    launch_bgemm(Lb.u.as<double>(), S.prev_x.as<double>(), phi.as<double>(), d1.as<GJob>(), (int)j1.size(), st);
+    launch_bgemm(phi.as<double>(), Rb.u.as<double>(), g, d2.as<GJob>(), (int)j2.size(), st);
+  } else {
+    launch_bgemm(S.prev_x.as<double>(), Rb.u.as<double>(), phi.as<double>(), d1.as<GJob>(), (int)j1.size(), st);
+    launch_bgemm(Lb.u.as<double>(), phi.as<double>(), g, d2.as<GJob>(), (int)j2.size(), st);
+  }
+  DMRG_CUDA(cudaGetLastError());
+  // |g|^2 (the oracle falls back to a random guess below norm 1e-12)
+  Problem& pm = const_cast<Problem&>(p);
+  double* sc = pm.dav_s.as<double>() + 60;
+  dav_dots(g, p.psi_size, 1, g, p.psi_size, pm.dav_partial.as<double>(), sc, 1, st);
+  double nrm2 = 0.0;
+  DMRG_CUDA(cudaMemcpyAsync(&nrm2, sc, sizeof(double), cudaMemcpyDeviceToHost, st));
+  DMRG_CUDA(cudaStreamSynchronize(st));
+  return std::sqrt(nrm2) > 1e-12;
+}
+
 }  // namespace
 
 void sweep_build_blocks(Context& c, const double* t, const double* v, int K, int N, int two_sz, int M_init) {
@@ -1223,6 +1348,9 @@ void sweep_build_blocks(Context& c, const double* t, const double* v, int K, int
     auto nbk = std::make_unique<DevBlock>();
     transform(c, EO, est.as<double>(), Dm.nb, Dm.esec_of_new, Dm.uoff, Dm.u.as<double>(), *nbk, 2 * j, 2 * K, false,
               cn);
+    nbk->u.take(Dm.u);
+    nbk->uoff = Dm.uoff;
+    nbk->esec = Dm.esec_of_new;
     S->R[j] = std::move(nbk);
   }
   c.sweep = std::move(S);
@@ -1245,12 +1373,27 @@ void sweep_run(Context& c, const int* Ms, int n_sweeps, double tol, double* ener
       sweep_problem(c, i);
       Problem& p = *c.prob;
       const double t1 = clk();
-      DevBuf x;
+      DevBuf x, guess;
       x.alloc(p.psi_size * sizeof(double));
+      guess.alloc(p.psi_size * sizeof(double));
       double e = 0.0;
       int it = 0;
       const unsigned long long step_id = (unsigned long long)s * K + i;
-      const bool conv = run_davidson(c, p, nullptr, tol, &e, x.as<double>(), &it, step_id << 32);
+      ensure_davidson_workspace(c, p);
+      const bool have_guess = predict_guess(c, i, fwd, p, guess.as<double>());
+      const bool conv = run_davidson(c, p, have_guess ? guess.as<double>() : nullptr, tol, &e, x.as<double>(), &it,
+                                     step_id << 32);
+      // the solver's psi (before any noise) seeds the next step's guess
+      S.prev_x.alloc(p.psi_size * sizeof(double));
+      DMRG_CUDA(cudaMemcpyAsync(S.prev_x.as<double>(), x.as<double>(), p.psi_size * sizeof(double),
+                                cudaMemcpyDeviceToDevice, c.stream));
+      S.prev_blocks = p.blocks;
+      S.prev_EL = S.EL;
+      S.prev_ER = S.ER;
+      S.prev_site = i;
+      S.prev_fwd = fwd;
+      S.prev_size = p.psi_size;
+      S.has_prev = true;
       if (c.opts.noise > 0.0) {
         // perturbative noise: decimate s x + noise z / |z|, renormalized, with
         // z seeded N(0,1) numbers of the noise stream and s = sign(x . z)
@@ -1279,10 +1422,16 @@ void sweep_run(Context& c, const int* Ms, int n_sweeps, double tol, double* ener
       if (fwd) {
         transform(c, p.L, p.store.as<double>(), D.nb, D.esec_of_new, D.uoff, D.u.as<double>(), *nbk, 2 * (i + 1),
                   2 * K, true, S.prob_cn);
+        nbk->u.take(D.u);
+        nbk->uoff = D.uoff;
+        nbk->esec = D.esec_of_new;
         S.L[i + 1] = std::move(nbk);
       } else {
         transform(c, p.R, p.store.as<double>(), D.nb, D.esec_of_new, D.uoff, D.u.as<double>(), *nbk, 2 * (i + 1),
                   2 * K, false, S.prob_cn);
+        nbk->u.take(D.u);
+        nbk->uoff = D.uoff;
+        nbk->esec = D.esec_of_new;
         S.R[i + 1] = std::move(nbk);
       }
       const double t4 = clk();

@@ -56,3 +56,34 @@ def test_config1_full_m_equals_stored_fci():
     d.build_blocks(256)
     e, disc = d.sweep([256, 256])
     assert all(abs(x - gold["energy"]) < 1e-9 for x in e)
+
+
+def test_wavefunction_prediction_is_exact_at_full_bond_dimension():
+    """At full bond dimension every kept basis spans its whole space, so the
+    previous ground state carried to the next bond (predict) is the same
+    state: unit norm and Rayleigh quotient equal to the FCI energy. A wrong
+    index, block or transpose in the carry breaks both."""
+    from oracle.cn import mixed_terms
+    from oracle.fock import fci_energy
+    from oracle.sigma import sigma_blocks
+    K, N, s = 5, 5, 1
+    t, v = random_integrals(K, 3)
+    e_fci = fci_energy(t, v, N, s)
+    d = PlainDMRG(t, v, N, s, seed=2, dav_tol=1e-24, dav_max_iter=400)
+    d.build_blocks(4 ** K)
+    checked = 0
+    for sweep in range(3):
+        fwd = sweep % 2 == 0
+        for i in (range(0, K - 1) if fwd else range(K - 2, -1, -1)):
+            g = d.predict(i, fwd)
+            if g is not None and d.prev[0] != i:
+                EL, oL, ER, oR = d.enlarged(i)
+                from oracle.sigma import psi_layout
+                lay, size = psi_layout(EL, ER, d.Q)
+                assert abs(np.linalg.norm(g) - 1.0) < 1e-10
+                e = g @ sigma_blocks(g, lay, mixed_terms(i + 1, K, d.cut), oL, oR)
+                assert abs(e - e_fci) < 1e-9, (sweep, i, e, e_fci)
+                checked += 1
+            d.step(i, fwd, 4 ** K, sweep * K + i)
+    assert checked == 3 * (K - 2)
+    assert all(rec["nmv"] <= 3 for rec in d.log[K - 1:])   # converged guesses after the first sweep

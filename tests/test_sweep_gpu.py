@@ -55,10 +55,14 @@ def test_full_m_sweeps_equal_fci(K, N, s, M):
     try:
         capi.dmrg_build_blocks(ctx, t, v, K, N, s, M)
         e, d = capi.dmrg_sweep(ctx, [M] * 3, 1e-12)
+        log = capi.dmrg_sweep_log(ctx)
     finally:
         capi.dmrg_destroy(ctx)
     assert np.all(np.abs(e - ref) < 1e-9), (e, ref)
     assert np.all(d < 1e-20)
+    # at full M the previous ground state carried to the next bond is exact,
+    # so every solve after the first sweep starts converged
+    assert all(g["iters"] <= 3 for g in log[K - 1:]), [g["iters"] for g in log]
 
 
 def test_initial_blocks_equal_oracle():
@@ -109,6 +113,7 @@ def test_truncated_sweeps_follow_oracle():
     for g, o in zip(log, ora.log):
         assert (g["site"], g["forward"], g["psi_size"]) == (o["i"], int(o["forward"]), o["dim"])
         assert g["converged"] and o["converged"]
+        assert abs(g["iters"] - o["nmv"]) <= 2, (g, o)   # same carried guess on both sides
         assert abs(g["energy"] - o["energy"]) < 1e-9, (g, o)
         assert abs(g["discarded"] - o["discarded"]) <= 1e-6 * o["discarded"] + 1e-14, (g, o)
     assert np.all(np.abs(e - np.array(e_ref)) < 1e-9), (e, e_ref)
