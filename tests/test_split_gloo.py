@@ -6,6 +6,7 @@ import os
 import socket
 
 import numpy as np
+import pytest
 import torch
 import torch.distributed as dist
 import torch.multiprocessing as mp
@@ -19,7 +20,18 @@ def _free_port():
     return port
 
 
-def _problem():
+def _problem(cn=False):
+    if cn:  # a CN bond (Eq. h-cn) over exact Fock-space blocks: K=4, cut after 2 orbitals
+        from oracle.cn import cn_terms
+        from oracle.nc import Integrals, fock_ops_exact
+        from oracle.sigma import psi_layout
+        from synth import random_integrals, random_unit_vector
+        t, v = random_integrals(4, 6)
+        ints = Integrals(t, v)
+        bL, _, oL = fock_ops_exact(ints, list(range(4)), "L", "cn")
+        bR, _, oR = fock_ops_exact(ints, list(range(4, 8)), "R", "cn")
+        lay, size = psi_layout(bL, bR, (4, 0))
+        return lay, cn_terms(4, 8), oL, oR, random_unit_vector(size, 5)
     from oracle.nc import nc_terms
     from oracle.sigma import psi_layout, synthetic_ops
     from synth import gaussian_sector_dims, mirrored_sectors, random_unit_vector
@@ -30,12 +42,12 @@ def _problem():
     return lay, nc_terms(6, 12), oL, oR, random_unit_vector(size, 3)
 
 
-def _rank_main(rank, world, port, out_path):
+def _rank_main(rank, world, port, out_path, cn=False):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     from oracle.sigma import sigma_part
-    lay, terms, oL, oR, x = _problem()
+    lay, terms, oL, oR, x = _problem(cn)
     part = torch.from_numpy(sigma_part(x, lay, terms, oL, oR, rank, world))
     dist.all_reduce(part, op=dist.ReduceOp.SUM)
     if rank == 0:
@@ -44,11 +56,13 @@ def _rank_main(rank, world, port, out_path):
     dist.destroy_process_group()
 
 
-def test_allreduce_of_parts_is_full_sigma(tmp_path):
+@pytest.mark.parametrize("cn", [False, True])
+def test_allreduce_of_parts_is_full_sigma(tmp_path, cn):
+    """NC terms (Eq. proc-def-nc) and CN terms (Eq. proc-def-cn)."""
     from oracle.sigma import sigma_blocks
     out = str(tmp_path / "sigma.npy")
-    mp.spawn(_rank_main, args=(2, _free_port(), out), nprocs=2, join=True)
-    lay, terms, oL, oR, x = _problem()
+    mp.spawn(_rank_main, args=(2, _free_port(), out, cn), nprocs=2, join=True)
+    lay, terms, oL, oR, x = _problem(cn)
     full = sigma_blocks(x, lay, terms, oL, oR)
     got = np.load(out)
     assert np.abs(got - full).max() <= 1e-13 * np.abs(full).max()
