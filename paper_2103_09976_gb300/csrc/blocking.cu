@@ -30,13 +30,25 @@ __device__ __forceinline__ int find_sector(const int* q, int nq, int n, int s) {
 // operator, in order, find the block sector ib the term reads (enlarged
 // input sector minus the site state's quantum numbers), the source block
 // and its output sector ob, and add coef * sign * source into the chunk
-// (rows of ob within Qout, columns of ib within Qin). Each destination
-// element is owned by one thread (index mod blockDim) for the zeroing and
-// every update, so terms are applied in order without barriers and the
-// sums are deterministic. Signs: block x site takes (-1)^{N(block in)} when
-// the site part is odd; site x block takes (-1)^{N(site in)} when the block
-// operator is odd.
-__global__ void blocking_kernel(BlockingDev d) {
+// (rows of ob within Qout, columns of ib within Qin). Terms are resolved 256
+// at a time, one per thread, into shared memory (the lookups are dependent
+// global loads, so doing them in parallel hides their latency), then applied
+// in term order. Each destination element is owned by one thread (index mod
+// blockDim) for the zeroing and every update, so terms are applied in order
+// without atomics and the sums are deterministic. Signs: block x site takes
+// (-1)^{N(block in)} when the site part is odd; site x block takes
+// (-1)^{N(site in)} when the block operator is odd.
+struct RTerm {        // one resolved term
+  long long soff;     // source block offset
+  double w;           // coefficient times sign
+  int r0, c0, rows, cols;
+  int kind;           // 0 skip, 1 identity, 2 source, 3 source transposed
+  int store2;         // source in the second store
+};
+constexpr int BLK_THREADS = 256;
+
+__global__ void __launch_bounds__(BLK_THREADS) blocking_kernel(BlockingDev d) {
+  __shared__ RTerm rt[BLK_THREADS];
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int bi = blockIdx.x; bi < d.ndst; bi += gridDim.x) {
     const BDst db = d.dsts[bi];
@@ -45,51 +57,67 @@ __global__ void blocking_kernel(BlockingDev d) {
     for (long long e = tid; e < ne; e += nt) dst[e] = 0.0;
     const int qin_n = d.eq[2 * db.Qin], qin_s = d.eq[2 * db.Qin + 1];
     const int qout_n = d.eq[2 * db.Qout], qout_s = d.eq[2 * db.Qout + 1];
-    for (int t = d.term_start[db.k]; t < d.term_start[db.k + 1]; ++t) {
-      const BTerm tm = d.terms[t];
-      const int ib = find_sector(d.bq, d.nb, qin_n - c_site_n[tm.nin], qin_s - c_site_s[tm.nin]);
-      if (ib < 0) continue;
-      const int c0 = d.chunk_off[db.Qin * d.nb + ib];
-      if (c0 < 0) continue;
-      int ob = ib, par = 0;
-      long long soff = -1;
-      if (tm.src >= 0) {
-        const int dn = d.src_dq[2 * tm.src], ds = d.src_dq[2 * tm.src + 1];
-        par = d.src_par[tm.src];
-        if (!tm.trans) {
-          soff = d.srcblk[(long long)tm.src * d.nb + ib];
-          if (soff < 0) continue;
-          ob = find_sector(d.bq, d.nb, d.bq[2 * ib] + dn, d.bq[2 * ib + 1] + ds);
-        } else {
-          ob = find_sector(d.bq, d.nb, d.bq[2 * ib] - dn, d.bq[2 * ib + 1] - ds);
-          if (ob >= 0) soff = d.srcblk[(long long)tm.src * d.nb + ob];
-          if (soff < 0) continue;
+    const int t_end = d.term_start[db.k + 1];
+    for (int t0 = d.term_start[db.k]; t0 < t_end; t0 += nt) {
+      const int nhere = min(nt, t_end - t0);
+      if (tid < nhere) {
+        RTerm& r = rt[tid];
+        r.kind = 0;
+        const BTerm tm = d.terms[t0 + tid];
+        const int ib = find_sector(d.bq, d.nb, qin_n - c_site_n[tm.nin], qin_s - c_site_s[tm.nin]);
+        const int c0 = ib >= 0 ? d.chunk_off[db.Qin * d.nb + ib] : -1;
+        int ob = ib, par = 0;
+        long long soff = -1;
+        bool ok = c0 >= 0;
+        if (ok && tm.src >= 0) {
+          const int dn = d.src_dq[2 * tm.src], ds = d.src_dq[2 * tm.src + 1];
+          par = d.src_par[tm.src];
+          if (!tm.trans) {
+            soff = d.srcblk[(long long)tm.src * d.nb + ib];
+            ob = soff < 0 ? -1 : find_sector(d.bq, d.nb, d.bq[2 * ib] + dn, d.bq[2 * ib + 1] + ds);
+          } else {
+            ob = find_sector(d.bq, d.nb, d.bq[2 * ib] - dn, d.bq[2 * ib + 1] - ds);
+            if (ob >= 0) soff = d.srcblk[(long long)tm.src * d.nb + ob];
+          }
+          ok = soff >= 0 && ob >= 0;
         }
-        if (ob < 0) continue;
-      }
-      if (d.bq[2 * ob] + c_site_n[tm.nout] != qout_n || d.bq[2 * ob + 1] + c_site_s[tm.nout] != qout_s) {
-        if (tid == 0) atomicExch(d.err, 1);
-        continue;
-      }
-      const int r0 = d.chunk_off[db.Qout * d.nb + ob];
-      if (r0 < 0) continue;
-      const int rows = d.bdim[ob], cols = d.bdim[ib];
-      const double* __restrict__ S = tm.src >= d.nsrc1 ? d.src_store2 : d.src_store;
-      bool neg;
-      if (d.left) neg = ((c_site_n[tm.nout] - c_site_n[tm.nin]) & 1) && (d.bq[2 * ib] & 1);
-      else neg = par && (c_site_n[tm.nin] & 1);
-      const double w = neg ? -tm.coef : tm.coef;
-      for (int i = 0; i < rows; ++i) {
-        const long long base = (long long)(r0 + i) * db.cols + c0;
-        int j = (int)(((long long)tid - base % nt + nt) % nt);  // first column this thread owns
-        for (; j < cols; j += nt) {
-          double v;
-          if (tm.src < 0) v = (i == j) ? 1.0 : 0.0;
-          else if (!tm.trans) v = S[soff + (long long)i * cols + j];
-          else v = S[soff + (long long)j * rows + i];
-          dst[base + j] += w * v;
+        if (ok && (d.bq[2 * ob] + c_site_n[tm.nout] != qout_n || d.bq[2 * ob + 1] + c_site_s[tm.nout] != qout_s)) {
+          atomicExch(d.err, 1);
+          ok = false;
+        }
+        const int r0 = ok ? d.chunk_off[db.Qout * d.nb + ob] : -1;
+        if (ok && r0 >= 0) {
+          bool neg;
+          if (d.left) neg = ((c_site_n[tm.nout] - c_site_n[tm.nin]) & 1) && (d.bq[2 * ib] & 1);
+          else neg = par && (c_site_n[tm.nin] & 1);
+          r.soff = soff;
+          r.w = neg ? -tm.coef : tm.coef;
+          r.r0 = r0;
+          r.c0 = c0;
+          r.rows = d.bdim[ob];
+          r.cols = d.bdim[ib];
+          r.kind = tm.src < 0 ? 1 : (tm.trans ? 3 : 2);
+          r.store2 = tm.src >= d.nsrc1;
         }
       }
+      __syncthreads();
+      for (int q = 0; q < nhere; ++q) {
+        const RTerm r = rt[q];
+        if (r.kind == 0) continue;
+        const double* __restrict__ S = r.store2 ? d.src_store2 : d.src_store;
+        for (int i = 0; i < r.rows; ++i) {
+          const long long base = (long long)(r.r0 + i) * db.cols + r.c0;
+          int j = (int)(((long long)tid - base % nt + nt) % nt);  // first column this thread owns
+          for (; j < r.cols; j += nt) {
+            double v;
+            if (r.kind == 1) v = (i == j) ? 1.0 : 0.0;
+            else if (r.kind == 2) v = S[r.soff + (long long)i * r.cols + j];
+            else v = S[r.soff + (long long)j * r.rows + i];
+            dst[base + j] += r.w * v;
+          }
+        }
+      }
+      __syncthreads();
     }
   }
 }
@@ -302,8 +330,37 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// |A|_F^2 of every block's work matrix into w[w_off] (scratch until the
+// singular values are written there).
+__global__ void svd_norm_kernel(const SvdBlock* __restrict__ sb, int nb, const double* __restrict__ work,
+                                double* __restrict__ w) {
+  __shared__ double red[32];
+  for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+    const SvdBlock s = sb[b];
+    const long long na = (long long)s.d * s.m;
+    double v = 0.0;
+    for (long long e = threadIdx.x; e < na; e += blockDim.x) v = fma(work[s.a_off + e], work[s.a_off + e], v);
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double x = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+      x = warp_sum(x);
+      if (threadIdx.x == 0) w[s.w_off] = x;
+    }
+    __syncthreads();
+  }
+}
+
+// A pair is rotated while its cosine |a_p . a_q| / (|a_p| |a_q|) exceeds
+// tol = max(1e-15, eps sqrt(m)) (the rounding floor of an m-term dot
+// product), and only if both vectors exceed 1e-15 |A|_F: vectors below that
+// are numerical zeros (a block with more rows than columns has them), whose
+// mutual cosines are rounding noise and would never settle. Sweeps stop when
+// no pair of any block is above its tolerance (at most 30).
 __global__ void svd_jacobi_kernel(const SvdBlock* __restrict__ sb, int nb, int total_pairs, int max_rounds,
-                                  double* __restrict__ work, unsigned long long* __restrict__ off_max) {
+                                  double* __restrict__ work, const double* __restrict__ fro,
+                                  unsigned long long* __restrict__ off_max) {
   namespace cgp = cooperative_groups;
   cgp::grid_group grid = cgp::this_grid();
   const int lane = threadIdx.x & 31;
@@ -340,10 +397,12 @@ __global__ void svd_jacobi_kernel(const SvdBlock* __restrict__ sb, int nb, int t
         al = warp_sum(al);
         be = warp_sum(be);
         ga = warp_sum(ga);
-        if (ga == 0.0 || al == 0.0 || be == 0.0) continue;
+        const double floor2 = 1e-30 * fro[s.w_off];
+        if (ga == 0.0 || al <= floor2 || be <= floor2) continue;
+        const double tol = fmax(1e-15, 2.220446049250313e-16 * sqrt((double)s.m));
         const double cosv = fabs(ga) / sqrt(al * be);
-        local = fmax(local, cosv);
-        if (cosv < 1e-15) continue;
+        local = fmax(local, cosv / tol);
+        if (cosv < tol) continue;
         const double zeta = (be - al) / (2.0 * ga);
         const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
         const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
@@ -367,7 +426,7 @@ __global__ void svd_jacobi_kernel(const SvdBlock* __restrict__ sb, int nb, int t
     const double worst = __longlong_as_double((long long)off_max[slot]);
     if (blockIdx.x == 0 && threadIdx.x == 0) off_max[slot ^ 1] = 0ull;
     grid.sync();
-    if (worst < 1e-15) break;
+    if (worst < 1.0) break;
   }
 }
 
@@ -403,7 +462,7 @@ __global__ void svd_finish_kernel(const SvdBlock* __restrict__ sb, int nb, const
 void launch_blocking(const BlockingDev& d, cudaStream_t st) {
   if (d.ndst <= 0) return;
   const int grid = d.ndst < 152 * 64 ? d.ndst : 152 * 64;
-  blocking_kernel<<<grid, 256, 0, st>>>(d);
+  blocking_kernel<<<grid, BLK_THREADS, 0, st>>>(d);
 }
 
 void launch_opcomb(const double* src, const long long* xoff, const double* coef, const CombClass* cls, int ncls,
@@ -451,7 +510,10 @@ void launch_svd_blocks(const double* psi, const SvdBlock* sb, int nb, int total_
     int grid = n_sm * per_sm;
     unsigned long long* off_max = reinterpret_cast<unsigned long long*>(work);  // first 2 words of work
     cudaMemsetAsync(off_max, 0, 2 * sizeof(unsigned long long), st);
-    void* args[] = {(void*)&sb, (void*)&nb, (void*)&total_pairs, (void*)&max_rounds, (void*)&work, (void*)&off_max};
+    svd_norm_kernel<<<nb < 65535 ? nb : 65535, 256, 0, st>>>(sb, nb, work, w);
+    const double* fro = w;
+    void* args[] = {(void*)&sb,   (void*)&nb,  (void*)&total_pairs, (void*)&max_rounds,
+                    (void*)&work, (void*)&fro, (void*)&off_max};
     const cudaError_t e = cudaLaunchCooperativeKernel((void*)svd_jacobi_kernel, dim3(grid), dim3(256), args, 0, st);
     if (e != cudaSuccess) return;  // the caller's cudaGetLastError reports it
   }
