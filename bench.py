@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--no-sweeps", action="store_true")
     return ap.parse_args()
 
 
@@ -223,6 +224,22 @@ def serve_section(n_req, device):
             "rate_per_s": rate, "rejected": len(rej) + len(rej2)}
 
 
+def sweeps_section(device):
+    """Two sweeps of a FeMoco-shaped problem with the NC partition everywhere
+    and with the mixed NC/CN partition (Sec. III.A): wall time (initial blocks
+    included), energies, converged steps."""
+    from paper_2103_09976_gb300 import sweeps
+    out = {"workload": "K=36 spatial orbitals, N=53, 2Sz=1, FeMoco-shaped integrals (seed 2), M 250 then 250; "
+                       "bf16x3 sigma, FP64 Davidson (tol 1e-6, at most 60 products, carried start vectors), "
+                       "FP64 decimation and transformation; mixed cut after 18 orbitals"}
+    for name, cut in (("nc", -1), ("mixed_nc_cn", 18)):
+        r = sweeps.run(36, [250, 250], cut, "BF16X3", device=device)
+        out[name] = {"s": r["build_s"] + r["sweeps_s"], "energies": r["energies"], "converged": r["converged"],
+                     "steps": r["steps"], "phase_s": r["phase_s"]}
+    out["nc_over_mixed"] = out["nc"]["s"] / out["mixed_nc_cn"]["s"]
+    return out
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -366,6 +383,11 @@ def main():
            "serving": serving,
            "clocks": clocks,
            "sigma_info": info}
+    if rank == 0 and world == 1 and not args.no_sweeps:
+        try:
+            out["sweeps"] = sweeps_section(local)
+        except Exception as ex:  # reported, not fatal: the headline above is complete
+            out["sweeps"] = {"error": str(ex)[:300]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.M)
     if rank == 0:
