@@ -87,8 +87,8 @@ struct DevBuf {
   }
   template <class T>
   T* as() const { return reinterpret_cast<T*>(p); }
-  template <class T>
-  void upload(const std::vector<T>& v, cudaStream_t s) {
+  template <class T, class A>
+  void upload(const std::vector<T, A>& v, cudaStream_t s) {
     alloc(v.size() * sizeof(T));
     if (!v.empty())
       DMRG_CUDA(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));

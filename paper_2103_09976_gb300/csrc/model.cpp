@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <thread>
 
 namespace dmrg {
 
@@ -199,7 +200,22 @@ void build_tasks(const std::vector<PsiBlock>& blocks, const OpSet& L, const OpSe
   // output block index by left sector
   std::vector<int> blk_of_qL(L.basis.size(), -1);
   for (size_t b = 0; b < blocks.size(); ++b) blk_of_qL[blocks[b].qL] = (int)b;
-  std::vector<std::vector<Task>> per_out(blocks.size());
+  // first stored-block index of every operator (left operators, then right)
+  std::vector<int> first_L(L.ops.size()), first_R(R.ops.size());
+  int nblk = 0;
+  for (size_t k = 0; k < L.ops.size(); ++k) {
+    first_L[k] = nblk;
+    nblk += (int)L.ops[k].blocks.size();
+  }
+  for (size_t k = 0; k < R.ops.size(); ++k) {
+    first_R[k] = nblk;
+    nblk += (int)R.ops[k].blocks.size();
+  }
+  struct TaskB {
+    Task k;
+    int a, b;
+  };
+  std::vector<std::vector<TaskB>> per_out(blocks.size());
   double flops = 0, bytes = 0;
   for (const Term& t : terms) {
     for (size_t b = 0; b < blocks.size(); ++b) {
@@ -224,7 +240,9 @@ void build_tasks(const std::vector<PsiBlock>& blocks, const OpSet& L, const OpSe
       k.in_blk = (int)b;
       k.flags = (t.tL ? 1 : 0) | (t.tR ? 2 : 0);
       k.scale = t.coef * sign;
-      per_out[ob].push_back(k);
+      const int ia = bl ? first_L[t.opL] + (int)(bl - L.ops[t.opL].blocks.data()) : -1;
+      const int ib = br ? first_R[t.opR] + (int)(br - R.ops[t.opR].blocks.data()) : -1;
+      per_out[ob].push_back({k, ia, ib});
       double m = in.mL, nn = in.mR, mo = blocks[ob].mL, no = blocks[ob].mR;
       if (!bl)
         flops += 2 * m * nn * no;
@@ -243,7 +261,16 @@ void build_tasks(const std::vector<PsiBlock>& blocks, const OpSet& L, const OpSe
   for (size_t b = 0; b < blocks.size(); ++b)
     wl.out_start[b + 1] = wl.out_start[b] + (int)per_out[b].size();
   wl.tasks.reserve(wl.out_start.back());
-  for (auto& v : per_out) wl.tasks.insert(wl.tasks.end(), v.begin(), v.end());
+  wl.task_ablk.clear();
+  wl.task_bblk.clear();
+  wl.task_ablk.reserve(wl.out_start.back());
+  wl.task_bblk.reserve(wl.out_start.back());
+  for (auto& v : per_out)
+    for (const TaskB& x : v) {
+      wl.tasks.push_back(x.k);
+      wl.task_ablk.push_back(x.a);
+      wl.task_bblk.push_back(x.b);
+    }
   wl.items.clear();
   wl.groups.clear();
   wl.schedule.clear();
@@ -389,13 +416,20 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
     plan.psi.push_back(p);
   }
   plan.psi_tiles = pt + 64;
-  // base task records (identity factors made explicit)
+  // base task records (identity factors made explicit); build_tasks names
+  // each task's stored blocks by index, else they are looked up by offset
+  const bool have_idx = wl.task_ablk.size() == wl.tasks.size() && wl.task_bblk.size() == wl.tasks.size();
+  auto stored = [&](long long off, int idx) -> const TcBlock& {
+    if (!have_idx) return block_at(off);
+    if (idx < 0 || idx >= (int)offs.size() || offs[idx] != off) throw Error(1, "internal: task block index");
+    return plan.opblocks[idx];
+  };
   std::vector<TcTask> base(wl.tasks.size());
   for (size_t t = 0; t < wl.tasks.size(); ++t) {
     const Task& k = wl.tasks[t];
     const PsiBlock& in = blocks[k.in_blk];
-    TcBlock a = k.aoff >= 0 ? block_at(k.aoff) : plan.identL[in.qL];
-    TcBlock b = k.boff >= 0 ? block_at(k.boff) : plan.identR[in.qR];
+    TcBlock a = k.aoff >= 0 ? stored(k.aoff, have_idx ? wl.task_ablk[t] : -1) : plan.identL[in.qL];
+    TcBlock b = k.boff >= 0 ? stored(k.boff, have_idx ? wl.task_bblk[t] : -1) : plan.identR[in.qR];
     TcTask x{};
     x.a_tile = a.tile;
     x.aR8 = a.R8;
@@ -411,9 +445,11 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
   // order tasks of each output block by (right transposed, input block, left
   // transposed): packed units then share the layout of their second product
   // and consecutive tasks share psi tiles
+  std::vector<int> idx;
+  std::vector<TcTask> tmp;
   for (size_t b = 0; b < blocks.size(); ++b) {
     const int t0 = wl.out_start[b], t1 = wl.out_start[b + 1];
-    std::vector<int> idx(t1 - t0);
+    idx.resize(t1 - t0);
     std::iota(idx.begin(), idx.end(), t0);
     std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
       const int kx = ((base[x].flags >> 1) & 1), ky = ((base[y].flags >> 1) & 1);
@@ -421,7 +457,7 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
       if (base[x].in_blk != base[y].in_blk) return base[x].in_blk < base[y].in_blk;
       return (base[x].flags & 1) < (base[y].flags & 1);
     });
-    std::vector<TcTask> tmp;
+    tmp.clear();
     for (int i : idx) tmp.push_back(base[i]);
     std::copy(tmp.begin(), tmp.end(), base.begin() + t0);
   }
@@ -438,6 +474,8 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
   }
   const double target = total / std::max(1, want_items);
   std::vector<double> icost;
+  plan.tasks.reserve(base.size());
+  plan.units.reserve(base.size());
   for (size_t b = 0; b < blocks.size(); ++b) {
     const PsiBlock& ob = blocks[b];
     const int t0 = wl.out_start[b], t1 = wl.out_start[b + 1];
@@ -528,64 +566,83 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
   std::iota(plan.schedule.begin(), plan.schedule.end(), 0);
   std::stable_sort(plan.schedule.begin(), plan.schedule.end(),
                    [&](int a, int b) { return icost[a] > icost[b]; });
-  // records
+  // records: one per unit (one REC_ZERO per item without units), written in
+  // item order; items are independent, so ranges of them fill in parallel
   static_assert(sizeof(TcTaskRec) == 64 && sizeof(TcRec) == 304, "record layout");
-  plan.recs.clear();
-  size_t nrec = 0;
-  for (const TcItem& it : plan.items) nrec += std::max(1, it.u_end - it.u_begin);
-  plan.recs.reserve(nrec);
   plan.item_rec.assign(plan.items.size() + 1, 0);
-  for (size_t i = 0; i < plan.items.size(); ++i) {
-    const TcItem& it = plan.items[i];
-    plan.item_rec[i] = (int)plan.recs.size();
-    auto header = [&](TcRec& r) {
-      r.r0 = it.r0;
-      r.nrows = it.nrows;
-      r.c0 = it.c0;
-      r.ncols = it.ncols;
-      r.slot = it.slot;
-    };
-    if (it.u_begin == it.u_end) {
-      TcRec r{};
-      r.flags = REC_ZERO;
-      header(r);
-      plan.recs.push_back(r);
-      continue;
-    }
-    for (int u = it.u_begin; u < it.u_end; ++u) {
-      const TcUnit& un = plan.units[u];
-      TcRec r{};
-      r.flags = un.flags;
-      r.ntask = un.t_end - un.t_begin;
-      r.pass = un.pass;
-      r.width = un.width;
-      r.pad[0] = un.width / 8;  // K groups of the packed second product
-      header(r);
-      for (int k = 0; k < r.ntask; ++k) {
-        const TcTask& t = plan.tasks[un.t_begin + k];
-        const TcPsiBlock& p = plan.psi[t.in_blk];
-        TcTaskRec& x = r.t[k];
-        x.a_tile = t.a_tile;
-        x.b_tile = t.b_tile;
-        x.p_tile = p.tile;
-        x.aR8 = (short)t.aR8;
-        x.aC8 = (short)t.aC8;
-        x.bR8 = (short)t.bR8;
-        x.bC8 = (short)t.bC8;
-        x.pR8 = (short)p.R8;
-        x.pC8 = (short)p.C8;
-        x.xcol = (short)t.xcol;
-        x.k1a = (short)t.k1a;
-        x.k1b = (short)t.k1b;
-        x.k2 = (short)t.k2;
-        x.pn = p.n;
-        x.flags = t.flags;
-        x.scale = t.scale;
+  for (size_t i = 0; i < plan.items.size(); ++i)
+    plan.item_rec[i + 1] = plan.item_rec[i] + std::max(1, plan.items[i].u_end - plan.items[i].u_begin);
+  plan.recs.clear();
+  plan.recs.resize((size_t)plan.item_rec.back());  // uninitialized: every record is written below
+  auto fill = [&](size_t i0, size_t i1) {
+    for (size_t i = i0; i < i1; ++i) {
+      const TcItem& it = plan.items[i];
+      TcRec* out = plan.recs.data() + plan.item_rec[i];
+      auto header = [&](TcRec& r) {
+        r.r0 = it.r0;
+        r.nrows = it.nrows;
+        r.c0 = it.c0;
+        r.ncols = it.ncols;
+        r.slot = it.slot;
+      };
+      if (it.u_begin == it.u_end) {
+        *out = TcRec{};
+        out->flags = REC_ZERO;
+        header(*out);
+        continue;
       }
-      plan.recs.push_back(r);
+      for (int u = it.u_begin; u < it.u_end; ++u, ++out) {
+        const TcUnit& un = plan.units[u];
+        TcRec& r = *out;
+        r = TcRec{};
+        r.flags = un.flags;
+        r.ntask = un.t_end - un.t_begin;
+        r.pass = un.pass;
+        r.width = un.width;
+        r.pad[0] = un.width / 8;  // K groups of the packed second product
+        header(r);
+        for (int k = 0; k < r.ntask; ++k) {
+          const TcTask& t = plan.tasks[un.t_begin + k];
+          const TcPsiBlock& p = plan.psi[t.in_blk];
+          TcTaskRec& x = r.t[k];
+          x.a_tile = t.a_tile;
+          x.b_tile = t.b_tile;
+          x.p_tile = p.tile;
+          x.aR8 = (short)t.aR8;
+          x.aC8 = (short)t.aC8;
+          x.bR8 = (short)t.bR8;
+          x.bC8 = (short)t.bC8;
+          x.pR8 = (short)p.R8;
+          x.pC8 = (short)p.C8;
+          x.xcol = (short)t.xcol;
+          x.k1a = (short)t.k1a;
+          x.k1b = (short)t.k1b;
+          x.k2 = (short)t.k2;
+          x.pn = p.n;
+          x.flags = t.flags;
+          x.scale = t.scale;
+        }
+      }
     }
+  };
+  const size_t nit = plan.items.size();
+  const int nth = (int)std::min<size_t>(8, std::max<size_t>(1, std::min<size_t>(std::thread::hardware_concurrency(),
+                                                                                  plan.recs.size() / 65536)));
+  if (nth <= 1) {
+    fill(0, nit);
+  } else {  // item ranges of about equal record counts
+    std::vector<std::thread> pool;
+    size_t i0 = 0;
+    for (int th = 0; th < nth; ++th) {
+      const long long goal = (long long)plan.recs.size() * (th + 1) / nth;
+      size_t i1 = th == nth - 1 ? nit : (size_t)(std::lower_bound(plan.item_rec.begin(), plan.item_rec.end() - 1,
+                                                                  (int)goal) - plan.item_rec.begin());
+      i1 = std::max(i1, i0);
+      pool.emplace_back(fill, i0, i1);
+      i0 = i1;
+    }
+    for (auto& t : pool) t.join();
   }
-  plan.item_rec.back() = (int)plan.recs.size();
 }
 
 }  // namespace dmrg

@@ -9,6 +9,8 @@
 
 #include <cstdint>
 #include <map>
+#include <memory>
+#include <utility>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -165,6 +167,9 @@ struct WorkList {
   long long scratch_elems = 0;
   double flops = 0;          // algorithmic (min order)
   double bytes_ops = 0;      // operator bytes read (FP64), each product reading its two blocks
+  // host only, parallel to tasks: index of each task's left / right stored
+  // block in store order (left operators' blocks, then right), -1 = identity
+  std::vector<int> task_ablk, task_bblk;
 };
 
 struct TileShape {
@@ -259,6 +264,27 @@ struct TcRec {                // 304 bytes
   TcTaskRec t[4];
 };
 
+// Allocator whose resize() leaves elements uninitialized (records are
+// written in parallel, each by the thread that fills its item).
+template <class T>
+struct NoInit : std::allocator<T> {
+  template <class U>
+  struct rebind {
+    using other = NoInit<U>;
+  };
+  NoInit() = default;
+  template <class U>
+  NoInit(const NoInit<U>&) noexcept {}
+  template <class U>
+  void construct(U* p) noexcept {
+    ::new (static_cast<void*>(p)) U;
+  }
+  template <class U, class... A>
+  void construct(U* p, A&&... a) {
+    ::new (static_cast<void*>(p)) U(std::forward<A>(a)...);
+  }
+};
+
 struct TcPlan {
   std::vector<TcBlock> opblocks;        // tiles of every stored block, store order
   std::vector<long long> op_first;      // index of the first TcBlock of each op (L ops then R ops)
@@ -272,7 +298,7 @@ struct TcPlan {
   std::vector<int> schedule;
   std::vector<Group> groups;
   long long scratch_elems = 0;
-  std::vector<TcRec> recs;              // one per unit (or one REC_ZERO per empty item)
+  std::vector<TcRec, NoInit<TcRec>> recs;  // one per unit (or one REC_ZERO per empty item)
   std::vector<int> item_rec;            // records of item i: [item_rec[i], item_rec[i+1])
 };
 
