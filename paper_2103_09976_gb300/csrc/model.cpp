@@ -215,62 +215,91 @@ void build_tasks(const std::vector<PsiBlock>& blocks, const OpSet& L, const OpSe
     Task k;
     int a, b;
   };
-  std::vector<std::vector<TaskB>> per_out(blocks.size());
-  double flops = 0, bytes = 0;
-  for (const Term& t : terms) {
-    for (size_t b = 0; b < blocks.size(); ++b) {
-      const PsiBlock& in = blocks[b];
-      int qLo = in.qL, qRo = in.qR;
-      const OpBlock* bl = nullptr;
-      const OpBlock* br = nullptr;
-      if (t.opL >= 0) {
-        qLo = resolve(L.ops[t.opL], L.basis, in.qL, t.tL, &bl);
-        if (qLo < 0) continue;
+  // terms are split into contiguous ranges handled by up to 8 threads; each
+  // range keeps its tasks per output block, and the ranges are joined in
+  // term order, so the list is the same as a sequential pass over the terms
+  const size_t nterm = terms.size();
+  const int nth = (int)std::min<size_t>(8, std::max<size_t>(1, std::min<size_t>(std::thread::hardware_concurrency(),
+                                                                                  nterm * blocks.size() / 200000)));
+  std::vector<std::vector<std::vector<TaskB>>> per_out(nth, std::vector<std::vector<TaskB>>(blocks.size()));
+  std::vector<double> th_flops(nth, 0.0), th_bytes(nth, 0.0);
+  auto work = [&](int th) {
+    const size_t t_lo = nterm * th / nth, t_hi = nterm * (th + 1) / nth;
+    double flops = 0, bytes = 0;
+    for (size_t ti = t_lo; ti < t_hi; ++ti) {
+      const Term& t = terms[ti];
+      for (size_t b = 0; b < blocks.size(); ++b) {
+        const PsiBlock& in = blocks[b];
+        int qLo = in.qL, qRo = in.qR;
+        const OpBlock* bl = nullptr;
+        const OpBlock* br = nullptr;
+        if (t.opL >= 0) {
+          qLo = resolve(L.ops[t.opL], L.basis, in.qL, t.tL, &bl);
+          if (qLo < 0) continue;
+        }
+        if (t.opR >= 0) {
+          qRo = resolve(R.ops[t.opR], R.basis, in.qR, t.tR, &br);
+          if (qRo < 0) continue;
+        }
+        int ob = blk_of_qL[qLo];
+        if (ob < 0 || blocks[ob].qR != qRo) continue;
+        double sign = (t.parR && (L.basis.q[in.qL].n & 1)) ? -1.0 : 1.0;
+        Task k;
+        k.aoff = bl ? bl->off : -1;
+        k.boff = br ? br->off : -1;
+        k.in_blk = (int)b;
+        k.flags = (t.tL ? 1 : 0) | (t.tR ? 2 : 0);
+        k.scale = t.coef * sign;
+        const int ia = bl ? first_L[t.opL] + (int)(bl - L.ops[t.opL].blocks.data()) : -1;
+        const int ib = br ? first_R[t.opR] + (int)(br - R.ops[t.opR].blocks.data()) : -1;
+        per_out[th][ob].push_back({k, ia, ib});
+        double m = in.mL, nn = in.mR, mo = blocks[ob].mL, no = blocks[ob].mR;
+        if (!bl)
+          flops += 2 * m * nn * no;
+        else if (!br)
+          flops += 2 * mo * m * nn;
+        else
+          flops += std::min(2 * mo * m * nn + 2 * mo * nn * no, 2 * m * nn * no + 2 * mo * m * no);
+        if (bl) bytes += 8.0 * mo * m;
+        if (br) bytes += 8.0 * no * nn;
       }
-      if (t.opR >= 0) {
-        qRo = resolve(R.ops[t.opR], R.basis, in.qR, t.tR, &br);
-        if (qRo < 0) continue;
-      }
-      int ob = blk_of_qL[qLo];
-      if (ob < 0 || blocks[ob].qR != qRo) continue;
-      double sign = (t.parR && (L.basis.q[in.qL].n & 1)) ? -1.0 : 1.0;
-      Task k;
-      k.aoff = bl ? bl->off : -1;
-      k.boff = br ? br->off : -1;
-      k.in_blk = (int)b;
-      k.flags = (t.tL ? 1 : 0) | (t.tR ? 2 : 0);
-      k.scale = t.coef * sign;
-      const int ia = bl ? first_L[t.opL] + (int)(bl - L.ops[t.opL].blocks.data()) : -1;
-      const int ib = br ? first_R[t.opR] + (int)(br - R.ops[t.opR].blocks.data()) : -1;
-      per_out[ob].push_back({k, ia, ib});
-      double m = in.mL, nn = in.mR, mo = blocks[ob].mL, no = blocks[ob].mR;
-      if (!bl)
-        flops += 2 * m * nn * no;
-      else if (!br)
-        flops += 2 * mo * m * nn;
-      else
-        flops += std::min(2 * mo * m * nn + 2 * mo * nn * no, 2 * m * nn * no + 2 * mo * m * no);
-      if (bl) bytes += 8.0 * mo * m;
-      if (br) bytes += 8.0 * no * nn;
     }
+    th_flops[th] = flops;
+    th_bytes[th] = bytes;
+  };
+  if (nth == 1) {
+    work(0);
+  } else {
+    std::vector<std::thread> pool;
+    for (int th = 0; th < nth; ++th) pool.emplace_back(work, th);
+    for (auto& x : pool) x.join();
+  }
+  double flops = 0, bytes = 0;
+  for (int th = 0; th < nth; ++th) {
+    flops += th_flops[th];
+    bytes += th_bytes[th];
   }
   wl.tasks.clear();
   wl.flops = flops;
   wl.bytes_ops = bytes;
   wl.out_start.assign(blocks.size() + 1, 0);
-  for (size_t b = 0; b < blocks.size(); ++b)
-    wl.out_start[b + 1] = wl.out_start[b] + (int)per_out[b].size();
+  for (size_t b = 0; b < blocks.size(); ++b) {
+    size_t nb = 0;
+    for (int th = 0; th < nth; ++th) nb += per_out[th][b].size();
+    wl.out_start[b + 1] = wl.out_start[b] + (int)nb;
+  }
   wl.tasks.reserve(wl.out_start.back());
   wl.task_ablk.clear();
   wl.task_bblk.clear();
   wl.task_ablk.reserve(wl.out_start.back());
   wl.task_bblk.reserve(wl.out_start.back());
-  for (auto& v : per_out)
-    for (const TaskB& x : v) {
-      wl.tasks.push_back(x.k);
-      wl.task_ablk.push_back(x.a);
-      wl.task_bblk.push_back(x.b);
-    }
+  for (size_t b = 0; b < blocks.size(); ++b)
+    for (int th = 0; th < nth; ++th)
+      for (const TaskB& x : per_out[th][b]) {
+        wl.tasks.push_back(x.k);
+        wl.task_ablk.push_back(x.a);
+        wl.task_bblk.push_back(x.b);
+      }
   wl.items.clear();
   wl.groups.clear();
   wl.schedule.clear();
