@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <functional>
 #include <numeric>
 #include <thread>
 
@@ -422,10 +423,9 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
       }
     }
   if (!std::is_sorted(offs.begin(), offs.end())) throw Error(1, "internal: operator blocks out of store order");
-  auto block_at = [&](long long off) -> const TcBlock& {
+  auto find_off = [&](long long off) {  // index of the stored block at element offset off, or -1
     const auto it = std::lower_bound(offs.begin(), offs.end(), off);
-    if (it == offs.end() || *it != off) throw Error(1, "internal: task names no stored block");
-    return plan.opblocks[it - offs.begin()];
+    return (it == offs.end() || *it != off) ? -1 : (int)(it - offs.begin());
   };
   for (int i = 0; i < L.basis.size(); ++i) {
     TcBlock t{tile, ceil8(L.basis.dim[i]), ceil8(L.basis.dim[i])};
@@ -448,48 +448,84 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
   // base task records (identity factors made explicit); build_tasks names
   // each task's stored blocks by index, else they are looked up by offset
   const bool have_idx = wl.task_ablk.size() == wl.tasks.size() && wl.task_bblk.size() == wl.tasks.size();
-  auto stored = [&](long long off, int idx) -> const TcBlock& {
-    if (!have_idx) return block_at(off);
-    if (idx < 0 || idx >= (int)offs.size() || offs[idx] != off) throw Error(1, "internal: task block index");
-    return plan.opblocks[idx];
+  // Output blocks are independent: contiguous block ranges of about equal
+  // task counts are handled by up to 8 threads (base records, per-block task
+  // order, items and units into parts with local indices); the parts are
+  // joined in block order with their task / unit / item / scratch offsets,
+  // so the plan is the same as one pass over the blocks.
+  const size_t nblk = blocks.size();
+  const int nparts = (int)std::min<size_t>(8, std::max<size_t>(1, std::min<size_t>(std::thread::hardware_concurrency(),
+                                                                                     wl.tasks.size() / 100000)));
+  std::vector<size_t> bstart(nparts + 1, nblk);
+  bstart[0] = 0;
+  for (int j = 1; j < nparts; ++j) {
+    const long long goal = (long long)wl.tasks.size() * j / nparts;
+    bstart[j] = (size_t)(std::lower_bound(wl.out_start.begin(), wl.out_start.begin() + nblk, (int)goal) -
+                         wl.out_start.begin());
+    bstart[j] = std::max(bstart[j], bstart[j - 1]);
+  }
+  auto in_parallel = [&](const std::function<void(int)>& fn) {
+    if (nparts == 1) {
+      fn(0);
+      return;
+    }
+    std::vector<std::thread> pool;
+    for (int j = 0; j < nparts; ++j) pool.emplace_back(fn, j);
+    for (auto& x : pool) x.join();
   };
   std::vector<TcTask> base(wl.tasks.size());
-  for (size_t t = 0; t < wl.tasks.size(); ++t) {
-    const Task& k = wl.tasks[t];
-    const PsiBlock& in = blocks[k.in_blk];
-    TcBlock a = k.aoff >= 0 ? stored(k.aoff, have_idx ? wl.task_ablk[t] : -1) : plan.identL[in.qL];
-    TcBlock b = k.boff >= 0 ? stored(k.boff, have_idx ? wl.task_bblk[t] : -1) : plan.identR[in.qR];
-    TcTask x{};
-    x.a_tile = a.tile;
-    x.aR8 = a.R8;
-    x.aC8 = a.C8;
-    x.b_tile = b.tile;
-    x.bR8 = b.R8;
-    x.bC8 = b.C8;
-    x.in_blk = k.in_blk;
-    x.flags = (k.aoff >= 0 ? (k.flags & 1) : 0) | (k.boff >= 0 ? (k.flags & 2) : 0);
-    x.scale = (float)k.scale;
-    base[t] = x;
-  }
-  // order tasks of each output block by (right transposed, input block, left
-  // transposed): packed units then share the layout of their second product
-  // and consecutive tasks share psi tiles
-  std::vector<int> idx;
-  std::vector<TcTask> tmp;
-  for (size_t b = 0; b < blocks.size(); ++b) {
-    const int t0 = wl.out_start[b], t1 = wl.out_start[b + 1];
-    idx.resize(t1 - t0);
-    std::iota(idx.begin(), idx.end(), t0);
-    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
-      const int kx = ((base[x].flags >> 1) & 1), ky = ((base[y].flags >> 1) & 1);
-      if (kx != ky) return kx < ky;
-      if (base[x].in_blk != base[y].in_blk) return base[x].in_blk < base[y].in_blk;
-      return (base[x].flags & 1) < (base[y].flags & 1);
-    });
-    tmp.clear();
-    for (int i : idx) tmp.push_back(base[i]);
-    std::copy(tmp.begin(), tmp.end(), base.begin() + t0);
-  }
+  std::vector<char> bad(nparts, 0);
+  in_parallel([&](int j) {
+    for (int t = wl.out_start[bstart[j]]; t < wl.out_start[bstart[j + 1]]; ++t) {
+      const Task& k = wl.tasks[t];
+      const PsiBlock& in = blocks[k.in_blk];
+      TcBlock a = plan.identL[in.qL], b = plan.identR[in.qR];
+      if (k.aoff >= 0) {
+        const int i = have_idx ? wl.task_ablk[t] : -1;
+        const int f = have_idx ? i : find_off(k.aoff);
+        if (f < 0 || f >= (int)offs.size() || offs[f] != k.aoff) bad[j] = 1;
+        else a = plan.opblocks[f];
+      }
+      if (k.boff >= 0) {
+        const int i = have_idx ? wl.task_bblk[t] : -1;
+        const int f = have_idx ? i : find_off(k.boff);
+        if (f < 0 || f >= (int)offs.size() || offs[f] != k.boff) bad[j] = 1;
+        else b = plan.opblocks[f];
+      }
+      TcTask x{};
+      x.a_tile = a.tile;
+      x.aR8 = a.R8;
+      x.aC8 = a.C8;
+      x.b_tile = b.tile;
+      x.bR8 = b.R8;
+      x.bC8 = b.C8;
+      x.in_blk = k.in_blk;
+      x.flags = (k.aoff >= 0 ? (k.flags & 1) : 0) | (k.boff >= 0 ? (k.flags & 2) : 0);
+      x.scale = (float)k.scale;
+      base[t] = x;
+    }
+    // order tasks of each output block by (right transposed, input block, left
+    // transposed): packed units then share the layout of their second product
+    // and consecutive tasks share psi tiles
+    std::vector<int> idx;
+    std::vector<TcTask> tmp;
+    for (size_t ob = bstart[j]; ob < bstart[j + 1]; ++ob) {
+      const int t0 = wl.out_start[ob], t1 = wl.out_start[ob + 1];
+      idx.resize(t1 - t0);
+      std::iota(idx.begin(), idx.end(), t0);
+      std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+        const int kx = ((base[x].flags >> 1) & 1), ky = ((base[y].flags >> 1) & 1);
+        if (kx != ky) return kx < ky;
+        if (base[x].in_blk != base[y].in_blk) return base[x].in_blk < base[y].in_blk;
+        return (base[x].flags & 1) < (base[y].flags & 1);
+      });
+      tmp.clear();
+      for (int i : idx) tmp.push_back(base[i]);
+      std::copy(tmp.begin(), tmp.end(), base.begin() + t0);
+    }
+  });
+  for (char x : bad)
+    if (x) throw Error(1, "internal: a task names no stored block");
   // MMA work of a task on one 128 x 128 tile (rows padded to 128)
   auto cost = [&](const TcTask& k) {
     const TcPsiBlock& in = plan.psi[k.in_blk];
@@ -502,30 +538,35 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
     for (int t = wl.out_start[b]; t < wl.out_start[b + 1]; ++t) total += ntile * cost(base[t]);
   }
   const double target = total / std::max(1, want_items);
-  std::vector<double> icost;
-  plan.tasks.reserve(base.size());
-  plan.units.reserve(base.size());
-  for (size_t b = 0; b < blocks.size(); ++b) {
+  struct Part {
+    std::vector<TcTask> tasks;
+    std::vector<TcUnit> units;
+    std::vector<TcItem> items;
+    std::vector<Group> groups;
+    std::vector<double> icost;
+    long long scratch = 0;
+  };
+  auto plan_block = [&](size_t b, Part& P) {
     const PsiBlock& ob = blocks[b];
     const int t0 = wl.out_start[b], t1 = wl.out_start[b + 1];
     for (int r0 = 0; r0 < ob.mL; r0 += 128)
       for (int c0 = 0; c0 < ob.mR; c0 += 128) {
         const int nr = std::min(128, ob.mL - r0), nc = std::min(128, ob.mR - c0);
-        Group g{(int)b, r0, nr, c0, nc, (int)plan.items.size(), 0, 0};
+        Group g{(int)b, r0, nr, c0, nc, (int)P.items.size(), 0, 0};
         int t = t0;
         do {  // one item per iteration (at least one, even with no tasks)
-          TcItem it{(int)b, r0, nr, c0, nc, (int)plan.units.size(), 0, 0, plan.scratch_elems};
-          const int item_idx = (int)plan.items.size();
+          TcItem it{(int)b, r0, nr, c0, nc, (int)P.units.size(), 0, 0, P.scratch};
+          const int item_idx = (int)P.items.size();
           double acc = 0;
-          int seg = 0, seg_first_unit = (int)plan.units.size();
+          int seg = 0, seg_first_unit = (int)P.units.size();
           bool first_seg = true;
           auto end_segment = [&]() {
-            if (plan.units.size() > (size_t)seg_first_unit) {
-              plan.units.back().flags |= UNIT_ENDS_SEGMENT | (first_seg ? UNIT_FIRST_SEGMENT : 0);
+            if (P.units.size() > (size_t)seg_first_unit) {
+              P.units.back().flags |= UNIT_ENDS_SEGMENT | (first_seg ? UNIT_FIRST_SEGMENT : 0);
               first_seg = false;
             }
             seg = 0;
-            seg_first_unit = (int)plan.units.size();
+            seg_first_unit = (int)P.units.size();
           };
           while (t < t1 && (acc == 0 || acc + cost(base[t]) <= target)) {
             TcTask k = base[t];
@@ -534,7 +575,7 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
             if (k1 > 0 && k1 <= 128 && k2 <= 128) {
               // packed unit: greedily add following small tasks with the same
               // right-operand orientation; tasks on the same psi block share its tiles
-              TcUnit u{item_idx, (int)plan.tasks.size(), 0, 0, UNIT_PACKED, 0, {0, 0}};
+              TcUnit u{item_idx, (int)P.tasks.size(), 0, 0, UNIT_PACKED, 0, {0, 0}};
               int w = 0, s1 = 0, last_in = -1, last_k1b = 0;
               const int tB0 = (k.flags >> 1) & 1;
               while (t < t1 && seg < seg_tasks && (acc == 0 || acc + cost(base[t]) <= target)) {
@@ -561,20 +602,20 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
                 last_in = x.in_blk;
                 w += n16;
                 s1 += a1;
-                plan.tasks.push_back(x);
+                P.tasks.push_back(x);
                 acc += cost(x);
                 ++t;
                 ++seg;
               }
-              u.t_end = (int)plan.tasks.size();
+              u.t_end = (int)P.tasks.size();
               u.width = w;
-              plan.units.push_back(u);
+              P.units.push_back(u);
             } else {
-              plan.tasks.push_back(k);
+              P.tasks.push_back(k);
               const int npass = (ib.n + 127) / 128;
               for (int p = 0; p < npass; ++p)
-                plan.units.push_back({item_idx, (int)plan.tasks.size() - 1, (int)plan.tasks.size(), p, 0,
-                                      std::min(128, ib.n - 128 * p), {0, 0}});
+                P.units.push_back({item_idx, (int)P.tasks.size() - 1, (int)P.tasks.size(), p, 0,
+                                   std::min(128, ib.n - 128 * p), {0, 0}});
               acc += cost(k);
               ++t;
               ++seg;
@@ -582,14 +623,62 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
             if (seg >= seg_tasks) end_segment();
           }
           end_segment();
-          it.u_end = (int)plan.units.size();
-          plan.items.push_back(it);
-          plan.scratch_elems += (long long)nr * nc;
-          icost.push_back(acc);
+          it.u_end = (int)P.units.size();
+          P.items.push_back(it);
+          P.scratch += (long long)nr * nc;
+          P.icost.push_back(acc);
         } while (t < t1);
-        g.i_end = (int)plan.items.size();
-        plan.groups.push_back(g);
+        g.i_end = (int)P.items.size();
+        P.groups.push_back(g);
       }
+  };
+  std::vector<Part> parts(nparts);
+  in_parallel([&](int j) {
+    parts[j].tasks.reserve(wl.out_start[bstart[j + 1]] - wl.out_start[bstart[j]]);
+    for (size_t b = bstart[j]; b < bstart[j + 1]; ++b) plan_block(b, parts[j]);
+  });
+  std::vector<double> icost;
+  {
+    std::vector<size_t> T(nparts + 1, 0), U(nparts + 1, 0), I(nparts + 1, 0), G(nparts + 1, 0);
+    std::vector<long long> S(nparts + 1, 0);
+    for (int j = 0; j < nparts; ++j) {
+      T[j + 1] = T[j] + parts[j].tasks.size();
+      U[j + 1] = U[j] + parts[j].units.size();
+      I[j + 1] = I[j] + parts[j].items.size();
+      G[j + 1] = G[j] + parts[j].groups.size();
+      S[j + 1] = S[j] + parts[j].scratch;
+    }
+    plan.tasks.resize(T[nparts]);
+    plan.units.resize(U[nparts]);
+    plan.items.resize(I[nparts]);
+    plan.groups.resize(G[nparts]);
+    icost.resize(I[nparts]);
+    plan.scratch_elems = S[nparts];
+    in_parallel([&](int j) {
+      const Part& P = parts[j];
+      std::copy(P.tasks.begin(), P.tasks.end(), plan.tasks.begin() + T[j]);
+      for (size_t k = 0; k < P.units.size(); ++k) {
+        TcUnit u = P.units[k];
+        u.item += (int)I[j];
+        u.t_begin += (int)T[j];
+        u.t_end += (int)T[j];
+        plan.units[U[j] + k] = u;
+      }
+      for (size_t k = 0; k < P.items.size(); ++k) {
+        TcItem it = P.items[k];
+        it.u_begin += (int)U[j];
+        it.u_end += (int)U[j];
+        it.slot += S[j];
+        plan.items[I[j] + k] = it;
+      }
+      for (size_t k = 0; k < P.groups.size(); ++k) {
+        Group g = P.groups[k];
+        g.i_begin += (int)I[j];
+        g.i_end += (int)I[j];
+        plan.groups[G[j] + k] = g;
+      }
+      std::copy(P.icost.begin(), P.icost.end(), icost.begin() + I[j]);
+    });
   }
   plan.schedule.resize(plan.items.size());
   std::iota(plan.schedule.begin(), plan.schedule.end(), 0);
