@@ -33,11 +33,12 @@ __device__ __forceinline__ int find_sector(const int* q, int nq, int n, int s) {
 // (rows of ob within Qout, columns of ib within Qin). Terms are resolved 256
 // at a time, one per thread, into shared memory (the lookups are dependent
 // global loads, so doing them in parallel hides their latency), then applied
-// in term order. Each destination element is owned by one thread (index mod
-// blockDim) for the zeroing and every update, so terms are applied in order
-// without atomics and the sums are deterministic. Signs: block x site takes
-// (-1)^{N(block in)} when the site part is odd; site x block takes
-// (-1)^{N(site in)} when the block operator is odd.
+// in term order. Each destination element (row R, column C) is owned by one
+// thread - warp R mod 8, lane C mod 32 - for every update, so terms are
+// applied in order without atomics and the sums are deterministic; a warp
+// walks its rows of a chunk and its lanes read consecutive columns. Signs:
+// block x site takes (-1)^{N(block in)} when the site part is odd; site x
+// block takes (-1)^{N(site in)} when the block operator is odd.
 struct RTerm {        // one resolved term
   long long soff;     // source block offset
   double w;           // coefficient times sign
@@ -46,15 +47,18 @@ struct RTerm {        // one resolved term
   int store2;         // source in the second store
 };
 constexpr int BLK_THREADS = 256;
+static_assert(BLK_THREADS == 256, "the update ownership assumes 8 warps");
 
 __global__ void __launch_bounds__(BLK_THREADS) blocking_kernel(BlockingDev d) {
   __shared__ RTerm rt[BLK_THREADS];
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31;  // 8 warps (BLK_THREADS = 256)
   for (int bi = blockIdx.x; bi < d.ndst; bi += gridDim.x) {
     const BDst db = d.dsts[bi];
     double* dst = d.dst_store + db.off;
     const long long ne = (long long)db.rows * db.cols;
     for (long long e = tid; e < ne; e += nt) dst[e] = 0.0;
+    __syncthreads();  // zeroing and the updates below own elements differently
     const int qin_n = d.eq[2 * db.Qin], qin_s = d.eq[2 * db.Qin + 1];
     const int qout_n = d.eq[2 * db.Qout], qout_s = d.eq[2 * db.Qout + 1];
     const int t_end = d.term_start[db.k + 1];
@@ -105,15 +109,15 @@ __global__ void __launch_bounds__(BLK_THREADS) blocking_kernel(BlockingDev d) {
         const RTerm r = rt[q];
         if (r.kind == 0) continue;
         const double* __restrict__ S = r.store2 ? d.src_store2 : d.src_store;
-        for (int i = 0; i < r.rows; ++i) {
-          const long long base = (long long)(r.r0 + i) * db.cols + r.c0;
-          int j = (int)(((long long)tid - base % nt + nt) % nt);  // first column this thread owns
-          for (; j < r.cols; j += nt) {
+        // rows of the destination with (row mod 8) = warp, columns with (col mod 32) = lane
+        for (int i = (warp - r.r0) & 7; i < r.rows; i += 8) {
+          double* drow = dst + (long long)(r.r0 + i) * db.cols + r.c0;
+          for (int j = (lane - r.c0) & 31; j < r.cols; j += 32) {
             double v;
             if (r.kind == 1) v = (i == j) ? 1.0 : 0.0;
             else if (r.kind == 2) v = S[r.soff + (long long)i * r.cols + j];
             else v = S[r.soff + (long long)j * r.rows + i];
-            dst[base + j] += r.w * v;
+            drow[j] += r.w * v;
           }
         }
       }
