@@ -1246,9 +1246,8 @@ bool predict_guess(Context& c, int i, bool forward, const Problem& p, double* g)
   }
   DMRG_CUDA(cudaGetLastError());
   // |g|^2 (the oracle falls back to a random guess below norm 1e-12)
-  Problem& pm = const_cast<Problem&>(p);
-  double* sc = pm.dav_s.as<double>() + 60;
-  dav_dots(g, p.psi_size, 1, g, p.psi_size, pm.dav_partial.as<double>(), sc, 1, st);
+  double* sc = p.dav_s.as<double>() + 60;  // scratch scalar of the Davidson workspace
+  dav_dots(g, p.psi_size, 1, g, p.psi_size, p.dav_partial.as<double>(), sc, 1, st);
   double nrm2 = 0.0;
   DMRG_CUDA(cudaMemcpyAsync(&nrm2, sc, sizeof(double), cudaMemcpyDeviceToHost, st));
   DMRG_CUDA(cudaStreamSynchronize(st));
