@@ -1,6 +1,8 @@
-// Sweep kernels: blocking (Eq. blocked-ops), decimation (per-sector Gram
-// matrix and Jacobi eigensolver), orthonormal bases for the initial MPS.
-// The transformation of Eq. op-trans runs on the FP64 sigma kernel with a
+// Sweep kernels: blocking (Eq. blocked-ops), the normal-to-complementary
+// sums of the mixed NC/CN scheme (Sec. III.A), decimation (one-sided Jacobi
+// SVD of the psi blocks), orthonormal bases for the initial MPS, and the
+// small GEMMs that carry a wavefunction to the next bond. The
+// transformation of Eq. op-trans runs on the FP64 sigma kernel with a
 // dedicated work list (see sweep.cpp).
 #include <cooperative_groups.h>
 

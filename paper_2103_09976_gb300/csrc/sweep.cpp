@@ -1,6 +1,7 @@
 // Two-site DMRG sweeps on the device (Appendix A): blocking (Eq.
-// blocked-ops), solving (Eq. eff-eigsh, device Davidson over the NC sigma),
-// decimation (per-sector Gram matrix + Jacobi, global truncation) and
+// blocked-ops), solving (Eq. eff-eigsh, device Davidson over the NC or CN
+// sigma, started from the previous step's wavefunction), decimation
+// (one-sided Jacobi SVD of every psi block, global truncation) and
 // transformation (Eq. op-trans). The host decides which blocks to add and
 // which states to keep; every floating-point step runs in CUDA kernels.
 //
@@ -1045,8 +1046,10 @@ struct Decim {
 };
 
 // Decimation of psi (device, problem layout) keeping at most M states
-// (Appendix A step iii): per-sector Gram matrix, Jacobi eigenpairs, global
-// sort by (s desc, q_L asc, index asc), kept count min(M, sum min(mL, mR)).
+// (Appendix A step iii): singular vectors and values of every psi block by
+// one-sided Jacobi on the device, global sort by (s desc, q_L asc, index
+// asc), kept count min(M, sum min(mL, mR)) (plus one state per quantum
+// number with keep_one_per_q).
 void decimate(Context& c, Problem& p, const Enlarged& E, const double* psi, int M, bool forward, Decim& D) {
   cudaStream_t st = c.stream;
   const int nb = (int)p.blocks.size();
