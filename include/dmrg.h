@@ -231,8 +231,9 @@ dmrg_status dmrg_davidson(dmrg_ctx* ctx, int site, const double* psi0, double to
  * Full problem from integrals: t is K*K row-major (symmetric), v is K^4
  * row-major chemist's notation (ij|kl) with the 8-fold symmetry (Appendix B,
  * Eq. qc-hamil). Host pointers. Builds the initial right-canonical MPS with
- * bond dimension <= M_init (seeded) and all right-block NC operators
- * (blocking + transformation, right to left). Target: N electrons, 2Sz.
+ * bond dimension <= M_init (seeded) and all right-block operators
+ * (blocking + transformation, right to left; NC form, or CN form right of
+ * dmrg_opts.mixed_cut). Target: N electrons, 2Sz.
  */
 dmrg_status dmrg_build_blocks(dmrg_ctx* ctx, const double* t, const double* v, int K, int N,
                               int two_sz, int M_init);
@@ -241,7 +242,11 @@ dmrg_status dmrg_build_blocks(dmrg_ctx* ctx, const double* t, const double* v, i
  * Two-site sweeps (Appendix A): M_schedule[s] is the bond dimension of sweep
  * s (forward on even s, backward on odd s). energies[s] = lowest Davidson
  * energy of sweep s; max_discard[s] = largest discarded weight of sweep s
- * (either may be NULL). Davidson tolerance `tol` per step.
+ * (either may be NULL). Davidson tolerance `tol` per step. Each solve starts
+ * from the previous step's wavefunction carried to the new bond (projected
+ * on the block just kept, expanded through the stored basis of the block
+ * entered; at the turn of a sweep the wavefunction itself); the first step
+ * after dmrg_build_blocks starts from seeded normals.
  */
 dmrg_status dmrg_sweep(dmrg_ctx* ctx, const int* M_schedule, int n_sweeps, double tol,
                        double* energies, double* max_discard);
