@@ -177,9 +177,15 @@ int main(int argc, char** argv) {
   }
 
   std::printf("{\"psi_size\": %lld, \"blocks\": %zu, \"terms\": %zu, \"tasks\": %zu, \"flops\": %.17g, "
-              "\"plan_tasks\": %zu, \"units\": %zu, \"items\": %zu, \"errors\": [",
+              "\"plan_tasks\": %zu, \"units\": %zu, \"items\": %zu, \"layout\": [",
               size, blocks.size(), terms.size(), wl.tasks.size(), wl.flops, plan.tasks.size(), plan.units.size(),
               plan.items.size());
+  for (size_t b = 0; b < blocks.size(); ++b) {
+    const PsiBlock& pb = blocks[b];
+    std::printf("%s[%d, %d, %d, %d, %d, %d, %lld]", b ? ", " : "", L.q[pb.qL].n, L.q[pb.qL].s, R.q[pb.qR].n,
+                R.q[pb.qR].s, pb.mL, pb.mR, pb.off);
+  }
+  std::printf("], \"errors\": [");
   for (size_t i = 0; i < errors.size(); ++i) std::printf("%s\"%s\"", i ? ", " : "", errors[i].c_str());
   std::printf("]}\n");
   return 0;

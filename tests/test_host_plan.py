@@ -1,8 +1,9 @@
 """Host logic of the sigma work lists, on the CPU: the library's own C++
 (tests/host/plan_check.cpp linked against csrc/model.cpp, no CUDA calls)
 builds the operator tables, the NC or CN term list, the task list and the
-tensor-core plan; its product count and algorithmic flops must equal the
-oracle's independent count over the same sectors (oracle.sigma.sigma_flops),
+tensor-core plan; its psi layout must equal the oracle's exactly, its
+product count and algorithmic flops the oracle's independent count over the
+same sectors (oracle.sigma.sigma_flops),
 and the plan must pass its structural checks (every task once, units in
 order, 128 x 128 tiles of every output block, scratch slots, schedule,
 records)."""
@@ -87,6 +88,8 @@ def test_task_list_and_plan_match_the_oracle_count(checker, tmp_path, nsp, ntot,
     terms = cn_terms(nL, n) if cn else nc_terms(nL, n)
     dqL, dqR = _dq_maps(nL, n, cn)
     assert got["psi_size"] == size and got["blocks"] == len(layout) and got["terms"] == len(terms)
+    # sector bookkeeping: the psi layout is bit-identical to the oracle's
+    assert got["layout"] == [[qL[0], qL[1], qR[0], qR[1], mL, mR, off] for qL, qR, mL, mR, off in layout]
     assert got["tasks"] == got["plan_tasks"] == _products(layout, terms, dqL, dqR)
     ref = sigma_flops(layout, terms, dqL, dqR, bL, bR)
     assert abs(got["flops"] - ref) <= 1e-12 * ref
