@@ -80,3 +80,13 @@ def test_option_checks_come_before_the_device(libpath):
         with pytest.raises(capi.DMRGError) as e:
             capi.dmrg_create(**kw)
         assert e.value.status == capi.DMRG_EINVAL, kw
+
+
+@pytest.mark.parametrize("module", ["sweeps", "serve", "precision_sweep"])
+def test_command_line_tools_start_without_a_gpu(module):
+    """The user-facing tools parse their arguments and import the binding
+    without touching the device (the device is needed only to run them)."""
+    import sys
+    r = subprocess.run([sys.executable, "-m", f"paper_2103_09976_gb300.{module}", "--help"], capture_output=True,
+                       text=True, timeout=120, cwd=os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    assert r.returncode == 0 and "usage" in r.stdout
