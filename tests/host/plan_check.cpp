@@ -54,13 +54,17 @@ int main(int argc, char** argv) {
   TcPlan plan;
   build_tc_plan(blocks, oL, oR, wl, plan, 152 * 4, 32);
 
-  // (1) every task of the list, with its operator tiles, appears in the plan once
+  // (1) every task of the list, with its operator tiles, appears in the plan
+  //     once per 128 x 128 tile of its output block
   std::vector<long long> offs;
   for (const OpSet* s : {&oL, &oR})
     for (const OpDesc& o : s->ops)
       for (const OpBlock& b : o.blocks) offs.push_back(b.off);
   using Key = std::tuple<int, int, long long, long long, unsigned>;
   std::vector<Key> want, got;
+  std::vector<int> out_of(wl.tasks.size(), -1);
+  for (size_t b = 0; b < blocks.size(); ++b)
+    for (int t = wl.out_start[b]; t < wl.out_start[b + 1]; ++t) out_of[t] = (int)b;
   for (size_t t = 0; t < wl.tasks.size(); ++t) {
     const Task& k = wl.tasks[t];
     const PsiBlock& in = blocks[k.in_blk];
@@ -79,7 +83,9 @@ int main(int argc, char** argv) {
     unsigned bits;
     std::memcpy(&bits, &sc, 4);
     const int fl = (k.aoff >= 0 ? (k.flags & 1) : 0) | (k.boff >= 0 ? (k.flags & 2) : 0);
-    want.emplace_back(k.in_blk, fl, at, bt, bits);
+    const PsiBlock& ob = blocks[out_of[t]];
+    const int ntile = ((ob.mL + 127) / 128) * ((ob.mR + 127) / 128);
+    for (int r = 0; r < ntile; ++r) want.emplace_back(k.in_blk, fl, at, bt, bits);
   }
   for (const TcTask& x : plan.tasks) {
     unsigned bits;

@@ -3,7 +3,8 @@
 builds the operator tables, the NC or CN term list, the task list and the
 tensor-core plan; its psi layout must equal the oracle's exactly, its
 product count and algorithmic flops the oracle's independent count over the
-same sectors (oracle.sigma.sigma_flops),
+same sectors (oracle.sigma.sigma_flops; the plan holds every product once per
+128 x 128 tile of its output block),
 and the plan must pass its structural checks (every task once, units in
 order, 128 x 128 tiles of every output block, scratch slots, schedule,
 records)."""
@@ -55,7 +56,9 @@ def _dq_maps(nL, n, cn):
     return dqL, dqR
 
 
-def _products(layout, terms, dqL, dqR):
+def _products(layout, terms, dqL, dqR, weight=None):
+    """Number of (term, psi block) products; with weight, each product counts
+    weight[output block's left sector] times."""
     blk = {qL: qR for qL, qR, mL, mR, off in layout}
     count = 0
     for kl, tl, kr, tr, c in terms:
@@ -63,15 +66,26 @@ def _products(layout, terms, dqL, dqR):
         dy = (0, 0) if kr is None else (dqR[kr] if not tr else (-dqR[kr][0], -dqR[kr][1]))
         for qL, qR in blk.items():
             qLo = qadd(qL, dx)
-            count += qLo in blk and blk[qLo] == qadd(qR, dy)
+            if qLo in blk and blk[qLo] == qadd(qR, dy):
+                count += 1 if weight is None else weight[qLo]
     return count
 
 
+# sectors with blocks above 128 rows / columns: several output tiles per block
+# and psi blocks wider than one 128-column pass
+BIG = [(3, -1, 40), (3, 1, 40), (4, -2, 129), (4, 0, 300), (4, 2, 130), (5, -1, 64), (5, 1, 200), (6, 0, 17)]
+
+
 @pytest.mark.parametrize("nsp,ntot,two_sz,M,cn", [(6, 12, 0, 150, False), (6, 12, 0, 150, True),
-                                                  (8, 9, 1, 300, True), (54, 30, 0, 400, False)])
+                                                  (8, 9, 1, 300, True), (54, 30, 0, 400, False),
+                                                  (4, 8, 0, None, False), (4, 8, 0, None, True)])
 def test_task_list_and_plan_match_the_oracle_count(checker, tmp_path, nsp, ntot, two_sz, M, cn):
-    left = gaussian_sector_dims(M, n_spatial=nsp, n_tot=ntot, two_sz_tot=two_sz)
-    right = mirrored_sectors(left, n_tot=ntot, two_sz_tot=two_sz)
+    if M is None:
+        left = BIG
+        right = sorted((ntot - n, two_sz - s, d) for n, s, d in BIG)
+    else:
+        left = gaussian_sector_dims(M, n_spatial=nsp, n_tot=ntot, two_sz_tot=two_sz)
+        right = mirrored_sectors(left, n_tot=ntot, two_sz_tot=two_sz)
     path = tmp_path / "sectors.txt"
     with open(path, "w") as f:
         f.write(f"{len(left)} {len(right)}\n")
@@ -90,6 +104,8 @@ def test_task_list_and_plan_match_the_oracle_count(checker, tmp_path, nsp, ntot,
     assert got["psi_size"] == size and got["blocks"] == len(layout) and got["terms"] == len(terms)
     # sector bookkeeping: the psi layout is bit-identical to the oracle's
     assert got["layout"] == [[qL[0], qL[1], qR[0], qR[1], mL, mR, off] for qL, qR, mL, mR, off in layout]
-    assert got["tasks"] == got["plan_tasks"] == _products(layout, terms, dqL, dqR)
+    assert got["tasks"] == _products(layout, terms, dqL, dqR)
+    tiles = {qL: ((mL + 127) // 128) * ((mR + 127) // 128) for qL, qR, mL, mR, off in layout}
+    assert got["plan_tasks"] == _products(layout, terms, dqL, dqR, tiles)
     ref = sigma_flops(layout, terms, dqL, dqR, bL, bR)
     assert abs(got["flops"] - ref) <= 1e-12 * ref
