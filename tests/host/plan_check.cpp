@@ -54,6 +54,48 @@ int main(int argc, char** argv) {
   TcPlan plan;
   build_tc_plan(blocks, oL, oR, wl, plan, 152 * 4, 32);
 
+  // (0) FP64 work list: groups tile every output block into 32 x 256 tiles;
+  //     the items of a group split the block's task range in order; slots
+  //     are consecutive; the schedule is a permutation
+  {
+    size_t g = 0;
+    long long sl = 0;
+    int ni = 0;
+    for (size_t b = 0; b < blocks.size(); ++b)
+      for (int r0 = 0; r0 < blocks[b].mL; r0 += 32)
+        for (int c0 = 0; c0 < blocks[b].mR; c0 += 256, ++g) {
+          if (g >= wl.groups.size()) {
+            fail("fp64: missing group");
+            continue;
+          }
+          const Group& gr = wl.groups[g];
+          if (gr.out != (int)b || gr.r0 != r0 || gr.c0 != c0 || gr.nrows != std::min(32, blocks[b].mL - r0) ||
+              gr.ncols != std::min(256, blocks[b].mR - c0) || gr.i_begin != ni || gr.i_end <= gr.i_begin)
+            fail("fp64: group");
+          int t = wl.out_start[b];
+          for (int i = gr.i_begin; i < gr.i_end && i < (int)wl.items.size(); ++i) {
+            const Item& it = wl.items[i];
+            if (it.out != gr.out || it.r0 != gr.r0 || it.c0 != gr.c0 || it.nrows != gr.nrows || it.ncols != gr.ncols)
+              fail("fp64: item tile");
+            if (it.t_begin != t || it.t_end < it.t_begin) fail("fp64: item task range");
+            if (it.slot != sl) fail("fp64: slot");
+            sl += (long long)it.nrows * it.ncols;
+            t = it.t_end;
+          }
+          if (t != wl.out_start[b + 1]) fail("fp64: items do not cover the block's tasks");
+          ni = gr.i_end;
+        }
+    if (g != wl.groups.size() || ni != (int)wl.items.size()) fail("fp64: extra groups or items");
+    if (sl != wl.scratch_elems) fail("fp64: scratch size");
+    std::vector<int> sch = wl.schedule;
+    std::sort(sch.begin(), sch.end());
+    for (size_t i = 0; i < sch.size(); ++i)
+      if (sch[i] != (int)i) {
+        fail("fp64: schedule");
+        break;
+      }
+  }
+
   // (1) every task of the list, with its operator tiles, appears in the plan
   //     once per 128 x 128 tile of its output block
   std::vector<long long> offs;

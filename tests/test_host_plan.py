@@ -5,9 +5,10 @@ tensor-core plan; its psi layout must equal the oracle's exactly, its
 product count and algorithmic flops the oracle's independent count over the
 same sectors (oracle.sigma.sigma_flops; the plan holds every product once per
 128 x 128 tile of its output block),
-and the plan must pass its structural checks (every task once, units in
-order, 128 x 128 tiles of every output block, scratch slots, schedule,
-records)."""
+and both work lists must pass their structural checks (FP64: 32 x 256 tiles
+whose items split each block's tasks in order; tensor-core plan: every task
+once per tile, units in order, 128 x 128 tiles of every output block,
+scratch slots, schedule, records)."""
 
 import json
 import os
