@@ -233,6 +233,10 @@ int main(int argc, char** argv) {
     std::printf("%s[%d, %d, %d, %d, %d, %d, %lld]", b ? ", " : "", L.q[pb.qL].n, L.q[pb.qL].s, R.q[pb.qR].n,
                 R.q[pb.qR].s, pb.mL, pb.mR, pb.off);
   }
+  std::printf("], \"ranks3\": [");
+  const std::vector<int> rk = cn ? cn_term_ranks(nL, n, 3) : nc_term_ranks(nL, n, 3);
+  if (rk.size() != terms.size()) fail("rank count");
+  for (size_t t = 0; t < rk.size(); ++t) std::printf("%s%d", t ? ", " : "", rk[t]);
   std::printf("], \"errors\": [");
   for (size_t i = 0; i < errors.size(); ++i) std::printf("%s\"%s\"", i ? ", " : "", errors[i].c_str());
   std::printf("]}\n");

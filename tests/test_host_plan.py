@@ -4,7 +4,8 @@ builds the operator tables, the NC or CN term list, the task list and the
 tensor-core plan; its psi layout must equal the oracle's exactly, its
 product count and algorithmic flops the oracle's independent count over the
 same sectors (oracle.sigma.sigma_flops; the plan holds every product once per
-128 x 128 tile of its output block),
+128 x 128 tile of its output block), its sub-Hamiltonian rank of every term
+the oracle's (nc_term_rank),
 and both work lists must pass their structural checks (FP64: 32 x 256 tiles
 whose items split each block's tasks in order; tensor-core plan: every task
 once per tile, units in order, 128 x 128 tiles of every output block,
@@ -20,7 +21,7 @@ import pytest
 from oracle.blocks import Basis, qadd
 from oracle.cn import cn_terms
 from oracle.nc import nc_terms, spin
-from oracle.sigma import psi_layout, sigma_flops, synthetic_op_specs
+from oracle.sigma import nc_term_rank, psi_layout, sigma_flops, synthetic_op_specs
 from synth import gaussian_sector_dims, mirrored_sectors
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -110,3 +111,5 @@ def test_task_list_and_plan_match_the_oracle_count(checker, tmp_path, nsp, ntot,
     assert got["plan_tasks"] == _products(layout, terms, dqL, dqR, tiles)
     ref = sigma_flops(layout, terms, dqL, dqR, bL, bR)
     assert abs(got["flops"] - ref) <= 1e-12 * ref
+    # sub-Hamiltonian ranks of the terms (Eqs. proc-def-nc / proc-def-cn), 3 ranks
+    assert got["ranks3"] == [nc_term_rank(t, 3) for t in terms]
