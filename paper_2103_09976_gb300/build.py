@@ -27,6 +27,7 @@ SOURCES = [
     "davidson_host.cpp",
     "blocking.cu",
     "sweep.cpp",
+    "terms.cpp",
     "server.cpp",
 ]
 

@@ -122,14 +122,7 @@ void launch_blocking(const BlockingDev& d, cudaStream_t st);
 // src + xoff[x_start + i]), Y_o at dst + y_off + o * E, C row-major at
 // coef + c_off. One 64 x 128 tile of (o, element) per CTA, FP64 tensor
 // instructions, k in steps of 16 sources.
-struct CombClass {
-  long long y_off, c_off, E;
-  int x_start, n_out, n_in;
-  int tile_start;   // first tile of the class in the launch
-  int tiles_e;      // tiles along E
-  int pad;
-};
-constexpr int COMB_TM = 64, COMB_TN = 128;
+// (CombClass, COMB_TM and COMB_TN are in model.h.)
 // Small strided GEMMs C = A B (one job per CTA, FP64, fixed summation
 // order): A(i, k) = A[a + (ta ? k * lda + i : i * lda + k)], B(k, j) =
 // B[b + (tb ? j * ldb + k : k * ldb + j)], C[c + i * ldc + j], i < m, j < n,

@@ -158,6 +158,17 @@ struct Group {
   int out, r0, nrows, c0, ncols, i_begin, i_end, pad;
 };
 
+// One class of the normal-to-complementary sums (Sec. III.A): operators of
+// one shift, so one block structure of E elements; see launch_opcomb.
+struct CombClass {
+  long long y_off, c_off, E;
+  int x_start, n_out, n_in;
+  int tile_start;   // first tile of the class in the launch
+  int tiles_e;      // tiles along E
+  int pad;
+};
+constexpr int COMB_TM = 64, COMB_TN = 128;
+
 struct WorkList {
   std::vector<Task> tasks;        // grouped by output block
   std::vector<int> out_start;     // tasks of output block b: [out_start[b], out_start[b+1])
