@@ -19,10 +19,10 @@
 //
 // Blocking: each enlarged operator is a sum of terms (block operator or 1)
 // (x) (4x4 site matrix) derived by splitting every second-quantized string
-// into its block part and its site part (the formulas are in terms.cpp). Every nonzero
-// site-matrix element of a term becomes a scaled copy of one block-operator
-// block into one chunk of one enlarged block; a kernel applies the copies of
-// each destination block in a fixed order.
+// into its block part and its site part (the formulas are in terms.cpp).
+// Every nonzero site-matrix element of a term becomes a scaled copy of one
+// block-operator block into one chunk of one enlarged block; a kernel
+// applies the copies of each destination block in a fixed order.
 #include <algorithm>
 #include <chrono>
 #include <array>
