@@ -127,12 +127,7 @@ void launch_blocking(const BlockingDev& d, cudaStream_t st);
 // order): A(i, k) = A[a + (ta ? k * lda + i : i * lda + k)], B(k, j) =
 // B[b + (tb ? j * ldb + k : k * ldb + j)], C[c + i * ldc + j], i < m, j < n,
 // k < kk. Used to carry a wavefunction from one bond to the next.
-struct GJob {
-  long long a, b, c;
-  int m, n, kk;
-  int lda, ldb, ldc;
-  int ta, tb;
-};
+// (GJob is in model.h.)
 void launch_bgemm(const double* A, const double* B, double* C, const GJob* jobs, int njobs, cudaStream_t st);
 void launch_opcomb(const double* src, const long long* xoff, const double* coef, const CombClass* cls, int ncls,
                    int ntiles, double* dst, cudaStream_t st);

@@ -169,6 +169,16 @@ struct CombClass {
 };
 constexpr int COMB_TM = 64, COMB_TN = 128;
 
+// One small strided GEMM C = A B (see launch_bgemm): A(i, k) =
+// A[a + (ta ? k * lda + i : i * lda + k)], B(k, j) = B[b + (tb ? j * ldb + k :
+// k * ldb + j)], C[c + i * ldc + j], i < m, j < n, k < kk.
+struct GJob {
+  long long a, b, c;
+  int m, n, kk;
+  int lda, ldb, ldc;
+  int ta, tb;
+};
+
 struct WorkList {
   std::vector<Task> tasks;        // grouped by output block
   std::vector<int> out_start;     // tasks of output block b: [out_start[b], out_start[b+1])

@@ -502,70 +502,12 @@ bool predict_guess(Context& c, int i, bool forward, const Problem& p, double* g)
   const bool fw = forward && S.prev_fwd && S.prev_site == i - 1;
   const bool bw = !forward && !S.prev_fwd && S.prev_site == i + 1;
   if (!fw && !bw) return false;
-  std::vector<int> blk_of_qL(S.EL.basis.size(), -1);
-  for (size_t b = 0; b < p.blocks.size(); ++b) blk_of_qL[p.blocks[b].qL] = (int)b;
-  auto site_state = [](QN d) {
-    for (int n = 0; n < 4; ++n)
-      if (SITE_Q[n] == d) return n;
-    return -1;
-  };
   std::vector<GJob> j1, j2;
   long long phi_size = 0;
   const DevBlock& Lb = fw ? *S.L[i] : *S.L[i + 1];
   const DevBlock& Rb = fw ? *S.R[i + 1] : *S.R[i + 2];
-  if (fw) {  // Lb: kept states of the previous left enlarged block; Rb: basis over the new ER
-    std::vector<int> kept_of(S.prev_EL.basis.size(), -1);
-    for (size_t s = 0; s < Lb.esec.size(); ++s) kept_of[Lb.esec[s]] = (int)s;
-    for (const PsiBlock& pb : S.prev_blocks) {
-      const int s = kept_of[pb.qL];
-      if (s < 0) continue;
-      const int k = Lb.set.basis.dim[s];
-      const long long phi_off = phi_size;
-      phi_size += (long long)k * pb.mR;
-      j1.push_back({Lb.uoff[s], pb.off, phi_off, k, pb.mR, pb.mL, k, pb.mR, pb.mR, 1, 0});  // U^T psi
-      const QN qR = S.prev_ER.basis.q[pb.qR];
-      for (int jb = 0; jb < Rb.set.basis.size(); ++jb) {
-        const int offc = S.prev_ER.chunk_off[pb.qR][jb];
-        if (offc < 0) continue;
-        const int n = site_state(qR - Rb.set.basis.q[jb]);
-        if (n < 0) continue;
-        const int QLn = S.EL.basis.find(Lb.set.basis.q[s] + SITE_Q[n]);
-        if (QLn < 0) continue;
-        const int b = blk_of_qL[QLn];
-        if (b < 0 || p.blocks[b].qR != Rb.esec[jb]) continue;
-        const PsiBlock& nb = p.blocks[b];
-        const int r0 = S.EL.chunk_off[QLn][s], kr = Rb.set.basis.dim[jb];
-        j2.push_back({phi_off + offc, Rb.uoff[jb], nb.off + (long long)r0 * nb.mR, k, nb.mR, kr, pb.mR, kr, nb.mR,
-                      0, 1});  // phi[:, chunk] V^T
-      }
-    }
-  } else {  // Rb: kept states of the previous right enlarged block; Lb: basis over the new EL
-    std::vector<int> kept_of(S.prev_ER.basis.size(), -1);
-    for (size_t s = 0; s < Rb.esec.size(); ++s) kept_of[Rb.esec[s]] = (int)s;
-    for (const PsiBlock& pb : S.prev_blocks) {
-      const int s = kept_of[pb.qR];
-      if (s < 0) continue;
-      const int k = Rb.set.basis.dim[s];
-      const long long phi_off = phi_size;
-      phi_size += (long long)pb.mL * k;
-      j1.push_back({pb.off, Rb.uoff[s], phi_off, pb.mL, k, pb.mR, pb.mR, k, k, 0, 0});  // psi V
-      const QN qL = S.prev_EL.basis.q[pb.qL];
-      for (int ja = 0; ja < Lb.set.basis.size(); ++ja) {
-        const int offc = S.prev_EL.chunk_off[pb.qL][ja];
-        if (offc < 0) continue;
-        const int n = site_state(qL - Lb.set.basis.q[ja]);
-        if (n < 0) continue;
-        const int QRn = S.ER.basis.find(Rb.set.basis.q[s] + SITE_Q[n]);
-        if (QRn < 0) continue;
-        const int b = blk_of_qL[Lb.esec[ja]];
-        if (b < 0 || p.blocks[b].qR != QRn) continue;
-        const PsiBlock& nb = p.blocks[b];
-        const int c0 = S.ER.chunk_off[QRn][s], kl = Lb.set.basis.dim[ja];
-        j2.push_back({Lb.uoff[ja], phi_off + (long long)offc * k, nb.off + c0, nb.mL, k, kl, kl, k, nb.mR, 0,
-                      0});  // U phi[chunk, :]
-      }
-    }
-  }
+  carry_jobs(fw, S.prev_blocks, S.prev_EL, S.prev_ER, S.EL, S.ER, p.blocks, {&Lb.set.basis, &Lb.uoff, &Lb.esec},
+             {&Rb.set.basis, &Rb.uoff, &Rb.esec}, j1, j2, phi_size);
   if (j2.empty()) return false;
   DevBuf phi, d1, d2;
   phi.alloc(std::max<long long>(1, phi_size) * sizeof(double));

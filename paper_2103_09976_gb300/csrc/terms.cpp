@@ -537,5 +537,80 @@ std::vector<ETerms> right_terms_cn(const Ints& I, int s, bool dst_nc, const Comp
   return T;
 }
 
+void carry_jobs(bool forward, const std::vector<PsiBlock>& prev_blocks, const Enlarged& prev_EL,
+                const Enlarged& prev_ER, const Enlarged& EL, const Enlarged& ER, const std::vector<PsiBlock>& blocks,
+                const BlockBasis& Lb, const BlockBasis& Rb, std::vector<GJob>& j1, std::vector<GJob>& j2,
+                long long& phi_size) {
+  std::vector<int> blk_of_qL(EL.basis.size(), -1);
+  for (size_t b = 0; b < blocks.size(); ++b) blk_of_qL[blocks[b].qL] = (int)b;
+  auto site_state = [](QN d) {
+    for (int n = 0; n < 4; ++n)
+      if (SITE_Q[n] == d) return n;
+    return -1;
+  };
+  const Basis& lb = *Lb.basis;
+  const Basis& rb = *Rb.basis;
+  const std::vector<long long>& luoff = *Lb.uoff;
+  const std::vector<long long>& ruoff = *Rb.uoff;
+  const std::vector<int>& lesec = *Lb.esec;
+  const std::vector<int>& resec = *Rb.esec;
+  j1.clear();
+  j2.clear();
+  phi_size = 0;
+  if (forward) {  // Lb: kept states of the previous left enlarged block; Rb: basis over the new ER
+    std::vector<int> kept_of(prev_EL.basis.size(), -1);
+    for (size_t s = 0; s < lesec.size(); ++s) kept_of[lesec[s]] = (int)s;
+    for (const PsiBlock& pb : prev_blocks) {
+      const int s = kept_of[pb.qL];
+      if (s < 0) continue;
+      const int k = lb.dim[s];
+      const long long phi_off = phi_size;
+      phi_size += (long long)k * pb.mR;
+      j1.push_back({luoff[s], pb.off, phi_off, k, pb.mR, pb.mL, k, pb.mR, pb.mR, 1, 0});  // U^T psi
+      const QN qR = prev_ER.basis.q[pb.qR];
+      for (int jb = 0; jb < rb.size(); ++jb) {
+        const int offc = prev_ER.chunk_off[pb.qR][jb];
+        if (offc < 0) continue;
+        const int n = site_state(qR - rb.q[jb]);
+        if (n < 0) continue;
+        const int QLn = EL.basis.find(lb.q[s] + SITE_Q[n]);
+        if (QLn < 0) continue;
+        const int b = blk_of_qL[QLn];
+        if (b < 0 || blocks[b].qR != resec[jb]) continue;
+        const PsiBlock& nb = blocks[b];
+        const int r0 = EL.chunk_off[QLn][s], kr = rb.dim[jb];
+        j2.push_back({phi_off + offc, ruoff[jb], nb.off + (long long)r0 * nb.mR, k, nb.mR, kr, pb.mR, kr, nb.mR,
+                      0, 1});  // phi[:, chunk] V^T
+      }
+    }
+  } else {  // Rb: kept states of the previous right enlarged block; Lb: basis over the new EL
+    std::vector<int> kept_of(prev_ER.basis.size(), -1);
+    for (size_t s = 0; s < resec.size(); ++s) kept_of[resec[s]] = (int)s;
+    for (const PsiBlock& pb : prev_blocks) {
+      const int s = kept_of[pb.qR];
+      if (s < 0) continue;
+      const int k = rb.dim[s];
+      const long long phi_off = phi_size;
+      phi_size += (long long)pb.mL * k;
+      j1.push_back({pb.off, ruoff[s], phi_off, pb.mL, k, pb.mR, pb.mR, k, k, 0, 0});  // psi V
+      const QN qL = prev_EL.basis.q[pb.qL];
+      for (int ja = 0; ja < lb.size(); ++ja) {
+        const int offc = prev_EL.chunk_off[pb.qL][ja];
+        if (offc < 0) continue;
+        const int n = site_state(qL - lb.q[ja]);
+        if (n < 0) continue;
+        const int QRn = ER.basis.find(rb.q[s] + SITE_Q[n]);
+        if (QRn < 0) continue;
+        const int b = blk_of_qL[lesec[ja]];
+        if (b < 0 || blocks[b].qR != QRn) continue;
+        const PsiBlock& nb = blocks[b];
+        const int c0 = ER.chunk_off[QRn][s], kl = lb.dim[ja];
+        j2.push_back({luoff[ja], phi_off + (long long)offc * k, nb.off + c0, nb.mL, k, kl, kl, k, nb.mR, 0,
+                      0});  // U phi[chunk, :]
+      }
+    }
+  }
+}
+
 }  // namespace terms
 }  // namespace dmrg

@@ -175,5 +175,28 @@ std::vector<ETerms> left_terms_cn(const Ints& I, int s, bool src_nc, const CompS
 // [2s, n)) is in NC form when dst_nc (the transformation), else in CN form.
 std::vector<ETerms> right_terms_cn(const Ints& I, int s, bool dst_nc, const CompSet* cs, int nsrc1);
 
+// Kept states of a block over the enlarged basis it was made from: sector s
+// of `basis` is enlarged sector esec[s], its d x k basis matrix (row-major,
+// columns = states) at element uoff[s] of the block's basis store.
+struct BlockBasis {
+  const Basis* basis;
+  const std::vector<long long>* uoff;
+  const std::vector<int>* esec;
+};
+// The two GEMM passes that carry the previous step's psi (blocks
+// prev_blocks over prev_EL x prev_ER) to the next bond (blocks over EL x ER).
+// Moving right (forward): Lb holds the kept states of prev_EL, Rb the basis
+// of the block the sweep enters over ER; pass 1 phi = U^T psi per block,
+// pass 2 psi'[(l, n), :] = phi[l, (n, r)] V^T per chunk. Moving left: Rb
+// holds the kept states of prev_ER, Lb the basis over EL; phi = psi V, then
+// psi'[:, (n, r)] = U phi[(l, n), r]. Pass 1 reads (basis store, psi) or
+// (psi, basis store) and writes phi (phi_size elements); pass 2 reads
+// (phi, basis store) or (basis store, phi) and writes psi'; every element of
+// psi' is written by at most one job.
+void carry_jobs(bool forward, const std::vector<PsiBlock>& prev_blocks, const Enlarged& prev_EL,
+                const Enlarged& prev_ER, const Enlarged& EL, const Enlarged& ER, const std::vector<PsiBlock>& blocks,
+                const BlockBasis& Lb, const BlockBasis& Rb, std::vector<GJob>& j1, std::vector<GJob>& j2,
+                long long& phi_size);
+
 }  // namespace terms
 }  // namespace dmrg
