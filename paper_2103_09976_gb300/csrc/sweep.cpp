@@ -416,37 +416,15 @@ void decimate(Context& c, Problem& p, const Enlarged& E, const double* psi, int 
   std::vector<double> w(woff);
   DMRG_CUDA(cudaMemcpyAsync(w.data(), W.p, woff * sizeof(double), cudaMemcpyDeviceToHost, st));
   DMRG_CUDA(cudaStreamSynchronize(st));
-  struct Cand {
-    double s;
-    QN qL;
-    int idx, b;
-  };
-  std::vector<Cand> cand;
+  std::vector<std::vector<double>> sv(nb);  // singular values per block, descending
+  std::vector<QN> qLs(nb);
   for (int b = 0; b < nb; ++b) {
     const PsiBlock& pb = p.blocks[b];
     const int r = std::min(pb.mL, pb.mR);
-    for (int i = 0; i < r; ++i)
-      cand.push_back({std::sqrt(std::max(0.0, w[gb[b].w_off + i])), p.L.basis.q[pb.qL], i, b});
+    for (int i = 0; i < r; ++i) sv[b].push_back(std::sqrt(std::max(0.0, w[gb[b].w_off + i])));
+    qLs[b] = p.L.basis.q[pb.qL];
   }
-  std::stable_sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) {
-    if (a.s != b.s) return a.s > b.s;
-    if (!(a.qL == b.qL)) return a.qL < b.qL;
-    return a.idx < b.idx;
-  });
-  const size_t keep = std::min<size_t>((size_t)M, cand.size());
-  std::vector<int> kept(nb, 0);
-  D.discarded = 0.0;
-  for (size_t i = 0; i < cand.size(); ++i) {
-    if (i < keep) kept[cand[i].b]++;
-    else D.discarded += cand[i].s * cand[i].s;
-  }
-  if (c.opts.keep_one_per_q)  // every quantum number of psi keeps its largest state
-    for (int b = 0; b < nb; ++b)
-      if (kept[b] == 0 && std::min(p.blocks[b].mL, p.blocks[b].mR) > 0) {
-        kept[b] = 1;
-        const double s0 = std::sqrt(std::max(0.0, w[gb[b].w_off]));
-        D.discarded -= s0 * s0;
-      }
+  const std::vector<int> kept = select_kept(sv, qLs, M, c.opts.keep_one_per_q != 0, &D.discarded);
   // new basis: sectors of the growing side in ascending order
   std::vector<std::pair<QN, int>> secs;  // (q, block)
   for (int b = 0; b < nb; ++b)

@@ -612,5 +612,38 @@ void carry_jobs(bool forward, const std::vector<PsiBlock>& prev_blocks, const En
   }
 }
 
+std::vector<int> select_kept(const std::vector<std::vector<double>>& sv, const std::vector<QN>& qL, int M,
+                             bool keep_one_per_q, double* discarded) {
+  struct Cand {
+    double s;
+    QN qL;
+    int idx, b;
+  };
+  const int nb = (int)sv.size();
+  std::vector<Cand> cand;
+  for (int b = 0; b < nb; ++b)
+    for (int i = 0; i < (int)sv[b].size(); ++i) cand.push_back({sv[b][i], qL[b], i, b});
+  std::stable_sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) {
+    if (a.s != b.s) return a.s > b.s;
+    if (!(a.qL == b.qL)) return a.qL < b.qL;
+    return a.idx < b.idx;
+  });
+  const size_t keep = std::min<size_t>((size_t)std::max(0, M), cand.size());
+  std::vector<int> kept(nb, 0);
+  double disc = 0.0;
+  for (size_t i = 0; i < cand.size(); ++i) {
+    if (i < keep) kept[cand[i].b]++;
+    else disc += cand[i].s * cand[i].s;
+  }
+  if (keep_one_per_q)  // every quantum number of psi keeps its largest state
+    for (int b = 0; b < nb; ++b)
+      if (kept[b] == 0 && !sv[b].empty()) {
+        kept[b] = 1;
+        disc -= sv[b][0] * sv[b][0];
+      }
+  if (discarded) *discarded = disc;
+  return kept;
+}
+
 }  // namespace terms
 }  // namespace dmrg

@@ -198,5 +198,15 @@ void carry_jobs(bool forward, const std::vector<PsiBlock>& prev_blocks, const En
                 const BlockBasis& Lb, const BlockBasis& Rb, std::vector<GJob>& j1, std::vector<GJob>& j2,
                 long long& phi_size);
 
+// Global truncation (Appendix A, decimation): the singular values of all psi
+// blocks (sv[b] in descending order, min(mL, mR) of them; qL[b] the block's
+// left quantum number) sorted by (value descending, q_L ascending, index
+// ascending), the first min(M, count) kept, zero values included; with
+// keep_one_per_q a block none of whose values made the cut keeps its
+// largest (Sec. III keeps a state per quantum number). Returns the kept
+// count per block; *discarded = sum of the squares not kept.
+std::vector<int> select_kept(const std::vector<std::vector<double>>& sv, const std::vector<QN>& qL, int M,
+                             bool keep_one_per_q, double* discarded);
+
 }  // namespace terms
 }  // namespace dmrg
