@@ -502,8 +502,7 @@ void launch_svd_blocks(const double* psi, const SvdBlock* sb, int nb, int total_
                        double* Q, double* w, double* work, bool left, int n_sm, cudaStream_t st) {
   if (nb <= 0) return;
   if ((size_t)max_d_hint * sizeof(double) > 48 * 1024)
-    cudaFuncSetAttribute(svd_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)((size_t)max_d_hint * sizeof(double)));
+    set_max_dynamic_smem((const void*)svd_finish_kernel, (int)((size_t)max_d_hint * sizeof(double)));
   {
     dim3 grid(32, nb < 65535 ? nb : 65535);
     svd_setup_kernel<<<grid, 256, 0, st>>>(psi, sb, nb, work, left ? 1 : 0);

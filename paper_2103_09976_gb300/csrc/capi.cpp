@@ -48,14 +48,28 @@ dmrg_status guarded(dmrg_ctx* ctx, F&& f) {
   }
 }
 
-bool is_device_ptr(const void* p) {
+}  // namespace
+
+// True for device or managed memory, false for host memory (pageable or
+// pinned). Device memory of another GPU is refused: the context's kernels
+// run on its own device and would fault on, or silently read across, a peer
+// GPU's memory.
+bool dmrg::is_device_ptr(const void* p, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeDevice) {
+    if (at.device != dev)
+      throw Error(DMRG_EINVAL, "buffer is device memory of GPU " + std::to_string(at.device) +
+                                   " but the context runs on GPU " + std::to_string(dev));
+    return true;
+  }
+  return at.type == cudaMemoryTypeManaged;
 }
+
+namespace {
 
 
 Problem& need_problem(Context& c, int site) {
@@ -392,7 +406,7 @@ void sigma_call(Context& c, Problem& p, const double* psi, double* sigma, F comp
   const char* a0 = (const char*)psi;
   const char* b0 = (const char*)sigma;
   if (a0 < b0 + bytes && b0 < a0 + bytes) throw Error(DMRG_EINVAL, "psi and sigma overlap");
-  bool dpsi = is_device_ptr(psi), dsig = is_device_ptr(sigma);
+  bool dpsi = is_device_ptr(psi, c.device), dsig = is_device_ptr(sigma, c.device);
   const double* xin = psi;
   double* yout = sigma;
   if (!dpsi) {
@@ -689,7 +703,15 @@ dmrg_status dmrg_sigma_part(dmrg_ctx* ctx, int site, int rank, int n_ranks, cons
 
 dmrg_status dmrg_sigma_noalloc(dmrg_ctx* ctx, int site, const double* psi, double* sigma) {
   if (!ctx) return DMRG_EINVAL;
-  return guarded(ctx, [&] { sigma_noalloc(ctx->c, need_problem(ctx->c, site), psi, sigma); });
+  return guarded(ctx, [&] {
+    Context& c = ctx->c;
+    // a context built from integrals keeps one bond's operators resident;
+    // building another bond's would allocate, so it is refused here
+    if (c.sweep && !sweep_problem_ready(c, site))
+      throw Error(DMRG_ESTATE, "dmrg_sigma_noalloc: the operators of bond " + std::to_string(site) +
+                                   " are not resident (call dmrg_sigma or dmrg_davidson at this bond first)");
+    sigma_noalloc(c, need_problem(c, site), psi, sigma);
+  });
 }
 
 dmrg_status dmrg_davidson(dmrg_ctx* ctx, int site, const double* psi0, double tol, double* energy,
@@ -704,13 +726,13 @@ dmrg_status dmrg_davidson(dmrg_ctx* ctx, int site, const double* psi0, double to
     if (c.opts.dav_max_space > 32) throw Error(DMRG_EINVAL, "dav_max_space must be <= 32");
     const size_t bytes = (size_t)p.psi_size * sizeof(double);
     const double* x0 = psi0;
-    if (psi0 && !is_device_ptr(psi0)) {
+    if (psi0 && !is_device_ptr(psi0, c.device)) {
       c.d_psi.alloc(bytes);
       DMRG_CUDA(cudaMemcpyAsync(c.d_psi.p, psi0, bytes, cudaMemcpyHostToDevice, c.stream));
       x0 = c.d_psi.as<double>();
     }
     double* xo = psi_out;
-    const bool host_out = psi_out && !is_device_ptr(psi_out);
+    const bool host_out = psi_out && !is_device_ptr(psi_out, c.device);
     if (host_out) {
       c.d_sigma.alloc(bytes);
       xo = c.d_sigma.as<double>();

@@ -232,6 +232,11 @@ void prepare_tc(Context& c, Problem& p);
 void check_device_error(Context& c, Problem& p);
 void sigma_noalloc(Context& c, Problem& p, const double* psi, double* sigma);
 void sweep_problem(Context& c, int site);
+// True when the context's resident problem is bond `site` of its sweep state.
+bool sweep_problem_ready(const Context& c, int site);
+// True for device or managed memory on device `dev`, false for host memory;
+// throws DMRG_EINVAL for device memory of another GPU.
+bool is_device_ptr(const void* p, int dev);
 void sweep_build_blocks(Context& c, const double* t, const double* v, int K, int N, int two_sz, int M_init);
 void sweep_run(Context& c, const int* Ms, int n_sweeps, double tol, double* energies, double* max_discard);
 const std::vector<dmrg_step_log>& sweep_log(const Context& c);

@@ -9,6 +9,12 @@
 
 namespace dmrg {
 
+// Raise the dynamic shared-memory limit of kernel `fn` to `bytes` on the
+// current device. The limit is a per-device attribute, so it is set once for
+// every (kernel, device) pair; safe to call from several host threads.
+// Throws dmrg::Error (DMRG_ECUDA) when the runtime refuses it.
+void set_max_dynamic_smem(const void* fn, int bytes);
+
 // ---------------------------------------------------------------- generator
 // One block of a synthetic operator: entries N(0,1) from counter off + i*cols + j
 // (symmetric blocks use the counter of (min(i,j), max(i,j))).

@@ -20,6 +20,12 @@
 // (rows, columns) and 4 (k), instead of to whole register micro-tiles.
 // Each warp owns a set of 8x8 sub-tiles of the output tile and of the
 // intermediate chunk; fragments come from shared memory.
+#include <mutex>
+#include <set>
+#include <string>
+#include <tuple>
+
+#include "../../include/dmrg.h"
 #include "kernels.h"
 
 namespace dmrg {
@@ -238,13 +244,23 @@ __global__ void reduce_kernel(SigmaDev a) {
 
 }  // namespace
 
+void set_max_dynamic_smem(const void* fn, int bytes) {
+  static std::mutex mu;
+  static std::set<std::tuple<const void*, int, int>> done;  // (kernel, device, bytes)
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) throw Error(DMRG_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count({fn, dev, bytes})) return;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess)
+    throw Error(DMRG_ECUDA, std::string("cudaFuncSetAttribute(max dynamic shared memory): ") + cudaGetErrorString(e));
+  done.insert({fn, dev, bytes});
+}
+
 void launch_sigma_f64(const SigmaDev& a, int n_sm, cudaStream_t st) {
-  static bool attr = false;
   const int smem = (int)sizeof(Smem);
-  if (!attr) {
-    cudaFuncSetAttribute(sigma_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    attr = true;
-  }
+  set_max_dynamic_smem((const void*)sigma_f64_kernel, smem);
   int grid = 2 * n_sm;  // two resident CTAs per SM overlap one's loads with the other's products
   if (grid > a.n_items) grid = a.n_items;
   if (grid < 1) grid = 1;

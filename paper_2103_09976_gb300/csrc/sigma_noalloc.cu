@@ -41,7 +41,9 @@ SymbolAddrs g_addr[64];  // per device ordinal, filled on first use
 
 // Host code cannot use g_sigma_scratch directly (in host code it names a
 // host-side stand-in): look up its device address once per device, with
-// that device current.
+// that device current. The addresses stay valid for the life of the
+// device's primary context; the library must not be used across a reset of
+// that context (cudaDeviceReset) in the same process.
 SymbolAddrs device_addrs(int dev) {
   if (dev < 0 || dev >= 64) throw Error(DMRG_EINVAL, "device ordinal out of range for dmrg_sigma_noalloc");
   std::lock_guard<std::mutex> lk(g_mu);
@@ -61,21 +63,12 @@ SymbolAddrs device_addrs(int dev) {
   return a;
 }
 
-bool on_device(const void* p) {
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
-
 }  // namespace
 
 void sigma_noalloc(Context& c, Problem& p, const double* psi, double* sigma) {
   DMRG_CUDA(cudaSetDevice(c.device));
   if (!psi || !sigma) throw Error(DMRG_EINVAL, "psi and sigma must not be NULL");
-  if (!on_device(psi) || !on_device(sigma))
+  if (!is_device_ptr(psi, c.device) || !is_device_ptr(sigma, c.device))
     throw Error(DMRG_EINVAL, "dmrg_sigma_noalloc needs device pointers for psi and sigma");
   const size_t bytes = (size_t)p.psi_size * sizeof(double);
   const char* a0 = (const char*)psi;

@@ -745,14 +745,10 @@ void launch_split_psi(const double* psi, const PsiBlock* blocks, const TcPsiBloc
 }
 
 void launch_sigma_tc(const TcDev& a, int n_sm, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(sigma_tc_kernel<6, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    cudaFuncSetAttribute(sigma_tc_kernel<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    cudaFuncSetAttribute(sigma_tc_kernel<6, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    cudaFuncSetAttribute(sigma_tc_kernel<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    attr = true;
-  }
+  set_max_dynamic_smem((const void*)sigma_tc_kernel<6, false>, SMEM_BYTES);
+  set_max_dynamic_smem((const void*)sigma_tc_kernel<3, false>, SMEM_BYTES);
+  set_max_dynamic_smem((const void*)sigma_tc_kernel<6, true>, SMEM_BYTES);
+  set_max_dynamic_smem((const void*)sigma_tc_kernel<3, true>, SMEM_BYTES);
   int grid = n_sm < a.n_items ? n_sm : a.n_items;
   if (grid < 1) grid = 1;
   const bool prof = a.wait_prof != nullptr;

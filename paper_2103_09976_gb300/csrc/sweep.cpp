@@ -336,6 +336,10 @@ void transform(Context& c, const OpSet& EO, const double* enl_store, const Basis
 
 // Build (if needed) the two-site problem at bond `site`: enlarged blocks
 // L[site] x s_site and s_{site+1} x R[site+2], NC terms, sigma work list.
+bool sweep_problem_ready(const Context& c, int site) {
+  return c.sweep && c.prob && c.sweep->prob_site == site;
+}
+
 void sweep_problem(Context& c, int site) {
   SweepState& S = *c.sweep;
   if (site < 0 || site > S.K - 2) throw Error(DMRG_EINVAL, "site out of range (0 .. K-2)");
