@@ -11,7 +11,14 @@ order) over its CUDA-event duration, against cuBLAS DGEMM measured in the
 same run; mixed precision: algorithmic bytes (every stored operator element
 once as three bf16 slices, psi, sigma) over the kernel duration, against the
 measured HBM bandwidth.
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--M 2000] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--M 2000] [--impl ours|reference] [--replicas]
+
+With N > 1 ranks (torchrun, one GPU each) the sigma is split by the paper's
+sub-Hamiltonian partition (Sec. II.B): every rank stores only the operators
+of its sub-Hamiltonian (dmrg_load_synthetic_part, about 1/N of the store),
+computes its part of sigma, and one NCCL all-reduce of |psi| doubles per
+step sums the parts (strong scaling: the job does one full sigma per step).
+--replicas instead runs N independent full problems (weak scaling).
 """
 
 import argparse
@@ -42,6 +49,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--no-sweeps", action="store_true")
+    ap.add_argument("--replicas", action="store_true",
+                    help="N>1: N independent full problems instead of the sub-Hamiltonian split")
     return ap.parse_args()
 
 
@@ -204,6 +213,12 @@ def replica_value(flops_per_step, step_s, world):
     return world * flops_per_step / step_s / 1e12
 
 
+def split_value(flops_full, step_s):
+    """Whole-job throughput of the sub-Hamiltonian split: one full sigma per
+    step, its work divided among the ranks; step_s is the slowest rank's."""
+    return flops_full / step_s / 1e12
+
+
 def serve_section(n_req, device):
     """Davidson solves through the native serving loop: first a burst (all
     requests at t=0) to measure capacity, then a Poisson stream at 80% of it."""
@@ -260,18 +275,34 @@ def main():
     from synth import random_unit_vector
 
     left, right = workload(args.M)
+    split = world > 1 and not args.replicas
     ctx = capi.dmrg_create(device=local)
-    capi.dmrg_load_synthetic(ctx, K_ORB, 2 * K_ORB, N_EL, TWO_SZ, left, right, SEED)
+    if split:   # this rank's sub-Hamiltonian: its terms and only the operators they use
+        capi.dmrg_load_synthetic_part(ctx, K_ORB, 2 * K_ORB, N_EL, TWO_SZ, left, right, SEED, rank, world)
+    else:
+        capi.dmrg_load_synthetic(ctx, K_ORB, 2 * K_ORB, N_EL, TWO_SZ, left, right, SEED)
     info = capi.dmrg_get_sigma_info(ctx)
     n = info["psi_size"]
     x_h = random_unit_vector(n, SEED)
     x = torch.from_numpy(x_h).cuda()
     y = torch.zeros(n, dtype=torch.float64, device="cuda")
     stream = torch.cuda.ExternalStream(capi.dmrg_stream(ctx))
+    flops_full = info["flops"]
+    if split:   # the job's work per step: all ranks' parts of one sigma
+        t = torch.tensor([info["flops"]], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t)
+        flops_full = float(t.item())
+
+    def step(xin, yout):
+        """One sigma of the job: this rank's part, then (split) the sum over ranks."""
+        capi.dmrg_sigma(ctx, -1, xin, yout)
+        if split:
+            with torch.cuda.stream(stream):
+                dist.all_reduce(yout)
 
     tuned = capi.dmrg_autotune(ctx, -1)   # work-list split and order of the FP64 kernel
     for _ in range(max(3, args.warmup)):
-        capi.dmrg_sigma(ctx, -1, x, y)
+        step(x, y)
     torch.cuda.synchronize()
     clk = Clocks(local)
     clk.start()
@@ -282,10 +313,12 @@ def main():
     # timed steps: each sigma is one replay of its captured graph
     e0.record(stream)
     for _ in range(args.steps):
-        capi.dmrg_sigma(ctx, -1, x, y)
+        step(x, y)
     e1.record(stream)
     e1.synchronize()
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     step_s = e0.elapsed_time(e1) / 1e3 / args.steps
     # kernel durations for the roofline: the same steps launched directly
     # with CUDA events around each kernel on the library's stream
@@ -299,20 +332,38 @@ def main():
     if dist:
         step_s = world_max(step_s, dist, "cuda")
 
-    # end to end through the C ABI with pinned host buffers
+    # end to end with pinned host buffers: psi in, sigma out every step
     xp = torch.from_numpy(x_h).pin_memory()
     yp = torch.zeros(n, dtype=torch.float64).pin_memory()
-    capi.dmrg_sigma(ctx, -1, xp, yp)
+
+    def e2e_step():
+        if not split:   # the C ABI stages host buffers itself
+            capi.dmrg_sigma(ctx, -1, xp, yp)
+            return
+        with torch.cuda.stream(stream):
+            xd = xp.to("cuda", non_blocking=True)
+            yd = torch.empty_like(xd)
+        step(xd, yd)
+        with torch.cuda.stream(stream):
+            yp.copy_(yd, non_blocking=True)
+        stream.synchronize()
+
+    e2e_step()
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        capi.dmrg_sigma(ctx, -1, xp, yp)
+        e2e_step()
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    if dist:
+        e2e_s = world_max(e2e_s, dist, "cuda")
     ok = bool(np.allclose(yp.numpy(), y.cpu().numpy(), rtol=0, atol=1e-12 * float(y.abs().max())))
 
     # tensor-core sigma (bf16 slices) on the same context and psi
     flops = info["flops"]
     mixed = {}
+    mixed_precisions = () if split else (("bf16x3", capi.DMRG_BF16X3, 6, 6), ("bf16x2", capi.DMRG_BF16X2, 3, 6))
     y64 = y.clone()
     peaks = {}
     try:
@@ -321,7 +372,7 @@ def main():
         peaks = {}
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     bf16 = float(peaks.get("bf16_tflops", 1900.0))
-    for name, prec, nprod, bytes_per_elem in (("bf16x3", capi.DMRG_BF16X3, 6, 6), ("bf16x2", capi.DMRG_BF16X2, 3, 6)):
+    for name, prec, nprod, bytes_per_elem in mixed_precisions:
         capi.dmrg_set_precision(ctx, prec)
         capi.dmrg_sigma(ctx, -1, x, y)  # builds the bf16 operator slices
         capi.dmrg_sync(ctx)
@@ -357,15 +408,17 @@ def main():
     capi.dmrg_set_precision(ctx, capi.DMRG_FP64)
     peak64 = fp64_gemm_peak(torch)
     capi.dmrg_destroy(ctx)
-    serving = None if args.no_serve else serve_section(args.serve_requests, local)
+    serving = None if (args.no_serve or world > 1) else serve_section(args.serve_requests, local)
 
     kern_s = k_ms / 1e3 / max(1, k_n)
     achieved = flops / kern_s / 1e12
-    value = replica_value(flops, step_s, world)
+    value = split_value(flops_full, step_s) if split else replica_value(flops, step_s, world)
     out = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
            "warmup": max(3, args.warmup), "ms_per_step": step_s * 1e3, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": config(args.M),
+           "scaling": "strong" if split else "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": dict(config(args.M), parallelism=(f"sub-Hamiltonian split over {world} ranks, NCCL all-reduce "
+                                                       "of sigma" if split else
+                                                       (f"{world} replicas" if world > 1 else "1 GPU"))),
            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
                         "frac": achieved / peak64,
                         "traffic": F64_TRAFFIC_M2000 if args.M == 2000 else None,
@@ -377,7 +430,8 @@ def main():
                                        f"{bf16 * 1.25 / 2250.0:.3f} TFLOP/s",
                         "kernel_ms": kern_s * 1e3, "reduce_ms": r_ms / max(1, r_n),
                         "autotuned": {"items_per_sm": tuned[0], "per_task_cost": tuned[1], "tune_ms": tuned[2]}},
-           "e2e": {"value": flops / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 8 * n,
+           "e2e": {"value": (flops_full if split else world * flops) / e2e_s / 1e12, "unit": "TFLOP/s",
+                   "h2d_bytes_per_step": 8 * n,
                    "d2h_bytes_per_step": 8 * n, "matches_device_result": ok},
            "gpu_launches": 2 * args.steps,
            "mixed": mixed,

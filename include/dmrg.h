@@ -53,9 +53,11 @@ typedef enum {
 /* Arithmetic of the sigma products. FP64: plain double on the FP64 pipes.
  * BF16X3: every operand split into three bf16 slices x = hi + mid + lo
  * (24 significant bits); each GEMM is the sum of the 6 slice products with
- * i + j <= 2 on the tensor cores (tcgen05, FP32 accumulation); partial sums
- * of at most 32 terms are added in FP64. BF16X2: the first two slices and
- * the 3 products with i + j <= 1 (16 significant bits). */
+ * i + j <= 2 on the tensor cores (tcgen05, FP32 accumulation, correction
+ * products before the main ones); every FP32 accumulation of a sigma tile
+ * spans at most dmrg_opts.tc_chain main MMA steps of 16 along K before it is
+ * added into a running sum of FP32 pairs (about 48 bits). BF16X2: the first
+ * two slices and the 3 products with i + j <= 1 (16 significant bits). */
 typedef enum { DMRG_FP64 = 0, DMRG_BF16X2 = 1, DMRG_BF16X3 = 2 } dmrg_prec;
 
 typedef struct {
@@ -81,9 +83,15 @@ typedef struct {
                                   operators on the left, normal ones on the right); blocks switch
                                   form by the normal-to-complementary transformation at the cut.
                                   Takes effect at dmrg_build_blocks. */
+  int tc_chain;                /* tensor-core sigma: main (hi x hi) MMA steps of 16 along K that one
+                                  FP32 accumulation of a sigma tile may hold before it is added into
+                                  the running sum (at least one term per accumulation). The FP32
+                                  rounding error of sigma grows about linearly with it. 0 = default
+                                  (8 for BF16X3; for BF16X2 one accumulation per 64-column half of
+                                  every unit of stacked terms); -1 = that unbounded setting for both. */
 } dmrg_opts;
 
-/* Fill *o with defaults: FP64, 24, 200, 0, 0.0, seed 0, device 0, graphs 1, mixed_cut -1. */
+/* Fill *o with defaults: FP64, 24, 200, 0, 0.0, seed 0, device 0, graphs 1, mixed_cut -1, tc_chain 0. */
 void dmrg_default_opts(dmrg_opts* o);
 
 /* Create a context on opts->device (NULL opts = defaults). *out is NULL on failure. */
@@ -127,6 +135,39 @@ dmrg_status dmrg_sync(dmrg_ctx* ctx);
 dmrg_status dmrg_load_synthetic(dmrg_ctx* ctx, int n_left_modes, int n_modes, int N, int two_sz,
                                 int n_sec_left, const int* sec_left, int n_sec_right,
                                 const int* sec_right, unsigned long long seed);
+
+/*
+ * One sub-Hamiltonian of the synthetic middle-bond problem, for running the
+ * sigma across processes or GPUs (Sec. II.B, Eqs. sum-h, sub-h, proc-def and
+ * proc-def-nc: H = sum_p H^(p), the NC terms assigned to rank p by their
+ * left-block indices - one index i -> i mod n_ranks, an index pair i <= j ->
+ * j(j+1)/2 + i mod n_ranks, H_L x 1 and 1 x H_R -> rank 0). Arguments as
+ * dmrg_load_synthetic, plus 0 <= rank < n_ranks. The context keeps only
+ * rank's terms and stores only the operators those terms use, each block
+ * drawn with the same counters as in the full store (so the values equal
+ * dmrg_load_synthetic's); every operator belongs to exactly one rank, so
+ * each rank holds about 1/n_ranks of the operator memory. dmrg_sigma on this
+ * context then returns sigma^(rank) = H_eff^(rank) psi; the sum over all
+ * ranks (one all-reduce of psi_size doubles) is the full sigma.
+ * dmrg_sigma_part is refused on such a context. n_ranks = 1 is
+ * dmrg_load_synthetic.
+ */
+dmrg_status dmrg_load_synthetic_part(dmrg_ctx* ctx, int n_left_modes, int n_modes, int N, int two_sz,
+                                     int n_sec_left, const int* sec_left, int n_sec_right,
+                                     const int* sec_right, unsigned long long seed, int rank, int n_ranks);
+
+/*
+ * Host-only description of the partition above (no GPU or context needed):
+ * for rank of n_ranks, the number of its terms, the operator elements it
+ * stores, the elements of the full store (any output may be NULL), and the
+ * positions of its terms in the full NC term list (the first max_ids of them
+ * into term_ids; max_ids may be 0). Errors: DMRG_EINVAL for malformed
+ * arguments, message via dmrg_last_error(NULL).
+ */
+dmrg_status dmrg_partition_info(int n_left_modes, int n_modes, int N, int two_sz, int n_sec_left,
+                                const int* sec_left, int n_sec_right, const int* sec_right, int rank,
+                                int n_ranks, long long* n_terms, long long* op_elements, long long* total_elements,
+                                int* term_ids, int max_ids);
 
 /*
  * Layout of psi at bond `site` (site = -1 for a synthetic context; for a

@@ -22,6 +22,7 @@ SOURCES = [
     "generate.cu",
     "sigma_f64.cu",
     "sigma_tc.cu",
+    "sigma_small.cu",
     "sigma_noalloc.cu",
     "davidson.cu",
     "davidson_host.cpp",

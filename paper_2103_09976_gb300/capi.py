@@ -24,7 +24,7 @@ class dmrg_opts(ctypes.Structure):
     _fields_ = [("sigma_prec", ctypes.c_int), ("dav_max_space", ctypes.c_int),
                 ("dav_max_iter", ctypes.c_int), ("keep_one_per_q", ctypes.c_int),
                 ("noise", ctypes.c_double), ("seed", ctypes.c_ulonglong), ("device", ctypes.c_int),
-                ("graphs", ctypes.c_int), ("mixed_cut", ctypes.c_int)]
+                ("graphs", ctypes.c_int), ("mixed_cut", ctypes.c_int), ("tc_chain", ctypes.c_int)]
 
 
 class dmrg_sigma_info(ctypes.Structure):
@@ -67,6 +67,9 @@ SIGNATURES = {
     "dmrg_stream": (_P, [_P]),
     "dmrg_set_precision": (_I, [_P, _I]),
     "dmrg_load_synthetic": (_I, [_P, _I, _I, _I, _I, _I, _P, _I, _P, _ULL]),
+    "dmrg_load_synthetic_part": (_I, [_P, _I, _I, _I, _I, _I, _P, _I, _P, _ULL, _I, _I]),
+    "dmrg_partition_info": (_I, [_I, _I, _I, _I, _I, _P, _I, _P, _I, _I, ctypes.POINTER(_LL),
+                                 ctypes.POINTER(_LL), ctypes.POINTER(_LL), _P, _I]),
     "dmrg_psi_layout": (_I, [_P, _I, ctypes.POINTER(_I), _P, _P, _P, _P, ctypes.POINTER(_LL)]),
     "dmrg_get_sigma_info": (_I, [_P, _I, ctypes.POINTER(dmrg_sigma_info)]),
     "dmrg_sigma": (_I, [_P, _I, _P, _P]),
@@ -175,6 +178,26 @@ def dmrg_load_synthetic(ctx, n_left_modes, n_modes, N, two_sz, sec_left, sec_rig
     R = _sec_array(sec_right)
     _check(ctx, lib().dmrg_load_synthetic(ctx, n_left_modes, n_modes, N, two_sz, len(L), _ptr(L),
                                           len(R), _ptr(R), int(seed)))
+
+
+def dmrg_load_synthetic_part(ctx, n_left_modes, n_modes, N, two_sz, sec_left, sec_right, seed, rank, n_ranks):
+    L = _sec_array(sec_left)
+    R = _sec_array(sec_right)
+    _check(ctx, lib().dmrg_load_synthetic_part(ctx, n_left_modes, n_modes, N, two_sz, len(L), _ptr(L),
+                                               len(R), _ptr(R), int(seed), int(rank), int(n_ranks)))
+
+
+def dmrg_partition_info(n_left_modes, n_modes, N, two_sz, sec_left, sec_right, rank, n_ranks, max_ids=0):
+    """Host-only: dict(n_terms, op_elements, total_elements, term_ids) of sub-Hamiltonian rank."""
+    L = _sec_array(sec_left)
+    R = _sec_array(sec_right)
+    nt, oe, te = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+    ids = np.zeros(max(1, max_ids), dtype=np.int32)
+    _check(None, lib().dmrg_partition_info(n_left_modes, n_modes, N, two_sz, len(L), _ptr(L), len(R), _ptr(R),
+                                           int(rank), int(n_ranks), ctypes.byref(nt), ctypes.byref(oe),
+                                           ctypes.byref(te), _ptr(ids), int(max_ids)))
+    return {"n_terms": nt.value, "op_elements": oe.value, "total_elements": te.value,
+            "term_ids": ids[:min(max_ids, nt.value)]}
 
 
 def dmrg_psi_layout(ctx, site=-1):

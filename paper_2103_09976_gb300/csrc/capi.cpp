@@ -120,7 +120,7 @@ static_assert(sizeof(TcItem) == sizeof(Item), "reduction reads TcItem as Item");
 
 void prepare_tc(Context& c, Problem& p) {
   cudaStream_t st = c.stream;
-  build_tc_plan(p.blocks, p.L, p.R, p.wl, p.tc, c.n_sm * 4, 32);
+  build_tc_plan(p.blocks, p.L, p.R, p.wl, p.tc, TcShape{c.n_sm * 4});
   const size_t split_bytes = (size_t)p.tc.n_tiles * 384;
   size_t freeb = 0, totb = 0;
   DMRG_CUDA(cudaMemGetInfo(&freeb, &totb));
@@ -149,8 +149,9 @@ void prepare_tc(Context& c, Problem& p) {
   launch_split_ops(p.store.as<double>(), d_jobs.as<SplitJob>(), (long long)jobs.size(), p.split.p, st);
   DMRG_CUDA(cudaGetLastError());
   p.d_tc_recs.upload(p.tc.recs, st);
-  p.d_tc_item_rec.upload(p.tc.item_rec, st);
   p.d_tc_items.upload(p.tc.items, st);
+  p.d_tc_small.upload(p.tc.small, st);
+  p.d_tc_small_sched.upload(p.tc.small_schedule, st);
   p.d_tc_groups.upload(p.tc.groups, st);
   p.d_tc_sched.upload(p.tc.schedule, st);
   p.d_tc_pblk.upload(p.tc.psi, st);
@@ -184,14 +185,19 @@ static void run_sigma_tc(Context& c, Problem& p, const double* d_psi, double* d_
   TcDev t;
   t.op = p.split.p;
   t.psi = p.psi_split.p;
-  t.recs = p.d_tc_recs.as<TcRec>();
-  t.item_rec = p.d_tc_item_rec.as<int>();
+  t.recs = p.d_tc_recs.as<TcUnitRec>();
+  t.items = p.d_tc_items.as<TcItem>();
   t.schedule = p.d_tc_sched.as<int>();
-  t.n_items = (int)p.tc.items.size();
+  t.n_items = (int)p.tc.schedule.size();
   t.counter = p.d_counter.as<unsigned int>();
   t.scratch = p.d_tc_scratch.as<double>();
   t.err = p.d_err.as<int>();
   t.nprod = c.opts.sigma_prec == DMRG_BF16X3 ? 6 : 3;
+  // by default BF16X3 bounds each FP32 accumulation to 8 main MMA steps (128
+  // products along K); BF16X2, whose slices carry 16 bits, flushes once per
+  // half of every unit
+  const int chain = c.opts.tc_chain;
+  t.max_chain = chain > 0 ? chain : (chain == 0 && c.opts.sigma_prec == DMRG_BF16X3 ? 8 : 0);
   t.wait_prof = nullptr;
   if (c.prof.on && c.prof.waits) {
     if (!c.d_wait_prof.p) {
@@ -203,6 +209,16 @@ static void run_sigma_tc(Context& c, Problem& p, const double* d_psi, double* d_
   DMRG_CUDA(cudaMemsetAsync(p.d_counter.p, 0, sizeof(unsigned int), c.stream));
   {
     ProfScope ps_(c.prof, 0, c.stream);
+    SmallDev sd;
+    sd.store = p.store.as<double>();
+    sd.psi = d_psi;
+    sd.blocks = p.d_blocks.as<PsiBlock>();
+    sd.terms = p.d_tc_small.as<SmallTerm>();
+    sd.items = p.d_tc_items.as<TcItem>();
+    sd.schedule = p.d_tc_small_sched.as<int>();
+    sd.n_items = (int)p.tc.small_schedule.size();
+    sd.scratch = p.d_tc_scratch.as<double>();
+    launch_sigma_small(sd, c.n_sm, c.stream);
     launch_sigma_tc(t, c.n_sm, c.stream);
   }
   DMRG_CUDA(cudaGetLastError());
@@ -448,9 +464,19 @@ static void build_synthetic_tables(Problem& p, int nL, int n, int N, int two_sz,
 }
 
 void load_synthetic(Context& c, int nL, int n, int N, int two_sz, const Basis& bL, const Basis& bR,
-                    unsigned long long seed) {
+                    unsigned long long seed, int rank, int n_ranks) {
   auto p = std::make_unique<Problem>();
   build_synthetic_tables(*p, nL, n, N, two_sz, bL, bR);
+  // canonical store offset of every block: the generator's counter base
+  std::vector<long long> canon;
+  if (n_ranks > 1) {  // one sub-Hamiltonian: its terms and only the operators they use
+    Partition part;
+    partition_nc(p->L, p->R, nL, n, rank, n_ranks, part);
+    p->terms = std::move(part.terms);
+    canon = std::move(part.canon_off);
+    p->part_rank = rank;
+    p->part_n = n_ranks;
+  }
   long long elems = p->L.elements + p->R.elements;
   size_t freeb = 0, totb = 0;
   DMRG_CUDA(cudaMemGetInfo(&freeb, &totb));
@@ -464,7 +490,10 @@ void load_synthetic(Context& c, int nL, int n, int N, int two_sz, const Basis& b
   std::vector<GenBlock> gb;
   for (const OpSet* s : {&p->L, &p->R})
     for (const OpDesc& o : s->ops)
-      for (const OpBlock& b : o.blocks) gb.push_back({b.off, b.rows, b.cols, o.sym ? 1 : 0, 0});
+      for (const OpBlock& b : o.blocks) {
+        const long long ctr = canon.empty() ? b.off : canon[gb.size()];
+        gb.push_back({b.off, ctr, b.rows, b.cols, o.sym ? 1 : 0, 0});
+      }
   DevBuf d_gb;
   d_gb.upload(gb, c.stream);
   launch_gen_blocks(p->store.as<double>(), d_gb.as<GenBlock>(), (long long)gb.size(), (uint64_t)seed, c.stream);
@@ -518,6 +547,7 @@ void dmrg_default_opts(dmrg_opts* o) {
   o->device = 0;
   o->graphs = 1;
   o->mixed_cut = -1;
+  o->tc_chain = 0;
 }
 
 dmrg_status dmrg_create(dmrg_ctx** out, const dmrg_opts* opts) {
@@ -536,6 +566,7 @@ dmrg_status dmrg_create(dmrg_ctx** out, const dmrg_opts* opts) {
     if (o.keep_one_per_q != 0 && o.keep_one_per_q != 1) throw Error(DMRG_EINVAL, "keep_one_per_q must be 0 or 1");
     if (!(o.noise >= 0.0) || !std::isfinite(o.noise)) throw Error(DMRG_EINVAL, "noise must be finite and >= 0");
     if (o.mixed_cut < -1) throw Error(DMRG_EINVAL, "mixed_cut must be -1 (NC everywhere) or >= 0");
+    if (o.tc_chain < -1) throw Error(DMRG_EINVAL, "tc_chain must be -1 (unbounded), 0 (default) or >= 1");
     if (o.sigma_prec < DMRG_FP64 || o.sigma_prec > DMRG_BF16X3)
       throw Error(DMRG_EINVAL, "unknown sigma precision");
     int ndev = 0;
@@ -588,7 +619,39 @@ dmrg_status dmrg_load_synthetic(dmrg_ctx* ctx, int n_left_modes, int n_modes, in
     Context& c = ctx->c;
     DMRG_CUDA(cudaSetDevice(c.device));
     load_synthetic(c, n_left_modes, n_modes, N, two_sz, parse_sectors(n_sec_left, sec_left),
-                   parse_sectors(n_sec_right, sec_right), seed);
+                   parse_sectors(n_sec_right, sec_right), seed, 0, 1);
+  });
+}
+
+dmrg_status dmrg_load_synthetic_part(dmrg_ctx* ctx, int n_left_modes, int n_modes, int N, int two_sz,
+                                     int n_sec_left, const int* sec_left, int n_sec_right,
+                                     const int* sec_right, unsigned long long seed, int rank, int n_ranks) {
+  if (!ctx) return DMRG_EINVAL;
+  return guarded(ctx, [&] {
+    if (n_ranks < 1 || rank < 0 || rank >= n_ranks) throw Error(DMRG_EINVAL, "need 0 <= rank < n_ranks");
+    Context& c = ctx->c;
+    DMRG_CUDA(cudaSetDevice(c.device));
+    load_synthetic(c, n_left_modes, n_modes, N, two_sz, parse_sectors(n_sec_left, sec_left),
+                   parse_sectors(n_sec_right, sec_right), seed, rank, n_ranks);
+  });
+}
+
+dmrg_status dmrg_partition_info(int n_left_modes, int n_modes, int N, int two_sz, int n_sec_left,
+                                const int* sec_left, int n_sec_right, const int* sec_right, int rank,
+                                int n_ranks, long long* n_terms, long long* op_elements, long long* total_elements,
+                                int* term_ids, int max_ids) {
+  return guarded(nullptr, [&] {
+    if (n_ranks < 1 || rank < 0 || rank >= n_ranks) throw Error(DMRG_EINVAL, "need 0 <= rank < n_ranks");
+    if (max_ids < 0 || (max_ids > 0 && !term_ids)) throw Error(DMRG_EINVAL, "term_ids must hold max_ids entries");
+    Problem p;
+    build_synthetic_tables(p, n_left_modes, n_modes, N, two_sz, parse_sectors(n_sec_left, sec_left),
+                           parse_sectors(n_sec_right, sec_right));
+    if (total_elements) *total_elements = p.L.elements + p.R.elements;
+    Partition part;
+    partition_nc(p.L, p.R, n_left_modes, n_modes, rank, n_ranks, part);
+    if (n_terms) *n_terms = (long long)part.terms.size();
+    if (op_elements) *op_elements = part.elements;
+    for (int i = 0; i < max_ids && i < (int)part.term_ids.size(); ++i) term_ids[i] = part.term_ids[i];
   });
 }
 
@@ -697,6 +760,9 @@ dmrg_status dmrg_sigma_part(dmrg_ctx* ctx, int site, int rank, int n_ranks, cons
     if (n_ranks < 1 || rank < 0 || rank >= n_ranks) throw Error(DMRG_EINVAL, "need 0 <= rank < n_ranks");
     DMRG_CUDA(cudaSetDevice(c.device));
     Problem& p = need_problem(c, site);
+    if (p.part_n > 1)
+      throw Error(DMRG_EINVAL, "the context already holds one sub-Hamiltonian (dmrg_load_synthetic_part); "
+                               "use dmrg_sigma");
     sigma_call(c, p, psi, sigma, [&](const double* x, double* y) { run_sigma_part(c, p, rank, n_ranks, x, y); });
   });
 }

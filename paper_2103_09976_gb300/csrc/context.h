@@ -130,6 +130,7 @@ struct DevWork {
 struct Problem {
   int nL = 0, n = 0;
   bool cn = false;           // terms of the CN partition (App. B, Eq. h-cn) instead of NC
+  int part_rank = 0, part_n = 1;  // sub-Hamiltonian held (Sec. II.B); part_n = 1: the whole H
   QN Q;
   OpSet L, R;
   std::vector<PsiBlock> blocks;
@@ -148,7 +149,7 @@ struct Problem {
   DevBuf dav_V, dav_AV, dav_diag, dav_x, dav_ax, dav_r, dav_t, dav_partial, dav_H, dav_w, dav_Y, dav_s;
   DevBuf d_dstart, d_dtask;
   DevBuf split, psi_split;         // slice-interleaved bf16 tiles of the operators / of psi
-  DevBuf d_tc_recs, d_tc_item_rec, d_tc_items, d_tc_groups, d_tc_sched, d_tc_pblk, d_tc_scratch, d_err;
+  DevBuf d_tc_recs, d_tc_items, d_tc_small, d_tc_small_sched, d_tc_groups, d_tc_sched, d_tc_pblk, d_tc_scratch, d_err;
   GraphCache graphs;
   // FP64 work-list tuning (dmrg_autotune): items per SM and per-task cost term
   int items_per_sm = 8;
@@ -223,8 +224,10 @@ struct Context {
 void release_context_buffers(Context& c);
 void prepare_worklist(Context& c, Problem& p);
 Basis parse_sectors(int n, const int* s);
+// Synthetic middle-bond problem; with n_ranks > 1 only sub-Hamiltonian
+// `rank` (its terms and the operators they use).
 void load_synthetic(Context& c, int nL, int n, int N, int two_sz, const Basis& bL, const Basis& bR,
-                    unsigned long long seed);
+                    unsigned long long seed, int rank, int n_ranks);
 // Device bytes a synthetic problem needs for one Davidson solve (an upper estimate).
 long long synthetic_footprint(int nL, int n, int N, int two_sz, const Basis& bL, const Basis& bR, int prec,
                               int dav_space, int n_sm);

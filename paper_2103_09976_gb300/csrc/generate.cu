@@ -34,7 +34,7 @@ __global__ void gen_blocks_kernel(double* __restrict__ store, const GenBlock* __
     for (long long e = threadIdx.x; e < n; e += blockDim.x) {
       int i = (int)(e / gb.cols), j = (int)(e - (long long)i * gb.cols);
       long long idx = (gb.sym && i > j) ? (long long)j * gb.cols + i : e;
-      store[gb.off + e] = sm_normal(key, (uint64_t)(gb.off + idx));
+      store[gb.off + e] = sm_normal(key, (uint64_t)(gb.ctr + idx));
     }
   }
 }

@@ -16,10 +16,11 @@ namespace dmrg {
 void set_max_dynamic_smem(const void* fn, int bytes);
 
 // ---------------------------------------------------------------- generator
-// One block of a synthetic operator: entries N(0,1) from counter off + i*cols + j
-// (symmetric blocks use the counter of (min(i,j), max(i,j))).
+// One block of a synthetic operator, written at element offset `off`: entries
+// N(0,1) from counter ctr + i*cols + j (symmetric blocks use the counter of
+// (min(i,j), max(i,j))); ctr is the block's offset in the full canonical store.
 struct GenBlock {
-  long long off;
+  long long off, ctr;
   int rows, cols;
   int sym, pad;
 };
@@ -62,16 +63,30 @@ struct SplitJob {
 struct TcDev {
   const void* op;             // operator tiles, slice-interleaved (3 x 128 B per tile position)
   const void* psi;            // psi tiles, same layout
-  const TcRec* recs;          // unit records, grouped by item
-  const int* item_rec;        // records of item i: [item_rec[i], item_rec[i+1])
+  const TcUnitRec* recs;      // unit records, grouped by item
+  const TcItem* items;        // records of item i: [items[i].r_begin, items[i].r_end)
   const int* schedule;        // item order, most expensive first
   int n_items;
   unsigned int* counter;      // next item to take; zero at launch
   double* scratch;
   int* err;                   // nonzero after a bounded wait gave up
   int nprod;                  // 6 (three slices) or 3 (two slices)
+  int max_chain;              // main MMA steps per FP32 accumulation (flush group); <= 0: one group per half
   unsigned long long* wait_prof;  // optional [17]: wait cycles per barrier kind, total cycles
 };
+
+// Small classes of the mixed-precision sigma on the CUDA cores (see TC_SMALL_MAX).
+struct SmallDev {
+  const double* store;        // FP64 operator store
+  const double* psi;          // psi (FP64, the layout of `blocks`)
+  const PsiBlock* blocks;
+  const SmallTerm* terms;
+  const TcItem* items;        // kind-1 items index terms
+  const int* schedule;        // kind-1 items, most expensive first
+  int n_items;
+  double* scratch;            // partial tiles (item slots)
+};
+void launch_sigma_small(const SmallDev& a, int n_sm, cudaStream_t st);
 
 void launch_split_ops(const double* store, const SplitJob* jobs, long long njobs, void* out, cudaStream_t st);
 void launch_split_psi(const double* psi, const PsiBlock* blocks, const TcPsiBlock* pb, int nblk, void* out,

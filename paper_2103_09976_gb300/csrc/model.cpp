@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <functional>
 #include <numeric>
 #include <thread>
@@ -163,6 +164,43 @@ std::vector<int> cn_term_ranks(int nL, int n, int n_ranks) {
   for (int p = nL; p < n; ++p)
     for (int q = nL; q < n; ++q) r.push_back(two(p, q));
   return r;
+}
+
+void partition_nc(OpSet& L, OpSet& R, int nL, int n, int rank, int n_ranks, Partition& out) {
+  if (n_ranks < 1 || rank < 0 || rank >= n_ranks) throw Error(1, "need 0 <= rank < n_ranks");
+  const std::vector<Term> all = nc_terms(nL, n);
+  const std::vector<int> rk = nc_term_ranks(nL, n, n_ranks);
+  if (rk.size() != all.size()) throw Error(1, "internal: term rank count");
+  out = Partition();
+  std::vector<char> useL(L.ops.size(), 0), useR(R.ops.size(), 0);
+  for (size_t t = 0; t < all.size(); ++t) {
+    if (rk[t] != rank) continue;
+    out.terms.push_back(all[t]);
+    out.term_ids.push_back((int)t);
+    if (all[t].opL >= 0) useL.at(all[t].opL) = 1;
+    if (all[t].opR >= 0) useR.at(all[t].opR) = 1;
+  }
+  long long cur = 0;
+  auto relayout = [&](OpSet& S, const std::vector<char>& use) {
+    const long long start = cur;
+    for (size_t k = 0; k < S.ops.size(); ++k) {
+      OpDesc& o = S.ops[k];
+      if (!use[k]) {
+        o.blocks.clear();
+        std::fill(o.by_qin.begin(), o.by_qin.end(), -1);
+        continue;
+      }
+      for (OpBlock& b : o.blocks) {
+        out.canon_off.push_back(b.off);
+        b.off = cur;
+        cur += (long long)b.rows * b.cols;
+      }
+    }
+    S.elements = cur - start;
+  };
+  relayout(L, useL);
+  relayout(R, useR);
+  out.elements = cur;
 }
 
 std::vector<PsiBlock> psi_layout(const Basis& L, const Basis& R, QN Qtot, long long* size) {
@@ -389,39 +427,22 @@ void build_items(const std::vector<PsiBlock>& blocks, WorkList& wl, const TileSh
 namespace dmrg {
 
 static inline int ceil8(int x) { return (x + 7) / 8; }
-
-int tc_k1_tiles(const TcTask& t, const TcPsiBlock& ib, int r0) {
-  if (ib.R8 > 4 || ib.C8 > 8) return 0;               // m <= 32, n <= 64
-  const bool tA = t.flags & 1;
-  const int rg0 = r0 / 8;
-  int ol = tA ? t.aR8 * std::min(16, t.aC8 - rg0)      // K groups x M groups
-              : std::min(16, t.aR8 - rg0) * t.aC8;     // M groups x K groups
-  return ol + ib.R8 * ib.C8;
-}
-
-int tc_k2_tiles(const TcTask& t, int c0) {  // tiles of the right operand for one task
-  const bool tB = t.flags & 2;
-  const int cg0 = c0 / 8;
-  return tB ? t.bR8 * std::min(16, t.bC8 - cg0) : std::min(16, t.bR8 - cg0) * t.bC8;
-}
+static inline int up16(int x) { return (x + 15) & ~15; }
 
 void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const OpSet& R,
-                   const WorkList& wl, TcPlan& plan, int want_items, int seg_tasks) {
+                   const WorkList& wl, TcPlan& plan, const TcShape& shape) {
   plan = TcPlan();
-  // element offset -> tiled block: offsets grow in store order, so a sorted
-  // array and binary search map them
+  // tiles of every stored block, in store order, then identity blocks
   std::vector<long long> offs;
   long long tile = 0;
   for (const OpSet* s : {&L, &R})
-    for (const OpDesc& o : s->ops) {
-      plan.op_first.push_back((long long)plan.opblocks.size());
+    for (const OpDesc& o : s->ops)
       for (const OpBlock& b : o.blocks) {
         TcBlock t{tile, ceil8(b.rows), ceil8(b.cols)};
         tile += (long long)t.R8 * t.C8;
         plan.opblocks.push_back(t);
         offs.push_back(b.off);
       }
-    }
   if (!std::is_sorted(offs.begin(), offs.end())) throw Error(1, "internal: operator blocks out of store order");
   auto find_off = [&](long long off) {  // index of the stored block at element offset off, or -1
     const auto it = std::lower_bound(offs.begin(), offs.end(), off);
@@ -437,7 +458,7 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
     tile += (long long)t.R8 * t.C8;
     plan.identR.push_back(t);
   }
-  plan.n_tiles = tile + 64;  // slack: descriptor reads past the last tile stay in bounds
+  plan.n_tiles = tile + 64;  // slack: operand reads past the last tile stay in bounds
   long long pt = 0;
   for (const PsiBlock& b : blocks) {
     TcPsiBlock p{pt, 2 * ((b.mL + 15) / 16), ceil8(b.mR), b.mL, b.mR};
@@ -445,15 +466,20 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
     plan.psi.push_back(p);
   }
   plan.psi_tiles = pt + 64;
-  // base task records (identity factors made explicit); build_tasks names
-  // each task's stored blocks by index, else they are looked up by offset
+
+  // one record per task: its stored blocks (identity factors made explicit)
+  struct Base {
+    long long a_tile, b_tile;
+    int aR8, aC8, bR8, bC8;
+    int in_blk, flags;
+    float scale;
+    int task;
+  };
   const bool have_idx = wl.task_ablk.size() == wl.tasks.size() && wl.task_bblk.size() == wl.tasks.size();
-  // Output blocks are independent: contiguous block ranges of about equal
-  // task counts are handled by up to 8 threads (base records, per-block task
-  // order, items and units into parts with local indices); the parts are
-  // joined in block order with their task / unit / item / scratch offsets,
-  // so the plan is the same as one pass over the blocks.
   const size_t nblk = blocks.size();
+  // output blocks are independent: contiguous block ranges of about equal
+  // task counts are planned by up to 8 threads and joined in block order,
+  // so the plan is the same as one pass over the blocks
   const int nparts = (int)std::min<size_t>(8, std::max<size_t>(1, std::min<size_t>(std::thread::hardware_concurrency(),
                                                                                      wl.tasks.size() / 100000)));
   std::vector<size_t> bstart(nparts + 1, nblk);
@@ -473,7 +499,7 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
     for (int j = 0; j < nparts; ++j) pool.emplace_back(fn, j);
     for (auto& x : pool) x.join();
   };
-  std::vector<TcTask> base(wl.tasks.size());
+  std::vector<Base> base(wl.tasks.size());
   std::vector<char> bad(nparts, 0);
   in_parallel([&](int j) {
     for (int t = wl.out_start[bstart[j]]; t < wl.out_start[bstart[j + 1]]; ++t) {
@@ -481,18 +507,16 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
       const PsiBlock& in = blocks[k.in_blk];
       TcBlock a = plan.identL[in.qL], b = plan.identR[in.qR];
       if (k.aoff >= 0) {
-        const int i = have_idx ? wl.task_ablk[t] : -1;
-        const int f = have_idx ? i : find_off(k.aoff);
+        const int f = have_idx ? wl.task_ablk[t] : find_off(k.aoff);
         if (f < 0 || f >= (int)offs.size() || offs[f] != k.aoff) bad[j] = 1;
         else a = plan.opblocks[f];
       }
       if (k.boff >= 0) {
-        const int i = have_idx ? wl.task_bblk[t] : -1;
-        const int f = have_idx ? i : find_off(k.boff);
+        const int f = have_idx ? wl.task_bblk[t] : find_off(k.boff);
         if (f < 0 || f >= (int)offs.size() || offs[f] != k.boff) bad[j] = 1;
         else b = plan.opblocks[f];
       }
-      TcTask x{};
+      Base x;
       x.a_tile = a.tile;
       x.aR8 = a.R8;
       x.aC8 = a.C8;
@@ -502,265 +526,239 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
       x.in_blk = k.in_blk;
       x.flags = (k.aoff >= 0 ? (k.flags & 1) : 0) | (k.boff >= 0 ? (k.flags & 2) : 0);
       x.scale = (float)k.scale;
+      x.task = t;
       base[t] = x;
-    }
-    // order tasks of each output block by (right transposed, input block, left
-    // transposed): packed units then share the layout of their second product
-    // and consecutive tasks share psi tiles
-    std::vector<int> idx;
-    std::vector<TcTask> tmp;
-    for (size_t ob = bstart[j]; ob < bstart[j + 1]; ++ob) {
-      const int t0 = wl.out_start[ob], t1 = wl.out_start[ob + 1];
-      idx.resize(t1 - t0);
-      std::iota(idx.begin(), idx.end(), t0);
-      std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
-        const int kx = ((base[x].flags >> 1) & 1), ky = ((base[y].flags >> 1) & 1);
-        if (kx != ky) return kx < ky;
-        if (base[x].in_blk != base[y].in_blk) return base[x].in_blk < base[y].in_blk;
-        return (base[x].flags & 1) < (base[y].flags & 1);
-      });
-      tmp.clear();
-      for (int i : idx) tmp.push_back(base[i]);
-      std::copy(tmp.begin(), tmp.end(), base.begin() + t0);
     }
   });
   for (char x : bad)
     if (x) throw Error(1, "internal: a task names no stored block");
-  // MMA work of a task on one 128 x 128 tile (rows padded to 128)
-  auto cost = [&](const TcTask& k) {
-    const TcPsiBlock& in = plan.psi[k.in_blk];
-    double n16 = 16.0 * ((in.n + 15) / 16), m16 = 8.0 * in.R8;
-    return 128.0 * n16 * m16 + 128.0 * n16 * 128.0 + 4096.0;  // + fixed per-task overhead
+
+  // MMA multiply-adds of one slice product (rows padded to 128, N and K to 16)
+  auto unit_macs = [&](int G, int tn, int m, int n) {
+    double s1 = 0, s2 = 0;
+    for (int c = 0; c < n; c += 128) s1 += 128.0 * up16(std::min(128, n - c)) * up16(m);
+    for (int c = 0; c < n; c += 64) s2 += 128.0 * up16(tn) * up16(std::min(64, n - c));
+    return s1 + G * s2;
   };
+  const double unit_overhead = 128.0 * 128 * 64;  // fixed cost of a unit in the item split
   double total = 0;
-  for (size_t b = 0; b < blocks.size(); ++b) {
-    int ntile = ((blocks[b].mL + 127) / 128) * ((blocks[b].mR + 127) / 128);
-    for (int t = wl.out_start[b]; t < wl.out_start[b + 1]; ++t) total += ntile * cost(base[t]);
-  }
-  const double target = total / std::max(1, want_items);
-  struct Part {
-    std::vector<TcTask> tasks;
-    std::vector<TcUnit> units;
-    std::vector<TcItem> items;
-    std::vector<Group> groups;
-    std::vector<double> icost;
-    long long scratch = 0;
-  };
-  auto plan_block = [&](size_t b, Part& P) {
+  for (size_t b = 0; b < nblk; ++b) {
     const PsiBlock& ob = blocks[b];
-    const int t0 = wl.out_start[b], t1 = wl.out_start[b + 1];
     for (int r0 = 0; r0 < ob.mL; r0 += 128)
       for (int c0 = 0; c0 < ob.mR; c0 += 128) {
-        const int nr = std::min(128, ob.mL - r0), nc = std::min(128, ob.mR - c0);
-        Group g{(int)b, r0, nr, c0, nc, (int)P.items.size(), 0, 0};
-        int t = t0;
-        do {  // one item per iteration (at least one, even with no tasks)
-          TcItem it{(int)b, r0, nr, c0, nc, (int)P.units.size(), 0, 0, P.scratch};
-          const int item_idx = (int)P.items.size();
-          double acc = 0;
-          int seg = 0, seg_first_unit = (int)P.units.size();
-          bool first_seg = true;
-          auto end_segment = [&]() {
-            if (P.units.size() > (size_t)seg_first_unit) {
-              P.units.back().flags |= UNIT_ENDS_SEGMENT | (first_seg ? UNIT_FIRST_SEGMENT : 0);
-              first_seg = false;
-            }
-            seg = 0;
-            seg_first_unit = (int)P.units.size();
-          };
-          while (t < t1 && (acc == 0 || acc + cost(base[t]) <= target)) {
-            TcTask k = base[t];
-            const TcPsiBlock& ib = plan.psi[k.in_blk];
-            int k1 = tc_k1_tiles(k, ib, r0), k2 = tc_k2_tiles(k, c0);
-            if (k1 > 0 && k1 <= 128 && k2 <= 128) {
-              // packed unit: greedily add following small tasks with the same
-              // right-operand orientation; tasks on the same psi block share its tiles
-              TcUnit u{item_idx, (int)P.tasks.size(), 0, 0, UNIT_PACKED, 0, {0, 0}};
-              int w = 0, s1 = 0, last_in = -1, last_k1b = 0;
-              const int tB0 = (k.flags >> 1) & 1;
-              while (t < t1 && seg < seg_tasks && (acc == 0 || acc + cost(base[t]) <= target)) {
-                TcTask x = base[t];
-                const TcPsiBlock& xb = plan.psi[x.in_blk];
-                int a1 = tc_k1_tiles(x, xb, r0);
-                const bool share = x.in_blk == last_in;
-                if (share) a1 -= xb.R8 * xb.C8;
-                int n16 = 16 * ((xb.n + 15) / 16);
-                if (tc_k1_tiles(x, xb, r0) == 0 || ((x.flags >> 1) & 1) != tB0 || w + n16 > 64 || s1 + a1 > 128) break;
-                x.xcol = w;
-                x.k1a = s1;
-                const bool tA = x.flags & 1;
-                const int rg0 = r0 / 8;
-                const int ol = tA ? x.aR8 * std::min(16, x.aC8 - rg0) : std::min(16, x.aR8 - rg0) * x.aC8;
-                if (share) {
-                  x.k1b = last_k1b;
-                  x.flags |= 4;  // psi tiles already in the stage
-                } else {
-                  x.k1b = s1 + ol;
-                  last_k1b = x.k1b;
-                }
-                x.k2 = 0;
-                last_in = x.in_blk;
-                w += n16;
-                s1 += a1;
-                P.tasks.push_back(x);
-                acc += cost(x);
-                ++t;
-                ++seg;
-              }
-              u.t_end = (int)P.tasks.size();
-              u.width = w;
-              P.units.push_back(u);
-            } else {
-              P.tasks.push_back(k);
-              const int npass = (ib.n + 127) / 128;
-              for (int p = 0; p < npass; ++p)
-                P.units.push_back({item_idx, (int)P.tasks.size() - 1, (int)P.tasks.size(), p, 0,
-                                   std::min(128, ib.n - 128 * p), {0, 0}});
-              acc += cost(k);
-              ++t;
-              ++seg;
-            }
-            if (seg >= seg_tasks) end_segment();
-          }
-          end_segment();
-          it.u_end = (int)P.units.size();
-          P.items.push_back(it);
-          P.scratch += (long long)nr * nc;
-          P.icost.push_back(acc);
-        } while (t < t1);
-        g.i_end = (int)P.items.size();
-        P.groups.push_back(g);
-      }
-  };
-  std::vector<Part> parts(nparts);
-  in_parallel([&](int j) {
-    parts[j].tasks.reserve(wl.out_start[bstart[j + 1]] - wl.out_start[bstart[j]]);
-    for (size_t b = bstart[j]; b < bstart[j + 1]; ++b) plan_block(b, parts[j]);
-  });
-  std::vector<double> icost;
-  {
-    std::vector<size_t> T(nparts + 1, 0), U(nparts + 1, 0), I(nparts + 1, 0), G(nparts + 1, 0);
-    std::vector<long long> S(nparts + 1, 0);
-    for (int j = 0; j < nparts; ++j) {
-      T[j + 1] = T[j] + parts[j].tasks.size();
-      U[j + 1] = U[j] + parts[j].units.size();
-      I[j + 1] = I[j] + parts[j].items.size();
-      G[j + 1] = G[j] + parts[j].groups.size();
-      S[j + 1] = S[j] + parts[j].scratch;
-    }
-    plan.tasks.resize(T[nparts]);
-    plan.units.resize(U[nparts]);
-    plan.items.resize(I[nparts]);
-    plan.groups.resize(G[nparts]);
-    icost.resize(I[nparts]);
-    plan.scratch_elems = S[nparts];
-    in_parallel([&](int j) {
-      const Part& P = parts[j];
-      std::copy(P.tasks.begin(), P.tasks.end(), plan.tasks.begin() + T[j]);
-      for (size_t k = 0; k < P.units.size(); ++k) {
-        TcUnit u = P.units[k];
-        u.item += (int)I[j];
-        u.t_begin += (int)T[j];
-        u.t_end += (int)T[j];
-        plan.units[U[j] + k] = u;
-      }
-      for (size_t k = 0; k < P.items.size(); ++k) {
-        TcItem it = P.items[k];
-        it.u_begin += (int)U[j];
-        it.u_end += (int)U[j];
-        it.slot += S[j];
-        plan.items[I[j] + k] = it;
-      }
-      for (size_t k = 0; k < P.groups.size(); ++k) {
-        Group g = P.groups[k];
-        g.i_begin += (int)I[j];
-        g.i_end += (int)I[j];
-        plan.groups[G[j] + k] = g;
-      }
-      std::copy(P.icost.begin(), P.icost.end(), icost.begin() + I[j]);
-    });
-  }
-  plan.schedule.resize(plan.items.size());
-  std::iota(plan.schedule.begin(), plan.schedule.end(), 0);
-  std::stable_sort(plan.schedule.begin(), plan.schedule.end(),
-                   [&](int a, int b) { return icost[a] > icost[b]; });
-  // records: one per unit (one REC_ZERO per item without units), written in
-  // item order; items are independent, so ranges of them fill in parallel
-  static_assert(sizeof(TcTaskRec) == 64 && sizeof(TcRec) == 304, "record layout");
-  plan.item_rec.assign(plan.items.size() + 1, 0);
-  for (size_t i = 0; i < plan.items.size(); ++i)
-    plan.item_rec[i + 1] = plan.item_rec[i] + std::max(1, plan.items[i].u_end - plan.items[i].u_begin);
-  plan.recs.clear();
-  plan.recs.resize((size_t)plan.item_rec.back());  // uninitialized: every record is written below
-  auto fill = [&](size_t i0, size_t i1) {
-    for (size_t i = i0; i < i1; ++i) {
-      const TcItem& it = plan.items[i];
-      TcRec* out = plan.recs.data() + plan.item_rec[i];
-      auto header = [&](TcRec& r) {
-        r.r0 = it.r0;
-        r.nrows = it.nrows;
-        r.c0 = it.c0;
-        r.ncols = it.ncols;
-        r.slot = it.slot;
-      };
-      if (it.u_begin == it.u_end) {
-        *out = TcRec{};
-        out->flags = REC_ZERO;
-        header(*out);
-        continue;
-      }
-      for (int u = it.u_begin; u < it.u_end; ++u, ++out) {
-        const TcUnit& un = plan.units[u];
-        TcRec& r = *out;
-        r = TcRec{};
-        r.flags = un.flags;
-        r.ntask = un.t_end - un.t_begin;
-        r.pass = un.pass;
-        r.width = un.width;
-        r.pad[0] = un.width / 8;  // K groups of the packed second product
-        header(r);
-        for (int k = 0; k < r.ntask; ++k) {
-          const TcTask& t = plan.tasks[un.t_begin + k];
-          const TcPsiBlock& p = plan.psi[t.in_blk];
-          TcTaskRec& x = r.t[k];
-          x.a_tile = t.a_tile;
-          x.b_tile = t.b_tile;
-          x.p_tile = p.tile;
-          x.aR8 = (short)t.aR8;
-          x.aC8 = (short)t.aC8;
-          x.bR8 = (short)t.bR8;
-          x.bC8 = (short)t.bC8;
-          x.pR8 = (short)p.R8;
-          x.pC8 = (short)p.C8;
-          x.xcol = (short)t.xcol;
-          x.k1a = (short)t.k1a;
-          x.k1b = (short)t.k1b;
-          x.k2 = (short)t.k2;
-          x.pn = p.n;
-          x.flags = t.flags;
-          x.scale = t.scale;
+        const int tm = std::min(128, ob.mL - r0), tn = std::min(128, ob.mR - c0);
+        const int G = std::max(1, 16 / ceil8(tm));
+        for (int t = wl.out_start[b]; t < wl.out_start[b + 1]; ++t) {
+          const TcPsiBlock& ib = plan.psi[base[t].in_blk];
+          total += unit_macs(1, tn, ib.m, ib.n) / G + unit_overhead / G;
         }
       }
-    }
-  };
-  const size_t nit = plan.items.size();
-  const int nth = (int)std::min<size_t>(8, std::max<size_t>(1, std::min<size_t>(std::thread::hardware_concurrency(),
-                                                                                  plan.recs.size() / 65536)));
-  if (nth <= 1) {
-    fill(0, nit);
-  } else {  // item ranges of about equal record counts
-    std::vector<std::thread> pool;
-    size_t i0 = 0;
-    for (int th = 0; th < nth; ++th) {
-      const long long goal = (long long)plan.recs.size() * (th + 1) / nth;
-      size_t i1 = th == nth - 1 ? nit : (size_t)(std::lower_bound(plan.item_rec.begin(), plan.item_rec.end() - 1,
-                                                                  (int)goal) - plan.item_rec.begin());
-      i1 = std::max(i1, i0);
-      pool.emplace_back(fill, i0, i1);
-      i0 = i1;
-    }
-    for (auto& t : pool) t.join();
   }
+  const double target = total / std::max(1, shape.want_items);
+
+  struct Unit {  // one unit: positions [t0, t1) of its part's sorted task order
+    int t0, t1;
+  };
+  struct Part {
+    std::vector<TcItem> items;           // kind 0: r_begin/r_end index units; kind 1: small terms
+    std::vector<Group> groups;
+    std::vector<std::pair<int, Unit>> units;  // (output block, unit)
+    std::vector<SmallTerm> small;
+    std::vector<double> icost;
+    std::vector<int> order;              // sorted task indices, per block contiguous
+    long long scratch = 0;
+    long long n_terms = 0;
+    double macs = 0;
+  };
+  constexpr int SMALL_ITEM = 512;        // small terms per CUDA-core item
+  std::vector<Part> parts(nparts);
+  in_parallel([&](int j) {
+    Part& P = parts[j];
+    for (size_t b = bstart[j]; b < bstart[j + 1]; ++b) {
+      const PsiBlock& ob = blocks[b];
+      const int t0 = wl.out_start[b], t1 = wl.out_start[b + 1];
+      // classes: tasks of the block ordered by (input block, left transposed,
+      // right transposed); equal keys are contiguous
+      const int obase = (int)P.order.size();
+      for (int t = t0; t < t1; ++t) P.order.push_back(t);
+      std::stable_sort(P.order.begin() + obase, P.order.end(), [&](int x, int y) {
+        if (base[x].in_blk != base[y].in_blk) return base[x].in_blk < base[y].in_blk;
+        return (base[x].flags & 3) < (base[y].flags & 3);
+      });
+      for (int r0 = 0; r0 < ob.mL; r0 += 128)
+        for (int c0 = 0; c0 < ob.mR; c0 += 128) {
+          const int tm = std::min(128, ob.mL - r0), tn = std::min(128, ob.mR - c0);
+          const int G = std::max(1, 16 / ceil8(tm));
+          Group g{(int)b, r0, tm, c0, tn, (int)P.items.size(), 0, 0};
+          if (t0 == t1) {  // no contribution: one empty item writes zeros
+            P.items.push_back({(int)b, r0, tm, c0, tn, (int)P.units.size(), (int)P.units.size(), 0, P.scratch});
+            P.scratch += (long long)tm * tn;
+            P.icost.push_back(0);
+            g.i_end = (int)P.items.size();
+            P.groups.push_back(g);
+            continue;
+          }
+          TcItem it{(int)b, r0, tm, c0, tn, (int)P.units.size(), 0, 0, P.scratch};
+          double acc = 0;
+          const size_t small0 = P.small.size();
+          int k = obase;
+          const int kend = obase + (t1 - t0);
+          while (k < kend) {
+            // the class of order[k]: same input block and flags
+            const Base& h = base[P.order[k]];
+            int e = k;
+            while (e < kend && base[P.order[e]].in_blk == h.in_blk && (base[P.order[e]].flags & 3) == (h.flags & 3)) ++e;
+            const TcPsiBlock& ib = plan.psi[h.in_blk];
+            // CUDA-core class: the whole output block (one tile) and the psi block are small
+            if (std::max(std::max(ob.mL, ob.mR), std::max(ib.m, ib.n)) <= TC_SMALL_MAX) {
+              for (int q = k; q < e; ++q) {
+                const Task& tk = wl.tasks[base[P.order[q]].task];
+                P.small.push_back({tk.aoff, tk.boff, tk.in_blk, tk.flags & 3, tk.scale});
+              }
+              P.n_terms += e - k;
+              k = e;
+              continue;
+            }
+            for (int u0 = k; u0 < e; u0 += G) {
+              const int u1 = std::min(e, u0 + G);
+              const double c = unit_macs(u1 - u0, tn, ib.m, ib.n) + unit_overhead;
+              if (acc > 0 && acc + c > target) {  // close the item
+                it.r_end = (int)P.units.size();
+                P.items.push_back(it);
+                P.icost.push_back(acc);
+                P.scratch += (long long)tm * tn;
+                it = TcItem{(int)b, r0, tm, c0, tn, (int)P.units.size(), 0, 0, P.scratch};
+                acc = 0;
+              }
+              P.units.push_back({(int)b, Unit{u0, u1}});  // positions in P.order
+              acc += c;
+              P.macs += unit_macs(u1 - u0, tn, ib.m, ib.n);
+              P.n_terms += u1 - u0;
+            }
+            k = e;
+          }
+          if (acc > 0) {
+            it.r_end = (int)P.units.size();
+            P.items.push_back(it);
+            P.icost.push_back(acc);
+            P.scratch += (long long)tm * tn;
+          }
+          for (size_t s0 = small0; s0 < P.small.size(); s0 += SMALL_ITEM) {  // CUDA-core items
+            const size_t s1 = std::min(P.small.size(), s0 + SMALL_ITEM);
+            double c = 0;
+            for (size_t q = s0; q < s1; ++q) {
+              const PsiBlock& ib = blocks[P.small[q].in_blk];
+              c += 2.0 * ((double)tm * ib.mL * ib.mR + (double)tm * ib.mR * tn);
+            }
+            P.items.push_back({(int)b, r0, tm, c0, tn, (int)s0, (int)s1, 1, P.scratch});
+            P.icost.push_back(c);
+            P.scratch += (long long)tm * tn;
+          }
+          g.i_end = (int)P.items.size();
+          P.groups.push_back(g);
+        }
+    }
+  });
+  // join the parts: kind-0 items index records (one per unit, one TC_ZERO
+  // record per item without units), kind-1 items index small terms
+  std::vector<size_t> I(nparts + 1, 0), G(nparts + 1, 0), U(nparts + 1, 0), SM(nparts + 1, 0);
+  std::vector<long long> S(nparts + 1, 0);
+  for (int j = 0; j < nparts; ++j) {
+    const Part& P = parts[j];
+    I[j + 1] = I[j] + P.items.size();
+    G[j + 1] = G[j] + P.groups.size();
+    size_t nrec = 0;
+    for (const TcItem& it : P.items)
+      if (it.kind == 0) nrec += std::max(1, it.r_end - it.r_begin);
+    U[j + 1] = U[j] + nrec;
+    SM[j + 1] = SM[j] + P.small.size();
+    S[j + 1] = S[j] + P.scratch;
+    plan.n_terms += P.n_terms;
+    plan.mma_macs += P.macs;
+  }
+  plan.items.resize(I[nparts]);
+  plan.groups.resize(G[nparts]);
+  plan.scratch_elems = S[nparts];
+  plan.recs.resize(U[nparts]);  // uninitialized: every record is written below
+  plan.small.resize(SM[nparts]);
+  plan.n_units = 0;
+  std::vector<double> icost(I[nparts]);
+  in_parallel([&](int j) {
+    const Part& P = parts[j];
+    std::copy(P.small.begin(), P.small.end(), plan.small.begin() + SM[j]);
+    size_t rec = U[j];
+    for (size_t i = 0; i < P.items.size(); ++i) {
+      TcItem it = P.items[i];
+      it.slot += S[j];
+      icost[I[j] + i] = P.icost[i];
+      if (it.kind == 1) {
+        it.r_begin += (int)SM[j];
+        it.r_end += (int)SM[j];
+        plan.items[I[j] + i] = it;
+        continue;
+      }
+      const int ub = it.r_begin, ue = it.r_end;
+      it.r_begin = (int)rec;
+      const int tm = it.nrows, tn = it.ncols, tm8 = ceil8(tm);
+      auto header = [&](TcUnitRec& r) {
+        r.tm = tm;
+        r.tn = tn;
+        r.tm8 = tm8;
+        r.r0g = it.r0 / 8;
+        r.c0g = it.c0 / 8;
+        r.slot = it.slot;
+        r.pad[0] = r.pad[1] = 0;
+      };
+      if (ub == ue) {
+        TcUnitRec& r = plan.recs[rec++];
+        std::memset(&r, 0, sizeof(r));
+        header(r);
+        r.flags = TC_ZERO | TC_ITEM_FIRST | TC_ITEM_LAST;
+      } else {
+        for (int u = ub; u < ue; ++u) {
+          const Unit& un = P.units[u].second;
+          TcUnitRec& r = plan.recs[rec++];
+          std::memset(&r, 0, sizeof(r));
+          header(r);
+          const Base& h = base[P.order[un.t0]];
+          const TcPsiBlock& ib = plan.psi[h.in_blk];
+          r.flags = (h.flags & 1 ? TC_TA : 0) | (h.flags & 2 ? TC_TB : 0) | (u == ub ? TC_ITEM_FIRST : 0) |
+                    (u == ue - 1 ? TC_ITEM_LAST : 0);
+          r.nterm = un.t1 - un.t0;
+          r.m = ib.m;
+          r.n = ib.n;
+          r.aR8 = (short)h.aR8;
+          r.aC8 = (short)h.aC8;
+          r.bR8 = (short)h.bR8;
+          r.bC8 = (short)h.bC8;
+          r.pR8 = (short)ib.R8;
+          r.pC8 = (short)ib.C8;
+          r.p_tile = ib.tile;
+          r.rsv = 0;
+          for (int q = 0; q < r.nterm; ++q) {
+            const Base& x = base[P.order[un.t0 + q]];
+            r.t[q].a_tile = x.a_tile;
+            r.t[q].b_tile = x.b_tile;
+            r.t[q].scale = x.scale;
+            r.t[q].pad = 0;
+          }
+        }
+      }
+      it.r_end = (int)rec;
+      plan.items[I[j] + i] = it;
+    }
+    for (size_t k = 0; k < P.groups.size(); ++k) {
+      Group g = P.groups[k];
+      g.i_begin += (int)I[j];
+      g.i_end += (int)I[j];
+      plan.groups[G[j] + k] = g;
+    }
+  });
+  for (const Part& P : parts) plan.n_units += (long long)P.units.size();
+  for (size_t i = 0; i < plan.items.size(); ++i) (plan.items[i].kind ? plan.small_schedule : plan.schedule).push_back((int)i);
+  auto by_cost = [&](int a, int b) { return icost[a] > icost[b]; };
+  std::stable_sort(plan.schedule.begin(), plan.schedule.end(), by_cost);
+  std::stable_sort(plan.small_schedule.begin(), plan.small_schedule.end(), by_cost);
 }
 
 }  // namespace dmrg

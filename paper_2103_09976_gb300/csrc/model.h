@@ -130,6 +130,21 @@ std::vector<int> nc_term_ranks(int nL, int n, int n_ranks);
 // its right-block pair p <= r (the larger indices).
 std::vector<int> cn_term_ranks(int nL, int n, int n_ranks);
 
+// Sub-Hamiltonian `rank` of n_ranks of an NC middle-bond problem (Sec. II.B,
+// Eqs. sum-h, sub-h, proc-def): the terms nc_term_ranks gives that rank,
+// their positions in the full term list, and the operators they use. On
+// return L and R keep only those operators' blocks (the others have none),
+// laid out contiguously from offset 0 (left operators first); canon_off
+// holds, per kept block in the new store order, its element offset in the
+// full canonical store (where the synthetic generator's counters start).
+struct Partition {
+  std::vector<Term> terms;
+  std::vector<int> term_ids;
+  std::vector<long long> canon_off;
+  long long elements = 0;
+};
+void partition_nc(OpSet& L, OpSet& R, int nL, int n, int rank, int n_ranks, Partition& out);
+
 struct PsiBlock {
   int qL, qR;       // sector indices in the left / right basis
   int mL, mR;
@@ -215,74 +230,75 @@ namespace dmrg {
 // Split operator store: every stored block S (r x c) is kept as three bf16
 // slices S = hi + mid + lo, each in 8x8 "core-matrix" tiles: tile (i8, j8)
 // holds rows 8*i8.., cols 8*j8.. as 8 rows of 8 contiguous elements (128 B),
-// tiles ordered j8 fastest; padding elements are zero. The same tiles serve
-// as a K-major operand (S as MN x K) or an MN-major one (S^T) of tcgen05.mma.
+// tiles ordered j8 fastest, the three slices of one tile position
+// interleaved (384 B); padding elements are zero. The same tiles serve as a
+// K-major operand (S as MN x K) or an MN-major one (S^T) of tcgen05.mma.
 struct TcBlock {
-  long long tile;   // first tile (128-byte units) in each slice array
+  long long tile;   // first tile position of the block
   int R8, C8;       // tile rows / cols of the stored block
 };
 
-struct TcTask {
-  long long a_tile, b_tile;   // tiles of the left / right operator block (identity blocks included)
-  int aR8, aC8;               // stored tile geometry of the left block
-  int bR8, bC8;               // stored tile geometry of the right block
-  int in_blk;
-  int flags;                  // bit0: left used transposed, bit1: right used transposed, bit2: psi shared
-  float scale;
-  int xcol;                   // packed units: first X column of this task (multiple of 16)
-  int k1a, k1b, k2;           // packed units: tile offsets of its regions in the stage slices
-  int pad;
-};
-
-// A unit is what one pass of the pipeline processes: either several small
-// tasks packed side by side (one stage of operator/psi tiles, X columns
-// concatenated, second product K-concatenated) or one 128-column pass of a
-// large task. Units of an item form segments of at most 64 tasks; each
-// segment's FP32 sigma tile is added into the item's FP64 slot.
-enum { UNIT_PACKED = 1, UNIT_ENDS_SEGMENT = 2, UNIT_FIRST_SEGMENT = 4 };
-struct TcUnit {
-  int item;
-  int t_begin, t_end;
-  int pass;
-  int flags;
-  int width;                  // packed: X columns used (<= 64)
-  int pad[2];
-};
-
-// Output tile and its unit range; same layout as Item (u_begin/u_end in the
-// place of the task range) so the reduction can read it.
-struct TcItem {
-  int out, r0, nrows, c0, ncols, u_begin, u_end, pad;
-  long long slot;
-};
-
 struct TcPsiBlock {
-  long long tile;   // first tile of the block in the psi slice arrays
+  long long tile;   // first tile position of the block in the psi split
   int R8, C8;       // rows padded to an even number of tile rows
   int m, n;
 };
 
-// Self-contained record of one unit as the kernel reads it (bulk-copied into
-// a shared-memory ring): the unit, its output tile, and up to 4 task records
-// with the geometry of their psi blocks inline.
-struct TcTaskRec {            // 64 bytes
-  long long a_tile, b_tile, p_tile;
-  short aR8, aC8, bR8, bC8, pR8, pC8;
-  short xcol, k1a, k1b, k2;
-  int pn;                     // psi block columns
-  int flags;                  // bit0: left transposed, bit1: right transposed, bit2: psi tiles shared
-  float scale;
-  int pad[2];
+// Work of the tensor-core sigma. For one output tile (rows r0.. of at most
+// 128, columns c0.. of at most 128) of output block b', the products of all
+// terms that read the same psi block b with the same transposition flags
+// form a class: sigma_b'[tile] += sum_t c_t L_t[rows, :] psi_b R_t[cols, :]^T.
+// A unit is up to TC_MAX_G terms of one class whose left-operator rows are
+// stacked in one 128-row operand, so one chain of MMAs gives X_t = L_t psi_b
+// for all of them (stage 1); each term's X_t R_t^T then accumulates into the
+// tile (stage 2). Stage 1 runs over 128-column chunks of psi; stage 2 over
+// 64-column halves of each chunk. The FP32 tile accumulator is added into
+// the item's running sum (FP32 pairs, about 48 bits) after every flush group
+// of terms within one half (the launch bounds the main MMA steps of a
+// group), which bounds the length of any FP32 accumulation chain.
+constexpr int TC_MAX_G = 16;
+enum { TC_TA = 1, TC_TB = 2, TC_ZERO = 4, TC_DONE = 8, TC_ITEM_FIRST = 16, TC_ITEM_LAST = 32 };
+struct TcTermRec {          // 24 bytes
+  long long a_tile, b_tile; // left / right operator blocks (identity blocks included)
+  float scale;              // coefficient times fermion sign
+  int pad;
 };
-enum { REC_ZERO = 8, REC_DONE = 16 };
-struct TcRec {                // 304 bytes
-  int flags;                  // UNIT_* | REC_ZERO (item without tasks) | REC_DONE
-  int ntask;
-  int pass, width;
-  int r0, nrows, c0, ncols;
+struct TcUnitRec {          // 80-byte header + 16 terms = 464 bytes
+  int flags;                // TC_TA (left used transposed), TC_TB (right transposed), TC_ZERO, TC_DONE,
+                            // TC_ITEM_FIRST / TC_ITEM_LAST (first / last record of an item)
+  int nterm;                // terms in the unit (<= TC_MAX_G)
+  int tm, tn;               // rows / columns of the output tile
+  int tm8;                  // row groups of one term in the stacked operand (ceil(tm / 8))
+  int r0g, c0g;             // tile origin (row / column group) inside the output block
+  int m, n;                 // psi block rows / columns
+  int rsv;                  // reserved (zero)
+  short aR8, aC8, bR8, bC8; // stored tile geometry of the left / right blocks
+  short pR8, pC8;           // psi tile geometry
+  long long p_tile;         // psi tiles
+  long long slot;           // the item's partial tile (tm x tn, row-major)
+  int pad[2];
+  TcTermRec t[TC_MAX_G];
+};
+
+// Output tile and its record range; same layout as Item (r_begin/r_end in
+// the place of the task range) so the reduction can read it. kind 0: unit
+// records of the tensor-core kernel; kind 1: small terms (SmallTerm) of the
+// CUDA-core kernel.
+struct TcItem {
+  int out, r0, nrows, c0, ncols, r_begin, r_end, kind;
   long long slot;
-  int pad[2];                 // pad[0]: K groups of a packed unit's second product
-  TcTaskRec t[4];
+};
+
+// Classes whose blocks (output tile and psi block) are all at most
+// TC_SMALL_MAX wide fill a tcgen05 instruction (128 x 16 x 16 at least) by a
+// few percent; they run on the CUDA cores instead, in FP32 products of the
+// FP64 operators (K <= 32 per product) with FP64 sums over terms.
+constexpr int TC_SMALL_MAX = 32;
+struct SmallTerm {          // 32 bytes
+  long long a_off, b_off;   // FP64 store offsets of the left / right blocks, -1 = identity
+  int in_blk;               // psi block
+  int flags;                // bit0: left used transposed, bit1: right used transposed
+  double scale;
 };
 
 // Allocator whose resize() leaves elements uninitialized (records are
@@ -308,25 +324,26 @@ struct NoInit : std::allocator<T> {
 
 struct TcPlan {
   std::vector<TcBlock> opblocks;        // tiles of every stored block, store order
-  std::vector<long long> op_first;      // index of the first TcBlock of each op (L ops then R ops)
   std::vector<TcBlock> identL, identR;  // identity blocks per sector of the left / right basis
-  long long n_tiles = 0;                // tiles per slice array
+  long long n_tiles = 0;                // tile positions of the operator split
   std::vector<TcPsiBlock> psi;
   long long psi_tiles = 0;
-  std::vector<TcTask> tasks;            // in item order
-  std::vector<TcUnit> units;
-  std::vector<TcItem> items;
-  std::vector<int> schedule;
+  std::vector<TcItem> items;            // grouped by output tile
+  std::vector<int> schedule;            // kind-0 items, most expensive first
   std::vector<Group> groups;
   long long scratch_elems = 0;
-  std::vector<TcRec, NoInit<TcRec>> recs;  // one per unit (or one REC_ZERO per empty item)
-  std::vector<int> item_rec;            // records of item i: [item_rec[i], item_rec[i+1])
+  std::vector<TcUnitRec, NoInit<TcUnitRec>> recs;  // kind-0 item i: records [items[i].r_begin, items[i].r_end)
+  std::vector<SmallTerm> small;         // kind-1 item i: terms [items[i].r_begin, items[i].r_end)
+  std::vector<int> small_schedule;      // kind-1 items, most expensive first
+  long long n_terms = 0;                // term products (tasks x tiles), counted once
+  long long n_units = 0;
+  double mma_macs = 0;                  // multiply-adds issued per slice product (padding included)
 };
 
-// Tiles of a task's regions in a packed unit (0 if the task cannot be packed).
-int tc_k1_tiles(const TcTask& t, const TcPsiBlock& ib, int r0);
-int tc_k2_tiles(const TcTask& t, int c0);
+struct TcShape {
+  int want_items;           // items to split the work into (a multiple of the SM count)
+};
 void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const OpSet& R,
-                   const WorkList& wl, TcPlan& plan, int want_items, int seg_tasks);
+                   const WorkList& wl, TcPlan& plan, const TcShape& shape);
 
 }  // namespace dmrg

@@ -98,7 +98,7 @@ struct dmrg_server {
         c.opts.seed = job.r.seed;
         load_synthetic(c, job.r.n_left_modes, job.r.n_modes, job.r.N, job.r.two_sz,
                        parse_sectors((int)job.left.size() / 3, job.left.data()),
-                       parse_sectors((int)job.right.size() / 3, job.right.data()), job.r.seed);
+                       parse_sectors((int)job.right.size() / 3, job.right.data()), job.r.seed, 0, 1);
         res.t_loaded = now();
         double e = 0.0;
         int it = 0;

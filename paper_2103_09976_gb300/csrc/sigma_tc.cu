@@ -1,27 +1,44 @@
 // Mixed-precision sigma = H_eff . psi on the 5th-generation tensor cores.
 //
 // Same decomposition as the FP64 path (Sec. II.D-E: a flat list of
-// (term, sector) products, summed per output tile, partials reduced in a
-// fixed order), with every product
-//     S[r0:r0+128, c0:c0+128] += scale * (X_L psi_b) X_R^T
-// computed by tcgen05.mma kind::f16 on bf16 slices: each FP64 operand is
-// split x = hi + mid + lo (three bf16 numbers, 24 significant bits) and a
-// product a*b is taken as the sum of the slice products with i + j <= 2
-// (6 MMAs, BF16X3) or i + j <= 1 (3 MMAs, BF16X2), accumulated in FP32 in
-// tensor memory. The intermediate X = X_L psi_b never leaves the SM: it is
-// read from TMEM, scaled, re-split into bf16 slices and written to shared
-// memory as the A operand of the second product.
+// (term, sector) products summed per output tile, partial tiles reduced in a
+// fixed order), reorganized for tcgen05.mma. Every FP64 operand is split
+// x = hi + mid + lo (three bf16 numbers, 24 significant bits) and a product
+// a*b is the sum of the slice products with i + j <= 2 (6 MMAs, BF16X3) or
+// i + j <= 1 (3 MMAs, BF16X2), accumulated in FP32 in tensor memory.
+//
+// Work unit: up to 16 terms of one class (same output tile, same psi block,
+// same transposition flags). Their left operators' rows are stacked into one
+// 128-row A operand, so one MMA chain gives the intermediates
+// X_t = L_t[rows, :] psi_b of all of them at once (stage 1); X leaves the
+// tensor memory only to be scaled by c_t and re-split into bf16 slices in
+// shared memory, where it is the A operand of each term's
+// sigma[tile] += X_t R_t[cols, :]^T (stage 2). Stage 1 runs over 128-column
+// chunks of psi, stage 2 over 64-column halves of each chunk.
+//
+// Accuracy: within a chain the correction products are issued before the
+// main (hi x hi) ones, while the accumulator is still small. The FP32 tile
+// accumulator is added into a per-thread compensated (Kahan) FP32 running sum
+// (about 33 bits) after every flush group: the terms of one half whose main MMA steps fit the
+// launch's chain limit (at least one term), or both halves of a chunk of a
+// one-term unit when they fit together. The sum is written to the item's
+// FP64 partial tile at the end of the item. This bounds the length of every
+// FP32 accumulation chain of stage 2.
 //
 // Warp roles (320 threads): warp 0 streams operator and psi tiles with
 // cp.async.bulk into a 3-stage ring; warp 1 issues the MMAs; warps 2-9 are
-// the epilogue (two warps per TMEM lane quarter, 32 columns each). Operands are stored in 8x8 core-matrix tiles, so one stored
-// block serves as a K-major operand (S) or an MN-major one (S^T) with no
-// copy: transposed terms only change the shared-memory descriptors.
+// the epilogue (two warps per TMEM lane quarter, 64 columns each). Tensor
+// memory: two 128-column X buffers, two 128-column tile accumulators.
+// Operands are stored in 8x8 core-matrix tiles, so one stored block serves as
+// a K-major operand (S) or an MN-major one (S^T) with no copy: transposed
+// terms only change the shared-memory descriptors.
 //
 // Every wait on an mbarrier is bounded (about one second of clock); on a
 // timeout the kernel raises a flag in *err, stops issuing work, waits (again
 // bounded) for its own copies, frees its tensor memory and returns.
 #include <cuda_bf16.h>
+
+#include <cstddef>
 
 #include "kernels.h"
 
@@ -35,19 +52,18 @@ constexpr int STAGES = 3;
 // Operator and psi tiles are stored slice-interleaved: tile position k holds
 // its hi, mid and lo 8x8 bf16 tiles at bytes 384k, 384k+128, 384k+256, in
 // global memory and in the stages alike.
-constexpr int TILE3 = 384;                      // bytes per tile position (3 slices)
+constexpr int TILE3 = 384;
 constexpr int STAGE_TILES = 128;                // tile positions per stage
 constexpr int STAGE_BYTES = STAGE_TILES * TILE3;  // 48 KB
-constexpr int PSI_TILE = 64;                    // psi tiles of a large task's K1 stage start here
-constexpr int A2_SLICE = 16 * 1024;             // X chunk: 16 row groups x 8 K groups
-constexpr int A2_OFF = STAGES * STAGE_BYTES;
-constexpr int NMETA = 16;                       // unit records in the shared-memory ring
-constexpr int PREFETCH = 8;                     // records fetched ahead of the producer
-constexpr int META_OFF = A2_OFF + 3 * A2_SLICE;
-constexpr int BAR_OFF = META_OFF + NMETA * (int)sizeof(TcRec);
-constexpr int SLACK_OFF = BAR_OFF + 512;
-constexpr int SLACK = 8192;                     // descriptor reads past packed regions stay inside
-constexpr int SMEM_BYTES = SLACK_OFF + SLACK;
+constexpr int PSI_TILE = 64;                    // psi tiles of a stage-1 stage start here
+constexpr int A2_SLICE = 16 * 1024;             // X half: 16 row groups x 8 K groups x 128 B
+constexpr int A2_OFF = 0;                       // A2 first: reads past its last slice land in stage 0
+constexpr int STAGE_OFF = 3 * A2_SLICE;
+constexpr int NMETA = 8;                        // unit records in the shared-memory ring
+constexpr int PREFETCH = 4;                     // records fetched ahead of the producer
+constexpr int META_OFF = STAGE_OFF + STAGES * STAGE_BYTES;
+constexpr int BAR_OFF = META_OFF + NMETA * (int)sizeof(TcUnitRec);
+constexpr int SMEM_BYTES = BAR_OFF + 512;
 constexpr long long WAIT_CYCLES = 2000000000ll; // ~1 s at 2 GHz
 
 // barrier slots (8 bytes each)
@@ -57,6 +73,8 @@ enum { B_FULL = 0, B_EMPTY = STAGES, B_XFULL = 2 * STAGES, B_XEMPTY = 2 * STAGES
        B_TMEM = B_MEMPTY + NMETA, B_ABORT = B_TMEM + 1 };
 static_assert(8 * (B_ABORT + 1) <= 512, "barrier region");
 static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
+static_assert(sizeof(TcUnitRec) == 464 && offsetof(TcUnitRec, t) == 80, "record layout");
+static_assert(META_OFF % 16 == 0 && sizeof(TcUnitRec) % 16 == 0, "records are bulk-copied");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -159,101 +177,134 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// slice products (i, j): i indexes the A slices, j the B slices
-
-__device__ __forceinline__ int rec_k1(const TcRec& r) {
-  return (r.flags & UNIT_PACKED) ? 1 : (r.t[0].pR8 + 3) / 4;
+// ------------------------------------------------------ unit geometry
+__device__ __forceinline__ int n_chunks(const TcUnitRec& r) { return (r.n + 127) >> 7; }
+__device__ __forceinline__ int chunk_cols(const TcUnitRec& r, int j) { return min(128, r.n - 128 * j); }
+__device__ __forceinline__ int n_halves(const TcUnitRec& r, int j) { return (chunk_cols(r, j) + 63) >> 6; }
+__device__ __forceinline__ int half_cols(const TcUnitRec& r, int j, int h) { return min(64, chunk_cols(r, j) - 64 * h); }
+__device__ __forceinline__ int k1_stages(const TcUnitRec& r) { return (r.pR8 + 3) >> 2; }
+__device__ __forceinline__ int tn8e(const TcUnitRec& r) { return 2 * ((r.tn + 15) >> 4); }  // N groups read by the MMA
+__device__ __forceinline__ int kg2_of(int kw) { return 2 * ((kw + 15) >> 4); }               // K groups of a half
+__device__ __forceinline__ int terms_per_stage(const TcUnitRec& r, int kw) {
+  return max(1, min(r.nterm, STAGE_TILES / (tn8e(r) * kg2_of(kw))));
 }
-__device__ __forceinline__ int rec_k2(const TcRec& r) {
-  return (r.flags & UNIT_PACKED) ? 1 : (r.width + 63) / 64;
+// Terms per flush group: the most whose main K steps in one half stay within
+// max_chain (at least one); max_chain <= 0: the whole unit.
+__device__ __forceinline__ int flush_terms(const TcUnitRec& r, int max_chain) {
+  const int steps = (min(64, r.n) + 15) >> 4;
+  return max_chain > 0 ? max(1, min(r.nterm, max_chain / steps)) : r.nterm;
+}
+// A unit of one term whose chunk fits the chain limit accumulates both
+// halves of chunk j in one group (one flush per chunk instead of per half).
+__device__ __forceinline__ bool whole_chunk_group(const TcUnitRec& r, int j, int max_chain) {
+  return r.nterm == 1 && (max_chain <= 0 || ((chunk_cols(r, j) + 15) >> 4) <= max_chain);
 }
 
-// The copies of one stage, distributed over the producer warp: lane `lane`
-// calls f(src_tile, operand (0 operator, 1 psi), dst_tile, n_tiles) for its
-// own copies only. Every copy moves n_tiles tile positions (all 3 slices).
+// A unit's geometry, read once from its record in shared memory (the
+// barrier waits clobber memory, so fields read in loops would be re-read).
+struct UnitGeo {
+  int flags, G, tm8, tn, tn8, te, r0g, c0g, n, aR8, aC8, bR8, bC8, pR8, pC8;
+  long long p_tile;
+};
+__device__ __forceinline__ UnitGeo geo_of(const TcUnitRec& r) {
+  UnitGeo g;
+  g.flags = r.flags;
+  g.G = r.nterm;
+  g.tm8 = r.tm8;
+  g.tn = r.tn;
+  g.tn8 = (r.tn + 7) >> 3;
+  g.te = 2 * ((r.tn + 15) >> 4);
+  g.r0g = r.r0g;
+  g.c0g = r.c0g;
+  g.n = r.n;
+  g.aR8 = r.aR8;
+  g.aC8 = r.aC8;
+  g.bR8 = r.bR8;
+  g.bC8 = r.bC8;
+  g.pR8 = r.pR8;
+  g.pC8 = r.pC8;
+  g.p_tile = r.p_tile;
+  return g;
+}
+
+// Copies of one stage-1 stage (psi columns of chunk j, K groups 4k..4k+3):
+// the stacked left-operator rows of every term ([M group][K group], or
+// [K group][M group] when the left operator is used transposed) and the psi
+// tiles ([K group][N group] from PSI_TILE on). Each lane issues copies
+// lane, lane + 32, ...; f(src_tile, operand (0 operators, 1 psi), dst_tile,
+// n_tiles) moves n_tiles tile positions (3 slices). Returns the stage's tile
+// count (the same on every lane).
 template <class F>
-__device__ __forceinline__ void lane_copies(const TcRec& u, int k1_stage, int k2_stage, int lane, F&& f) {
-  const int rg0 = u.r0 / 8, cg0 = u.c0 / 8;
-  if (u.flags & UNIT_PACKED) {
-    if (k1_stage >= 0) {
-      if (lane >= u.ntask) return;
-      const TcTaskRec& tk = u.t[lane];
-      const int aR8 = tk.aR8, aC8 = tk.aC8;
-      if (!(tk.flags & 1)) {
-        f(tk.a_tile + (long long)rg0 * aC8, 0, tk.k1a, min(16, aR8 - rg0) * aC8);
-      } else {
-        const int nmg = min(16, aC8 - rg0);
-        if (nmg == aC8) f(tk.a_tile, 0, tk.k1a, aR8 * aC8);
-        else
-          for (int kg = 0; kg < aR8; ++kg) f(tk.a_tile + (long long)kg * aC8 + rg0, 0, tk.k1a + kg * nmg, nmg);
-      }
-      if (!(tk.flags & 4)) f(tk.p_tile, 1, tk.k1b, (int)tk.pR8 * tk.pC8);
+__device__ __forceinline__ uint32_t copies_s1(const TcUnitRec& r, const UnitGeo& g, int j, int k, int lane, F&& f) {
+  const int kg0 = 4 * k;
+  const bool tA = g.flags & TC_TA;
+  const int nkA = tA ? min(4, g.aR8 - kg0) : min(4, g.aC8 - kg0);  // K groups of A in this stage
+  const int nA = nkA > 0 ? (tA ? g.G * nkA : g.G * g.tm8) : 0;     // A copies
+  const int perA = tA ? g.tm8 : nkA;                                // tiles per A copy
+  const int nkP = min(4, g.pR8 - kg0), nn = min(16, g.pC8 - 16 * j);
+  for (int c = lane; c < nA; c += 32) {
+    if (!tA) {
+      const int q = c / g.tm8, rg = c - q * g.tm8;
+      f(r.t[q].a_tile + (long long)(g.r0g + rg) * g.aC8 + kg0, 0, (q * g.tm8 + rg) * 4, perA);
     } else {
-      // unit-wide layout of the K-concatenated right operand: the K groups
-      // of task t start at xcol/8
-      const int kgu = u.pad[0];
-      const bool tB = u.t[0].flags & 2;
-      if (!tB) {
-        const int nng = min(16, u.t[0].bR8 - cg0);
-        for (int j = lane; j < u.ntask * nng; j += 32) {
-          const TcTaskRec& tk = u.t[j / nng];
-          const int ng = j % nng;
-          f(tk.b_tile + (long long)(cg0 + ng) * tk.bC8, 0, ng * kgu + tk.xcol / 8, tk.bC8);
-        }
-      } else {
-        if (lane >= u.ntask) return;
-        const TcTaskRec& tk = u.t[lane];
-        const int bR8 = tk.bR8, bC8 = tk.bC8, nng = min(16, bC8 - cg0), kx = tk.xcol / 8;
-        if (nng == bC8) f(tk.b_tile, 0, kx * nng, bR8 * bC8);
-        else
-          for (int kg = 0; kg < bR8; ++kg) f(tk.b_tile + (long long)kg * bC8 + cg0, 0, (kx + kg) * nng, nng);
-      }
-    }
-    return;
-  }
-  const TcTaskRec& tk = u.t[0];
-  const int aR8 = tk.aR8, aC8 = tk.aC8, bR8 = tk.bR8, bC8 = tk.bC8, pR8 = tk.pR8, pC8 = tk.pC8;
-  const bool tA = tk.flags & 1, tB = tk.flags & 2;
-  if (k1_stage >= 0) {  // one K chunk (4 K groups) of a large task
-    const int kg0 = 4 * k1_stage;
-    const int nA = !tA ? min(16, aR8 - rg0) : min(4, aR8 - kg0);
-    const int nB = min(4, pR8 - kg0);
-    if (lane < nA) {
-      if (!tA) f(tk.a_tile + (long long)(rg0 + lane) * aC8 + kg0, 0, lane * 4, min(4, aC8 - kg0));
-      else f(tk.a_tile + (long long)(kg0 + lane) * aC8 + rg0, 0, lane * 16, min(16, aC8 - rg0));
-    } else if (lane < nA + nB) {
-      const int r = lane - nA;
-      f(tk.p_tile + (long long)(kg0 + r) * pC8 + u.pass * 16, 1, PSI_TILE + r * 16, min(16, pC8 - u.pass * 16));
-    }
-  } else {  // one 64-column K chunk of the second product of a large task
-    const int kgx = u.pass * 16 + k2_stage * 8;
-    if (!tB) {
-      if (lane < min(16, bR8 - cg0)) f(tk.b_tile + (long long)(cg0 + lane) * bC8 + kgx, 0, lane * 8, min(8, bC8 - kgx));
-    } else {
-      if (lane < min(8, bR8 - kgx)) f(tk.b_tile + (long long)(kgx + lane) * bC8 + cg0, 0, lane * 16, min(16, bC8 - cg0));
+      const int q = c / nkA, kg = c - q * nkA;
+      f(r.t[q].a_tile + (long long)(kg0 + kg) * g.aC8 + g.r0g, 0, kg * 16 + q * g.tm8, perA);
     }
   }
+  if (lane < nkP) f(g.p_tile + (long long)(kg0 + lane) * g.pC8 + 16 * j, 1, PSI_TILE + lane * 16, nn);
+  return (uint32_t)(nA * perA + max(nkP, 0) * nn);
+}
+
+// Copies of one stage-2 stage: the right-operator tiles (output columns of
+// the tile, K groups of half h of chunk j) of terms q0..q1-1, each term in a
+// region of te x kg2 tile positions ([N group][K group], or [K group][N
+// group] when the right operator is used transposed). As copies_s1.
+template <class F>
+__device__ __forceinline__ uint32_t copies_s2(const TcUnitRec& r, const UnitGeo& g, int j, int h, int q0, int q1,
+                                              int lane, F&& f) {
+  const int kw = min(64, min(128, g.n - 128 * j) - 64 * h), kg2 = kg2_of(kw), kgx = 16 * j + 8 * h;
+  const bool tB = g.flags & TC_TB;
+  const int nkB = tB ? min(kg2, g.bR8 - kgx) : min(kg2, g.bC8 - kgx);  // K groups of B present
+  const int per = tB ? g.tn8 : nkB;
+  const int span = tB ? nkB : g.tn8;                                  // copies per term
+  const int ncopy = (q1 - q0) * span;
+  for (int c = lane; c < ncopy; c += 32) {
+    const int qq = c / span, x = c - qq * span, reg = qq * g.te * kg2;
+    if (!tB)
+      f(r.t[q0 + qq].b_tile + (long long)(g.c0g + x) * g.bC8 + kgx, 0, reg + x * kg2, per);
+    else
+      f(r.t[q0 + qq].b_tile + (long long)(kgx + x) * g.bC8 + g.c0g, 0, reg + x * g.te, per);
+  }
+  return (uint32_t)(ncopy * per);
 }
 
 }  // namespace
 
-// Slice pair of product p (i + j <= 2 ordering: hh, hm, mh, hl, mm, lh).
+// Slice pair of product p (hh, hm, mh, hl, mm, lh): i indexes the A slices,
+// j the B slices.
 __device__ __forceinline__ constexpr int prod_i(int p) { return (p == 2 || p == 4) ? 1 : (p == 5 ? 2 : 0); }
 __device__ __forceinline__ constexpr int prod_j(int p) { return (p == 1 || p == 4) ? 1 : (p == 3 ? 2 : 0); }
 
-// One K chain of slice products into tmem_d. Descriptors differ only in the
-// start-address field, so each MMA adds its byte offset >> 4 to a base.
+// One K chain of slice products into tmem_d: the correction products of all
+// K steps first, then the main (hi x hi) ones. Descriptors differ only in
+// the start-address field, so each MMA adds its byte offset >> 4 to a base.
+// `first`: the next MMA overwrites the accumulator (cleared after it).
 template <int NPROD>
 __device__ __forceinline__ void mma_chain(uint32_t tmem_d, uint64_t ad0, uint64_t bd0, uint32_t a_slice,
                                           uint32_t b_slice, uint32_t a_kstep, uint32_t b_kstep, int nks,
-                                          uint32_t idesc, bool acc_first) {
+                                          uint32_t idesc, bool& first) {
   for (int ks = 0; ks < nks; ++ks) {
 #pragma unroll
-    for (int p = 0; p < NPROD; ++p) {
-      const uint64_t ad = ad0 + ((prod_i(p) * a_slice + (uint32_t)ks * a_kstep) >> 4);
-      const uint64_t bd = bd0 + ((prod_j(p) * b_slice + (uint32_t)ks * b_kstep) >> 4);
-      mma(tmem_d, ad, bd, idesc, (acc_first || ks > 0 || p > 0) ? 1u : 0u);
+    for (int p = 1; p < NPROD; ++p) {
+      mma(tmem_d, ad0 + ((prod_i(p) * a_slice + (uint32_t)ks * a_kstep) >> 4),
+          bd0 + ((prod_j(p) * b_slice + (uint32_t)ks * b_kstep) >> 4), idesc, first ? 0u : 1u);
+      first = false;
     }
+  }
+  for (int ks = 0; ks < nks; ++ks) {
+    mma(tmem_d, ad0 + (((uint32_t)ks * a_kstep) >> 4), bd0 + (((uint32_t)ks * b_kstep) >> 4), idesc,
+        first ? 0u : 1u);
+    first = false;
   }
 }
 
@@ -267,7 +318,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
   auto bar = [&](int k) { return bars + 8u * (uint32_t)k; };
   volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + BAR_OFF + 8 * B_ABORT);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + BAR_OFF + 8 * B_TMEM);
-  TcRec* ring = reinterpret_cast<TcRec*>(sm + META_OFF);
+  TcUnitRec* ring = reinterpret_cast<TcUnitRec*>(sm + META_OFF);
 
   const long long t_start = clock64();
   if (tid < 16) s_wait[tid] = 0ull;
@@ -275,7 +326,6 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
   // finite operand data or zeros, so padded K positions multiply to 0 and
   // padded rows stay finite.
   for (int i = tid; i < META_OFF / 16; i += NTHR) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
-  for (int i = tid; i < SLACK / 16; i += NTHR) reinterpret_cast<uint4*>(sm + SLACK_OFF)[i] = make_uint4(0, 0, 0, 0);
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(bar(B_FULL + s), 1);
@@ -312,20 +362,42 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
     bool ok = true;
     const char* const ops = (const char*)a.op;
     const char* const ps = (const char*)a.psi;
-    auto produce = [&](const TcRec& u, int k1, int k2) {
+    // one stage: wait for it to be free, announce its bytes, issue the copies
+    auto produce = [&](auto&& copies) {
       if (!ok) return;
       if (!mbar_wait<PROF>(bar(B_EMPTY + stage), phase, abort_flag, a.err, 1)) { ok = false; return; }
-      uint32_t tiles = 0;
-      lane_copies(u, k1, k2, lane, [&](long long, int, int, int n) { tiles += (uint32_t)n; });
-      tiles = __reduce_add_sync(0xffffffffu, tiles);
-      if (lane == 0) mbar_expect_tx(bar(B_FULL + stage), (uint32_t)TILE3 * tiles);
+      const uint32_t sdst = sbase + STAGE_OFF + stage * STAGE_BYTES;
+      const uint32_t fb = bar(B_FULL + stage);
+      // the byte count is announced before any copy can complete: lane 0
+      // arrives with the expected bytes first, then all lanes issue copies
+      const uint32_t tiles = copies([&](long long, int, int, int) {}, true);
+      if (lane == 0) mbar_expect_tx(fb, (uint32_t)TILE3 * tiles);
       __syncwarp();
-      const uint32_t sdst = sbase + stage * STAGE_BYTES;
-      lane_copies(u, k1, k2, lane, [&](long long src, int which, int dst, int n) {
-        bulk_g2s(sdst + (uint32_t)dst * TILE3, (which ? ps : ops) + src * TILE3, (uint32_t)TILE3 * (uint32_t)n,
-                 bar(B_FULL + stage));
-      });
+      copies([&](long long src, int which, int dst, int n) {
+        bulk_g2s(sdst + (uint32_t)dst * TILE3, (which ? ps : ops) + src * TILE3, (uint32_t)TILE3 * (uint32_t)n, fb);
+      }, false);
       if (++stage == STAGES) { stage = 0; phase ^= 1; }
+    };
+    auto produce_s1 = [&](const TcUnitRec& u, int j) {
+      const UnitGeo g = geo_of(u);
+      const int nk1 = (g.pR8 + 3) >> 2;
+      for (int k = 0; k < nk1; ++k)
+        produce([&](auto&& f, bool count_only) -> uint32_t {
+          if (count_only) return copies_s1(u, g, j, k, 32, f);  // lane 32 issues nothing
+          return copies_s1(u, g, j, k, lane, f);
+        });
+    };
+    auto produce_s2 = [&](const TcUnitRec& u, int j) {
+      const UnitGeo g = geo_of(u);
+      const int ccols = min(128, g.n - 128 * j);
+      for (int h = 0; h < (ccols + 63) >> 6; ++h) {
+        const int kw = min(64, ccols - 64 * h);
+        const int P = max(1, min(g.G, STAGE_TILES / (g.te * kg2_of(kw))));
+        for (int q0 = 0; q0 < g.G; q0 += P)
+          produce([&](auto&& f, bool count_only) -> uint32_t {
+            return copies_s2(u, g, j, h, q0, min(g.G, q0 + P), count_only ? 32 : lane, f);
+          });
+      }
     };
     bool no_more = false;
     int pf_r = 0, pf_end = 0;  // prefetch cursor: next record and end of its item
@@ -338,15 +410,15 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
         q = __shfl_sync(0xffffffffu, q, 0);
         if (q >= a.n_items) { no_more = true; return false; }
         const int it = a.schedule[q];
-        pf_r = a.item_rec[it];
-        pf_end = a.item_rec[it + 1];
+        pf_r = a.items[it].r_begin;
+        pf_end = a.items[it].r_end;
       }
       const int slot = (int)(pf_s % NMETA);
       const uint32_t par = (uint32_t)(((pf_s / NMETA) & 1) ^ 1);
       if (!mbar_wait<PROF>(bar(B_MEMPTY + slot), par, abort_flag, a.err, 9)) { ok = false; return false; }
       if (lane == 0) {
-        mbar_expect_tx(bar(B_MFULL + slot), (uint32_t)sizeof(TcRec));
-        bulk_g2s(smem_u32(ring + slot), a.recs + pf_r, (uint32_t)sizeof(TcRec), bar(B_MFULL + slot));
+        mbar_expect_tx(bar(B_MFULL + slot), (uint32_t)sizeof(TcUnitRec));
+        bulk_g2s(smem_u32(ring + slot), a.recs + pf_r, (uint32_t)sizeof(TcUnitRec), bar(B_MFULL + slot));
       }
       __syncwarp();
       ++pf_r;
@@ -354,7 +426,17 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
       return true;
     };
     long long s = 0;
-    int prev_slot = -1;
+    int prev_slot = -1, prev_j = 0;  // sub-unit whose stage 2 is still to be produced
+    auto finish_prev = [&]() {
+      if (prev_slot < 0) return;
+      const TcUnitRec& pu = ring[prev_slot];
+      produce_s2(pu, prev_j);
+      if (prev_j == n_chunks(pu) - 1) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar(B_MEMPTY + prev_slot));
+      }
+      prev_slot = -1;
+    };
     for (;;) {
       while (ok && pf_s < s + PREFETCH && prefetch_one()) {
       }
@@ -362,41 +444,37 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
       if (s == pf_s) break;  // nothing left
       const int slot = (int)(s % NMETA);
       if (!mbar_wait<PROF>(bar(B_MFULL + slot), (uint32_t)((s / NMETA) & 1), abort_flag, a.err, 10)) { ok = false; break; }
-      const TcRec& u = ring[slot];
-      if (!(u.flags & REC_ZERO))
-        for (int k = 0; k < rec_k1(u); ++k) produce(u, k, -1);
-      if (prev_slot >= 0) {
-        const TcRec& pu = ring[prev_slot];
-        for (int h = 0; h < rec_k2(pu); ++h) produce(pu, -1, h);
-        __syncwarp();
-        if (lane == 0) mbar_arrive(bar(B_MEMPTY + prev_slot));
-      }
-      if (u.flags & REC_ZERO) {
+      const TcUnitRec& u = ring[slot];
+      if (u.flags & TC_ZERO) {
         __syncwarp();
         if (lane == 0) mbar_arrive(bar(B_MEMPTY + slot));
-        prev_slot = -1;
       } else {
-        prev_slot = slot;
+        for (int j = 0; j < n_chunks(u) && ok; ++j) {
+          produce_s1(u, j);
+          finish_prev();
+          prev_slot = slot;
+          prev_j = j;
+        }
       }
       ++s;
     }
-    if (ok && prev_slot >= 0) {
-      const TcRec& pu = ring[prev_slot];
-      for (int h = 0; h < rec_k2(pu); ++h) produce(pu, -1, h);
-      __syncwarp();
-      if (lane == 0) mbar_arrive(bar(B_MEMPTY + prev_slot));
-    }
-    // terminator record
+    // terminator record, pushed before the last sub-unit's stage-2 operands:
+    // the MMA issuer reads it before it consumes those stages, and they can
+    // be more than the ring holds
     if (ok) {
       const int slot = (int)(s % NMETA);
       const uint32_t par = (uint32_t)(((s / NMETA) & 1) ^ 1);
       if (mbar_wait<PROF>(bar(B_MEMPTY + slot), par, abort_flag, a.err, 11)) {
         if (lane == 0) {
-          ring[slot].flags = REC_DONE;
+          ring[slot].flags = TC_DONE;
           mbar_arrive(bar(B_MFULL + slot));
         }
+      } else {
+        ok = false;
       }
+      __syncwarp();
     }
+    if (ok) finish_prev();
     __syncwarp();
     // drain: wait (bounded) until the MMA side released every stage we filled
     for (int k = 0; k < STAGES; ++k) {
@@ -417,11 +495,11 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
       uint32_t xcnt = 0, xph_empty = 3u;   // bit b: expected parity of X-empty[b]
       uint32_t a2_full_ph = 0;
       uint32_t sb = 0, sph_empty = 3u;     // bit b: expected parity of S-empty[b]
-      bool seg_open = false, ok = true;
+      bool ok = true;
       auto acquire = [&]() -> uint32_t {
         if (!mbar_wait<PROF>(bar(B_FULL + stage), phase, abort_flag, a.err, 4)) { ok = false; return 0; }
         asm volatile("tcgen05.fence::after_thread_sync;\n");
-        return sbase + stage * STAGE_BYTES;
+        return sbase + STAGE_OFF + stage * STAGE_BYTES;
       };
       auto release = [&]() {
         const long long t0 = tick();
@@ -429,46 +507,26 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
         tock(15, t0);
         if (++stage == STAGES) { stage = 0; phase ^= 1; }
       };
-      auto mma_k1 = [&](const TcRec& u) {
+      // stage 1 of sub-unit (u, j): X = stacked left rows x psi chunk j
+      auto mma_s1 = [&](const TcUnitRec& u, int j) {
         const uint32_t xb = xcnt & 1;
         if (!mbar_wait<PROF>(bar(B_XEMPTY + xb), (xph_empty >> xb) & 1u, abort_flag, a.err, 3)) { ok = false; return; }
         xph_empty ^= 1u << xb;
         asm volatile("tcgen05.fence::after_thread_sync;\n");
         const uint32_t tmem_x = tmem + xb * 128;
-        if (u.flags & UNIT_PACKED) {
+        const int tA = (u.flags & TC_TA) ? 1 : 0;
+        const uint32_t id1 = idesc_bf16(16 * ((chunk_cols(u, j) + 15) / 16), tA, 1);
+        const uint32_t a_lbo = tA ? 16u * TILE3 : TILE3, a_sbo = tA ? TILE3 : 4u * TILE3;
+        const int pR8 = u.pR8, nk1 = k1_stages(u);  // read once: the waits below clobber memory
+        bool first = true;
+        for (int k = 0; k < nk1 && ok; ++k) {
           const uint32_t sst = acquire();
           if (!ok) return;
-          const int rg0 = u.r0 / 8;
-          for (int t = 0; t < u.ntask; ++t) {
-            const TcTaskRec& tk = u.t[t];
-            const int tA = tk.flags & 1;
-            const int aC8 = tk.aC8, pC8 = tk.pC8;
-            const int n16 = 16 * ((tk.pn + 15) / 16);
-            const uint32_t a_lbo = tA ? (uint32_t)min(16, aC8 - rg0) * TILE3 : TILE3;
-            const uint32_t a_sbo = tA ? TILE3 : (uint32_t)aC8 * TILE3;
-            const uint32_t b_lbo = (uint32_t)pC8 * TILE3;
-            const long long t0 = tick();
-            mma_chain<NPROD>(tmem_x + tk.xcol, sdesc(sst + tk.k1a * TILE3, a_lbo, a_sbo),
-                             sdesc(sst + tk.k1b * TILE3, b_lbo, TILE3), 128u, 128u, 2 * a_lbo, 2 * b_lbo,
-                             tk.pR8 / 2, idesc_bf16(n16, tA, 1), false);
-            tock(14, t0);
-          }
+          const long long t0 = tick();
+          mma_chain<NPROD>(tmem_x, sdesc(sst, a_lbo, a_sbo), sdesc(sst + PSI_TILE * TILE3, 16u * TILE3, TILE3),
+                           128u, 128u, 2 * a_lbo, 2 * 16u * TILE3, min(4, pR8 - 4 * k) / 2, id1, first);
+          tock(14, t0);
           release();
-        } else {
-          const TcTaskRec& tk = u.t[0];
-          const int tA = tk.flags & 1;
-          const uint32_t id1 = idesc_bf16(16 * ((u.width + 15) / 16), tA, 1);
-          const uint32_t a_lbo = tA ? 16u * TILE3 : TILE3, a_sbo = tA ? TILE3 : 4u * TILE3;
-          const int pR8 = tk.pR8, nk = (pR8 + 3) / 4;
-          for (int k = 0; k < nk && ok; ++k) {
-            const uint32_t sst = acquire();
-            if (!ok) return;
-            const long long t0 = tick();
-            mma_chain<NPROD>(tmem_x, sdesc(sst, a_lbo, a_sbo), sdesc(sst + PSI_TILE * TILE3, 16u * TILE3, TILE3),
-                             128u, 128u, 2 * a_lbo, 2 * 16u * TILE3, min(4, pR8 - 4 * k) / 2, id1, k > 0);
-            tock(14, t0);
-            release();
-          }
         }
         {
           const long long t0 = tick();
@@ -477,90 +535,112 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
         }
         ++xcnt;
       };
-      auto mma_k2 = [&](const TcRec& u) {
-        const uint32_t id_n = (uint32_t)(16 * ((u.ncols + 15) / 16));
+      // stage 2 of sub-unit (u, j): per half, per term, sigma += X_t R_t^T,
+      // the tile accumulator switching buffers after every flush group
+      auto mma_s2 = [&](const TcUnitRec& u, int j) {
         const uint32_t a2 = sbase + A2_OFF;
-        const int nk2 = rec_k2(u);
-        for (int h = 0; h < nk2 && ok; ++h) {
+        const int tB = (u.flags & TC_TB) ? 1 : 0, te = tn8e(u), G = u.nterm, F = flush_terms(u, a.max_chain);
+        const uint32_t id2 = idesc_bf16(16 * ((u.tn + 15) / 16), 0, tB);
+        const int nh = n_halves(u, j), tm8 = u.tm8, ccols = chunk_cols(u, j);
+        const bool whole = whole_chunk_group(u, j, a.max_chain);
+        bool first = true;
+        for (int h = 0; h < nh && ok; ++h) {
           if (!mbar_wait<PROF>(bar(B_A2FULL), a2_full_ph, abort_flag, a.err, 5)) { ok = false; return; }
           a2_full_ph ^= 1;
-          if (!seg_open) {
-            if (!mbar_wait<PROF>(bar(B_SEMPTY + sb), (sph_empty >> sb) & 1u, abort_flag, a.err, 2)) { ok = false; return; }
-            sph_empty ^= 1u << sb;
+          const int kw = min(64, ccols - 64 * h), kg2 = kg2_of(kw), P = max(1, min(G, STAGE_TILES / (te * kg2)));
+          const uint32_t b_lbo = tB ? (uint32_t)te * TILE3 : TILE3;
+          const uint32_t b_sbo = tB ? TILE3 : (uint32_t)kg2 * TILE3;
+          for (int q0 = 0; q0 < G && ok; q0 += P) {
+            const uint32_t sst = acquire();
+            if (!ok) return;
+            for (int q = q0; q < min(G, q0 + P); ++q) {
+              const bool gstart = whole ? h == 0 : q % F == 0;
+              const bool gend = whole ? h == nh - 1 : (q % F == F - 1 || q == G - 1);
+              if (gstart) {  // a flush group starts: its tile accumulator must be free
+                if (!mbar_wait<PROF>(bar(B_SEMPTY + sb), (sph_empty >> sb) & 1u, abort_flag, a.err, 2)) {
+                  ok = false;
+                  return;
+                }
+                sph_empty ^= 1u << sb;
+                asm volatile("tcgen05.fence::after_thread_sync;\n");
+                first = true;
+              }
+              const long long t0 = tick();
+              mma_chain<NPROD>(tmem + 256 + sb * 128, sdesc(a2 + (uint32_t)(q * tm8) * 1024u, 128u, 1024u),
+                               sdesc(sst + (uint32_t)((q - q0) * te * kg2) * TILE3, b_lbo, b_sbo), A2_SLICE, 128u,
+                               2 * 128u, 2 * b_lbo, kg2 / 2, id2, first);
+              tock(14, t0);
+              if (gend) {  // the group ends: hand the accumulator to the epilogue
+                const long long t1 = tick();
+                commit(bar(B_SFULL + sb));
+                tock(15, t1);
+                sb ^= 1;
+              }
+            }
+            release();
           }
-          const uint32_t sst = acquire();
-          if (!ok) return;
-          const uint32_t tmem_s = tmem + 256 + sb * 128;
-          const int tB = (u.t[0].flags >> 1) & 1;
-          const uint32_t id2 = idesc_bf16((int)id_n, 0, tB);
-          uint32_t b_lbo, b_sbo;
-          int nks;
-          if (u.flags & UNIT_PACKED) {  // one K-concatenated chain for all tasks of the unit
-            const int nng = min(16, u.t[0].bC8 - u.c0 / 8);
-            b_lbo = tB ? (uint32_t)nng * TILE3 : TILE3;
-            b_sbo = tB ? TILE3 : (uint32_t)u.pad[0] * TILE3;
-            nks = u.width / 16;
-          } else {
-            b_lbo = tB ? 16u * TILE3 : TILE3;
-            b_sbo = tB ? TILE3 : 8u * TILE3;
-            nks = (min(64, u.width - h * 64) + 15) / 16;
-          }
-          const long long t0 = tick();
-          mma_chain<NPROD>(tmem_s, sdesc(a2, 128u, 1024u), sdesc(sst, b_lbo, b_sbo), A2_SLICE, 128u, 2 * 128u,
-                           2 * b_lbo, nks, id2, seg_open);
-          tock(14, t0);
-          seg_open = true;
-          release();
           const long long t1 = tick();
           commit(bar(B_A2EMPTY));
           tock(15, t1);
         }
-        if (ok && (u.flags & UNIT_ENDS_SEGMENT)) {
-          commit(bar(B_SFULL + sb));
-          sb ^= 1;
-          seg_open = false;
-        }
       };
       long long s = 0;
-      int prev_slot = -1;
+      int prev_slot = -1, prev_j = 0;
+      auto finish_prev = [&]() {
+        if (prev_slot < 0 || !ok) return;
+        const TcUnitRec& pu = ring[prev_slot];
+        mma_s2(pu, prev_j);
+        if (prev_j == n_chunks(pu) - 1) mbar_arrive(bar(B_MEMPTY + prev_slot));
+        prev_slot = -1;
+      };
       while (ok) {
         const int slot = (int)(s % NMETA);
         if (!mbar_wait<PROF>(bar(B_MFULL + slot), (uint32_t)((s / NMETA) & 1), abort_flag, a.err, 12)) { ok = false; break; }
-        const TcRec& u = ring[slot];
+        const TcUnitRec& u = ring[slot];
         const int fl = u.flags;
-        if (fl & REC_DONE) break;
-        if (!(fl & REC_ZERO)) mma_k1(u);
-        if (prev_slot >= 0 && ok) {
-          mma_k2(ring[prev_slot]);
-          mbar_arrive(bar(B_MEMPTY + prev_slot));
-        }
-        if (fl & REC_ZERO) {
+        if (fl & TC_DONE) break;
+        if (fl & TC_ZERO) {
           mbar_arrive(bar(B_MEMPTY + slot));
-          prev_slot = -1;
         } else {
-          prev_slot = slot;
+          for (int j = 0; j < n_chunks(u) && ok; ++j) {
+            mma_s1(u, j);
+            finish_prev();
+            prev_slot = slot;
+            prev_j = j;
+          }
         }
         ++s;
       }
-      if (ok && prev_slot >= 0) {
-        mma_k2(ring[prev_slot]);
-        mbar_arrive(bar(B_MEMPTY + prev_slot));
-      }
+      finish_prev();
     }
     __syncwarp();
   } else {
     // ---------------------------------------------------------- epilogue
     const int e = warp - 2;                    // 0 .. NEPI-1
     const int quarter = warp & 3;              // TMEM lanes 32*quarter .. +31
-    const int half = e >> 2;                   // columns 32*half of each 64-column chunk
-    const int row = quarter * 32 + lane;       // output / X row owned by this thread
+    const int half = e >> 2;                   // columns 64*half .. +63 of a tile, 32*half .. +31 of an X half
+    const int row = quarter * 32 + lane;       // TMEM lane owned by this thread
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-    uint32_t xcnt = 0, xph_full = 0;    // bit b: expected parity of X-full[b]
+    uint32_t xcnt = 0, xph_full = 0;           // bit b: expected parity of X-full[b]
     uint32_t a2_empty_ph = 1;
-    uint32_t sb = 0, sph_full = 0;      // bit b: expected parity of S-full[b]
+    uint32_t sb = 0, sph_full = 0;             // bit b: expected parity of S-full[b]
     bool ok = true;
     __nv_bfloat16* a2 = reinterpret_cast<__nv_bfloat16*>(sm + A2_OFF);
-    // write 32 K-columns (half of a 64-column chunk) of A2 for this row
+    // running sum of this thread's 64 tile columns: compensated (Kahan) FP32
+    // sums s and their compensation c, the sum being s - c. c is the rounding
+    // error of the last addition (below half an ulp of s) and is kept in bf16,
+    // two per register: its own 8 bits leave a residual of about 2^-9 ulp(s)
+    // per addition, so the running sum holds about 33 bits.
+    float ahi[2][32];
+    uint32_t alc[2][16];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) ahi[c][i] = 0.f;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) alc[c][i] = 0u;
+    }
+    // write 32 K-columns (half of a 64-column X half) of A2 for this row
     auto write_a2 = [&](const float* v) {
 #pragma unroll
       for (int g = 0; g < 4; ++g) {
@@ -588,80 +668,122 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
       __syncwarp();
       if (lane == 0) mbar_arrive(bar(B_A2FULL));
     };
+    // add the tile accumulator of the next flush group into the running sum
+    auto flush = [&](const TcUnitRec& u) -> bool {
+      if (!mbar_wait<PROF>(bar(B_SFULL + sb), (sph_full >> sb) & 1u, abort_flag, a.err, 8)) return false;
+      sph_full ^= 1u << sb;
+      asm volatile("tcgen05.fence::after_thread_sync;\n");
+      if (quarter * 32 < u.tm) {  // warp-uniform: this warp owns tile rows
+        const bool rv = row < u.tm;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const int col0 = half * 64 + c * 32;
+          if (col0 < u.tn) {  // warp-uniform
+            float w[32];
+            tmem_ld32(tmem + lane_off + 256 + sb * 128 + col0, w);
+            const int nc = u.tn - col0;
+            if (rv) {
+#pragma unroll
+              for (int g8 = 0; g8 < 4; ++g8) {
+                if (g8 * 8 < nc) {  // warp-uniform: skip column groups past the tile
+#pragma unroll
+                  for (int k = 4 * g8; k < 4 * g8 + 4; ++k) {  // Kahan: s + (w - c), the new error in c
+                    float cc[2] = {__uint_as_float(alc[c][k] << 16), __uint_as_float(alc[c][k] & 0xFFFF0000u)};
+#pragma unroll
+                    for (int e2 = 0; e2 < 2; ++e2) {
+                      const int i = 2 * k + e2;
+                      const float y = (i < nc ? w[i] : 0.0f) - cc[e2];
+                      const float t = ahi[c][i] + y;
+                      cc[e2] = (t - ahi[c][i]) - y;
+                      ahi[c][i] = t;
+                    }
+                    alc[c][k] = bf16x2_bits(cc[0], cc[1]);
+                  }
+                }
+              }
+            }
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(B_SEMPTY + sb));
+      sb ^= 1;
+      return true;
+    };
     long long s = 0;
     while (ok) {
       const int slot = (int)(s % NMETA);
       if (!mbar_wait<PROF>(bar(B_MFULL + slot), (uint32_t)((s / NMETA) & 1), abort_flag, a.err, 13)) { ok = false; break; }
-      const TcRec& u = ring[slot];
+      const TcUnitRec& u = ring[slot];
       const int fl = u.flags;
-      if (fl & REC_DONE) break;
+      if (fl & TC_DONE) break;
       double* out = a.scratch + u.slot;
-      if (fl & REC_ZERO) {
-        if (row < u.nrows)
-          for (int c = half * 64; c < min(u.ncols, half * 64 + 64); ++c) out[(long long)row * u.ncols + c] = 0.0;
+      if (fl & TC_ZERO) {
+        if (row < u.tm)
+          for (int c = half * 64; c < min(u.tn, half * 64 + 64); ++c) out[(long long)row * u.tn + c] = 0.0;
       } else {
-        const uint32_t xb = xcnt & 1;
-        if (!mbar_wait<PROF>(bar(B_XFULL + xb), (xph_full >> xb) & 1u, abort_flag, a.err, 6)) { ok = false; break; }
-        xph_full ^= 1u << xb;
-        asm volatile("tcgen05.fence::after_thread_sync;\n");
-        const uint32_t xaddr = tmem + lane_off + xb * 128;
-        float v[32];
-        const int nh = (fl & UNIT_PACKED) ? 1 : (u.width + 63) / 64;
-        for (int h = 0; h < nh; ++h) {
-          tmem_ld32(xaddr + h * 64 + half * 32, v);
-          if (h == nh - 1) {
-            asm volatile("tcgen05.fence::before_thread_sync;\n");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(bar(B_XEMPTY + xb));
+        if (fl & TC_ITEM_FIRST) {
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) ahi[c][i] = 0.f;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) alc[c][i] = 0u;
           }
-          // scale valid columns, zero the rest (K padding of the second product)
-          const int c0 = h * 64 + half * 32;
-          if (fl & UNIT_PACKED) {
-            float cs[32];
-#pragma unroll
-            for (int j = 0; j < 32; ++j) cs[j] = 0.0f;
-            for (int t = 0; t < u.ntask; ++t) {
-              const int x0 = u.t[t].xcol - c0, x1 = x0 + u.t[t].pn;
-              const float sc = u.t[t].scale;
-#pragma unroll
-              for (int j = 0; j < 32; ++j)
-                if (j >= x0 && j < x1) cs[j] = sc;
-            }
-#pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = cs[j] != 0.0f ? v[j] * cs[j] : 0.0f;
-          } else {
-            const float sc = u.t[0].scale;
-            const int valid = u.width - c0;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = j < valid ? v[j] * sc : 0.0f;
-          }
-          if (!mbar_wait<PROF>(bar(B_A2EMPTY), a2_empty_ph, abort_flag, a.err, 7)) { ok = false; break; }
-          a2_empty_ph ^= 1;
-          write_a2(v);
         }
-        ++xcnt;
-        if (!ok) break;
-        if (fl & UNIT_ENDS_SEGMENT) {
-          // segment's FP32 sigma tile -> FP64 slot (store on the first segment, add after)
-          if (!mbar_wait<PROF>(bar(B_SFULL + sb), (sph_full >> sb) & 1u, abort_flag, a.err, 8)) { ok = false; break; }
-          sph_full ^= 1u << sb;
+        // the term (and its scale) of this row of the stacked X
+        const int q = row / (u.tm8 * 8), rr = row - q * (u.tm8 * 8);
+        const float sc = (q < u.nterm && rr < u.tm) ? u.t[q].scale : 0.0f;
+        for (int j = 0; j < n_chunks(u) && ok; ++j) {
+          const uint32_t xb = xcnt & 1;
+          if (!mbar_wait<PROF>(bar(B_XFULL + xb), (xph_full >> xb) & 1u, abort_flag, a.err, 6)) { ok = false; break; }
+          xph_full ^= 1u << xb;
           asm volatile("tcgen05.fence::after_thread_sync;\n");
-          const bool first = fl & UNIT_FIRST_SEGMENT;
-          for (int c0 = half * 64; c0 < min(u.ncols, half * 64 + 64); c0 += 32) {
-            float w[32];
-            tmem_ld32(tmem + lane_off + 256 + sb * 128 + c0, w);
-            if (row < u.nrows) {
-              const int nc = min(32, u.ncols - c0);
-              double* o = out + (long long)row * u.ncols + c0;
+          const int nh = n_halves(u, j);
+          const bool whole = whole_chunk_group(u, j, a.max_chain);
+          const bool wrows = quarter * 32 < u.nterm * u.tm8 * 8;  // warp-uniform: stacked rows here
+          for (int h = 0; h < nh && ok; ++h) {
+            if (!mbar_wait<PROF>(bar(B_A2EMPTY), a2_empty_ph, abort_flag, a.err, 7)) { ok = false; break; }
+            a2_empty_ph ^= 1;
+            // this warp's 32 K-columns are read by the MMA only below 16 * ceil(kw / 16)
+            const int kw = half_cols(u, j, h);
+            const bool wvalid = wrows && half * 32 < 16 * ((kw + 15) >> 4);
+            float v[32];
+            if (wvalid) tmem_ld32(tmem + lane_off + xb * 128 + h * 64 + half * 32, v);
+            if (h == nh - 1) {
+              asm volatile("tcgen05.fence::before_thread_sync;\n");
+              __syncwarp();
+              if (lane == 0) mbar_arrive(bar(B_XEMPTY + xb));
+            }
+            if (wvalid) {
+              // scale valid columns, zero the rest (K padding of stage 2)
+              const int valid = kw - half * 32;
 #pragma unroll
-              for (int c = 0; c < 32; ++c)
-                if (c < nc) o[c] = first ? (double)w[c] : o[c] + (double)w[c];
+              for (int i = 0; i < 32; ++i) v[i] = i < valid ? v[i] * sc : 0.0f;
+              write_a2(v);
+            } else {  // no stacked rows here (A2 rows that feed only unread D rows) or K columns never read
+              __syncwarp();
+              if (lane == 0) mbar_arrive(bar(B_A2FULL));
+            }
+            // flush groups of this half, in the order the MMA issues them
+            if (whole) {
+              if (h == nh - 1) ok = flush(u);
+            } else {
+              for (int g0 = 0; g0 < u.nterm && ok; g0 += flush_terms(u, a.max_chain)) ok = flush(u);
             }
           }
-          asm volatile("tcgen05.fence::before_thread_sync;\n");
-          __syncwarp();
-          if (lane == 0) mbar_arrive(bar(B_SEMPTY + sb));
-          sb ^= 1;
+          ++xcnt;
+        }
+        if (ok && (fl & TC_ITEM_LAST) && row < u.tm) {
+#pragma unroll
+          for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              const int col = half * 64 + c * 32 + i;
+              const float cc = __uint_as_float((i & 1) ? (alc[c][i >> 1] & 0xFFFF0000u) : (alc[c][i >> 1] << 16));
+              if (col < u.tn) out[(long long)row * u.tn + col] = (double)ahi[c][i] - (double)cc;
+            }
         }
       }
       __syncwarp();
@@ -745,6 +867,7 @@ void launch_split_psi(const double* psi, const PsiBlock* blocks, const TcPsiBloc
 }
 
 void launch_sigma_tc(const TcDev& a, int n_sm, cudaStream_t st) {
+  if (a.n_items <= 0) return;
   set_max_dynamic_smem((const void*)sigma_tc_kernel<6, false>, SMEM_BYTES);
   set_max_dynamic_smem((const void*)sigma_tc_kernel<3, false>, SMEM_BYTES);
   set_max_dynamic_smem((const void*)sigma_tc_kernel<6, true>, SMEM_BYTES);

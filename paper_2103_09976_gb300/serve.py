@@ -8,6 +8,14 @@ with synthetic N(0,1) operator blocks seeded per request; latency is
 completion time minus arrival time.
 
     python -m paper_2103_09976_gb300.serve --requests 48 --rate 0
+
+With --rate auto the stream runs twice: first with every request arriving
+at once (the burst measures the capacity in solves/s), then as a Poisson
+stream at 80% of that capacity. The full request mix (256 solves, K in
+{24, 36, 54, 76, 108}, M in {250, 500, 1000, 2000, 4000}):
+
+    python -m paper_2103_09976_gb300.serve --requests 256 --rate auto \
+        --k 24,36,54,76,108 --m 250,500,1000,2000,4000
 """
 
 import argparse
@@ -32,6 +40,7 @@ def run_stream(requests, n_slots=4, budget_bytes=160 << 30, prec=capi.DMRG_BF16X
     arrival times (scaled by rate_scale; 0 = all at once) and collect results."""
     srv = capi.dmrg_server_create(device, n_slots, budget_bytes)
     results, rejected = {}, {}
+    peak = [0, 0]  # largest device bytes admitted at once, most solves running at once
     try:
         t0 = time.perf_counter()
         pending = sorted(requests, key=lambda r: r["t_arrive"])
@@ -49,8 +58,12 @@ def run_stream(requests, n_slots=4, budget_bytes=160 << 30, prec=capi.DMRG_BF16X
                 submitted += 1
             for res in capi.dmrg_server_poll(srv, 64, wait_ms=5):
                 results[res["id"]] = res
+            _, running, in_use = capi.dmrg_server_pending(srv)
+            peak[0] = max(peak[0], in_use)
+            peak[1] = max(peak[1], running)
     finally:
         capi.dmrg_server_destroy(srv)
+    run_stream.peak_bytes, run_stream.peak_running = peak
     return results, rejected
 
 
@@ -71,7 +84,8 @@ def main():
     from synth.requests import poisson_requests
     ap = argparse.ArgumentParser()
     ap.add_argument("--requests", type=int, default=48)
-    ap.add_argument("--rate", type=float, default=4.0, help="arrivals per second (0 = all at once)")
+    ap.add_argument("--rate", default="4.0",
+                    help="arrivals per second (0 = all at once; auto = burst, then Poisson at 80%% of its rate)")
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--budget-gb", type=float, default=160.0)
     ap.add_argument("--k", default="24,36,54")
@@ -80,13 +94,26 @@ def main():
     args = ap.parse_args()
     ks = tuple(int(x) for x in args.k.split(","))
     ms = tuple(int(x) for x in args.m.split(","))
-    reqs = poisson_requests(args.requests, rate_per_s=max(args.rate, 1e-9), seed=5, k_choices=ks, m_choices=ms)
-    res, rej = run_stream(reqs, n_slots=args.slots, budget_bytes=int(args.budget_gb * (1 << 30)),
-                          max_iter=args.max_iter, rate_scale=1.0 if args.rate > 0 else 0.0)
-    out = summarize(res, reqs)
-    out.update({"rejected": len(rej), "slots": args.slots, "budget_gb": args.budget_gb,
-                "rate_per_s": args.rate, "precision": "bf16x3 sigma, FP64 Davidson"})
-    print(json.dumps(out))
+    budget = int(args.budget_gb * (1 << 30))
+
+    def phase(rate):
+        reqs = poisson_requests(args.requests, rate_per_s=max(rate, 1e-9), seed=5 if rate == 0 else 6,
+                                k_choices=ks, m_choices=ms)
+        res, rej = run_stream(reqs, n_slots=args.slots, budget_bytes=budget, max_iter=args.max_iter,
+                              rate_scale=1.0 if rate > 0 else 0.0)
+        out = summarize(res, reqs)
+        out.update({"rejected": len(rej), "rate_per_s": rate, "peak_bytes_in_use": run_stream.peak_bytes,
+                    "peak_running": run_stream.peak_running})
+        return out
+
+    common = {"slots": args.slots, "budget_gb": args.budget_gb, "requests": args.requests,
+              "precision": "bf16x3 sigma, FP64 Davidson", "max_iter": args.max_iter}
+    if args.rate == "auto":
+        burst = phase(0.0)
+        stream = phase(0.8 * burst["solves_per_s"])
+        print(json.dumps(dict(common, burst=burst, poisson_at_80pct=stream)))
+    else:
+        print(json.dumps(dict(common, **phase(float(args.rate)))))
 
 
 if __name__ == "__main__":

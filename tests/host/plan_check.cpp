@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <fstream>
+#include <map>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -52,7 +53,7 @@ int main(int argc, char** argv) {
   build_tasks(blocks, oL, oR, terms, wl);
   build_items(blocks, wl, TileShape{32, 256, 2e6, 16384.0}, 152 * 8);
   TcPlan plan;
-  build_tc_plan(blocks, oL, oR, wl, plan, 152 * 4, 32);
+  build_tc_plan(blocks, oL, oR, wl, plan, TcShape{152 * 4});
 
   // (0) FP64 work list: groups tile every output block into 32 x 256 tiles;
   //     the items of a group split the block's task range in order; slots
@@ -96,73 +97,112 @@ int main(int argc, char** argv) {
       }
   }
 
-  // (1) every task of the list, with its operator tiles, appears in the plan
-  //     once per 128 x 128 tile of its output block
+  // (1) every task of the list appears once per 128 x 128 tile of its output
+  //     block: in a tensor-core unit record (by its operator tiles) or in a
+  //     small-class term (by its store offsets), never in both
   std::vector<long long> offs;
   for (const OpSet* s : {&oL, &oR})
     for (const OpDesc& o : s->ops)
       for (const OpBlock& b : o.blocks) offs.push_back(b.off);
-  using Key = std::tuple<int, int, long long, long long, unsigned>;
+  std::map<long long, long long> off_of_tile;  // operator tile -> store offset (identity tiles absent)
+  for (size_t i = 0; i < plan.opblocks.size(); ++i) off_of_tile[plan.opblocks[i].tile] = offs[i];
+  std::map<long long, int> blk_of_ptile;
+  for (size_t i = 0; i < plan.psi.size(); ++i) blk_of_ptile[plan.psi[i].tile] = (int)i;
+  using Key = std::tuple<int, unsigned, long long, long long, unsigned>;
   std::vector<Key> want, got;
   std::vector<int> out_of(wl.tasks.size(), -1);
   for (size_t b = 0; b < blocks.size(); ++b)
     for (int t = wl.out_start[b]; t < wl.out_start[b + 1]; ++t) out_of[t] = (int)b;
   for (size_t t = 0; t < wl.tasks.size(); ++t) {
     const Task& k = wl.tasks[t];
-    const PsiBlock& in = blocks[k.in_blk];
-    long long at = plan.identL[in.qL].tile, bt = plan.identR[in.qR].tile;
-    if (k.aoff >= 0) {
-      const int i = wl.task_ablk[t];
-      if (i < 0 || offs[i] != k.aoff) fail("task left block index");
-      else at = plan.opblocks[i].tile;
-    }
-    if (k.boff >= 0) {
-      const int i = wl.task_bblk[t];
-      if (i < 0 || offs[i] != k.boff) fail("task right block index");
-      else bt = plan.opblocks[i].tile;
-    }
+    if (k.aoff >= 0 && (wl.task_ablk[t] < 0 || offs[wl.task_ablk[t]] != k.aoff)) fail("task left block index");
+    if (k.boff >= 0 && (wl.task_bblk[t] < 0 || offs[wl.task_bblk[t]] != k.boff)) fail("task right block index");
     const float sc = (float)k.scale;
     unsigned bits;
     std::memcpy(&bits, &sc, 4);
-    const int fl = (k.aoff >= 0 ? (k.flags & 1) : 0) | (k.boff >= 0 ? (k.flags & 2) : 0);
+    const unsigned fl = (k.aoff >= 0 ? (k.flags & 1) : 0) | (k.boff >= 0 ? (k.flags & 2) : 0);
     const PsiBlock& ob = blocks[out_of[t]];
     const int ntile = ((ob.mL + 127) / 128) * ((ob.mR + 127) / 128);
-    for (int r = 0; r < ntile; ++r) want.emplace_back(k.in_blk, fl, at, bt, bits);
+    for (int r = 0; r < ntile; ++r) want.emplace_back(k.in_blk, fl, k.aoff, k.boff, bits);
   }
-  for (const TcTask& x : plan.tasks) {
+  long long nterms = 0;
+  for (const TcUnitRec& r : plan.recs) {
+    if (r.flags & TC_ZERO) continue;
+    const unsigned fl = ((r.flags & TC_TA) ? 1u : 0u) | ((r.flags & TC_TB) ? 2u : 0u);
+    const auto pb = blk_of_ptile.find(r.p_tile);
+    if (pb == blk_of_ptile.end()) fail("record psi tile");
+    for (int q = 0; q < r.nterm && q < TC_MAX_G; ++q) {
+      unsigned bits;
+      std::memcpy(&bits, &r.t[q].scale, 4);
+      const auto ia = off_of_tile.find(r.t[q].a_tile), ib = off_of_tile.find(r.t[q].b_tile);
+      const long long ao = ia == off_of_tile.end() ? -1 : ia->second, bo = ib == off_of_tile.end() ? -1 : ib->second;
+      got.emplace_back(pb == blk_of_ptile.end() ? -1 : pb->second, fl, ao, bo, bits);
+    }
+    nterms += r.nterm;
+  }
+  for (const SmallTerm& x : plan.small) {
+    const float sc = (float)x.scale;
     unsigned bits;
-    std::memcpy(&bits, &x.scale, 4);
-    got.emplace_back(x.in_blk, x.flags & 3, x.a_tile, x.b_tile, bits);
+    std::memcpy(&bits, &sc, 4);
+    const unsigned fl = (x.a_off >= 0 ? (x.flags & 1) : 0) | (x.b_off >= 0 ? (x.flags & 2) : 0);
+    got.emplace_back(x.in_blk, fl, x.a_off, x.b_off, bits);
+    ++nterms;
   }
   std::sort(want.begin(), want.end());
   std::sort(got.begin(), got.end());
-  if (want != got) fail("plan tasks differ from the task list");
+  if (want != got) fail("plan terms differ from the task list");
+  if (nterms != plan.n_terms) fail("term count");
 
-  // (2) units of each item point back to it; task ranges tile the task list in order
-  int next_task = 0;
+  // (2) records of every tensor-core item: first / last flags, the item's
+  //     tile, unit geometry consistent with the blocks it reads; terms of
+  //     every small item: contiguous ranges, small blocks only
+  long long nunit = 0;
+  int next_rec = 0, next_small = 0;
   for (size_t i = 0; i < plan.items.size(); ++i) {
     const TcItem& it = plan.items[i];
-    for (int u = it.u_begin; u < it.u_end; ++u) {
-      const TcUnit& un = plan.units[u];
-      if (un.item != (int)i) fail("unit item");
-      if (un.t_begin >= un.t_end) fail("empty unit");
-      if (un.flags & UNIT_PACKED) {
-        if (un.t_begin != next_task) fail("packed unit out of order");
-        if (un.width > 64) fail("packed width");
-        next_task = un.t_end;
-      } else {
-        if (un.t_end != un.t_begin + 1) fail("pass unit of more than one task");
-        if (un.pass == 0) {
-          if (un.t_begin != next_task) fail("pass unit out of order");
-          next_task = un.t_end;
-        }
+    if (it.r_end <= it.r_begin) fail("item without records or terms");
+    if (it.kind == 1) {
+      if (it.r_begin != next_small) fail("small term ranges");
+      next_small = it.r_end;
+      if (it.nrows > TC_SMALL_MAX || it.ncols > TC_SMALL_MAX || it.r0 != 0 || it.c0 != 0) fail("small item tile");
+      for (int k = it.r_begin; k < it.r_end && k < (int)plan.small.size(); ++k) {
+        const PsiBlock& ib = blocks[plan.small[k].in_blk];
+        if (ib.mL > TC_SMALL_MAX || ib.mR > TC_SMALL_MAX) fail("small term with a large psi block");
       }
-      const TcTask& t = plan.tasks[un.t_begin];
-      if (plan.items[i].out < 0 || t.in_blk < 0 || t.in_blk >= (int)blocks.size()) fail("task input block");
+      continue;
     }
-    if (i + 1 < plan.items.size() && plan.items[i + 1].u_begin != it.u_end) fail("item unit ranges");
+    if (it.r_begin != next_rec) fail("item record ranges");
+    next_rec = it.r_end;
+    for (int k = it.r_begin; k < it.r_end && k < (int)plan.recs.size(); ++k) {
+      const TcUnitRec& r = plan.recs[k];
+      const bool first = k == it.r_begin, last = k == it.r_end - 1;
+      if (((r.flags & TC_ITEM_FIRST) != 0) != first || ((r.flags & TC_ITEM_LAST) != 0) != last) fail("item flags");
+      if (r.tm != it.nrows || r.tn != it.ncols || r.r0g * 8 != it.r0 || r.c0g * 8 != it.c0 || r.slot != it.slot)
+        fail("record tile");
+      if (r.tm8 != (r.tm + 7) / 8) fail("record tm8");
+      if (r.flags & TC_ZERO) {
+        if (it.r_end - it.r_begin != 1) fail("zero record in a non-empty item");
+        continue;
+      }
+      ++nunit;
+      if (r.nterm < 1 || (r.nterm * r.tm8 > 16 && r.nterm > 1)) fail("stacked rows exceed 128");
+      if (std::max(std::max(blocks[it.out].mL, blocks[it.out].mR), std::max(r.m, r.n)) <= TC_SMALL_MAX)
+        fail("small class in a unit");
+      const TcPsiBlock* pb = nullptr;
+      for (const TcPsiBlock& x : plan.psi)
+        if (x.tile == r.p_tile) pb = &x;
+      if (!pb || pb->m != r.m || pb->n != r.n || pb->R8 != r.pR8 || pb->C8 != r.pC8) fail("record psi block");
+      // the left block covers the tile rows (M) and psi rows (K); the right
+      // block covers the tile columns (N) and psi columns (K)
+      const bool tA = r.flags & TC_TA, tB = r.flags & TC_TB;
+      const int aM8 = tA ? r.aC8 : r.aR8, aK8 = tA ? r.aR8 : r.aC8;
+      const int bN8 = tB ? r.bC8 : r.bR8, bK8 = tB ? r.bR8 : r.bC8;
+      if (aK8 != (r.m + 7) / 8 || bK8 != (r.n + 7) / 8) fail("operand K extent");
+      if (r.r0g + r.tm8 > aM8 || r.c0g + (r.tn + 7) / 8 > bN8) fail("operand M / N extent");
+    }
   }
-  if (next_task != (int)plan.tasks.size()) fail("units do not cover the tasks");
+  if (next_rec != (int)plan.recs.size() || next_small != (int)plan.small.size()) fail("records or small terms unused");
+  if (nunit != plan.n_units) fail("unit count");
 
   // (3) groups tile every output block into 128 x 128 tiles; items of a group share its tile
   size_t gi = 0;
@@ -192,8 +232,14 @@ int main(int argc, char** argv) {
   if (gi != plan.groups.size()) fail("extra groups");
   if (slot != plan.scratch_elems) fail("scratch size");
 
-  // (4) the schedule is a permutation of the items
+  // (4) the two schedules together are a permutation of the items, each
+  //     holding the items of its kind
   std::vector<int> sch = plan.schedule;
+  for (int i : plan.schedule)
+    if (plan.items[i].kind != 0) fail("tensor-core schedule holds a small item");
+  for (int i : plan.small_schedule)
+    if (plan.items[i].kind != 1) fail("small schedule holds a tensor-core item");
+  sch.insert(sch.end(), plan.small_schedule.begin(), plan.small_schedule.end());
   std::sort(sch.begin(), sch.end());
   for (size_t i = 0; i < sch.size(); ++i)
     if (sch[i] != (int)i) {
@@ -202,32 +248,94 @@ int main(int argc, char** argv) {
     }
   if (sch.size() != plan.items.size()) fail("schedule size");
 
-  // (5) records: one per unit (one REC_ZERO per item without units), copies of the tasks
-  for (size_t i = 0; i < plan.items.size(); ++i) {
-    const TcItem& it = plan.items[i];
-    const int nrec = plan.item_rec[i + 1] - plan.item_rec[i];
-    if (nrec != std::max(1, it.u_end - it.u_begin)) fail("record count");
-    if (it.u_begin == it.u_end) {
-      if (!(plan.recs[plan.item_rec[i]].flags & REC_ZERO)) fail("empty item record");
-      continue;
+  // MMA instructions per slice product (stage 1 per K step of 16, stage 2 per
+  // term and K step) and stages, as the kernel issues them
+  long long mma_s1 = 0, mma_s2 = 0, stages = 0;
+  for (const TcUnitRec& r : plan.recs) {
+    if (r.flags & TC_ZERO) continue;
+    for (int j = 0; j < (r.n + 127) / 128; ++j) {
+      mma_s1 += r.pR8 / 2;
+      stages += (r.pR8 + 3) / 4;
+      const int ncols = std::min(128, r.n - 128 * j);
+      for (int h = 0; h < (ncols + 63) / 64; ++h) {
+        const int kw = std::min(64, ncols - 64 * h), kg2 = 2 * ((kw + 15) / 16);
+        const int te = 2 * ((r.tn + 15) / 16), P = std::max(1, std::min(r.nterm, 128 / (te * kg2)));
+        mma_s2 += (long long)r.nterm * (kg2 / 2);
+        stages += (r.nterm + P - 1) / P;
+      }
     }
-    for (int u = it.u_begin; u < it.u_end; ++u) {
-      const TcRec& r = plan.recs[plan.item_rec[i] + (u - it.u_begin)];
-      const TcUnit& un = plan.units[u];
-      if (r.ntask != un.t_end - un.t_begin || r.ntask > 4 || r.pass != un.pass || r.slot != it.slot) fail("record");
-      for (int k = 0; k < r.ntask && k < 4; ++k) {
-        const TcTask& t = plan.tasks[un.t_begin + k];
-        if (r.t[k].a_tile != t.a_tile || r.t[k].b_tile != t.b_tile || r.t[k].p_tile != plan.psi[t.in_blk].tile ||
-            r.t[k].scale != t.scale || r.t[k].flags != t.flags)
-          fail("record task");
+  }
+
+  // (6) the kernel's copies, enumerated with its own formulas: every copy
+  //     lands inside its 128-position stage (stage 1: operator rows below
+  //     position 64, psi at 64..127) and reads inside the split arrays
+  {
+    const long long op_tiles = plan.n_tiles, psi_tiles = plan.psi_tiles;
+    auto src_ok = [&](long long src, int n, bool psi) {
+      return src >= 0 && n > 0 && src + n <= (psi ? psi_tiles : op_tiles);
+    };
+    for (const TcUnitRec& r : plan.recs) {
+      if (r.flags & TC_ZERO) continue;
+      const int G = r.nterm, tm8 = r.tm8;
+      const int nchunk = (r.n + 127) / 128;
+      for (int j = 0; j < nchunk; ++j) {
+        for (int k = 0; k < (r.pR8 + 3) / 4; ++k) {
+          const int kg0 = 4 * k;
+          if (!(r.flags & TC_TA)) {
+            const int nk = std::min(4, (int)r.aC8 - kg0);
+            if (nk > 0)
+              for (int q = 0; q < G; ++q)
+                for (int rg = 0; rg < tm8; ++rg) {
+                  const int dst = (q * tm8 + rg) * 4;
+                  if (dst + nk > 64 || !src_ok(r.t[q].a_tile + (long long)(r.r0g + rg) * r.aC8 + kg0, nk, false))
+                    fail("stage-1 operator copy out of bounds");
+                }
+          } else {
+            for (int q = 0; q < G; ++q)
+              for (int kg = 0; kg < 4 && kg0 + kg < r.aR8; ++kg) {
+                const int dst = kg * 16 + q * tm8;
+                if (q * tm8 + tm8 > 16 || dst + tm8 > 64 ||
+                    !src_ok(r.t[q].a_tile + (long long)(kg0 + kg) * r.aC8 + r.r0g, tm8, false))
+                  fail("stage-1 transposed operator copy out of bounds");
+              }
+          }
+          const int nn = std::min(16, (int)r.pC8 - 16 * j);
+          for (int kg = 0; kg < 4 && kg0 + kg < r.pR8; ++kg)
+            if (64 + kg * 16 + nn > 128 || !src_ok(r.p_tile + (long long)(kg0 + kg) * r.pC8 + 16 * j, nn, true))
+              fail("stage-1 psi copy out of bounds");
+        }
+        const int ncols = std::min(128, r.n - 128 * j);
+        for (int h = 0; h < (ncols + 63) / 64; ++h) {
+          const int kw = std::min(64, ncols - 64 * h), kg2 = 2 * ((kw + 15) / 16), kgx = 16 * j + 8 * h;
+          const int te = 2 * ((r.tn + 15) / 16), tn8 = (r.tn + 7) / 8;
+          const int P = std::max(1, std::min(G, 128 / (te * kg2)));
+          for (int q0 = 0; q0 < G; q0 += P)
+            for (int q = q0; q < std::min(G, q0 + P); ++q) {
+              const int reg = (q - q0) * te * kg2;
+              if (reg + te * kg2 > 128) fail("stage-2 region beyond the stage");
+              if (!(r.flags & TC_TB)) {
+                const int nk = std::min(kg2, (int)r.bC8 - kgx);
+                for (int ng = 0; ng < tn8; ++ng)
+                  if (reg + ng * kg2 + nk > 128 ||
+                      !src_ok(r.t[q].b_tile + (long long)(r.c0g + ng) * r.bC8 + kgx, nk, false))
+                    fail("stage-2 operator copy out of bounds");
+              } else {
+                for (int kg = 0; kg < kg2 && kgx + kg < r.bR8; ++kg)
+                  if (reg + kg * te + tn8 > 128 ||
+                      !src_ok(r.t[q].b_tile + (long long)(kgx + kg) * r.bC8 + r.c0g, tn8, false))
+                    fail("stage-2 transposed operator copy out of bounds");
+              }
+            }
+        }
       }
     }
   }
 
   std::printf("{\"psi_size\": %lld, \"blocks\": %zu, \"terms\": %zu, \"tasks\": %zu, \"flops\": %.17g, "
-              "\"plan_tasks\": %zu, \"units\": %zu, \"items\": %zu, \"layout\": [",
-              size, blocks.size(), terms.size(), wl.tasks.size(), wl.flops, plan.tasks.size(), plan.units.size(),
-              plan.items.size());
+              "\"plan_tasks\": %lld, \"units\": %lld, \"items\": %zu, \"mma_s1\": %lld, \"mma_s2\": %lld, "
+              "\"stages\": %lld, \"layout\": [",
+              size, blocks.size(), terms.size(), wl.tasks.size(), wl.flops, plan.n_terms, plan.n_units,
+              plan.items.size(), mma_s1, mma_s2, stages);
   for (size_t b = 0; b < blocks.size(); ++b) {
     const PsiBlock& pb = blocks[b];
     std::printf("%s[%d, %d, %d, %d, %d, %d, %lld]", b ? ", " : "", L.q[pb.qL].n, L.q[pb.qL].s, R.q[pb.qR].n,

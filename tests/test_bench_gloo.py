@@ -1,5 +1,6 @@
 """The multi-rank logic of bench.py on two CPU ranks (gloo): the step time
-is the maximum over ranks, the value counts every replica's work, and the
+is the maximum over ranks, the value counts every replica's work (replica
+mode) or the one sigma the ranks share (sub-Hamiltonian split), and the
 reference arm prints only on rank 0."""
 
 import json
@@ -30,7 +31,7 @@ def _rank(rank, world, port, out):
     import bench
     step = [0.25, 0.75][rank]
     m = bench.world_max(step, dist, "cpu")
-    np.save(f"{out}_{rank}.npy", np.array([m, bench.replica_value(1e12, m, world)]))
+    np.save(f"{out}_{rank}.npy", np.array([m, bench.replica_value(1e12, m, world), bench.split_value(1e12, m)]))
     dist.destroy_process_group()
 
 
@@ -38,9 +39,10 @@ def test_step_time_is_max_over_ranks(tmp_path):
     out = str(tmp_path / "r")
     mp.spawn(_rank, args=(2, _port(), out), nprocs=2, join=True)
     for r in range(2):
-        m, v = np.load(f"{out}_{r}.npy")
+        m, v, sv = np.load(f"{out}_{r}.npy")
         assert m == 0.75
         assert abs(v - 2 * 1e12 / 0.75 / 1e12) < 1e-12
+        assert abs(sv - 1e12 / 0.75 / 1e12) < 1e-12
 
 
 def test_reference_arm_other_ranks_print_nothing():
