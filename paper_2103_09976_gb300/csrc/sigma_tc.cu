@@ -26,7 +26,8 @@
 // FP32 accumulation chain of stage 2.
 //
 // Warp roles (320 threads): warp 0 streams operator and psi tiles with
-// cp.async.bulk into a 3-stage ring; warp 1 issues the MMAs; warps 2-9 are
+// cp.async.bulk into a 3-stage ring; warp 1 issues the MMAs (one lane of a
+// warp that runs the control flow uniformly); warps 2-9 are
 // the epilogue (two warps per TMEM lane quarter, 64 columns each). Tensor
 // memory: two 128-column X buffers, two 128-column tile accumulators.
 // Operands are stored in 8x8 core-matrix tiles, so one stored block serves as
@@ -152,11 +153,6 @@ __device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
   return *reinterpret_cast<const uint32_t*>(&p);
 }
 
-__device__ __forceinline__ void mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
-  asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-               ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-}
 __device__ __forceinline__ void commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
                ::"r"(bar) : "memory");
@@ -185,9 +181,6 @@ __device__ __forceinline__ int half_cols(const TcUnitRec& r, int j, int h) { ret
 __device__ __forceinline__ int k1_stages(const TcUnitRec& r) { return (r.pR8 + 3) >> 2; }
 __device__ __forceinline__ int tn8e(const TcUnitRec& r) { return 2 * ((r.tn + 15) >> 4); }  // N groups read by the MMA
 __device__ __forceinline__ int kg2_of(int kw) { return 2 * ((kw + 15) >> 4); }               // K groups of a half
-__device__ __forceinline__ int terms_per_stage(const TcUnitRec& r, int kw) {
-  return max(1, min(r.nterm, STAGE_TILES / (tn8e(r) * kg2_of(kw))));
-}
 // Terms per flush group: the most whose main K steps in one half stay within
 // max_chain (at least one); max_chain <= 0: the whole unit.
 __device__ __forceinline__ int flush_terms(const TcUnitRec& r, int max_chain) {
@@ -289,22 +282,57 @@ __device__ __forceinline__ constexpr int prod_j(int p) { return (p == 1 || p == 
 // K steps first, then the main (hi x hi) ones. Descriptors differ only in
 // the start-address field, so each MMA adds its byte offset >> 4 to a base.
 // `first`: the next MMA overwrites the accumulator (cleared after it).
-template <int NPROD>
-__device__ __forceinline__ void mma_chain(uint32_t tmem_d, uint64_t ad0, uint64_t bd0, uint32_t a_slice,
-                                          uint32_t b_slice, uint32_t a_kstep, uint32_t b_kstep, int nks,
-                                          uint32_t idesc, bool& first) {
-  for (int ks = 0; ks < nks; ++ks) {
+// One MMA from descriptors given as 32-bit halves (the start-address field
+// is in the low half: offsets are added there, without a 64-bit add).
+__device__ __forceinline__ void mma_lohi(uint32_t tmem, uint32_t alo, uint32_t ahi, uint32_t blo, uint32_t bhi,
+                                         uint32_t idesc, uint32_t acc) {
+  asm volatile("{\n.reg .b64 ad, bd;\n.reg .pred p;\nmov.b64 ad, {%1, %2};\nmov.b64 bd, {%3, %4};\n"
+               "setp.ne.b32 p, %6, 0;\n"
+               "tcgen05.mma.cta_group::1.kind::f16 [%0], ad, bd, %5, p;\n}\n"
+               ::"r"(tmem), "r"(alo), "r"(ahi), "r"(blo), "r"(bhi), "r"(idesc), "r"(acc));
+}
+
+// One K chain of slice products into tmem_d: the correction products of all
+// NKS K steps first, then the main (hi x hi) ones. a / b: descriptors;
+// a_slice, b_slice: byte offsets of the mid slice; a_kstep, b_kstep: byte
+// offsets of one K step. All offsets are compile-time multiples after
+// unrolling, so the issuing loop is a run of MMAs on precomputed operands.
+// The whole warp evaluates the (uniform) descriptors; `leader` issues.
+// `first`: the next MMA overwrites the accumulator (cleared after it).
+template <int NPROD, int NKS>
+__device__ __forceinline__ void mma_chain_k(bool leader, uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t a_slice,
+                                            uint32_t b_slice, uint32_t a_kstep, uint32_t b_kstep, uint32_t idesc,
+                                            bool& first) {
+  const uint32_t alo = (uint32_t)a, ahi = (uint32_t)(a >> 32), blo = (uint32_t)b, bhi = (uint32_t)(b >> 32);
+  const uint32_t as16 = a_slice >> 4, bs16 = b_slice >> 4, ak16 = a_kstep >> 4, bk16 = b_kstep >> 4;
+  uint32_t acc = first ? 0u : 1u;
+  if (leader) {
 #pragma unroll
-    for (int p = 1; p < NPROD; ++p) {
-      mma(tmem_d, ad0 + ((prod_i(p) * a_slice + (uint32_t)ks * a_kstep) >> 4),
-          bd0 + ((prod_j(p) * b_slice + (uint32_t)ks * b_kstep) >> 4), idesc, first ? 0u : 1u);
-      first = false;
+    for (int ks = 0; ks < NKS; ++ks)
+#pragma unroll
+      for (int p = 1; p < NPROD; ++p) {
+        mma_lohi(tmem_d, alo + prod_i(p) * as16 + ks * ak16, ahi, blo + prod_j(p) * bs16 + ks * bk16, bhi, idesc,
+                 acc);
+        acc = 1u;
+      }
+#pragma unroll
+    for (int ks = 0; ks < NKS; ++ks) {
+      mma_lohi(tmem_d, alo + ks * ak16, ahi, blo + ks * bk16, bhi, idesc, acc);
+      acc = 1u;
     }
   }
-  for (int ks = 0; ks < nks; ++ks) {
-    mma(tmem_d, ad0 + (((uint32_t)ks * a_kstep) >> 4), bd0 + (((uint32_t)ks * b_kstep) >> 4), idesc,
-        first ? 0u : 1u);
-    first = false;
+  first = false;
+}
+
+template <int NPROD>
+__device__ __forceinline__ void mma_chain(bool leader, uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t a_slice,
+                                          uint32_t b_slice, uint32_t a_kstep, uint32_t b_kstep, int nks,
+                                          uint32_t idesc, bool& first) {
+  switch (nks) {
+    case 1: mma_chain_k<NPROD, 1>(leader, tmem_d, a, b, a_slice, b_slice, a_kstep, b_kstep, idesc, first); break;
+    case 2: mma_chain_k<NPROD, 2>(leader, tmem_d, a, b, a_slice, b_slice, a_kstep, b_kstep, idesc, first); break;
+    case 3: mma_chain_k<NPROD, 3>(leader, tmem_d, a, b, a_slice, b_slice, a_kstep, b_kstep, idesc, first); break;
+    default: mma_chain_k<NPROD, 4>(leader, tmem_d, a, b, a_slice, b_slice, a_kstep, b_kstep, idesc, first); break;
   }
 }
 
@@ -483,13 +511,17 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
     }
   } else if (warp == 1) {
     // --------------------------------------------------------------- MMA
-    if (lane == 0) {
+    // The whole warp runs this role's control flow, so descriptors and
+    // counters stay warp-uniform; lane 0 alone issues the MMAs, commits and
+    // arrivals.
+    {
+      const bool leader = lane == 0;
       // with profiling on, slots 14 / 15 of the wait accounting receive the
-      // cycles this thread spends issuing MMAs / committing them
+      // cycles this warp spends issuing MMAs / committing them
       constexpr bool prof = PROF;
       auto tick = [&]() -> long long { return prof ? clock64() : 0ll; };
       auto tock = [&](int slot, long long t0) {
-        if (prof) s_wait[slot] += (unsigned long long)(clock64() - t0);
+        if (prof && leader) s_wait[slot] += (unsigned long long)(clock64() - t0);
       };
       uint32_t stage = 0, phase = 0;
       uint32_t xcnt = 0, xph_empty = 3u;   // bit b: expected parity of X-empty[b]
@@ -503,7 +535,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
       };
       auto release = [&]() {
         const long long t0 = tick();
-        commit(bar(B_EMPTY + stage));
+        if (leader) commit(bar(B_EMPTY + stage));
         tock(15, t0);
         if (++stage == STAGES) { stage = 0; phase ^= 1; }
       };
@@ -523,14 +555,14 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
           const uint32_t sst = acquire();
           if (!ok) return;
           const long long t0 = tick();
-          mma_chain<NPROD>(tmem_x, sdesc(sst, a_lbo, a_sbo), sdesc(sst + PSI_TILE * TILE3, 16u * TILE3, TILE3),
+          mma_chain<NPROD>(leader, tmem_x, sdesc(sst, a_lbo, a_sbo), sdesc(sst + PSI_TILE * TILE3, 16u * TILE3, TILE3),
                            128u, 128u, 2 * a_lbo, 2 * 16u * TILE3, min(4, pR8 - 4 * k) / 2, id1, first);
           tock(14, t0);
           release();
         }
         {
           const long long t0 = tick();
-          commit(bar(B_XFULL + xb));
+          if (leader) commit(bar(B_XFULL + xb));
           tock(15, t0);
         }
         ++xcnt;
@@ -566,13 +598,13 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
                 first = true;
               }
               const long long t0 = tick();
-              mma_chain<NPROD>(tmem + 256 + sb * 128, sdesc(a2 + (uint32_t)(q * tm8) * 1024u, 128u, 1024u),
+              mma_chain<NPROD>(leader, tmem + 256 + sb * 128, sdesc(a2 + (uint32_t)(q * tm8) * 1024u, 128u, 1024u),
                                sdesc(sst + (uint32_t)((q - q0) * te * kg2) * TILE3, b_lbo, b_sbo), A2_SLICE, 128u,
                                2 * 128u, 2 * b_lbo, kg2 / 2, id2, first);
               tock(14, t0);
               if (gend) {  // the group ends: hand the accumulator to the epilogue
                 const long long t1 = tick();
-                commit(bar(B_SFULL + sb));
+                if (leader) commit(bar(B_SFULL + sb));
                 tock(15, t1);
                 sb ^= 1;
               }
@@ -580,7 +612,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
             release();
           }
           const long long t1 = tick();
-          commit(bar(B_A2EMPTY));
+          if (leader) commit(bar(B_A2EMPTY));
           tock(15, t1);
         }
       };
@@ -590,7 +622,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
         if (prev_slot < 0 || !ok) return;
         const TcUnitRec& pu = ring[prev_slot];
         mma_s2(pu, prev_j);
-        if (prev_j == n_chunks(pu) - 1) mbar_arrive(bar(B_MEMPTY + prev_slot));
+        if (prev_j == n_chunks(pu) - 1 && leader) mbar_arrive(bar(B_MEMPTY + prev_slot));
         prev_slot = -1;
       };
       while (ok) {
@@ -600,7 +632,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
         const int fl = u.flags;
         if (fl & TC_DONE) break;
         if (fl & TC_ZERO) {
-          mbar_arrive(bar(B_MEMPTY + slot));
+          if (leader) mbar_arrive(bar(B_MEMPTY + slot));
         } else {
           for (int j = 0; j < n_chunks(u) && ok; ++j) {
             mma_s1(u, j);
@@ -669,19 +701,19 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
       if (lane == 0) mbar_arrive(bar(B_A2FULL));
     };
     // add the tile accumulator of the next flush group into the running sum
-    auto flush = [&](const TcUnitRec& u) -> bool {
+    auto flush = [&](int tm, int tn) -> bool {
       if (!mbar_wait<PROF>(bar(B_SFULL + sb), (sph_full >> sb) & 1u, abort_flag, a.err, 8)) return false;
       sph_full ^= 1u << sb;
       asm volatile("tcgen05.fence::after_thread_sync;\n");
-      if (quarter * 32 < u.tm) {  // warp-uniform: this warp owns tile rows
-        const bool rv = row < u.tm;
+      if (quarter * 32 < tm) {  // warp-uniform: this warp owns tile rows
+        const bool rv = row < tm;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           const int col0 = half * 64 + c * 32;
-          if (col0 < u.tn) {  // warp-uniform
+          if (col0 < tn) {  // warp-uniform
             float w[32];
             tmem_ld32(tmem + lane_off + 256 + sb * 128 + col0, w);
-            const int nc = u.tn - col0;
+            const int nc = tn - col0;
             if (rv) {
 #pragma unroll
               for (int g8 = 0; g8 < 4; ++g8) {
@@ -712,6 +744,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
       return true;
     };
     long long s = 0;
+    int pend = 0, pend_tm = 0, pend_tn = 0;  // flush groups deferred past the next conversion
     while (ok) {
       const int slot = (int)(s % NMETA);
       if (!mbar_wait<PROF>(bar(B_MFULL + slot), (uint32_t)((s / NMETA) & 1), abort_flag, a.err, 13)) { ok = false; break; }
@@ -766,14 +799,31 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
               __syncwarp();
               if (lane == 0) mbar_arrive(bar(B_A2FULL));
             }
-            // flush groups of this half, in the order the MMA issues them
-            if (whole) {
-              if (h == nh - 1) ok = flush(u);
+            // flush groups in the order the MMA issues them. The groups of a
+            // half are flushed after the next half has been converted (off
+            // the MMA's critical path), unless the half has more than two:
+            // with two tile accumulators the MMA would then wait for them.
+            while (ok && pend > 0) {
+              ok = flush(pend_tm, pend_tn);
+              --pend;
+            }
+            const int F = flush_terms(u, a.max_chain);
+            const int ng = whole ? (h == nh - 1 ? 1 : 0) : (u.nterm + F - 1) / F;
+            if (ng <= 2) {
+              pend = ng;
+              pend_tm = u.tm;
+              pend_tn = u.tn;
             } else {
-              for (int g0 = 0; g0 < u.nterm && ok; g0 += flush_terms(u, a.max_chain)) ok = flush(u);
+              for (int g = 0; g < ng && ok; ++g) ok = flush(u.tm, u.tn);
             }
           }
           ++xcnt;
+        }
+        if (ok && (fl & TC_ITEM_LAST)) {  // the item's last groups, then its partial tile
+          while (ok && pend > 0) {
+            ok = flush(pend_tm, pend_tn);
+            --pend;
+          }
         }
         if (ok && (fl & TC_ITEM_LAST) && row < u.tm) {
 #pragma unroll

@@ -66,20 +66,22 @@ def test_noalloc_sweep_context_needs_resident_bond():
     ctx = capi.dmrg_create(device=0, seed=1)
     try:
         capi.dmrg_build_blocks(ctx, t, v, 4, 4, 0, 16)
-        n = capi.dmrg_psi_layout(ctx, 1)["size"]  # brings bond 1's operators in
-        # bond 0 is not resident: refused before anything is read or built
+        # right after dmrg_build_blocks the blocks of bond 0 exist; its
+        # operators are built on the device by the first call that needs them
+        n = capi.dmrg_psi_layout(ctx, 0)["size"]
+        # bond 1 is not resident: refused before anything is read or built
         big = torch.zeros(1 << 16, dtype=torch.float64, device="cuda")
         with pytest.raises(capi.DMRGError) as e:
-            capi.dmrg_sigma_noalloc(ctx, 0, big, torch.zeros_like(big))
+            capi.dmrg_sigma_noalloc(ctx, 1, big, torch.zeros_like(big))
         assert e.value.status == capi.DMRG_ESTATE
         x = torch.from_numpy(random_unit_vector(n, 3)).cuda()
         y = torch.zeros(n, dtype=torch.float64, device="cuda")
         ref = torch.zeros_like(y)
-        capi.dmrg_sigma(ctx, 1, x, ref)
+        capi.dmrg_sigma(ctx, 0, x, ref)
         capi.dmrg_sync(ctx)
         for _ in range(2):
             y.fill_(float("nan"))
-            capi.dmrg_sigma_noalloc(ctx, 1, x, y)
+            capi.dmrg_sigma_noalloc(ctx, 0, x, y)
             capi.dmrg_sync(ctx)
             r = ref.cpu().numpy()
             assert np.abs(y.cpu().numpy() - r).max() <= TOL * np.abs(r).max()
