@@ -73,6 +73,13 @@ def config(M, prec="fp64"):
 # profiles/sigma_f64_middle_bond_m2000_dram.md; valid for M=2000 only.
 F64_TRAFFIC_M2000 = 57.05e9
 
+# DRAM bytes per algorithmic byte of the mixed-precision sigma (small-class
+# and tensor-core kernels) measured by ncu on a smaller case of the same
+# workload and applied to the bench size (traffic grows with the operator
+# store); recorded in profiles/sigma_tc_middle_bond_m800_full.md.
+TC_TRAFFIC_PER_ALG_BYTE = None
+TC_TRAFFIC_SOURCE = "ncu dram bytes of sigma_tc_kernel at M=800 per algorithmic byte, scaled to this M"
+
 # ------------------------------------------------------------------ clocks
 class Clocks:
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -376,6 +383,7 @@ def main():
         capi.dmrg_set_precision(ctx, prec)
         capi.dmrg_sigma(ctx, -1, x, y)  # builds the bf16 operator slices
         capi.dmrg_sync(ctx)
+        tc_tuned = capi.dmrg_autotune(ctx, -1)  # items per SM of the tensor-core work split
         for _ in range(max(3, args.warmup)):
             capi.dmrg_sigma(ctx, -1, x, y)
         capi.dmrg_sync(ctx)
@@ -398,11 +406,16 @@ def main():
         # algorithmic bytes: every stored operator element once (6 B as three
         # bf16 slices) + psi read + sigma written (FP64)
         alg_bytes = info["op_elements"] * bytes_per_elem + 16.0 * n
+        traffic = TC_TRAFFIC_PER_ALG_BYTE * alg_bytes if (name == "bf16x3" and TC_TRAFFIC_PER_ALG_BYTE) else None
         mixed[name] = {"value": flops / step / 1e12, "unit": "TFLOP/s", "ms_per_step": step * 1e3,
                        "kernel_ms": kern * 1e3, "rel_err_vs_fp64_maxnorm": d, "rayleigh_rel_err_vs_fp64": rq,
+                       "speedup_vs_fp64_kernel": (k_ms / max(1, k_n)) / (kern * 1e3),
+                       "autotuned": {"tc_items_per_sm": tc_tuned[0], "tune_ms": tc_tuned[2]},
                        "roofline": {"bound": "hbm", "achieved": alg_bytes / kern / 1e9, "peak": hbm,
-                                    "unit": "GB/s", "frac": alg_bytes / kern / 1e9 / hbm, "traffic": None,
-                                    "kernel": "sigma_tc_kernel", "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                                    "unit": "GB/s", "frac": alg_bytes / kern / 1e9 / hbm, "traffic": traffic,
+                                    "traffic_source": TC_TRAFFIC_SOURCE if traffic else None,
+                                    "kernel": "sigma_small_kernel + sigma_tc_kernel (one sigma)",
+                                    "peak_source": "MEASURED_PEAKS.json hbm_gbs",
                                     "tensor_tflops_issued": nprod * flops / kern / 1e12,
                                     "tensor_frac_of_bf16_peak": nprod * flops / kern / 1e12 / bf16}}
     capi.dmrg_set_precision(ctx, capi.DMRG_FP64)

@@ -225,16 +225,20 @@ dmrg_status dmrg_sigma(dmrg_ctx* ctx, int site, const double* psi, double* sigma
 dmrg_status dmrg_sigma_noalloc(dmrg_ctx* ctx, int site, const double* psi, double* sigma);
 
 /*
- * Autotuner of the FP64 sigma work list: times one sigma (after one warm-up)
- * for every combination of items per SM {8, 16, 32} and per-task latency
- * cost {4096, 16384, 65536} (the item split and largest-first order of the
- * persistent kernel's work items, Sec. II.D-E collapsed into one list) on a
- * seeded psi, keeps the fastest and reports it (any output may be NULL;
- * best_ms = its time). Results stay bitwise deterministic for the chosen
- * setting; they can differ in the last bits from another setting because
- * items sum their tasks in another grouping. A tuned work list may need more
- * scratch than dmrg_sigma_noalloc holds. The default without tuning is
- * 8 items per SM and cost 16384.
+ * Autotuner of the sigma work lists, for the context's current precision.
+ * FP64: times one sigma (after one warm-up) for every combination of items
+ * per SM {8, 16, 32} and per-task latency cost {4096, 16384, 65536} (the
+ * item split and largest-first order of the persistent kernel's work items,
+ * Sec. II.D-E collapsed into one list) on a seeded psi, keeps the fastest
+ * and reports it. Mixed precision (BF16X3 / BF16X2): times the tensor-core
+ * path for {2, 4, 8, 16} items per SM (how each output tile's units of
+ * stacked terms are split into work items) and reports the choice in
+ * items_per_sm, with *per_task_cost = 0. Any output may be NULL; best_ms =
+ * the chosen setting's time. Results stay bitwise deterministic for the
+ * chosen setting; they can differ in the last bits from another setting
+ * because items sum their terms in another grouping. A tuned FP64 work list
+ * may need more scratch than dmrg_sigma_noalloc holds. Defaults without
+ * tuning: FP64 8 items per SM and cost 16384; tensor cores 4 items per SM.
  */
 dmrg_status dmrg_autotune(dmrg_ctx* ctx, int site, int* items_per_sm, double* per_task_cost, double* best_ms);
 

@@ -118,9 +118,26 @@ void prepare_worklist(Context& c, Problem& p) {
 
 static_assert(sizeof(TcItem) == sizeof(Item), "reduction reads TcItem as Item");
 
+// Work records of the tensor-core path for the problem's tuning (the split
+// operator store is unchanged by it).
+static void prepare_tc_plan(Context& c, Problem& p) {
+  cudaStream_t st = c.stream;
+  build_tc_plan(p.blocks, p.L, p.R, p.wl, p.tc, TcShape{c.n_sm * p.tc_items_per_sm});
+  p.d_tc_recs.upload(p.tc.recs, st);
+  p.d_tc_items.upload(p.tc.items, st);
+  p.d_tc_small.upload(p.tc.small, st);
+  p.d_tc_small_sched.upload(p.tc.small_schedule, st);
+  p.d_tc_groups.upload(p.tc.groups, st);
+  p.d_tc_sched.upload(p.tc.schedule, st);
+  p.d_tc_pblk.upload(p.tc.psi, st);
+  p.d_tc_scratch.alloc(std::max<long long>(1, p.tc.scratch_elems) * sizeof(double));
+  DMRG_CUDA(cudaStreamSynchronize(st));
+  p.graphs.clear();
+}
+
 void prepare_tc(Context& c, Problem& p) {
   cudaStream_t st = c.stream;
-  build_tc_plan(p.blocks, p.L, p.R, p.wl, p.tc, TcShape{c.n_sm * 4});
+  prepare_tc_plan(c, p);
   const size_t split_bytes = (size_t)p.tc.n_tiles * 384;
   size_t freeb = 0, totb = 0;
   DMRG_CUDA(cudaMemGetInfo(&freeb, &totb));
@@ -148,14 +165,6 @@ void prepare_tc(Context& c, Problem& p) {
   d_jobs.upload(jobs, st);
   launch_split_ops(p.store.as<double>(), d_jobs.as<SplitJob>(), (long long)jobs.size(), p.split.p, st);
   DMRG_CUDA(cudaGetLastError());
-  p.d_tc_recs.upload(p.tc.recs, st);
-  p.d_tc_items.upload(p.tc.items, st);
-  p.d_tc_small.upload(p.tc.small, st);
-  p.d_tc_small_sched.upload(p.tc.small_schedule, st);
-  p.d_tc_groups.upload(p.tc.groups, st);
-  p.d_tc_sched.upload(p.tc.schedule, st);
-  p.d_tc_pblk.upload(p.tc.psi, st);
-  p.d_tc_scratch.alloc(std::max<long long>(1, p.tc.scratch_elems) * sizeof(double));
   p.d_err.alloc(16);
   DMRG_CUDA(cudaMemsetAsync(p.d_err.p, 0, 16, st));
   DMRG_CUDA(cudaStreamSynchronize(st));
@@ -173,6 +182,9 @@ void check_device_error(Context& c, Problem& p) {
                                    "); the last sigma result is invalid");
   }
 }
+
+static void run_sigma_tc(Context& c, Problem& p, const double* d_psi, double* d_sigma);
+void run_sigma_tc_direct(Context& c, Problem& p, const double* d_psi, double* d_sigma) { run_sigma_tc(c, p, d_psi, d_sigma); }
 
 static void run_sigma_tc(Context& c, Problem& p, const double* d_psi, double* d_sigma) {
   if (!p.tc_ready) prepare_tc(c, p);
@@ -710,11 +722,49 @@ dmrg_status dmrg_autotune(dmrg_ctx* ctx, int site, int* items_per_sm, double* pe
     c.d_sigma.alloc(bytes);
     launch_gen_vector(c.d_psi.as<double>(), p.psi_size, 0x54554E45ull ^ c.opts.seed, 0ull, c.stream);
     DMRG_CUDA(cudaGetLastError());
-    const int cand_items[3] = {8, 16, 32};
-    const double cand_cost[3] = {4096.0, 16384.0, 65536.0};
     cudaEvent_t e0, e1;
     DMRG_CUDA(cudaEventCreate(&e0));
     DMRG_CUDA(cudaEventCreate(&e1));
+    if (c.opts.sigma_prec != DMRG_FP64) {
+      // tensor-core path: items per SM of the persistent kernel (the split
+      // of each output tile's units into items, largest first)
+      if (!p.tc_ready) prepare_tc(c, p);
+      const int cand[4] = {2, 4, 8, 16};
+      double best = 1e300;
+      int bi = p.tc_items_per_sm;
+      try {
+        for (int wi : cand) {
+          p.tc_items_per_sm = wi;
+          prepare_tc_plan(c, p);
+          run_sigma_tc_direct(c, p, c.d_psi.as<double>(), c.d_sigma.as<double>());  // warm-up
+          DMRG_CUDA(cudaEventRecord(e0, c.stream));
+          run_sigma_tc_direct(c, p, c.d_psi.as<double>(), c.d_sigma.as<double>());
+          DMRG_CUDA(cudaEventRecord(e1, c.stream));
+          DMRG_CUDA(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          DMRG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          if (ms < best) {
+            best = ms;
+            bi = wi;
+          }
+        }
+      } catch (...) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      p.tc_items_per_sm = bi;
+      prepare_tc_plan(c, p);
+      check_device_error(c, p);
+      if (items_per_sm) *items_per_sm = bi;
+      if (per_task_cost) *per_task_cost = 0.0;
+      if (best_ms) *best_ms = best;
+      return;
+    }
+    const int cand_items[3] = {8, 16, 32};
+    const double cand_cost[3] = {4096.0, 16384.0, 65536.0};
     double best = 1e300;
     int bi = p.items_per_sm;
     double bc = p.per_task_cost;

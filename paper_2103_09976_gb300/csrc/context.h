@@ -154,6 +154,8 @@ struct Problem {
   // FP64 work-list tuning (dmrg_autotune): items per SM and per-task cost term
   int items_per_sm = 8;
   double per_task_cost = 16384.0;
+  // tensor-core plan tuning (dmrg_autotune at a mixed precision): items per SM
+  int tc_items_per_sm = 4;
   // sub-Hamiltonian parts: (n_ranks, rank) -> work list of that rank's terms
   std::map<std::pair<int, int>, std::unique_ptr<DevWork>> parts;
 };
@@ -251,6 +253,7 @@ void ensure_davidson_workspace(Context& c, Problem& p);
 bool run_davidson(Context& c, Problem& p, const double* x0, double tol, double* energy, double* x_out,
                   int* iters, unsigned long long guess_counter_base);
 void run_sigma(Context& c, Problem& p, const double* d_psi, double* d_sigma);      // context precision
+void run_sigma_tc_direct(Context& c, Problem& p, const double* d_psi, double* d_sigma);  // mixed, no graph
 void run_sigma_f64(Context& c, Problem& p, const double* d_psi, double* d_sigma);  // always FP64
 // FP64 sigma of the terms that sub-Hamiltonian rank `rank` of n_ranks owns
 void run_sigma_part(Context& c, Problem& p, int rank, int n_ranks, const double* d_psi, double* d_sigma);

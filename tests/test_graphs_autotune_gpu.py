@@ -71,3 +71,34 @@ def test_autotune_keeps_parity_and_determinism():
     lay, _ = psi_layout(bL, bR, (6, 0))
     ref = sigma_blocks(x, lay, nc_terms(6, 12), oL, oR)
     assert np.abs(y1 - ref).max() <= TOL * np.abs(ref).max()
+
+
+def test_tensor_core_autotune_keeps_parity_and_determinism():
+    """At a mixed precision the tuner picks the tensor-core work split; the
+    tuned sigma stays within the BF16X3 bar of the oracle and bitwise
+    repeatable, through direct launches and graph replays."""
+    import torch
+    from oracle.nc import nc_terms
+    from oracle.sigma import psi_layout, sigma_blocks, synthetic_ops
+    from paper_2103_09976_gb300 import capi
+    from synth import random_unit_vector
+    ctx, left, right = _load(capi, 1200, 3, 6, 3, sigma_prec=capi.DMRG_BF16X3)
+    try:
+        w, c, ms = capi.dmrg_autotune(ctx)
+        n = capi.dmrg_psi_layout(ctx)["size"]
+        x_h = random_unit_vector(n, 13)
+        x = torch.from_numpy(x_h).cuda()
+        ys = []
+        for _ in range(3):   # direct, capture, replay
+            y = torch.zeros(n, dtype=torch.float64, device="cuda")
+            capi.dmrg_sigma(ctx, -1, x, y)
+            capi.dmrg_sync(ctx)
+            ys.append(y.cpu().numpy())
+    finally:
+        capi.dmrg_destroy(ctx)
+    assert w in (2, 4, 8, 16) and c == 0.0 and ms > 0
+    assert all(np.array_equal(ys[0], y) for y in ys[1:])
+    bL, bR, oL, oR, _ = synthetic_ops(left, right, 6, 12, seed=3)
+    lay, _ = psi_layout(bL, bR, (6, 0))
+    ref = sigma_blocks(x_h, lay, nc_terms(6, 12), oL, oR)
+    assert np.abs(ys[0] - ref).max() <= 2e-6 * np.abs(ref).max()
