@@ -474,6 +474,7 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
     int in_blk, flags;
     float scale;
     int task;
+    int a_blk, b_blk;  // split-block indices: stored blocks, then identities of the left and right sectors
   };
   const bool have_idx = wl.task_ablk.size() == wl.tasks.size() && wl.task_bblk.size() == wl.tasks.size();
   const size_t nblk = blocks.size();
@@ -506,17 +507,26 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
       const Task& k = wl.tasks[t];
       const PsiBlock& in = blocks[k.in_blk];
       TcBlock a = plan.identL[in.qL], b = plan.identR[in.qR];
+      int ab = (int)offs.size() + in.qL, bb = (int)offs.size() + L.basis.size() + in.qR;
       if (k.aoff >= 0) {
         const int f = have_idx ? wl.task_ablk[t] : find_off(k.aoff);
         if (f < 0 || f >= (int)offs.size() || offs[f] != k.aoff) bad[j] = 1;
-        else a = plan.opblocks[f];
+        else {
+          a = plan.opblocks[f];
+          ab = f;
+        }
       }
       if (k.boff >= 0) {
         const int f = have_idx ? wl.task_bblk[t] : find_off(k.boff);
         if (f < 0 || f >= (int)offs.size() || offs[f] != k.boff) bad[j] = 1;
-        else b = plan.opblocks[f];
+        else {
+          b = plan.opblocks[f];
+          bb = f;
+        }
       }
       Base x;
+      x.a_blk = ab;
+      x.b_blk = bb;
       x.a_tile = a.tile;
       x.aR8 = a.R8;
       x.aC8 = a.C8;
@@ -680,6 +690,7 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
   plan.groups.resize(G[nparts]);
   plan.scratch_elems = S[nparts];
   plan.recs.resize(U[nparts]);  // uninitialized: every record is written below
+  plan.term_blk.assign((size_t)U[nparts] * TC_MAX_G * 2, -1);
   plan.small.resize(SM[nparts]);
   plan.n_units = 0;
   std::vector<double> icost(I[nparts]);
@@ -734,13 +745,16 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
           r.pR8 = (short)ib.R8;
           r.pC8 = (short)ib.C8;
           r.p_tile = ib.tile;
-          r.rsv = 0;
+          r.pblk = h.in_blk;
+          const size_t ri = (size_t)(&r - plan.recs.data());
           for (int q = 0; q < r.nterm; ++q) {
             const Base& x = base[P.order[un.t0 + q]];
             r.t[q].a_tile = x.a_tile;
             r.t[q].b_tile = x.b_tile;
             r.t[q].scale = x.scale;
             r.t[q].pad = 0;
+            plan.term_blk[(ri * TC_MAX_G + q) * 2] = x.a_blk;
+            plan.term_blk[(ri * TC_MAX_G + q) * 2 + 1] = x.b_blk;
           }
         }
       }

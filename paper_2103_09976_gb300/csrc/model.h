@@ -271,7 +271,7 @@ struct TcUnitRec {          // 80-byte header + 16 terms = 464 bytes
   int tm8;                  // row groups of one term in the stacked operand (ceil(tm / 8))
   int r0g, c0g;             // tile origin (row / column group) inside the output block
   int m, n;                 // psi block rows / columns
-  int rsv;                  // reserved (zero)
+  int pblk;                 // psi block index
   short aR8, aC8, bR8, bC8; // stored tile geometry of the left / right blocks
   short pR8, pC8;           // psi tile geometry
   long long p_tile;         // psi tiles
@@ -334,6 +334,10 @@ struct TcPlan {
   long long scratch_elems = 0;
   std::vector<TcUnitRec, NoInit<TcUnitRec>> recs;  // kind-0 item i: records [items[i].r_begin, items[i].r_end)
   std::vector<SmallTerm> small;         // kind-1 item i: terms [items[i].r_begin, items[i].r_end)
+  // per record and term slot (record * TC_MAX_G + q): split-block indices of
+  // the left and right blocks (stored blocks in store order, then the
+  // identity blocks of the left and right sectors); -1 for unused slots
+  std::vector<int> term_blk;
   std::vector<int> small_schedule;      // kind-1 items, most expensive first
   long long n_terms = 0;                // term products (tasks x tiles), counted once
   long long n_units = 0;

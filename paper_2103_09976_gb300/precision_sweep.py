@@ -45,10 +45,15 @@ def one(M, steps=2, autotune=True):
             if prec == capi.DMRG_FP64 and autotune:
                 out["autotuned"] = capi.dmrg_autotune(ctx, -1)
             y = torch.zeros(n, dtype=torch.float64, device="cuda")
+            tuned = None
             try:
                 for _ in range(2):
                     capi.dmrg_sigma(ctx, -1, x, y)
                 capi.dmrg_sync(ctx)
+                if prec != capi.DMRG_FP64:   # tensor-core work split, picked by timing
+                    tuned = capi.dmrg_autotune(ctx, -1)
+                    capi.dmrg_sigma(ctx, -1, x, y)
+                    capi.dmrg_sync(ctx)
             except capi.DMRGError as ex:   # e.g. the bf16 slices do not fit next to the FP64 store
                 out[name] = {"error": str(ex)}
                 continue
@@ -60,6 +65,11 @@ def one(M, steps=2, autotune=True):
             e1.synchronize()
             s = e0.elapsed_time(e1) / 1e3 / steps
             r = {"ms": s * 1e3, "tflops": info["flops"] / s / 1e12, "prep_s": prep}
+            if tuned is not None:
+                nprod = 6 if prec == capi.DMRG_BF16X3 else 3
+                alg = 6.0 * info["op_elements"] + 16.0 * n   # operators once as 3 bf16 slices, psi, sigma
+                r.update({"tc_items_per_sm": tuned[0], "hbm_gbs": alg / s / 1e9,
+                          "tensor_tflops_issued": nprod * info["flops"] / s / 1e12})
             if ref is None:
                 ref = y.clone()
             else:
