@@ -384,9 +384,11 @@ void dmrg_server_destroy(dmrg_server* s);
  * same and also runs the tensor-core kernel's wait accounting (which slows
  * that kernel; see dmrg_profile_waits); 0 stops.
  * dmrg_profile_read synchronizes the stream and returns, for kernel id
- * `kernel` (0 = sigma product kernel, 1 = sigma reduction, 2 = Davidson
- * vector kernels, 3 = blocking / transformation kernels), the summed
- * duration in ms and the number of launches. DMRG_EINVAL for unknown ids.
+ * `kernel` (0 = sigma product kernels, 1 = sigma reduction, 2 = Davidson
+ * vector kernels, 3 = blocking / transformation kernels, 4 = the CUDA-core
+ * kernels of the mixed-precision sigma's small classes, also counted in 0),
+ * the summed duration in ms and the number of launches. DMRG_EINVAL for
+ * unknown ids.
  */
 dmrg_status dmrg_profile(dmrg_ctx* ctx, int enable);
 

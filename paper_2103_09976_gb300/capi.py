@@ -304,7 +304,7 @@ def dmrg_sweep_log(ctx):
     return [{f: getattr(buf[k], f) for f, _ in dmrg_step_log._fields_} for k in range(n.value)]
 
 
-KERNEL_SIGMA, KERNEL_REDUCE, KERNEL_DAVIDSON, KERNEL_BLOCKING = 0, 1, 2, 3
+KERNEL_SIGMA, KERNEL_REDUCE, KERNEL_DAVIDSON, KERNEL_BLOCKING, KERNEL_SIGMA_SMALL = 0, 1, 2, 3, 4
 
 
 def dmrg_profile(ctx, enable, waits=False):

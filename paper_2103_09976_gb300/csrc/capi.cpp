@@ -222,15 +222,19 @@ static void run_sigma_tc(Context& c, Problem& p, const double* d_psi, double* d_
   {
     ProfScope ps_(c.prof, 0, c.stream);
     SmallDev sd;
-    sd.store = p.store.as<double>();
-    sd.psi = d_psi;
-    sd.blocks = p.d_blocks.as<PsiBlock>();
+    sd.op = p.split.p;
+    sd.psi = p.psi_split.p;
+    sd.pblk = p.d_tc_pblk.as<TcPsiBlock>();
     sd.terms = p.d_tc_small.as<SmallTerm>();
     sd.items = p.d_tc_items.as<TcItem>();
     sd.schedule = p.d_tc_small_sched.as<int>();
     sd.n_items = (int)p.tc.small_schedule.size();
+    sd.n_mid = p.tc.n_small_mid;
     sd.scratch = p.d_tc_scratch.as<double>();
-    launch_sigma_small(sd, c.n_sm, c.stream);
+    {
+      ProfScope ps4_(c.prof, 4, c.stream);  // the small classes alone (also inside kind 0)
+      launch_sigma_small(sd, c.n_sm, c.stream);
+    }
     launch_sigma_tc(t, c.n_sm, c.stream);
   }
   DMRG_CUDA(cudaGetLastError());

@@ -162,13 +162,13 @@ struct Problem {
 
 // CUDA-event timing of kernel launches (dmrg_profile).
 struct Profiler {
-  static constexpr int kKinds = 4;
+  static constexpr int kKinds = 5;
   bool on = false;
   bool waits = false;   // also run the tensor-core kernel's wait accounting
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[kKinds];
   std::vector<cudaEvent_t> pool;
-  double ms[kKinds] = {0, 0, 0, 0};
-  long long launches[kKinds] = {0, 0, 0, 0};
+  double ms[kKinds] = {0, 0, 0, 0, 0};
+  long long launches[kKinds] = {0, 0, 0, 0, 0};
   cudaEvent_t get();
   void begin(int kind, cudaStream_t st, cudaEvent_t* a);
   void end(int kind, cudaStream_t st, cudaEvent_t a);

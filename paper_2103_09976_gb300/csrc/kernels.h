@@ -77,13 +77,14 @@ struct TcDev {
 
 // Small classes of the mixed-precision sigma on the CUDA cores (see TC_SMALL_MAX).
 struct SmallDev {
-  const double* store;        // FP64 operator store
-  const double* psi;          // psi (FP64, the layout of `blocks`)
-  const PsiBlock* blocks;
+  const void* op;             // operator split (the tensor-core kernel's tiles)
+  const void* psi;            // psi split
+  const TcPsiBlock* pblk;     // psi blocks: split tiles and dimensions
   const SmallTerm* terms;
-  const TcItem* items;        // kind-1 items index terms
-  const int* schedule;        // kind-1 items, most expensive first
+  const TcItem* items;        // kind-1/2 items index terms
+  const int* schedule;        // kind-2 items, then kind-1 items, each most expensive first
   int n_items;
+  int n_mid;                  // kind-2 items (all blocks <= TC_SMALL_MID) at the head of the schedule
   double* scratch;            // partial tiles (item slots)
 };
 void launch_sigma_small(const SmallDev& a, int n_sm, cudaStream_t st);

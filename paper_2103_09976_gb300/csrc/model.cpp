@@ -570,7 +570,7 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
     int t0, t1;
   };
   struct Part {
-    std::vector<TcItem> items;           // kind 0: r_begin/r_end index units; kind 1: small terms
+    std::vector<TcItem> items;           // kind 0: r_begin/r_end index units; kind 1/2: small terms
     std::vector<Group> groups;
     std::vector<std::pair<int, Unit>> units;  // (output block, unit)
     std::vector<SmallTerm> small;
@@ -610,7 +610,7 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
           }
           TcItem it{(int)b, r0, tm, c0, tn, (int)P.units.size(), 0, 0, P.scratch};
           double acc = 0;
-          const size_t small0 = P.small.size();
+          std::vector<SmallTerm> sm[2];  // CUDA-core terms: all blocks <= TC_SMALL_MID, the rest
           int k = obase;
           const int kend = obase + (t1 - t0);
           while (k < kend) {
@@ -620,10 +620,14 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
             while (e < kend && base[P.order[e]].in_blk == h.in_blk && (base[P.order[e]].flags & 3) == (h.flags & 3)) ++e;
             const TcPsiBlock& ib = plan.psi[h.in_blk];
             // CUDA-core class: the whole output block (one tile) and the psi block are small
-            if (std::max(std::max(ob.mL, ob.mR), std::max(ib.m, ib.n)) <= TC_SMALL_MAX) {
+            const int wmax = std::max(std::max(ob.mL, ob.mR), std::max(ib.m, ib.n));
+            if (wmax <= TC_SMALL_MAX) {
+              std::vector<SmallTerm>& dst = sm[wmax <= TC_SMALL_MID ? 0 : 1];
               for (int q = k; q < e; ++q) {
-                const Task& tk = wl.tasks[base[P.order[q]].task];
-                P.small.push_back({tk.aoff, tk.boff, tk.in_blk, tk.flags & 3, tk.scale});
+                const Base& x = base[P.order[q]];
+                const Task& tk = wl.tasks[x.task];
+                dst.push_back({tk.aoff < 0 ? -1 : x.a_tile, tk.boff < 0 ? -1 : x.b_tile, tk.in_blk, tk.flags & 3,
+                               tk.scale});
               }
               P.n_terms += e - k;
               k = e;
@@ -653,16 +657,20 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
             P.icost.push_back(acc);
             P.scratch += (long long)tm * tn;
           }
-          for (size_t s0 = small0; s0 < P.small.size(); s0 += SMALL_ITEM) {  // CUDA-core items
-            const size_t s1 = std::min(P.small.size(), s0 + SMALL_ITEM);
-            double c = 0;
-            for (size_t q = s0; q < s1; ++q) {
-              const PsiBlock& ib = blocks[P.small[q].in_blk];
-              c += 2.0 * ((double)tm * ib.mL * ib.mR + (double)tm * ib.mR * tn);
+          for (int cls = 0; cls < 2; ++cls) {  // CUDA-core items: kind 2 (<= TC_SMALL_MID), kind 1
+            const size_t base0 = P.small.size();
+            P.small.insert(P.small.end(), sm[cls].begin(), sm[cls].end());
+            for (size_t s0 = base0; s0 < P.small.size(); s0 += SMALL_ITEM) {
+              const size_t s1 = std::min(P.small.size(), s0 + SMALL_ITEM);
+              double c = 0;
+              for (size_t q = s0; q < s1; ++q) {
+                const PsiBlock& ib = blocks[P.small[q].in_blk];
+                c += 2.0 * ((double)tm * ib.mL * ib.mR + (double)tm * ib.mR * tn);
+              }
+              P.items.push_back({(int)b, r0, tm, c0, tn, (int)s0, (int)s1, cls == 0 ? 2 : 1, P.scratch});
+              P.icost.push_back(c);
+              P.scratch += (long long)tm * tn;
             }
-            P.items.push_back({(int)b, r0, tm, c0, tn, (int)s0, (int)s1, 1, P.scratch});
-            P.icost.push_back(c);
-            P.scratch += (long long)tm * tn;
           }
           g.i_end = (int)P.items.size();
           P.groups.push_back(g);
@@ -670,7 +678,7 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
     }
   });
   // join the parts: kind-0 items index records (one per unit, one TC_ZERO
-  // record per item without units), kind-1 items index small terms
+  // record per item without units), kind-1/2 items index small terms
   std::vector<size_t> I(nparts + 1, 0), G(nparts + 1, 0), U(nparts + 1, 0), SM(nparts + 1, 0);
   std::vector<long long> S(nparts + 1, 0);
   for (int j = 0; j < nparts; ++j) {
@@ -702,7 +710,7 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
       TcItem it = P.items[i];
       it.slot += S[j];
       icost[I[j] + i] = P.icost[i];
-      if (it.kind == 1) {
+      if (it.kind != 0) {
         it.r_begin += (int)SM[j];
         it.r_end += (int)SM[j];
         plan.items[I[j] + i] = it;
@@ -769,10 +777,17 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
     }
   });
   for (const Part& P : parts) plan.n_units += (long long)P.units.size();
-  for (size_t i = 0; i < plan.items.size(); ++i) (plan.items[i].kind ? plan.small_schedule : plan.schedule).push_back((int)i);
+  std::vector<int> small1;
+  for (size_t i = 0; i < plan.items.size(); ++i) {
+    const int kd = plan.items[i].kind;
+    (kd == 0 ? plan.schedule : kd == 2 ? plan.small_schedule : small1).push_back((int)i);
+  }
   auto by_cost = [&](int a, int b) { return icost[a] > icost[b]; };
   std::stable_sort(plan.schedule.begin(), plan.schedule.end(), by_cost);
   std::stable_sort(plan.small_schedule.begin(), plan.small_schedule.end(), by_cost);
+  std::stable_sort(small1.begin(), small1.end(), by_cost);
+  plan.n_small_mid = (int)plan.small_schedule.size();
+  plan.small_schedule.insert(plan.small_schedule.end(), small1.begin(), small1.end());
 }
 
 }  // namespace dmrg

@@ -282,7 +282,7 @@ struct TcUnitRec {          // 80-byte header + 16 terms = 464 bytes
 
 // Output tile and its record range; same layout as Item (r_begin/r_end in
 // the place of the task range) so the reduction can read it. kind 0: unit
-// records of the tensor-core kernel; kind 1: small terms (SmallTerm) of the
+// records of the tensor-core kernel; kind 1 / 2: small terms (SmallTerm) of the
 // CUDA-core kernel.
 struct TcItem {
   int out, r0, nrows, c0, ncols, r_begin, r_end, kind;
@@ -292,10 +292,14 @@ struct TcItem {
 // Classes whose blocks (output tile and psi block) are all at most
 // TC_SMALL_MAX wide fill a tcgen05 instruction (128 x 16 x 16 at least) by a
 // few percent; they run on the CUDA cores instead, in FP32 products of the
-// FP64 operators (K <= 32 per product) with FP64 sums over terms.
+// operators (hi + mid + lo of their split, K <= 32 per product) with FP64
+// sums over terms.
 constexpr int TC_SMALL_MAX = 32;
+// Small items whose blocks are all at most TC_SMALL_MID wide (kind 2) run
+// with a smaller footprint than the rest of the small classes (kind 1).
+constexpr int TC_SMALL_MID = 16;
 struct SmallTerm {          // 32 bytes
-  long long a_off, b_off;   // FP64 store offsets of the left / right blocks, -1 = identity
+  long long a_tile, b_tile; // first split tile of the left / right stored block, -1 = identity
   int in_blk;               // psi block
   int flags;                // bit0: left used transposed, bit1: right used transposed
   double scale;
@@ -333,12 +337,13 @@ struct TcPlan {
   std::vector<Group> groups;
   long long scratch_elems = 0;
   std::vector<TcUnitRec, NoInit<TcUnitRec>> recs;  // kind-0 item i: records [items[i].r_begin, items[i].r_end)
-  std::vector<SmallTerm> small;         // kind-1 item i: terms [items[i].r_begin, items[i].r_end)
+  std::vector<SmallTerm> small;         // kind-1/2 item i: terms [items[i].r_begin, items[i].r_end)
   // per record and term slot (record * TC_MAX_G + q): split-block indices of
   // the left and right blocks (stored blocks in store order, then the
   // identity blocks of the left and right sectors); -1 for unused slots
   std::vector<int> term_blk;
-  std::vector<int> small_schedule;      // kind-1 items, most expensive first
+  std::vector<int> small_schedule;      // kind-2 items, then kind-1 items, each most expensive first
+  int n_small_mid = 0;                  // kind-2 items (the head of small_schedule)
   long long n_terms = 0;                // term products (tasks x tiles), counted once
   long long n_units = 0;
   double mma_macs = 0;                  // multiply-adds issued per slice product (padding included)

@@ -99,7 +99,7 @@ int main(int argc, char** argv) {
 
   // (1) every task of the list appears once per 128 x 128 tile of its output
   //     block: in a tensor-core unit record (by its operator tiles) or in a
-  //     small-class term (by its store offsets), never in both
+  //     small-class term (by its operator tiles), never in both
   std::vector<long long> offs;
   for (const OpSet* s : {&oL, &oR})
     for (const OpDesc& o : s->ops)
@@ -144,8 +144,12 @@ int main(int argc, char** argv) {
     const float sc = (float)x.scale;
     unsigned bits;
     std::memcpy(&bits, &sc, 4);
-    const unsigned fl = (x.a_off >= 0 ? (x.flags & 1) : 0) | (x.b_off >= 0 ? (x.flags & 2) : 0);
-    got.emplace_back(x.in_blk, fl, x.a_off, x.b_off, bits);
+    const unsigned fl = (x.a_tile >= 0 ? (x.flags & 1) : 0) | (x.b_tile >= 0 ? (x.flags & 2) : 0);
+    const auto ia = off_of_tile.find(x.a_tile), ib = off_of_tile.find(x.b_tile);
+    if ((x.a_tile >= 0 && ia == off_of_tile.end()) || (x.b_tile >= 0 && ib == off_of_tile.end()))
+      fail("small term tile");
+    const long long ao = ia == off_of_tile.end() ? -1 : ia->second, bo = ib == off_of_tile.end() ? -1 : ib->second;
+    got.emplace_back(x.in_blk, fl, ao, bo, bits);
     ++nterms;
   }
   std::sort(want.begin(), want.end());
@@ -161,16 +165,22 @@ int main(int argc, char** argv) {
   for (size_t i = 0; i < plan.items.size(); ++i) {
     const TcItem& it = plan.items[i];
     if (it.r_end <= it.r_begin) fail("item without records or terms");
-    if (it.kind == 1) {
+    if (it.kind == 1 || it.kind == 2) {
+      // kind 2: every block at most TC_SMALL_MID wide; kind 1: at most
+      // TC_SMALL_MAX, and some block of every term wider than TC_SMALL_MID
+      const int lim = it.kind == 2 ? TC_SMALL_MID : TC_SMALL_MAX;
       if (it.r_begin != next_small) fail("small term ranges");
       next_small = it.r_end;
-      if (it.nrows > TC_SMALL_MAX || it.ncols > TC_SMALL_MAX || it.r0 != 0 || it.c0 != 0) fail("small item tile");
+      if (it.nrows > lim || it.ncols > lim || it.r0 != 0 || it.c0 != 0) fail("small item tile");
       for (int k = it.r_begin; k < it.r_end && k < (int)plan.small.size(); ++k) {
         const PsiBlock& ib = blocks[plan.small[k].in_blk];
-        if (ib.mL > TC_SMALL_MAX || ib.mR > TC_SMALL_MAX) fail("small term with a large psi block");
+        if (ib.mL > lim || ib.mR > lim) fail("small term with a large psi block");
+        if (it.kind == 1 && std::max(std::max(it.nrows, it.ncols), std::max(ib.mL, ib.mR)) <= TC_SMALL_MID)
+          fail("size class of a small term");
       }
       continue;
     }
+    if (it.kind != 0) fail("item kind");
     if (it.r_begin != next_rec) fail("item record ranges");
     next_rec = it.r_end;
     for (int k = it.r_begin; k < it.r_end && k < (int)plan.recs.size(); ++k) {
@@ -237,8 +247,9 @@ int main(int argc, char** argv) {
   std::vector<int> sch = plan.schedule;
   for (int i : plan.schedule)
     if (plan.items[i].kind != 0) fail("tensor-core schedule holds a small item");
-  for (int i : plan.small_schedule)
-    if (plan.items[i].kind != 1) fail("small schedule holds a tensor-core item");
+  for (size_t k = 0; k < plan.small_schedule.size(); ++k)  // kind 2 first, then kind 1
+    if (plan.items[plan.small_schedule[k]].kind != ((int)k < plan.n_small_mid ? 2 : 1))
+      fail("small schedule: kinds or their order");
   sch.insert(sch.end(), plan.small_schedule.begin(), plan.small_schedule.end());
   std::sort(sch.begin(), sch.end());
   for (size_t i = 0; i < sch.size(); ++i)
