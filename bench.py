@@ -370,7 +370,8 @@ def main():
     # tensor-core sigma (bf16 slices) on the same context and psi
     flops = info["flops"]
     mixed = {}
-    mixed_precisions = () if split else (("bf16x3", capi.DMRG_BF16X3, 6, 6), ("bf16x2", capi.DMRG_BF16X2, 3, 6))
+    mixed_precisions = () if split else (("bf16x3", capi.DMRG_BF16X3, 6, 6), ("bf16x2", capi.DMRG_BF16X2, 3, 6),
+                                         ("fp16x2", capi.DMRG_FP16X2, 3, 4))
     y64 = y.clone()
     peaks = {}
     try:
@@ -381,7 +382,7 @@ def main():
     bf16 = float(peaks.get("bf16_tflops", 1900.0))
     for name, prec, nprod, bytes_per_elem in mixed_precisions:
         capi.dmrg_set_precision(ctx, prec)
-        capi.dmrg_sigma(ctx, -1, x, y)  # builds the bf16 operator slices
+        capi.dmrg_sigma(ctx, -1, x, y)  # builds the operator slices of this precision
         capi.dmrg_sync(ctx)
         tc_tuned = capi.dmrg_autotune(ctx, -1)  # items per SM of the tensor-core work split
         for _ in range(max(3, args.warmup)):
@@ -404,7 +405,7 @@ def main():
         d = (y - y64).abs().max().item() / y64.abs().max().item()
         rq = abs(float(x @ y) - float(x @ y64)) / abs(float(x @ y64))
         # algorithmic bytes: every stored operator element once (6 B as three
-        # bf16 slices) + psi read + sigma written (FP64)
+        # bf16 slices, 4 B as two fp16 slices) + psi read + sigma written (FP64)
         alg_bytes = info["op_elements"] * bytes_per_elem + 16.0 * n
         traffic = TC_TRAFFIC_PER_ALG_BYTE * alg_bytes if (name == "bf16x3" and TC_TRAFFIC_PER_ALG_BYTE) else None
         mixed[name] = {"value": flops / step / 1e12, "unit": "TFLOP/s", "ms_per_step": step * 1e3,

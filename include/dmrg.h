@@ -56,9 +56,16 @@ typedef enum {
  * i + j <= 2 on the tensor cores (tcgen05, FP32 accumulation, correction
  * products before the main ones); every FP32 accumulation of a sigma tile
  * spans at most dmrg_opts.tc_chain main MMA steps of 16 along K before it is
- * added into a running sum of FP32 pairs (about 48 bits). BF16X2: the first
- * two slices and the 3 products with i + j <= 1 (16 significant bits). */
-typedef enum { DMRG_FP64 = 0, DMRG_BF16X2 = 1, DMRG_BF16X3 = 2 } dmrg_prec;
+ * added into a compensated FP32 running sum (about 33 bits). BF16X2: the
+ * first two slices and the 3 products with i + j <= 1 (16 significant bits).
+ * FP16X2: two fp16 slices x = hi + lo (22 significant bits) of operands
+ * scaled by powers of two (each operator block and psi so that its largest
+ * element lies in [2^14, 2^15)), the 3 products with i + j <= 1, FP32
+ * accumulation bounded as for BF16X3; the scales are exact and undone in
+ * the coefficients and the flushes. Classes whose blocks are all at most 32
+ * wide run on the CUDA cores in FP32 from the same split in every mixed
+ * mode. */
+typedef enum { DMRG_FP64 = 0, DMRG_BF16X2 = 1, DMRG_BF16X3 = 2, DMRG_FP16X2 = 3 } dmrg_prec;
 
 typedef struct {
   int sigma_prec;              /* dmrg_prec */
@@ -87,8 +94,9 @@ typedef struct {
                                   FP32 accumulation of a sigma tile may hold before it is added into
                                   the running sum (at least one term per accumulation). The FP32
                                   rounding error of sigma grows about linearly with it. 0 = default
-                                  (8 for BF16X3; for BF16X2 one accumulation per 64-column half of
-                                  every unit of stacked terms); -1 = that unbounded setting for both. */
+                                  (8 for BF16X3 and FP16X2; for BF16X2 one accumulation per
+                                  64-column half of every unit of stacked terms); -1 = that
+                                  unbounded setting for all three. */
 } dmrg_opts;
 
 /* Fill *o with defaults: FP64, 24, 200, 0, 0.0, seed 0, device 0, graphs 1, mixed_cut -1, tc_chain 0. */

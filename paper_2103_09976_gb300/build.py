@@ -23,6 +23,7 @@ SOURCES = [
     "sigma_f64.cu",
     "sigma_tc.cu",
     "sigma_small.cu",
+    "split_f16.cu",
     "sigma_noalloc.cu",
     "davidson.cu",
     "davidson_host.cpp",

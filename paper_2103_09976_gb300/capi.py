@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libdmrg.so")
 DMRG_OK, DMRG_EINVAL, DMRG_ENOMEM, DMRG_ECUDA, DMRG_ENOCONV, DMRG_ETIMEOUT, DMRG_ESTATE = range(7)
 STATUS_NAMES = ["DMRG_OK", "DMRG_EINVAL", "DMRG_ENOMEM", "DMRG_ECUDA", "DMRG_ENOCONV",
                 "DMRG_ETIMEOUT", "DMRG_ESTATE"]
-DMRG_FP64, DMRG_BF16X2, DMRG_BF16X3 = 0, 1, 2
+DMRG_FP64, DMRG_BF16X2, DMRG_BF16X3, DMRG_FP16X2 = 0, 1, 2, 3
 
 
 class dmrg_opts(ctypes.Structure):

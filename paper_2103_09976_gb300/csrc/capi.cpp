@@ -131,22 +131,20 @@ static void prepare_tc_plan(Context& c, Problem& p) {
   p.d_tc_sched.upload(p.tc.schedule, st);
   p.d_tc_pblk.upload(p.tc.psi, st);
   p.d_tc_scratch.alloc(std::max<long long>(1, p.tc.scratch_elems) * sizeof(double));
+  if (!p.d_err.p) {
+    p.d_err.alloc(16);
+    DMRG_CUDA(cudaMemsetAsync(p.d_err.p, 0, 16, st));
+  }
   DMRG_CUDA(cudaStreamSynchronize(st));
   p.graphs.clear();
+  p.tc_plan_ready = true;
+  ++p.tc_plan_gen;
 }
 
-void prepare_tc(Context& c, Problem& p) {
-  cudaStream_t st = c.stream;
-  prepare_tc_plan(c, p);
-  const size_t split_bytes = (size_t)p.tc.n_tiles * 384;
-  size_t freeb = 0, totb = 0;
-  DMRG_CUDA(cudaMemGetInfo(&freeb, &totb));
-  if ((double)split_bytes > 0.92 * (double)freeb)
-    throw Error(DMRG_ENOMEM, "bf16 split operator store does not fit in free device memory");
-  p.split.alloc(split_bytes);
-  DMRG_CUDA(cudaMemsetAsync(p.split.p, 0, split_bytes, st));
-  p.psi_split.alloc((size_t)p.tc.psi_tiles * 384);
-  DMRG_CUDA(cudaMemsetAsync(p.psi_split.p, 0, (size_t)p.tc.psi_tiles * 384, st));
+// Split jobs: every stored block in store order, then the identity blocks of
+// the left and of the right sectors (the order of the plan's split-block
+// indices).
+static std::vector<SplitJob> split_jobs(const Problem& p) {
   std::vector<SplitJob> jobs;
   jobs.reserve(p.tc.opblocks.size() + p.tc.identL.size() + p.tc.identR.size());
   size_t k = 0;
@@ -161,19 +159,105 @@ void prepare_tc(Context& c, Problem& p) {
     const auto& id = side == 0 ? p.tc.identL : p.tc.identR;
     for (int i = 0; i < B.size(); ++i) jobs.push_back({-1, B.dim[i], B.dim[i], id[i].tile, id[i].R8, id[i].C8});
   }
+  return jobs;
+}
+
+static void check_split_fits(size_t bytes, const char* what) {
+  size_t freeb = 0, totb = 0;
+  DMRG_CUDA(cudaMemGetInfo(&freeb, &totb));
+  if ((double)bytes > 0.92 * (double)freeb)
+    throw Error(DMRG_ENOMEM, std::string(what) + " does not fit in free device memory");
+}
+
+// bf16 split of the operators (BF16X3 / BF16X2); drops an fp16 split.
+static void ensure_split_bf16(Context& c, Problem& p) {
+  if (p.bf16_split_ready) return;
+  cudaStream_t st = c.stream;
+  if (p.f16_gen >= 0) {
+    p.graphs.clear();
+    p.split16.reset();
+    p.psi_split16.reset();
+    p.d_tc_recs16.reset();
+    p.d_tc_small16.reset();
+    p.f16_gen = -1;
+  }
+  const size_t split_bytes = (size_t)p.tc.n_tiles * 384;
+  check_split_fits(split_bytes, "bf16 split operator store");
+  p.split.alloc(split_bytes);
+  DMRG_CUDA(cudaMemsetAsync(p.split.p, 0, split_bytes, st));
+  p.psi_split.alloc((size_t)p.tc.psi_tiles * 384);
+  DMRG_CUDA(cudaMemsetAsync(p.psi_split.p, 0, (size_t)p.tc.psi_tiles * 384, st));
+  const std::vector<SplitJob> jobs = split_jobs(p);
   DevBuf d_jobs;
   d_jobs.upload(jobs, st);
   launch_split_ops(p.store.as<double>(), d_jobs.as<SplitJob>(), (long long)jobs.size(), p.split.p, st);
   DMRG_CUDA(cudaGetLastError());
-  p.d_err.alloc(16);
-  DMRG_CUDA(cudaMemsetAsync(p.d_err.p, 0, 16, st));
   DMRG_CUDA(cudaStreamSynchronize(st));
-  p.tc_ready = true;
+  p.bf16_split_ready = true;
+}
+
+// fp16 split of the scaled operators (FP16X2) and the records and small
+// terms of the current plan with coefficients for it; drops a bf16 split.
+static void ensure_split_f16(Context& c, Problem& p) {
+  cudaStream_t st = c.stream;
+  if (p.f16_gen < 0) {
+    if (p.bf16_split_ready) {
+      p.graphs.clear();
+      p.split.reset();
+      p.psi_split.reset();
+      p.bf16_split_ready = false;
+    }
+    const size_t split_bytes = (size_t)p.tc.n_tiles * 256;
+    check_split_fits(split_bytes, "fp16 split operator store");
+    p.split16.alloc(split_bytes);
+    DMRG_CUDA(cudaMemsetAsync(p.split16.p, 0, split_bytes, st));
+    p.psi_split16.alloc((size_t)p.tc.psi_tiles * 256);
+    DMRG_CUDA(cudaMemsetAsync(p.psi_split16.p, 0, (size_t)p.tc.psi_tiles * 256, st));
+    const std::vector<SplitJob> jobs = split_jobs(p);
+    DevBuf d_jobs;
+    d_jobs.upload(jobs, st);
+    p.d_exps.alloc(std::max<size_t>(1, jobs.size()) * sizeof(int));
+    launch_block_exp(p.store.as<double>(), d_jobs.as<SplitJob>(), (long long)jobs.size(), p.d_exps.as<int>(), st);
+    launch_split_ops16(p.store.as<double>(), d_jobs.as<SplitJob>(), (long long)jobs.size(), p.d_exps.as<int>(),
+                       p.split16.p, st);
+    DMRG_CUDA(cudaGetLastError());
+    p.d_psi_exp.alloc(16);
+    DMRG_CUDA(cudaStreamSynchronize(st));
+    p.f16_gen = 0;
+  }
+  if (p.f16_gen != p.tc_plan_gen) {
+    DevBuf d_tb, d_sb;
+    d_tb.upload(p.tc.term_blk, st);
+    d_sb.upload(p.tc.small_blk, st);
+    p.d_tc_recs16.alloc(std::max<size_t>(1, p.tc.recs.size()) * sizeof(TcUnitRec));
+    p.d_tc_small16.alloc(std::max<size_t>(1, p.tc.small.size()) * sizeof(SmallTerm));
+    launch_fix_recs16(p.d_tc_recs.as<TcUnitRec>(), (long long)p.tc.recs.size(), d_tb.as<int>(), p.d_exps.as<int>(),
+                      p.d_tc_recs16.as<TcUnitRec>(), st);
+    launch_fix_small16(p.d_tc_small.as<SmallTerm>(), (long long)p.tc.small.size(), d_sb.as<int>(),
+                       p.d_exps.as<int>(), p.d_tc_small16.as<SmallTerm>(), st);
+    DMRG_CUDA(cudaGetLastError());
+    DMRG_CUDA(cudaStreamSynchronize(st));
+    p.graphs.clear();
+    p.f16_gen = p.tc_plan_gen;
+  }
+}
+
+bool tc_ready_for(const Problem& p, int prec) {
+  if (!p.tc_plan_ready) return false;
+  return prec == DMRG_FP16X2 ? p.f16_gen == p.tc_plan_gen : p.bf16_split_ready;
+}
+
+void prepare_tc(Context& c, Problem& p) {
+  if (!p.tc_plan_ready) prepare_tc_plan(c, p);
+  if (c.opts.sigma_prec == DMRG_FP16X2)
+    ensure_split_f16(c, p);
+  else
+    ensure_split_bf16(c, p);
 }
 
 void check_device_error(Context& c, Problem& p) {
   DMRG_CUDA(cudaStreamSynchronize(c.stream));
-  if (!p.tc_ready) return;
+  if (!p.tc_plan_ready) return;
   int e = 0;
   DMRG_CUDA(cudaMemcpy(&e, p.d_err.p, sizeof(int), cudaMemcpyDeviceToHost));
   if (e) {
@@ -187,29 +271,37 @@ static void run_sigma_tc(Context& c, Problem& p, const double* d_psi, double* d_
 void run_sigma_tc_direct(Context& c, Problem& p, const double* d_psi, double* d_sigma) { run_sigma_tc(c, p, d_psi, d_sigma); }
 
 static void run_sigma_tc(Context& c, Problem& p, const double* d_psi, double* d_sigma) {
-  if (!p.tc_ready) prepare_tc(c, p);
+  const int prec = c.opts.sigma_prec;
+  if (!tc_ready_for(p, prec)) prepare_tc(c, p);
+  const bool f16 = prec == DMRG_FP16X2;
   {
     ProfScope ps_(c.prof, 2, c.stream);
-    launch_split_psi(d_psi, p.d_blocks.as<PsiBlock>(), p.d_tc_pblk.as<TcPsiBlock>(), (int)p.blocks.size(),
-                     p.psi_split.p, c.stream);
+    if (f16)
+      launch_split_psi16(d_psi, p.psi_size, p.d_blocks.as<PsiBlock>(), p.d_tc_pblk.as<TcPsiBlock>(),
+                         (int)p.blocks.size(), p.d_psi_exp.as<int>(), p.psi_split16.p, c.stream);
+    else
+      launch_split_psi(d_psi, p.d_blocks.as<PsiBlock>(), p.d_tc_pblk.as<TcPsiBlock>(), (int)p.blocks.size(),
+                       p.psi_split.p, c.stream);
   }
   DMRG_CUDA(cudaGetLastError());
   TcDev t;
-  t.op = p.split.p;
-  t.psi = p.psi_split.p;
-  t.recs = p.d_tc_recs.as<TcUnitRec>();
+  t.op = f16 ? p.split16.p : p.split.p;
+  t.psi = f16 ? p.psi_split16.p : p.psi_split.p;
+  t.psi_exp = p.d_psi_exp.as<int>();
+  t.f16 = f16 ? 1 : 0;
+  t.recs = f16 ? p.d_tc_recs16.as<TcUnitRec>() : p.d_tc_recs.as<TcUnitRec>();
   t.items = p.d_tc_items.as<TcItem>();
   t.schedule = p.d_tc_sched.as<int>();
   t.n_items = (int)p.tc.schedule.size();
   t.counter = p.d_counter.as<unsigned int>();
   t.scratch = p.d_tc_scratch.as<double>();
   t.err = p.d_err.as<int>();
-  t.nprod = c.opts.sigma_prec == DMRG_BF16X3 ? 6 : 3;
-  // by default BF16X3 bounds each FP32 accumulation to 8 main MMA steps (128
-  // products along K); BF16X2, whose slices carry 16 bits, flushes once per
-  // half of every unit
+  t.nprod = prec == DMRG_BF16X3 ? 6 : 3;
+  // by default BF16X3 and FP16X2 bound each FP32 accumulation to 8 main MMA
+  // steps (128 products along K); BF16X2, whose slices carry 16 bits,
+  // flushes once per half of every unit
   const int chain = c.opts.tc_chain;
-  t.max_chain = chain > 0 ? chain : (chain == 0 && c.opts.sigma_prec == DMRG_BF16X3 ? 8 : 0);
+  t.max_chain = chain > 0 ? chain : (chain == 0 && prec != DMRG_BF16X2 ? 8 : 0);
   t.wait_prof = nullptr;
   if (c.prof.on && c.prof.waits) {
     if (!c.d_wait_prof.p) {
@@ -222,10 +314,12 @@ static void run_sigma_tc(Context& c, Problem& p, const double* d_psi, double* d_
   {
     ProfScope ps_(c.prof, 0, c.stream);
     SmallDev sd;
-    sd.op = p.split.p;
-    sd.psi = p.psi_split.p;
+    sd.op = t.op;
+    sd.psi = t.psi;
+    sd.psi_exp = t.psi_exp;
+    sd.f16 = t.f16;
     sd.pblk = p.d_tc_pblk.as<TcPsiBlock>();
-    sd.terms = p.d_tc_small.as<SmallTerm>();
+    sd.terms = f16 ? p.d_tc_small16.as<SmallTerm>() : p.d_tc_small.as<SmallTerm>();
     sd.items = p.d_tc_items.as<TcItem>();
     sd.schedule = p.d_tc_small_sched.as<int>();
     sd.n_items = (int)p.tc.small_schedule.size();
@@ -268,7 +362,7 @@ void run_sigma(Context& c, Problem& p, const double* d_psi, double* d_sigma) {
     direct();
     return;
   }
-  if (prec != DMRG_FP64 && !p.tc_ready) prepare_tc(c, p);  // allocations stay outside any capture
+  if (prec != DMRG_FP64 && !tc_ready_for(p, prec)) prepare_tc(c, p);  // allocations stay outside any capture
   const GraphKey key{prec, d_psi, d_sigma};
   auto it = p.graphs.m.find(key);
   if (it == p.graphs.m.end()) {
@@ -583,7 +677,7 @@ dmrg_status dmrg_create(dmrg_ctx** out, const dmrg_opts* opts) {
     if (!(o.noise >= 0.0) || !std::isfinite(o.noise)) throw Error(DMRG_EINVAL, "noise must be finite and >= 0");
     if (o.mixed_cut < -1) throw Error(DMRG_EINVAL, "mixed_cut must be -1 (NC everywhere) or >= 0");
     if (o.tc_chain < -1) throw Error(DMRG_EINVAL, "tc_chain must be -1 (unbounded), 0 (default) or >= 1");
-    if (o.sigma_prec < DMRG_FP64 || o.sigma_prec > DMRG_BF16X3)
+    if (o.sigma_prec < DMRG_FP64 || o.sigma_prec > DMRG_FP16X2)
       throw Error(DMRG_EINVAL, "unknown sigma precision");
     int ndev = 0;
     DMRG_CUDA(cudaGetDeviceCount(&ndev));
@@ -622,7 +716,7 @@ void* dmrg_stream(dmrg_ctx* ctx) { return ctx ? (void*)ctx->c.stream : nullptr; 
 dmrg_status dmrg_set_precision(dmrg_ctx* ctx, int prec) {
   if (!ctx) return DMRG_EINVAL;
   return guarded(ctx, [&] {
-    if (prec < DMRG_FP64 || prec > DMRG_BF16X3) throw Error(DMRG_EINVAL, "unknown sigma precision");
+    if (prec < DMRG_FP64 || prec > DMRG_FP16X2) throw Error(DMRG_EINVAL, "unknown sigma precision");
     ctx->c.opts.sigma_prec = prec;
   });
 }
@@ -732,7 +826,7 @@ dmrg_status dmrg_autotune(dmrg_ctx* ctx, int site, int* items_per_sm, double* pe
     if (c.opts.sigma_prec != DMRG_FP64) {
       // tensor-core path: items per SM of the persistent kernel (the split
       // of each output tile's units into items, largest first)
-      if (!p.tc_ready) prepare_tc(c, p);
+      if (!tc_ready_for(p, c.opts.sigma_prec)) prepare_tc(c, p);
       const int cand[4] = {2, 4, 8, 16};
       double best = 1e300;
       int bi = p.tc_items_per_sm;
@@ -740,6 +834,7 @@ dmrg_status dmrg_autotune(dmrg_ctx* ctx, int site, int* items_per_sm, double* pe
         for (int wi : cand) {
           p.tc_items_per_sm = wi;
           prepare_tc_plan(c, p);
+          prepare_tc(c, p);  // FP16X2: records of the new plan
           run_sigma_tc_direct(c, p, c.d_psi.as<double>(), c.d_sigma.as<double>());  // warm-up
           DMRG_CUDA(cudaEventRecord(e0, c.stream));
           run_sigma_tc_direct(c, p, c.d_psi.as<double>(), c.d_sigma.as<double>());
@@ -761,6 +856,7 @@ dmrg_status dmrg_autotune(dmrg_ctx* ctx, int site, int* items_per_sm, double* pe
       cudaEventDestroy(e1);
       p.tc_items_per_sm = bi;
       prepare_tc_plan(c, p);
+      prepare_tc(c, p);
       check_device_error(c, p);
       if (items_per_sm) *items_per_sm = bi;
       if (per_task_cost) *per_task_cost = 0.0;

@@ -140,15 +140,23 @@ struct Problem {
   DevBuf store;              // FP64 operator store
   DevBuf d_tasks, d_items, d_groups, d_sched, d_blocks, d_scratch, d_counter;
   bool ready = false;
-  // tensor-core path (built on first mixed-precision sigma)
+  // tensor-core path (built on first mixed-precision sigma): the plan, and
+  // the split of the operators for the precision in use (bf16 for BF16X3 /
+  // BF16X2, fp16 for FP16X2; one at a time)
   TcPlan tc;
-  bool tc_ready = false;
+  bool tc_plan_ready = false;
+  long long tc_plan_gen = 0;       // plan builds so far
+  bool bf16_split_ready = false;
+  long long f16_gen = -1;          // plan build the FP16X2 records were made for; -1: no fp16 split
   // Davidson workspace (built on first use)
   bool dav_ready = false;
   int dav_space = 0;
   DevBuf dav_V, dav_AV, dav_diag, dav_x, dav_ax, dav_r, dav_t, dav_partial, dav_H, dav_w, dav_Y, dav_s;
   DevBuf d_dstart, d_dtask;
   DevBuf split, psi_split;         // slice-interleaved bf16 tiles of the operators / of psi
+  DevBuf split16, psi_split16;     // FP16X2: slice-interleaved fp16 tiles of the scaled operators / psi
+  DevBuf d_exps, d_psi_exp;        // FP16X2: block exponents (per split job), exponent of max |psi|
+  DevBuf d_tc_recs16, d_tc_small16;  // FP16X2: records and small terms with coefficients for the scaled split
   DevBuf d_tc_recs, d_tc_items, d_tc_small, d_tc_small_sched, d_tc_groups, d_tc_sched, d_tc_pblk, d_tc_scratch, d_err;
   GraphCache graphs;
   // FP64 work-list tuning (dmrg_autotune): items per SM and per-task cost term
@@ -234,6 +242,8 @@ void load_synthetic(Context& c, int nL, int n, int N, int two_sz, const Basis& b
 long long synthetic_footprint(int nL, int n, int N, int two_sz, const Basis& bL, const Basis& bR, int prec,
                               int dav_space, int n_sm);
 void prepare_tc(Context& c, Problem& p);
+// The tensor-core plan and the split for precision `prec` are on the device.
+bool tc_ready_for(const Problem& p, int prec);
 void check_device_error(Context& c, Problem& p);
 void sigma_noalloc(Context& c, Problem& p, const double* psi, double* sigma);
 void sweep_problem(Context& c, int site);

@@ -61,8 +61,9 @@ struct SplitJob {
 };
 
 struct TcDev {
-  const void* op;             // operator tiles, slice-interleaved (3 x 128 B per tile position)
+  const void* op;             // operator tiles, slice-interleaved (3 bf16 or 2 fp16 slices of 128 B per tile position)
   const void* psi;            // psi tiles, same layout
+  const int* psi_exp;         // FP16X2: exponent of max |psi| (psi_exponent), else unused
   const TcUnitRec* recs;      // unit records, grouped by item
   const TcItem* items;        // records of item i: [items[i].r_begin, items[i].r_end)
   const int* schedule;        // item order, most expensive first
@@ -70,7 +71,8 @@ struct TcDev {
   unsigned int* counter;      // next item to take; zero at launch
   double* scratch;
   int* err;                   // nonzero after a bounded wait gave up
-  int nprod;                  // 6 (three slices) or 3 (two slices)
+  int nprod;                  // 6 (three bf16 slices) or 3 (two slices)
+  int f16;                    // 1: FP16X2 (fp16 slices, 256-byte tile positions, scaled operands)
   int max_chain;              // main MMA steps per FP32 accumulation (flush group); <= 0: one group per half
   unsigned long long* wait_prof;  // optional [17]: wait cycles per barrier kind, total cycles
 };
@@ -79,6 +81,8 @@ struct TcDev {
 struct SmallDev {
   const void* op;             // operator split (the tensor-core kernel's tiles)
   const void* psi;            // psi split
+  const int* psi_exp;         // FP16X2 split: exponent of max |psi|, else unused
+  int f16;                    // 1: the split is FP16X2's (2 fp16 slices, scaled operands)
   const TcPsiBlock* pblk;     // psi blocks: split tiles and dimensions
   const SmallTerm* terms;
   const TcItem* items;        // kind-1/2 items index terms
@@ -93,6 +97,25 @@ void launch_split_ops(const double* store, const SplitJob* jobs, long long njobs
 void launch_split_psi(const double* psi, const PsiBlock* blocks, const TcPsiBlock* pb, int nblk, void* out,
                       cudaStream_t st);
 void launch_sigma_tc(const TcDev& a, int n_sm, cudaStream_t st);
+
+// FP16X2 split (split_f16.cu). Operator blocks and psi are scaled by powers
+// of two before the split: block b by 2^(14 - exps[b]), psi by
+// 2^(14 - psi_exponent(*e_psi)), where 2^e <= max |x| < 2^(e+1).
+void launch_block_exp(const double* store, const SplitJob* jobs, long long njobs, int* exps, cudaStream_t st);
+void launch_split_ops16(const double* store, const SplitJob* jobs, long long njobs, const int* exps, void* out,
+                        cudaStream_t st);
+void launch_split_psi16(const double* psi, long long n, const PsiBlock* blocks, const TcPsiBlock* pb, int nblk,
+                        int* e_psi, void* out, cudaStream_t st);
+// Records and small terms with coefficients for the scaled fp16 operands
+// (term_blk / small_blk: split-job indices of each term's left and right
+// blocks).
+void launch_fix_recs16(const TcUnitRec* in, long long n, const int* term_blk, const int* exps, TcUnitRec* out,
+                       cudaStream_t st);
+void launch_fix_small16(const SmallTerm* in, long long n, const int* small_blk, const int* exps, SmallTerm* out,
+                        cudaStream_t st);
+// The exponent written by launch_split_psi16 (an all-zero psi leaves the
+// initial value, far below any exponent: taken as 0).
+__host__ __device__ inline int psi_exponent(int e) { return e < -100000 ? 0 : e; }
 
 // ------------------------------------------------------------------- sweep
 // One term of an enlarged operator: coef * (source op `src`, transposed when

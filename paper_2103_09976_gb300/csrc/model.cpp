@@ -574,6 +574,7 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
     std::vector<Group> groups;
     std::vector<std::pair<int, Unit>> units;  // (output block, unit)
     std::vector<SmallTerm> small;
+    std::vector<int> small_blk;          // per small term: split-block indices of its left and right blocks
     std::vector<double> icost;
     std::vector<int> order;              // sorted task indices, per block contiguous
     long long scratch = 0;
@@ -611,6 +612,7 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
           TcItem it{(int)b, r0, tm, c0, tn, (int)P.units.size(), 0, 0, P.scratch};
           double acc = 0;
           std::vector<SmallTerm> sm[2];  // CUDA-core terms: all blocks <= TC_SMALL_MID, the rest
+          std::vector<int> smb[2];       // their split-block indices (left, right)
           int k = obase;
           const int kend = obase + (t1 - t0);
           while (k < kend) {
@@ -622,12 +624,14 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
             // CUDA-core class: the whole output block (one tile) and the psi block are small
             const int wmax = std::max(std::max(ob.mL, ob.mR), std::max(ib.m, ib.n));
             if (wmax <= TC_SMALL_MAX) {
-              std::vector<SmallTerm>& dst = sm[wmax <= TC_SMALL_MID ? 0 : 1];
+              const int cls = wmax <= TC_SMALL_MID ? 0 : 1;
               for (int q = k; q < e; ++q) {
                 const Base& x = base[P.order[q]];
                 const Task& tk = wl.tasks[x.task];
-                dst.push_back({tk.aoff < 0 ? -1 : x.a_tile, tk.boff < 0 ? -1 : x.b_tile, tk.in_blk, tk.flags & 3,
-                               tk.scale});
+                sm[cls].push_back({tk.aoff < 0 ? -1 : x.a_tile, tk.boff < 0 ? -1 : x.b_tile, tk.in_blk, tk.flags & 3,
+                                   tk.scale});
+                smb[cls].push_back(x.a_blk);
+                smb[cls].push_back(x.b_blk);
               }
               P.n_terms += e - k;
               k = e;
@@ -660,6 +664,7 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
           for (int cls = 0; cls < 2; ++cls) {  // CUDA-core items: kind 2 (<= TC_SMALL_MID), kind 1
             const size_t base0 = P.small.size();
             P.small.insert(P.small.end(), sm[cls].begin(), sm[cls].end());
+            P.small_blk.insert(P.small_blk.end(), smb[cls].begin(), smb[cls].end());
             for (size_t s0 = base0; s0 < P.small.size(); s0 += SMALL_ITEM) {
               const size_t s1 = std::min(P.small.size(), s0 + SMALL_ITEM);
               double c = 0;
@@ -700,11 +705,13 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
   plan.recs.resize(U[nparts]);  // uninitialized: every record is written below
   plan.term_blk.assign((size_t)U[nparts] * TC_MAX_G * 2, -1);
   plan.small.resize(SM[nparts]);
+  plan.small_blk.resize(2 * SM[nparts]);
   plan.n_units = 0;
   std::vector<double> icost(I[nparts]);
   in_parallel([&](int j) {
     const Part& P = parts[j];
     std::copy(P.small.begin(), P.small.end(), plan.small.begin() + SM[j]);
+    std::copy(P.small_blk.begin(), P.small_blk.end(), plan.small_blk.begin() + 2 * SM[j]);
     size_t rec = U[j];
     for (size_t i = 0; i < P.items.size(); ++i) {
       TcItem it = P.items[i];

@@ -342,6 +342,7 @@ struct TcPlan {
   // the left and right blocks (stored blocks in store order, then the
   // identity blocks of the left and right sectors); -1 for unused slots
   std::vector<int> term_blk;
+  std::vector<int> small_blk;           // per small term (2k, 2k+1): split-block indices as in term_blk
   std::vector<int> small_schedule;      // kind-2 items, then kind-1 items, each most expensive first
   int n_small_mid = 0;                  // kind-2 items (the head of small_schedule)
   long long n_terms = 0;                // term products (tasks x tiles), counted once

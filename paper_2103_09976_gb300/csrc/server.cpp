@@ -162,7 +162,7 @@ dmrg_status dmrg_server_submit(dmrg_server* s, const dmrg_request* r) {
     if (r->n_sec_left <= 0 || r->n_sec_right <= 0 || !r->sec_left || !r->sec_right)
       throw Error(DMRG_EINVAL, "empty sector list");
     if (!(r->tol > 0.0) || r->max_iter < 1) throw Error(DMRG_EINVAL, "tol must be positive, max_iter >= 1");
-    if (r->sigma_prec < DMRG_FP64 || r->sigma_prec > DMRG_BF16X3) throw Error(DMRG_EINVAL, "unknown precision");
+    if (r->sigma_prec < DMRG_FP64 || r->sigma_prec > DMRG_FP16X2) throw Error(DMRG_EINVAL, "unknown precision");
     job.left.assign(r->sec_left, r->sec_left + 3 * r->n_sec_left);
     job.right.assign(r->sec_right, r->sec_right + 3 * r->n_sec_right);
     job.r.sec_left = nullptr;

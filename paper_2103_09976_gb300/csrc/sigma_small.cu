@@ -19,6 +19,8 @@
 // the operands from their bf16 split (no FP64 -> FP32 conversion, which
 // runs on the narrow FP64 pipe), issues all loads of a block before storing
 // any, and computes register-blocked products from shared memory.
+#include <cuda_fp16.h>
+
 #include "kernels.h"
 
 namespace dmrg {
@@ -50,9 +52,10 @@ constexpr int small_smem();
 // FP32 within an ulp); the bf16 -> FP32 widening is a shift on the integer
 // pipe. Lane q takes tile row q (of 8 per tile) and reads its three 16-byte
 // slice rows, all loads of the block first; tile padding holds zeros.
-template <int D, int LD>
+template <int D, int LD, bool F16>
 __device__ __forceinline__ void load_tiles(float* T, const unsigned char* __restrict__ op, long long tile, int R8,
                                            int C8, bool trans, int lane) {
+  constexpr int TILE = F16 ? 256 : 384;  // bytes per tile position
   // tile rows per lane, taken PASS at a time (registers of the <= 32 class)
   constexpr int PER = (D / 8) * (D / 8) * 8 / 32, PASS = PER < 2 ? PER : 2;
   const int nrow = R8 * C8 * 8;
@@ -63,10 +66,10 @@ __device__ __forceinline__ void load_tiles(float* T, const unsigned char* __rest
     for (int k = 0; k < PASS; ++k) {
       const int q = lane + 32 * (k0 + k);
       if (q < nrow) {
-        const uint4* p = reinterpret_cast<const uint4*>(op + (tile + (q >> 3)) * 384 + (q & 7) * 16);
+        const uint4* p = reinterpret_cast<const uint4*>(op + (tile + (q >> 3)) * TILE + (q & 7) * 16);
         h[k] = __ldg(p);
         m[k] = __ldg(p + 8);
-        l[k] = __ldg(p + 16);
+        if (!F16) l[k] = __ldg(p + 16);
       }
     }
 #pragma unroll
@@ -74,14 +77,27 @@ __device__ __forceinline__ void load_tiles(float* T, const unsigned char* __rest
       const int q = lane + 32 * (k0 + k);
       if (q < nrow) {
         const int t = q >> 3, tr = t / C8, tc = t - tr * C8, r = 8 * tr + (q & 7), c0 = 8 * tc;
-        const uint32_t hw[4] = {h[k].x, h[k].y, h[k].z, h[k].w}, mw[4] = {m[k].x, m[k].y, m[k].z, m[k].w},
-                       lw[4] = {l[k].x, l[k].y, l[k].z, l[k].w};
+        const uint32_t hw[4] = {h[k].x, h[k].y, h[k].z, h[k].w}, mw[4] = {m[k].x, m[k].y, m[k].z, m[k].w};
+        uint32_t lw[4] = {0u, 0u, 0u, 0u};
+        if (!F16) {
+          lw[0] = l[k].x;
+          lw[1] = l[k].y;
+          lw[2] = l[k].z;
+          lw[3] = l[k].w;
+        }
         float v[8];
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
-          v[2 * w] = (__uint_as_float(hw[w] << 16) + __uint_as_float(mw[w] << 16)) + __uint_as_float(lw[w] << 16);
-          v[2 * w + 1] = (__uint_as_float(hw[w] & 0xFFFF0000u) + __uint_as_float(mw[w] & 0xFFFF0000u)) +
-                         __uint_as_float(lw[w] & 0xFFFF0000u);
+          if (!F16) {
+            v[2 * w] = (__uint_as_float(hw[w] << 16) + __uint_as_float(mw[w] << 16)) + __uint_as_float(lw[w] << 16);
+            v[2 * w + 1] = (__uint_as_float(hw[w] & 0xFFFF0000u) + __uint_as_float(mw[w] & 0xFFFF0000u)) +
+                           __uint_as_float(lw[w] & 0xFFFF0000u);
+          } else {  // fp16 hi + lo (scaled values; the coefficients undo the scales)
+            const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&hw[w]));
+            const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&mw[w]));
+            v[2 * w] = a.x + b.x;
+            v[2 * w + 1] = a.y + b.y;
+          }
         }
         if (!trans) {
           *reinterpret_cast<float4*>(T + r * LD + c0) = make_float4(v[0], v[1], v[2], v[3]);
@@ -167,7 +183,7 @@ __device__ __forceinline__ void term_product(float (&y)[Tile<D>::RI][Tile<D>::CJ
   }
 }
 
-template <int D>
+template <int D, bool F16>
 __global__ void __launch_bounds__(32 * SmallCfg<D>::NW, SmallCfg<D>::MINB) sigma_small_kernel(SmallDev a) {
   constexpr int NW = SmallCfg<D>::NW, LD = Tile<D>::LD, BLK = D * LD, RI = Tile<D>::RI, CJ = Tile<D>::CJ;
   // terms summed in FP32 (scaled products) before each FP64 addition
@@ -203,14 +219,14 @@ __global__ void __launch_bounds__(32 * SmallCfg<D>::NW, SmallCfg<D>::MINB) sigma
       // its stored tn x n (or n x tn when used transposed).
       const unsigned char* op = reinterpret_cast<const unsigned char*>(a.op);
       if (tk.in_blk != cur)
-        load_tiles<D, LD>(sPsi, reinterpret_cast<const unsigned char*>(a.psi), pb.tile, pb.R8, pb.C8, false, lane);
+        load_tiles<D, LD, F16>(sPsi, reinterpret_cast<const unsigned char*>(a.psi), pb.tile, pb.R8, pb.C8, false, lane);
       if (!idL) {
         const bool tA = tk.flags & 1;
-        load_tiles<D, LD>(sL, op, tk.a_tile, tA ? (m + 7) / 8 : (tm + 7) / 8, tA ? (tm + 7) / 8 : (m + 7) / 8, tA, lane);
+        load_tiles<D, LD, F16>(sL, op, tk.a_tile, tA ? (m + 7) / 8 : (tm + 7) / 8, tA ? (tm + 7) / 8 : (m + 7) / 8, tA, lane);
       }
       if (!idR) {
         const bool tB = tk.flags & 2;
-        load_tiles<D, LD>(sRt, op, tk.b_tile, tB ? (n + 7) / 8 : (tn + 7) / 8, tB ? (tn + 7) / 8 : (n + 7) / 8, !tB, lane);
+        load_tiles<D, LD, F16>(sRt, op, tk.b_tile, tB ? (n + 7) / 8 : (tn + 7) / 8, tB ? (tn + 7) / 8 : (n + 7) / 8, !tB, lane);
       }
       cur = tk.in_blk;
       __syncwarp();
@@ -256,10 +272,11 @@ __global__ void __launch_bounds__(32 * SmallCfg<D>::NW, SmallCfg<D>::MINB) sigma
       }
     __syncthreads();
     double* out = a.scratch + it.slot;
+    const double ps = F16 ? ldexp(1.0, psi_exponent(*a.psi_exp) - 14) : 1.0;  // undo psi's split scale
     for (int e = threadIdx.x; e < tm * tn; e += blockDim.x) {
       double v = sum[e];
       for (int w = 1; w < NW; ++w) v += sum[w * D * D + e];
-      out[e] = v;
+      out[e] = F16 ? v * ps : v;
     }
     __syncthreads();
   }
@@ -276,13 +293,17 @@ static_assert(TC_SMALL_MAX == 32 && TC_SMALL_MID == 16, "size classes");
 template <int D>
 void launch_class(const SmallDev& a, int n_items, const int* schedule, int n_sm, cudaStream_t st) {
   if (n_items <= 0) return;
-  set_max_dynamic_smem((const void*)sigma_small_kernel<D>, small_smem<D>());
+  const void* fn = a.f16 ? (const void*)sigma_small_kernel<D, true> : (const void*)sigma_small_kernel<D, false>;
+  set_max_dynamic_smem(fn, small_smem<D>());
   SmallDev b = a;
   b.schedule = schedule;
   b.n_items = n_items;
   int grid = SmallCfg<D>::MINB * n_sm;
   if (grid > n_items) grid = n_items;
-  sigma_small_kernel<D><<<grid, 32 * SmallCfg<D>::NW, small_smem<D>(), st>>>(b);
+  if (a.f16)
+    sigma_small_kernel<D, true><<<grid, 32 * SmallCfg<D>::NW, small_smem<D>(), st>>>(b);
+  else
+    sigma_small_kernel<D, false><<<grid, 32 * SmallCfg<D>::NW, small_smem<D>(), st>>>(b);
 }
 
 }  // namespace

@@ -38,6 +38,7 @@
 // timeout the kernel raises a flag in *err, stops issuing work, waits (again
 // bounded) for its own copies, frees its tensor memory and returns.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <cstddef>
 
@@ -49,33 +50,47 @@ namespace {
 
 constexpr int NEPI = 8;                         // epilogue warps
 constexpr int NTHR = 64 + 32 * NEPI;            // producer + MMA + epilogue
-constexpr int STAGES = 3;
-// Operator and psi tiles are stored slice-interleaved: tile position k holds
-// its hi, mid and lo 8x8 bf16 tiles at bytes 384k, 384k+128, 384k+256, in
-// global memory and in the stages alike.
-constexpr int TILE3 = 384;
-constexpr int STAGE_TILES = 128;                // tile positions per stage
-constexpr int STAGE_BYTES = STAGE_TILES * TILE3;  // 48 KB
-constexpr int PSI_TILE = 64;                    // psi tiles of a stage-1 stage start here
 constexpr int A2_SLICE = 16 * 1024;             // X half: 16 row groups x 8 K groups x 128 B
 constexpr int A2_OFF = 0;                       // A2 first: reads past its last slice land in stage 0
-constexpr int STAGE_OFF = 3 * A2_SLICE;
 constexpr int NMETA = 8;                        // unit records in the shared-memory ring
 constexpr int PREFETCH = 4;                     // records fetched ahead of the producer
-constexpr int META_OFF = STAGE_OFF + STAGES * STAGE_BYTES;
-constexpr int BAR_OFF = META_OFF + NMETA * (int)sizeof(TcUnitRec);
-constexpr int SMEM_BYTES = BAR_OFF + 512;
 constexpr long long WAIT_CYCLES = 2000000000ll; // ~1 s at 2 GHz
 
-// barrier slots (8 bytes each)
-enum { B_FULL = 0, B_EMPTY = STAGES, B_XFULL = 2 * STAGES, B_XEMPTY = 2 * STAGES + 2,
-       B_A2FULL = 2 * STAGES + 4, B_A2EMPTY = 2 * STAGES + 5, B_SFULL = 2 * STAGES + 6,
-       B_SEMPTY = 2 * STAGES + 8, B_MFULL = 2 * STAGES + 10, B_MEMPTY = B_MFULL + NMETA,
-       B_TMEM = B_MEMPTY + NMETA, B_ABORT = B_TMEM + 1 };
-static_assert(8 * (B_ABORT + 1) <= 512, "barrier region");
-static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
+// Shared-memory layout of one precision. Operator and psi tiles are stored
+// slice-interleaved: tile position k holds its NSL 8x8 slices (bf16 hi, mid,
+// lo; or fp16 hi, lo) at bytes TILE*k + 128*s, in global memory and in the
+// stages alike. The second-product operand (A2) holds NSL slices of X.
+// Stage geometry: STAGE_TILES tile positions per stage; a stage-1 stage
+// holds KG1 K groups of the stacked left operators (16 M groups) and of psi
+// (16 N groups, from PSI_TILE on). NA2 second-product operands (A2) let the
+// epilogue convert the next 64-column half while the MMAs read the last.
+template <bool F16>
+struct Lay {
+  static constexpr int NSL = F16 ? 2 : 3;
+  static constexpr int TILE = 128 * NSL;
+  static constexpr int STAGES = 3;
+  static constexpr int STAGE_TILES = F16 ? 192 : 128;
+  static constexpr int KG1 = F16 ? 6 : 4;
+  static constexpr int PSI_TILE = 16 * KG1;
+  static constexpr int NA2 = F16 ? 2 : 1;
+  static constexpr int A2_BYTES = NSL * A2_SLICE;  // one A2 buffer
+  static constexpr int STAGE_BYTES = STAGE_TILES * TILE;
+  static constexpr int STAGE_OFF = NA2 * A2_BYTES;
+  static constexpr int META_OFF = STAGE_OFF + STAGES * STAGE_BYTES;
+  static constexpr int BAR_OFF = META_OFF + NMETA * (int)sizeof(TcUnitRec);
+  static constexpr int SMEM_BYTES = BAR_OFF + 512;
+  // barrier slots (8 bytes each)
+  static constexpr int B_FULL = 0, B_EMPTY = STAGES, B_XFULL = 2 * STAGES, B_XEMPTY = 2 * STAGES + 2,
+                       B_A2FULL = 2 * STAGES + 4, B_A2EMPTY = B_A2FULL + NA2, B_SFULL = B_A2EMPTY + NA2,
+                       B_SEMPTY = B_SFULL + 2, B_MFULL = B_SEMPTY + 2, B_MEMPTY = B_MFULL + NMETA,
+                       B_TMEM = B_MEMPTY + NMETA, B_ABORT = B_TMEM + 1;
+  static_assert(8 * (B_ABORT + 1) <= 512, "barrier region");
+  static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
+  static_assert(META_OFF % 16 == 0, "records are bulk-copied");
+  static_assert(KG1 % 2 == 0 && 2 * PSI_TILE <= STAGE_TILES, "stage-1 stage");
+};
 static_assert(sizeof(TcUnitRec) == 464 && offsetof(TcUnitRec, t) == 80, "record layout");
-static_assert(META_OFF % 16 == 0 && sizeof(TcUnitRec) % 16 == 0, "records are bulk-copied");
+static_assert(sizeof(TcUnitRec) % 16 == 0, "records are bulk-copied");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -86,8 +101,12 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
 
-__device__ __forceinline__ uint32_t idesc_bf16(int n, int a_mn, int b_mn) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+// Instruction descriptor of kind::f16, M = 128, FP32 accumulator: A and B
+// both bf16 (F16 = false) or both fp16.
+template <bool F16>
+__device__ __forceinline__ uint32_t idesc_of(int n, int a_mn, int b_mn) {
+  const uint32_t fmt = F16 ? 0u : 1u;
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
          ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
@@ -178,7 +197,8 @@ __device__ __forceinline__ int n_chunks(const TcUnitRec& r) { return (r.n + 127)
 __device__ __forceinline__ int chunk_cols(const TcUnitRec& r, int j) { return min(128, r.n - 128 * j); }
 __device__ __forceinline__ int n_halves(const TcUnitRec& r, int j) { return (chunk_cols(r, j) + 63) >> 6; }
 __device__ __forceinline__ int half_cols(const TcUnitRec& r, int j, int h) { return min(64, chunk_cols(r, j) - 64 * h); }
-__device__ __forceinline__ int k1_stages(const TcUnitRec& r) { return (r.pR8 + 3) >> 2; }
+template <int KG1>
+__device__ __forceinline__ int k1_stages(const TcUnitRec& r) { return (r.pR8 + KG1 - 1) / KG1; }
 __device__ __forceinline__ int tn8e(const TcUnitRec& r) { return 2 * ((r.tn + 15) >> 4); }  // N groups read by the MMA
 __device__ __forceinline__ int kg2_of(int kw) { return 2 * ((kw + 15) >> 4); }               // K groups of a half
 // Terms per flush group: the most whose main K steps in one half stay within
@@ -220,25 +240,26 @@ __device__ __forceinline__ UnitGeo geo_of(const TcUnitRec& r) {
   return g;
 }
 
-// Copies of one stage-1 stage (psi columns of chunk j, K groups 4k..4k+3):
+// Copies of one stage-1 stage (psi columns of chunk j, K groups KG1*k ..):
 // the stacked left-operator rows of every term ([M group][K group], or
 // [K group][M group] when the left operator is used transposed) and the psi
 // tiles ([K group][N group] from PSI_TILE on). Each lane issues copies
 // lane, lane + 32, ...; f(src_tile, operand (0 operators, 1 psi), dst_tile,
 // n_tiles) moves n_tiles tile positions (3 slices). Returns the stage's tile
 // count (the same on every lane).
-template <class F>
+template <int KG1, class F>
 __device__ __forceinline__ uint32_t copies_s1(const TcUnitRec& r, const UnitGeo& g, int j, int k, int lane, F&& f) {
-  const int kg0 = 4 * k;
+  constexpr int PSI_TILE = 16 * KG1;
+  const int kg0 = KG1 * k;
   const bool tA = g.flags & TC_TA;
-  const int nkA = tA ? min(4, g.aR8 - kg0) : min(4, g.aC8 - kg0);  // K groups of A in this stage
-  const int nA = nkA > 0 ? (tA ? g.G * nkA : g.G * g.tm8) : 0;     // A copies
-  const int perA = tA ? g.tm8 : nkA;                                // tiles per A copy
-  const int nkP = min(4, g.pR8 - kg0), nn = min(16, g.pC8 - 16 * j);
+  const int nkA = tA ? min(KG1, g.aR8 - kg0) : min(KG1, g.aC8 - kg0);  // K groups of A in this stage
+  const int nA = nkA > 0 ? (tA ? g.G * nkA : g.G * g.tm8) : 0;         // A copies
+  const int perA = tA ? g.tm8 : nkA;                                    // tiles per A copy
+  const int nkP = min(KG1, g.pR8 - kg0), nn = min(16, g.pC8 - 16 * j);
   for (int c = lane; c < nA; c += 32) {
     if (!tA) {
       const int q = c / g.tm8, rg = c - q * g.tm8;
-      f(r.t[q].a_tile + (long long)(g.r0g + rg) * g.aC8 + kg0, 0, (q * g.tm8 + rg) * 4, perA);
+      f(r.t[q].a_tile + (long long)(g.r0g + rg) * g.aC8 + kg0, 0, (q * g.tm8 + rg) * KG1, perA);
     } else {
       const int q = c / nkA, kg = c - q * nkA;
       f(r.t[q].a_tile + (long long)(kg0 + kg) * g.aC8 + g.r0g, 0, kg * 16 + q * g.tm8, perA);
@@ -337,8 +358,16 @@ __device__ __forceinline__ void mma_chain(bool leader, uint32_t tmem_d, uint64_t
 }
 
 // PROF: record wait accounting and MMA-thread cycles into a.wait_prof.
-template <int NPROD, bool PROF>
+// F16: FP16X2 (two fp16 slices of scaled operands; see split_f16.cu).
+template <int NPROD, bool F16, bool PROF>
 __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
+  using L = Lay<F16>;
+  constexpr int TILE = L::TILE, STAGES = L::STAGES, STAGE_BYTES = L::STAGE_BYTES, STAGE_OFF = L::STAGE_OFF;
+  constexpr int META_OFF = L::META_OFF, BAR_OFF = L::BAR_OFF, STAGE_TILES = L::STAGE_TILES, KG1 = L::KG1,
+                PSI_TILE = L::PSI_TILE, NA2 = L::NA2, A2_BYTES = L::A2_BYTES;
+  constexpr int B_FULL = L::B_FULL, B_EMPTY = L::B_EMPTY, B_XFULL = L::B_XFULL, B_XEMPTY = L::B_XEMPTY,
+                B_A2FULL = L::B_A2FULL, B_A2EMPTY = L::B_A2EMPTY, B_SFULL = L::B_SFULL, B_SEMPTY = L::B_SEMPTY,
+                B_MFULL = L::B_MFULL, B_MEMPTY = L::B_MEMPTY, B_TMEM = L::B_TMEM, B_ABORT = L::B_ABORT;
   extern __shared__ __align__(1024) unsigned char sm[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t sbase = smem_u32(sm);
@@ -365,8 +394,10 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
       mbar_init(bar(B_SFULL + x), 1);
       mbar_init(bar(B_SEMPTY + x), NEPI);
     }
-    mbar_init(bar(B_A2FULL), NEPI);
-    mbar_init(bar(B_A2EMPTY), 1);
+    for (int b = 0; b < NA2; ++b) {
+      mbar_init(bar(B_A2FULL + b), NEPI);
+      mbar_init(bar(B_A2EMPTY + b), 1);
+    }
     for (int m = 0; m < NMETA; ++m) {
       mbar_init(bar(B_MFULL + m), 1);
       mbar_init(bar(B_MEMPTY + m), 2 + NEPI);  // producer + MMA + epilogue warps
@@ -399,20 +430,20 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
       // the byte count is announced before any copy can complete: lane 0
       // arrives with the expected bytes first, then all lanes issue copies
       const uint32_t tiles = copies([&](long long, int, int, int) {}, true);
-      if (lane == 0) mbar_expect_tx(fb, (uint32_t)TILE3 * tiles);
+      if (lane == 0) mbar_expect_tx(fb, (uint32_t)TILE * tiles);
       __syncwarp();
       copies([&](long long src, int which, int dst, int n) {
-        bulk_g2s(sdst + (uint32_t)dst * TILE3, (which ? ps : ops) + src * TILE3, (uint32_t)TILE3 * (uint32_t)n, fb);
+        bulk_g2s(sdst + (uint32_t)dst * TILE, (which ? ps : ops) + src * TILE, (uint32_t)TILE * (uint32_t)n, fb);
       }, false);
       if (++stage == STAGES) { stage = 0; phase ^= 1; }
     };
     auto produce_s1 = [&](const TcUnitRec& u, int j) {
       const UnitGeo g = geo_of(u);
-      const int nk1 = (g.pR8 + 3) >> 2;
+      const int nk1 = (g.pR8 + KG1 - 1) / KG1;
       for (int k = 0; k < nk1; ++k)
         produce([&](auto&& f, bool count_only) -> uint32_t {
-          if (count_only) return copies_s1(u, g, j, k, 32, f);  // lane 32 issues nothing
-          return copies_s1(u, g, j, k, lane, f);
+          if (count_only) return copies_s1<KG1>(u, g, j, k, 32, f);  // lane 32 issues nothing
+          return copies_s1<KG1>(u, g, j, k, lane, f);
         });
     };
     auto produce_s2 = [&](const TcUnitRec& u, int j) {
@@ -525,7 +556,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
       };
       uint32_t stage = 0, phase = 0;
       uint32_t xcnt = 0, xph_empty = 3u;   // bit b: expected parity of X-empty[b]
-      uint32_t a2_full_ph = 0;
+      uint32_t h2 = 0;                     // halves consumed: A2 buffer h2 % NA2, parity (h2 / NA2) & 1
       uint32_t sb = 0, sph_empty = 3u;     // bit b: expected parity of S-empty[b]
       bool ok = true;
       auto acquire = [&]() -> uint32_t {
@@ -547,16 +578,16 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
         asm volatile("tcgen05.fence::after_thread_sync;\n");
         const uint32_t tmem_x = tmem + xb * 128;
         const int tA = (u.flags & TC_TA) ? 1 : 0;
-        const uint32_t id1 = idesc_bf16(16 * ((chunk_cols(u, j) + 15) / 16), tA, 1);
-        const uint32_t a_lbo = tA ? 16u * TILE3 : TILE3, a_sbo = tA ? TILE3 : 4u * TILE3;
-        const int pR8 = u.pR8, nk1 = k1_stages(u);  // read once: the waits below clobber memory
+        const uint32_t id1 = idesc_of<F16>(16 * ((chunk_cols(u, j) + 15) / 16), tA, 1);
+        const uint32_t a_lbo = tA ? 16u * TILE : TILE, a_sbo = tA ? TILE : (uint32_t)KG1 * TILE;
+        const int pR8 = u.pR8, nk1 = k1_stages<KG1>(u);  // read once: the waits below clobber memory
         bool first = true;
         for (int k = 0; k < nk1 && ok; ++k) {
           const uint32_t sst = acquire();
           if (!ok) return;
           const long long t0 = tick();
-          mma_chain<NPROD>(leader, tmem_x, sdesc(sst, a_lbo, a_sbo), sdesc(sst + PSI_TILE * TILE3, 16u * TILE3, TILE3),
-                           128u, 128u, 2 * a_lbo, 2 * 16u * TILE3, min(4, pR8 - 4 * k) / 2, id1, first);
+          mma_chain<NPROD>(leader, tmem_x, sdesc(sst, a_lbo, a_sbo), sdesc(sst + PSI_TILE * TILE, 16u * TILE, TILE),
+                           128u, 128u, 2 * a_lbo, 2 * 16u * TILE, min(KG1, pR8 - KG1 * k) / 2, id1, first);
           tock(14, t0);
           release();
         }
@@ -570,18 +601,19 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
       // stage 2 of sub-unit (u, j): per half, per term, sigma += X_t R_t^T,
       // the tile accumulator switching buffers after every flush group
       auto mma_s2 = [&](const TcUnitRec& u, int j) {
-        const uint32_t a2 = sbase + A2_OFF;
         const int tB = (u.flags & TC_TB) ? 1 : 0, te = tn8e(u), G = u.nterm, F = flush_terms(u, a.max_chain);
-        const uint32_t id2 = idesc_bf16(16 * ((u.tn + 15) / 16), 0, tB);
+        const uint32_t id2 = idesc_of<F16>(16 * ((u.tn + 15) / 16), 0, tB);
         const int nh = n_halves(u, j), tm8 = u.tm8, ccols = chunk_cols(u, j);
         const bool whole = whole_chunk_group(u, j, a.max_chain);
         bool first = true;
         for (int h = 0; h < nh && ok; ++h) {
-          if (!mbar_wait<PROF>(bar(B_A2FULL), a2_full_ph, abort_flag, a.err, 5)) { ok = false; return; }
-          a2_full_ph ^= 1;
+          const uint32_t hb = h2 % NA2;
+          if (!mbar_wait<PROF>(bar(B_A2FULL + hb), (h2 / NA2) & 1u, abort_flag, a.err, 5)) { ok = false; return; }
+          ++h2;
+          const uint32_t a2 = sbase + A2_OFF + hb * A2_BYTES;
           const int kw = min(64, ccols - 64 * h), kg2 = kg2_of(kw), P = max(1, min(G, STAGE_TILES / (te * kg2)));
-          const uint32_t b_lbo = tB ? (uint32_t)te * TILE3 : TILE3;
-          const uint32_t b_sbo = tB ? TILE3 : (uint32_t)kg2 * TILE3;
+          const uint32_t b_lbo = tB ? (uint32_t)te * TILE : TILE;
+          const uint32_t b_sbo = tB ? TILE : (uint32_t)kg2 * TILE;
           for (int q0 = 0; q0 < G && ok; q0 += P) {
             const uint32_t sst = acquire();
             if (!ok) return;
@@ -599,7 +631,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
               }
               const long long t0 = tick();
               mma_chain<NPROD>(leader, tmem + 256 + sb * 128, sdesc(a2 + (uint32_t)(q * tm8) * 1024u, 128u, 1024u),
-                               sdesc(sst + (uint32_t)((q - q0) * te * kg2) * TILE3, b_lbo, b_sbo), A2_SLICE, 128u,
+                               sdesc(sst + (uint32_t)((q - q0) * te * kg2) * TILE, b_lbo, b_sbo), A2_SLICE, 128u,
                                2 * 128u, 2 * b_lbo, kg2 / 2, id2, first);
               tock(14, t0);
               if (gend) {  // the group ends: hand the accumulator to the epilogue
@@ -612,7 +644,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
             release();
           }
           const long long t1 = tick();
-          if (leader) commit(bar(B_A2EMPTY));
+          if (leader) commit(bar(B_A2EMPTY + hb));
           tock(15, t1);
         }
       };
@@ -654,10 +686,12 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
     const int row = quarter * 32 + lane;       // TMEM lane owned by this thread
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     uint32_t xcnt = 0, xph_full = 0;           // bit b: expected parity of X-full[b]
-    uint32_t a2_empty_ph = 1;
+    uint32_t h2 = 0;                           // halves converted: A2 buffer h2 % NA2, parity (h2 / NA2) & 1
     uint32_t sb = 0, sph_full = 0;             // bit b: expected parity of S-full[b]
     bool ok = true;
-    __nv_bfloat16* a2 = reinterpret_cast<__nv_bfloat16*>(sm + A2_OFF);
+    uint16_t* a2 = reinterpret_cast<uint16_t*>(sm + A2_OFF);  // the A2 buffer of the current half
+    // FP16X2: the flush undoes the unit's tile scale 2^(E - e_psi)
+    const int e_psi = F16 ? psi_exponent(*a.psi_exp) : 0;
     // running sum of this thread's 64 tile columns: compensated (Kahan) FP32
     // sums s and their compensation c, the sum being s - c. c is the rounding
     // error of the last addition (below half an ulp of s) and is kept in bf16,
@@ -679,29 +713,37 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
         uint32_t hw[4], mw[4], lw[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          // two columns at a time: one paired round-to-nearest conversion per
-          // slice; a bf16 value is the upper half of its float, so the
-          // residuals need only a mask or a shift and a subtraction
           const float x0 = v[g * 8 + 2 * q], x1 = v[g * 8 + 2 * q + 1];
-          const uint32_t hp = bf16x2_bits(x0, x1);
-          const float r0 = x0 - __uint_as_float(hp << 16), r1 = x1 - __uint_as_float(hp & 0xFFFF0000u);
-          const uint32_t mp = bf16x2_bits(r0, r1);
-          const float s0 = r0 - __uint_as_float(mp << 16), s1 = r1 - __uint_as_float(mp & 0xFFFF0000u);
-          hw[q] = hp;
-          mw[q] = mp;
-          lw[q] = bf16x2_bits(s0, s1);
+          if (!F16) {
+            // two columns at a time: one paired round-to-nearest conversion
+            // per slice; a bf16 value is the upper half of its float, so the
+            // residuals need only a mask or a shift and a subtraction
+            const uint32_t hp = bf16x2_bits(x0, x1);
+            const float r0 = x0 - __uint_as_float(hp << 16), r1 = x1 - __uint_as_float(hp & 0xFFFF0000u);
+            const uint32_t mp = bf16x2_bits(r0, r1);
+            const float s0 = r0 - __uint_as_float(mp << 16), s1 = r1 - __uint_as_float(mp & 0xFFFF0000u);
+            hw[q] = hp;
+            mw[q] = mp;
+            lw[q] = bf16x2_bits(s0, s1);
+          } else {  // fp16 hi and lo (the scaled X is below 2^14: no overflow)
+            const __half2 hp = __floats2half2_rn(x0, x1);
+            const float2 hf = __half22float2(hp);
+            const __half2 lp = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+            hw[q] = *reinterpret_cast<const uint32_t*>(&hp);
+            mw[q] = *reinterpret_cast<const uint32_t*>(&lp);
+          }
         }
-        const int off = (((row >> 3) * 8 + half * 4 + g) * 64 + (row & 7) * 8);
+        const int off = (((row >> 3) * 8 + half * 4 + g) * 64 + (row & 7) * 8);  // 2-byte elements
         *reinterpret_cast<uint4*>(a2 + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
         *reinterpret_cast<uint4*>(a2 + A2_SLICE / 2 + off) = make_uint4(mw[0], mw[1], mw[2], mw[3]);
-        *reinterpret_cast<uint4*>(a2 + A2_SLICE + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        if (!F16) *reinterpret_cast<uint4*>(a2 + A2_SLICE + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
       }
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       __syncwarp();
-      if (lane == 0) mbar_arrive(bar(B_A2FULL));
+      if (lane == 0) mbar_arrive(bar(B_A2FULL + (h2 - 1) % NA2));
     };
     // add the tile accumulator of the next flush group into the running sum
-    auto flush = [&](int tm, int tn) -> bool {
+    auto flush = [&](int tm, int tn, float fs) -> bool {
       if (!mbar_wait<PROF>(bar(B_SFULL + sb), (sph_full >> sb) & 1u, abort_flag, a.err, 8)) return false;
       sph_full ^= 1u << sb;
       asm volatile("tcgen05.fence::after_thread_sync;\n");
@@ -724,7 +766,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
 #pragma unroll
                     for (int e2 = 0; e2 < 2; ++e2) {
                       const int i = 2 * k + e2;
-                      const float y = (i < nc ? w[i] : 0.0f) - cc[e2];
+                      const float y = (i < nc ? (F16 ? w[i] * fs : w[i]) : 0.0f) - cc[e2];
                       const float t = ahi[c][i] + y;
                       cc[e2] = (t - ahi[c][i]) - y;
                       ahi[c][i] = t;
@@ -745,6 +787,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
     };
     long long s = 0;
     int pend = 0, pend_tm = 0, pend_tn = 0;  // flush groups deferred past the next conversion
+    float pend_fs = 1.0f;
     while (ok) {
       const int slot = (int)(s % NMETA);
       if (!mbar_wait<PROF>(bar(B_MFULL + slot), (uint32_t)((s / NMETA) & 1), abort_flag, a.err, 13)) { ok = false; break; }
@@ -768,6 +811,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
         // the term (and its scale) of this row of the stacked X
         const int q = row / (u.tm8 * 8), rr = row - q * (u.tm8 * 8);
         const float sc = (q < u.nterm && rr < u.tm) ? u.t[q].scale : 0.0f;
+        const float fs = F16 ? ldexpf(1.0f, e_psi - u.pad[0]) : 1.0f;
         for (int j = 0; j < n_chunks(u) && ok; ++j) {
           const uint32_t xb = xcnt & 1;
           if (!mbar_wait<PROF>(bar(B_XFULL + xb), (xph_full >> xb) & 1u, abort_flag, a.err, 6)) { ok = false; break; }
@@ -777,8 +821,13 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
           const bool whole = whole_chunk_group(u, j, a.max_chain);
           const bool wrows = quarter * 32 < u.nterm * u.tm8 * 8;  // warp-uniform: stacked rows here
           for (int h = 0; h < nh && ok; ++h) {
-            if (!mbar_wait<PROF>(bar(B_A2EMPTY), a2_empty_ph, abort_flag, a.err, 7)) { ok = false; break; }
-            a2_empty_ph ^= 1;
+            const uint32_t hb = h2 % NA2;
+            if (!mbar_wait<PROF>(bar(B_A2EMPTY + hb), ((h2 / NA2) & 1u) ^ 1u, abort_flag, a.err, 7)) {
+              ok = false;
+              break;
+            }
+            ++h2;
+            a2 = reinterpret_cast<uint16_t*>(sm + A2_OFF + hb * A2_BYTES);
             // this warp's 32 K-columns are read by the MMA only below 16 * ceil(kw / 16)
             const int kw = half_cols(u, j, h);
             const bool wvalid = wrows && half * 32 < 16 * ((kw + 15) >> 4);
@@ -797,14 +846,14 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
               write_a2(v);
             } else {  // no stacked rows here (A2 rows that feed only unread D rows) or K columns never read
               __syncwarp();
-              if (lane == 0) mbar_arrive(bar(B_A2FULL));
+              if (lane == 0) mbar_arrive(bar(B_A2FULL + hb));
             }
             // flush groups in the order the MMA issues them. The groups of a
             // half are flushed after the next half has been converted (off
             // the MMA's critical path), unless the half has more than two:
             // with two tile accumulators the MMA would then wait for them.
             while (ok && pend > 0) {
-              ok = flush(pend_tm, pend_tn);
+              ok = flush(pend_tm, pend_tn, pend_fs);
               --pend;
             }
             const int F = flush_terms(u, a.max_chain);
@@ -813,15 +862,16 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
               pend = ng;
               pend_tm = u.tm;
               pend_tn = u.tn;
+              pend_fs = fs;
             } else {
-              for (int g = 0; g < ng && ok; ++g) ok = flush(u.tm, u.tn);
+              for (int g = 0; g < ng && ok; ++g) ok = flush(u.tm, u.tn, fs);
             }
           }
           ++xcnt;
         }
         if (ok && (fl & TC_ITEM_LAST)) {  // the item's last groups, then its partial tile
           while (ok && pend > 0) {
-            ok = flush(pend_tm, pend_tn);
+            ok = flush(pend_tm, pend_tn, pend_fs);
             --pend;
           }
         }
@@ -916,26 +966,27 @@ void launch_split_psi(const double* psi, const PsiBlock* blocks, const TcPsiBloc
   split_psi_kernel<<<nblk, 256, 0, st>>>(psi, blocks, pb, nblk, (__nv_bfloat16*)out);
 }
 
+template <int NPROD, bool F16>
+static void launch_tc(const TcDev& a, int grid, cudaStream_t st) {
+  constexpr int SMEM = Lay<F16>::SMEM_BYTES;
+  set_max_dynamic_smem((const void*)sigma_tc_kernel<NPROD, F16, false>, SMEM);
+  set_max_dynamic_smem((const void*)sigma_tc_kernel<NPROD, F16, true>, SMEM);
+  if (a.wait_prof)
+    sigma_tc_kernel<NPROD, F16, true><<<grid, NTHR, SMEM, st>>>(a);
+  else
+    sigma_tc_kernel<NPROD, F16, false><<<grid, NTHR, SMEM, st>>>(a);
+}
+
 void launch_sigma_tc(const TcDev& a, int n_sm, cudaStream_t st) {
   if (a.n_items <= 0) return;
-  set_max_dynamic_smem((const void*)sigma_tc_kernel<6, false>, SMEM_BYTES);
-  set_max_dynamic_smem((const void*)sigma_tc_kernel<3, false>, SMEM_BYTES);
-  set_max_dynamic_smem((const void*)sigma_tc_kernel<6, true>, SMEM_BYTES);
-  set_max_dynamic_smem((const void*)sigma_tc_kernel<3, true>, SMEM_BYTES);
   int grid = n_sm < a.n_items ? n_sm : a.n_items;
   if (grid < 1) grid = 1;
-  const bool prof = a.wait_prof != nullptr;
-  if (a.nprod == 6) {
-    if (prof)
-      sigma_tc_kernel<6, true><<<grid, NTHR, SMEM_BYTES, st>>>(a);
-    else
-      sigma_tc_kernel<6, false><<<grid, NTHR, SMEM_BYTES, st>>>(a);
-  } else {
-    if (prof)
-      sigma_tc_kernel<3, true><<<grid, NTHR, SMEM_BYTES, st>>>(a);
-    else
-      sigma_tc_kernel<3, false><<<grid, NTHR, SMEM_BYTES, st>>>(a);
-  }
+  if (a.f16)
+    launch_tc<3, true>(a, grid, st);
+  else if (a.nprod == 6)
+    launch_tc<6, false>(a, grid, st);
+  else
+    launch_tc<3, false>(a, grid, st);
 }
 
 }  // namespace dmrg

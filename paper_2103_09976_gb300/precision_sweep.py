@@ -2,8 +2,8 @@
 
 K=108 (54|54 spatial orbitals), N=30, 2Sz=0, synthetic N(0,1) operator
 blocks (seed 1), psi ~ N(0,1) normalized: for each M, sigma in FP64 (after
-autotuning the FP64 work list) and with the BF16X3 / BF16X2 tensor-core
-products, each timed over graph replays with CUDA events on the library's
+autotuning the FP64 work list) and with the BF16X3 / BF16X2 / FP16X2
+tensor-core products, each timed over graph replays with CUDA events on the library's
 stream; errors of the mixed results against FP64: max-norm relative error of
 sigma and relative error of the Rayleigh quotient psi . sigma.
 
@@ -39,7 +39,8 @@ def one(M, steps=2, autotune=True):
         stream = torch.cuda.ExternalStream(capi.dmrg_stream(ctx))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ref = None
-        for name, prec in (("fp64", capi.DMRG_FP64), ("bf16x3", capi.DMRG_BF16X3), ("bf16x2", capi.DMRG_BF16X2)):
+        for name, prec in (("fp64", capi.DMRG_FP64), ("bf16x3", capi.DMRG_BF16X3), ("bf16x2", capi.DMRG_BF16X2),
+                           ("fp16x2", capi.DMRG_FP16X2)):
             capi.dmrg_set_precision(ctx, prec)
             t0 = time.perf_counter()
             if prec == capi.DMRG_FP64 and autotune:
@@ -54,7 +55,7 @@ def one(M, steps=2, autotune=True):
                     tuned = capi.dmrg_autotune(ctx, -1)
                     capi.dmrg_sigma(ctx, -1, x, y)
                     capi.dmrg_sync(ctx)
-            except capi.DMRGError as ex:   # e.g. the bf16 slices do not fit next to the FP64 store
+            except capi.DMRGError as ex:   # e.g. the split slices do not fit next to the FP64 store
                 out[name] = {"error": str(ex)}
                 continue
             prep = time.perf_counter() - t0
@@ -67,7 +68,8 @@ def one(M, steps=2, autotune=True):
             r = {"ms": s * 1e3, "tflops": info["flops"] / s / 1e12, "prep_s": prep}
             if tuned is not None:
                 nprod = 6 if prec == capi.DMRG_BF16X3 else 3
-                alg = 6.0 * info["op_elements"] + 16.0 * n   # operators once as 3 bf16 slices, psi, sigma
+                # operators once as 3 bf16 slices (2 fp16 slices for FP16X2), psi, sigma
+                alg = (4.0 if prec == capi.DMRG_FP16X2 else 6.0) * info["op_elements"] + 16.0 * n
                 r.update({"tc_items_per_sm": tuned[0], "hbm_gbs": alg / s / 1e9,
                           "tensor_tflops_issued": nprod * info["flops"] / s / 1e12})
             if ref is None:

@@ -242,6 +242,37 @@ int main(int argc, char** argv) {
   if (gi != plan.groups.size()) fail("extra groups");
   if (slot != plan.scratch_elems) fail("scratch size");
 
+  // (3b) split-block indices (the FP16X2 coefficients read the block
+  //      exponents through them): every record term and small term names the
+  //      split job whose tiles it reads (stored blocks, then the identities of
+  //      the left and of the right sectors)
+  {
+    std::vector<long long> job_tile;
+    for (const TcBlock& b : plan.opblocks) job_tile.push_back(b.tile);
+    for (const TcBlock& b : plan.identL) job_tile.push_back(b.tile);
+    for (const TcBlock& b : plan.identR) job_tile.push_back(b.tile);
+    const long long nj = (long long)job_tile.size();
+    auto names = [&](int j, long long tile) { return j >= 0 && j < nj && job_tile[j] == tile; };
+    if (plan.term_blk.size() != plan.recs.size() * TC_MAX_G * 2) fail("term_blk size");
+    else
+      for (size_t i = 0; i < plan.recs.size(); ++i) {
+        const TcUnitRec& r = plan.recs[i];
+        if (r.flags & TC_ZERO) continue;
+        for (int q = 0; q < r.nterm && q < TC_MAX_G; ++q)
+          if (!names(plan.term_blk[(i * TC_MAX_G + q) * 2], r.t[q].a_tile) ||
+              !names(plan.term_blk[(i * TC_MAX_G + q) * 2 + 1], r.t[q].b_tile))
+            fail("record term split-block index");
+      }
+    if (plan.small_blk.size() != 2 * plan.small.size()) fail("small_blk size");
+    else
+      for (size_t k = 0; k < plan.small.size(); ++k) {
+        const SmallTerm& x = plan.small[k];
+        if ((x.a_tile >= 0 && !names(plan.small_blk[2 * k], x.a_tile)) ||
+            (x.b_tile >= 0 && !names(plan.small_blk[2 * k + 1], x.b_tile)))
+          fail("small term split-block index");
+      }
+  }
+
   // (4) the two schedules together are a permutation of the items, each
   //     holding the items of its kind
   std::vector<int> sch = plan.schedule;
@@ -278,9 +309,12 @@ int main(int argc, char** argv) {
   }
 
   // (6) the kernel's copies, enumerated with its own formulas: every copy
-  //     lands inside its 128-position stage (stage 1: operator rows below
-  //     position 64, psi at 64..127) and reads inside the split arrays
-  {
+  //     lands inside its stage (stage 1: operator rows below position 16 KG1,
+  //     psi from there on) and reads inside the split arrays
+  // (ST tile positions per stage, KG1 K groups per stage-1 stage: 128 / 4 for
+  //     the bf16 kernels, 192 / 6 for FP16X2)
+  for (const auto& geo : {std::pair<int, int>{128, 4}, std::pair<int, int>{192, 6}}) {
+    const int ST = geo.first, KG1 = geo.second, PT = 16 * KG1;
     const long long op_tiles = plan.n_tiles, psi_tiles = plan.psi_tiles;
     auto src_ok = [&](long long src, int n, bool psi) {
       return src >= 0 && n > 0 && src + n <= (psi ? psi_tiles : op_tiles);
@@ -290,49 +324,49 @@ int main(int argc, char** argv) {
       const int G = r.nterm, tm8 = r.tm8;
       const int nchunk = (r.n + 127) / 128;
       for (int j = 0; j < nchunk; ++j) {
-        for (int k = 0; k < (r.pR8 + 3) / 4; ++k) {
-          const int kg0 = 4 * k;
+        for (int k = 0; k < (r.pR8 + KG1 - 1) / KG1; ++k) {
+          const int kg0 = KG1 * k;
           if (!(r.flags & TC_TA)) {
-            const int nk = std::min(4, (int)r.aC8 - kg0);
+            const int nk = std::min(KG1, (int)r.aC8 - kg0);
             if (nk > 0)
               for (int q = 0; q < G; ++q)
                 for (int rg = 0; rg < tm8; ++rg) {
-                  const int dst = (q * tm8 + rg) * 4;
-                  if (dst + nk > 64 || !src_ok(r.t[q].a_tile + (long long)(r.r0g + rg) * r.aC8 + kg0, nk, false))
+                  const int dst = (q * tm8 + rg) * KG1;
+                  if (dst + nk > PT || !src_ok(r.t[q].a_tile + (long long)(r.r0g + rg) * r.aC8 + kg0, nk, false))
                     fail("stage-1 operator copy out of bounds");
                 }
           } else {
             for (int q = 0; q < G; ++q)
-              for (int kg = 0; kg < 4 && kg0 + kg < r.aR8; ++kg) {
+              for (int kg = 0; kg < KG1 && kg0 + kg < r.aR8; ++kg) {
                 const int dst = kg * 16 + q * tm8;
-                if (q * tm8 + tm8 > 16 || dst + tm8 > 64 ||
+                if (q * tm8 + tm8 > 16 || dst + tm8 > PT ||
                     !src_ok(r.t[q].a_tile + (long long)(kg0 + kg) * r.aC8 + r.r0g, tm8, false))
                   fail("stage-1 transposed operator copy out of bounds");
               }
           }
           const int nn = std::min(16, (int)r.pC8 - 16 * j);
-          for (int kg = 0; kg < 4 && kg0 + kg < r.pR8; ++kg)
-            if (64 + kg * 16 + nn > 128 || !src_ok(r.p_tile + (long long)(kg0 + kg) * r.pC8 + 16 * j, nn, true))
+          for (int kg = 0; kg < KG1 && kg0 + kg < r.pR8; ++kg)
+            if (PT + kg * 16 + nn > ST || !src_ok(r.p_tile + (long long)(kg0 + kg) * r.pC8 + 16 * j, nn, true))
               fail("stage-1 psi copy out of bounds");
         }
         const int ncols = std::min(128, r.n - 128 * j);
         for (int h = 0; h < (ncols + 63) / 64; ++h) {
           const int kw = std::min(64, ncols - 64 * h), kg2 = 2 * ((kw + 15) / 16), kgx = 16 * j + 8 * h;
           const int te = 2 * ((r.tn + 15) / 16), tn8 = (r.tn + 7) / 8;
-          const int P = std::max(1, std::min(G, 128 / (te * kg2)));
+          const int P = std::max(1, std::min(G, ST / (te * kg2)));
           for (int q0 = 0; q0 < G; q0 += P)
             for (int q = q0; q < std::min(G, q0 + P); ++q) {
               const int reg = (q - q0) * te * kg2;
-              if (reg + te * kg2 > 128) fail("stage-2 region beyond the stage");
+              if (reg + te * kg2 > ST) fail("stage-2 region beyond the stage");
               if (!(r.flags & TC_TB)) {
                 const int nk = std::min(kg2, (int)r.bC8 - kgx);
                 for (int ng = 0; ng < tn8; ++ng)
-                  if (reg + ng * kg2 + nk > 128 ||
+                  if (reg + ng * kg2 + nk > ST ||
                       !src_ok(r.t[q].b_tile + (long long)(r.c0g + ng) * r.bC8 + kgx, nk, false))
                     fail("stage-2 operator copy out of bounds");
               } else {
                 for (int kg = 0; kg < kg2 && kgx + kg < r.bR8; ++kg)
-                  if (reg + kg * te + tn8 > 128 ||
+                  if (reg + kg * te + tn8 > ST ||
                       !src_ok(r.t[q].b_tile + (long long)(kgx + kg) * r.bC8 + r.c0g, tn8, false))
                     fail("stage-2 transposed operator copy out of bounds");
               }

@@ -24,7 +24,7 @@ def _exact(left, right, nL, n, Q, seed):
     return w, V
 
 
-@pytest.mark.parametrize("prec,bar", [(0, 1e-9), (2, 1e-5)])
+@pytest.mark.parametrize("prec,bar", [(0, 1e-9), (2, 1e-5), (3, 1e-5)])
 def test_davidson_lowest_eigenvalue(prec, bar):
     from paper_2103_09976_gb300 import capi
     from synth import gaussian_sector_dims, mirrored_sectors, random_unit_vector

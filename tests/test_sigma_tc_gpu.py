@@ -13,8 +13,10 @@ after at most 8 main steps and added into a compensated running sum (about
 1e-6). Measured: 0.9e-6 at blocks up to 107, 2.5e-6 at blocks up to 355:
 bar 5e-6 of max|sigma|. BF16X2 keeps 16 bits per operand (2^-17
 representation error, dropped slice products ~2^-16): measured 6.6e-6, bar
-2e-5. Small classes (all blocks at most 32 wide) run as FP32 products of at
-most 32 terms: about 1e-7.
+2e-5. FP16X2 keeps 22 bits per operand (two fp16 slices of operands scaled
+by powers of two, dropped lo x lo products ~2^-22) with the same bounded FP32
+accumulation as BF16X3: bar 5e-6. Small classes (all blocks at most 32 wide)
+run as FP32 products of at most 32 terms: about 1e-7.
 """
 
 import numpy as np
@@ -22,7 +24,7 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
-TOL = {1: 2e-5, 2: 5e-6}
+TOL = {1: 2e-5, 2: 5e-6, 3: 5e-6}
 
 
 @pytest.fixture(scope="module")
@@ -39,7 +41,7 @@ def _oracle_full(left, right, nL, n, Q, seed, x):
     return sigma_blocks(x, lay, nc_terms(nL, n), oL, oR)
 
 
-@pytest.mark.parametrize("prec", [2, 1])
+@pytest.mark.parametrize("prec", [2, 1, 3])
 @pytest.mark.parametrize("M,nsp,ntot,seed", [
     (24, 3, 6, 1),        # tiny blocks: every class on the CUDA cores
     (120, 4, 8, 2),
@@ -69,8 +71,9 @@ def test_sigma_tc_matches_oracle(capi, prec, M, nsp, ntot, seed):
 
 
 def test_sigma_tc_middle_bond_m2000_vs_fp64(capi):
-    """K=108 (54|54), N=30, M=2000: BF16X3 and BF16X2 against the FP64 GPU
-    path on the same context, plus the Rayleigh-quotient difference."""
+    """K=108 (54|54), N=30, M=2000: BF16X3, BF16X2 and FP16X2 against the
+    FP64 GPU path on the same context, plus the Rayleigh-quotient
+    difference."""
     from synth import gaussian_sector_dims, mirrored_sectors, random_unit_vector
     left = gaussian_sector_dims(2000)
     right = mirrored_sectors(left)
@@ -82,7 +85,7 @@ def test_sigma_tc_middle_bond_m2000_vs_fp64(capi):
         y64 = np.zeros_like(x)
         capi.dmrg_sigma(ctx, -1, x, y64)
         out = {}
-        for prec in (2, 1):
+        for prec in (2, 1, 3):
             capi.dmrg_set_precision(ctx, prec)
             y = np.zeros_like(x)
             capi.dmrg_sigma(ctx, -1, x, y)
@@ -94,3 +97,39 @@ def test_sigma_tc_middle_bond_m2000_vs_fp64(capi):
         assert err <= TOL[prec], (prec, err)
         rq = abs(x @ y - x @ y64) / abs(x @ y64)
         assert rq <= TOL[prec], (prec, rq)
+
+
+@pytest.mark.parametrize("factor", [1e-30, 1.0, 3e25])
+def test_fp16x2_psi_scale_is_exact(capi, factor):
+    """FP16X2 scales psi by a power of two from its largest element before the
+    fp16 split: sigma(a psi) = a sigma(psi) to the FP16X2 bar for psi far
+    outside the fp16 range, an all-zero psi gives exactly zero, and switching
+    between the fp16 and the bf16 split on one context keeps both results."""
+    from synth import gaussian_sector_dims, mirrored_sectors, random_unit_vector
+    left = gaussian_sector_dims(1200, n_spatial=3, n_tot=6)
+    right = mirrored_sectors(left, n_tot=6)
+    ctx = capi.dmrg_create(device=0)
+    try:
+        capi.dmrg_load_synthetic(ctx, 6, 12, 6, 0, left, right, 3)
+        size = capi.dmrg_psi_layout(ctx)["size"]
+        x = random_unit_vector(size, 13)
+        y64 = np.zeros_like(x)
+        capi.dmrg_sigma(ctx, -1, x, y64)
+        capi.dmrg_set_precision(ctx, 3)
+        y = np.zeros_like(x)
+        capi.dmrg_sigma(ctx, -1, x * factor, y)
+        z = np.ones_like(x)
+        capi.dmrg_sigma(ctx, -1, np.zeros_like(x), z)
+        capi.dmrg_set_precision(ctx, 2)
+        yb = np.zeros_like(x)
+        capi.dmrg_sigma(ctx, -1, x, yb)
+        capi.dmrg_set_precision(ctx, 3)
+        y2 = np.zeros_like(x)
+        capi.dmrg_sigma(ctx, -1, x * factor, y2)
+    finally:
+        capi.dmrg_destroy(ctx)
+    assert np.all(np.isfinite(y))
+    assert np.abs(y / factor - y64).max() <= TOL[3] * np.abs(y64).max()
+    assert np.abs(yb - y64).max() <= TOL[2] * np.abs(y64).max()
+    assert np.array_equal(y, y2)
+    assert not z.any()

@@ -6,7 +6,9 @@ sigma's own relative error: the bar is 1e-6 Ha. The Davidson tolerance on
 |r|^2 follows what each sigma can resolve: BF16X3 keeps 24 significant bits
 (relative error ~6e-8, |r|^2 floor far below 1e-10), BF16X2 16 bits
 (~1.5e-5, so |r|^2 of a vector of norm 1 with |H psi| ~ 10 cannot go much
-below ~1e-8); 1e-10 and 1e-8 respectively."""
+below ~1e-8), FP16X2 22 bits (~2.4e-7, |r|^2 floor ~1e-11); 1e-10, 1e-8 and
+1e-10 respectively. FP16X2 also meets the renormalized operators of real
+sweeps, whose blocks span many orders of magnitude (per-block scales)."""
 
 import json
 import os
@@ -19,7 +21,7 @@ pytestmark = pytest.mark.gpu
 GOLD = os.path.join(os.path.dirname(__file__), "golden", "fci_energies.json")
 
 
-@pytest.mark.parametrize("prec,tol", [("BF16X3", 1e-10), ("BF16X2", 1e-8)])
+@pytest.mark.parametrize("prec,tol", [("BF16X3", 1e-10), ("BF16X2", 1e-8), ("FP16X2", 1e-10)])
 def test_config1_mixed_sweeps_within_1e6_of_fci(prec, tol):
     from paper_2103_09976_gb300 import capi
     from synth import random_integrals
