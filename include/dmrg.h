@@ -56,7 +56,7 @@ typedef enum {
  * i + j <= 2 on the tensor cores (tcgen05, FP32 accumulation, correction
  * products before the main ones); every FP32 accumulation of a sigma tile
  * spans at most dmrg_opts.tc_chain main MMA steps of 16 along K before it is
- * added into a compensated FP32 running sum (about 33 bits). BF16X2: the
+ * added into an FP32 running sum of the item. BF16X2: the
  * first two slices and the 3 products with i + j <= 1 (16 significant bits).
  * FP16X2: two fp16 slices x = hi + lo (22 significant bits) of operands
  * scaled by powers of two (each operator block and psi so that its largest

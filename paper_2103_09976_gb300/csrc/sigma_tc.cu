@@ -18,12 +18,14 @@
 //
 // Accuracy: within a chain the correction products are issued before the
 // main (hi x hi) ones, while the accumulator is still small. The FP32 tile
-// accumulator is added into a per-thread compensated (Kahan) FP32 running sum
-// (about 33 bits) after every flush group: the terms of one half whose main MMA steps fit the
-// launch's chain limit (at least one term), or both halves of a chunk of a
-// one-term unit when they fit together. The sum is written to the item's
-// FP64 partial tile at the end of the item. This bounds the length of every
-// FP32 accumulation chain of stage 2.
+// accumulator is added into a per-thread FP32 running sum after every flush
+// group: the terms of one half whose main MMA steps fit the launch's chain
+// limit (at least one term), or both halves of a chunk of a one-term unit
+// when they fit together. The sum is written to the item's FP64 partial tile
+// at the end of the item. This bounds the length of every FP32 accumulation
+// chain of stage 2 in the tensor memory; the running sum adds one rounding
+// per flush group. (A compensated running sum cost about a fifth of the
+// kernel's time for a few percent of its error.)
 //
 // Warp roles (320 threads): warp 0 streams operator and psi tiles with
 // cp.async.bulk into a 3-stage ring; warp 1 issues the MMAs (one lane of a
@@ -692,20 +694,12 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
     uint16_t* a2 = reinterpret_cast<uint16_t*>(sm + A2_OFF);  // the A2 buffer of the current half
     // FP16X2: the flush undoes the unit's tile scale 2^(E - e_psi)
     const int e_psi = F16 ? psi_exponent(*a.psi_exp) : 0;
-    // running sum of this thread's 64 tile columns: compensated (Kahan) FP32
-    // sums s and their compensation c, the sum being s - c. c is the rounding
-    // error of the last addition (below half an ulp of s) and is kept in bf16,
-    // two per register: its own 8 bits leave a residual of about 2^-9 ulp(s)
-    // per addition, so the running sum holds about 33 bits.
+    // FP32 running sum of this thread's 64 tile columns
     float ahi[2][32];
-    uint32_t alc[2][16];
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
+    for (int c = 0; c < 2; ++c)
 #pragma unroll
       for (int i = 0; i < 32; ++i) ahi[c][i] = 0.f;
-#pragma unroll
-      for (int i = 0; i < 16; ++i) alc[c][i] = 0u;
-    }
     // write 32 K-columns (half of a 64-column X half) of A2 for this row
     auto write_a2 = [&](const float* v) {
 #pragma unroll
@@ -761,18 +755,8 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
               for (int g8 = 0; g8 < 4; ++g8) {
                 if (g8 * 8 < nc) {  // warp-uniform: skip column groups past the tile
 #pragma unroll
-                  for (int k = 4 * g8; k < 4 * g8 + 4; ++k) {  // Kahan: s + (w - c), the new error in c
-                    float cc[2] = {__uint_as_float(alc[c][k] << 16), __uint_as_float(alc[c][k] & 0xFFFF0000u)};
-#pragma unroll
-                    for (int e2 = 0; e2 < 2; ++e2) {
-                      const int i = 2 * k + e2;
-                      const float y = (i < nc ? (F16 ? w[i] * fs : w[i]) : 0.0f) - cc[e2];
-                      const float t = ahi[c][i] + y;
-                      cc[e2] = (t - ahi[c][i]) - y;
-                      ahi[c][i] = t;
-                    }
-                    alc[c][k] = bf16x2_bits(cc[0], cc[1]);
-                  }
+                  for (int i = 8 * g8; i < 8 * g8 + 8; ++i)
+                    if (i < nc) ahi[c][i] = F16 ? fmaf(w[i], fs, ahi[c][i]) : ahi[c][i] + w[i];
                 }
               }
             }
@@ -801,12 +785,9 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
       } else {
         if (fl & TC_ITEM_FIRST) {
 #pragma unroll
-          for (int c = 0; c < 2; ++c) {
+          for (int c = 0; c < 2; ++c)
 #pragma unroll
             for (int i = 0; i < 32; ++i) ahi[c][i] = 0.f;
-#pragma unroll
-            for (int i = 0; i < 16; ++i) alc[c][i] = 0u;
-          }
         }
         // the term (and its scale) of this row of the stacked X
         const int q = row / (u.tm8 * 8), rr = row - q * (u.tm8 * 8);
@@ -850,40 +831,36 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
             }
             // flush groups in the order the MMA issues them. The groups of a
             // half are flushed after the next half has been converted (off
-            // the MMA's critical path), unless the half has more than two:
-            // with two tile accumulators the MMA would then wait for them.
-            while (ok && pend > 0) {
-              ok = flush(pend_tm, pend_tn, pend_fs);
-              --pend;
-            }
+            // the MMA's critical path), unless the half has more than two
+            // (with two tile accumulators the MMA would then wait for them)
+            // or ends its item. One call site keeps the (unrolled) flush code
+            // once in the kernel.
             const int F = flush_terms(u, a.max_chain);
             const int ng = whole ? (h == nh - 1 ? 1 : 0) : (u.nterm + F - 1) / F;
-            if (ng <= 2) {
-              pend = ng;
-              pend_tm = u.tm;
-              pend_tn = u.tn;
-              pend_fs = fs;
-            } else {
-              for (int g = 0; g < ng && ok; ++g) ok = flush(u.tm, u.tn, fs);
+            const bool item_end = (fl & TC_ITEM_LAST) && j == n_chunks(u) - 1 && h == nh - 1;
+            const bool defer = ng <= 2 && !item_end;
+            const int nf = pend + (defer ? 0 : ng);
+            for (int g = 0; g < nf && ok; ++g) {
+              const bool old = g < pend;
+              ok = flush(old ? pend_tm : u.tm, old ? pend_tn : u.tn, old ? pend_fs : fs);
             }
+            pend = defer ? ng : 0;
+            pend_tm = u.tm;
+            pend_tn = u.tn;
+            pend_fs = fs;
           }
           ++xcnt;
         }
-        if (ok && (fl & TC_ITEM_LAST)) {  // the item's last groups, then its partial tile
-          while (ok && pend > 0) {
-            ok = flush(pend_tm, pend_tn, pend_fs);
-            --pend;
-          }
-        }
-        if (ok && (fl & TC_ITEM_LAST) && row < u.tm) {
+        if (ok && (fl & TC_ITEM_LAST) && row < u.tm) {  // the item's partial tile
+          // fields copied out first: stores through `out` could alias the
+          // record as far as the compiler knows
+          const int tn = u.tn, nvalid = tn - half * 64;
+          double* const orow = out + (long long)row * tn + half * 64;
 #pragma unroll
           for (int c = 0; c < 2; ++c)
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              const int col = half * 64 + c * 32 + i;
-              const float cc = __uint_as_float((i & 1) ? (alc[c][i >> 1] & 0xFFFF0000u) : (alc[c][i >> 1] << 16));
-              if (col < u.tn) out[(long long)row * u.tn + col] = (double)ahi[c][i] - (double)cc;
-            }
+            for (int i = 0; i < 32; ++i)
+              if (c * 32 + i < nvalid) orow[c * 32 + i] = (double)ahi[c][i];
         }
       }
       __syncwarp();

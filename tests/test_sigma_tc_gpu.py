@@ -9,9 +9,9 @@ number of main (hi x hi) MMAs in one accumulation: each such step can lose
 up to about 2^-23 of the running value. The intermediate X = L psi is one
 chain of m/16 main steps (m the psi block rows: up to 23 steps for the
 355-row blocks below, about 2.7e-6); the sigma tile accumulation is cut
-after at most 8 main steps and added into a compensated running sum (about
-1e-6). Measured: 0.9e-6 at blocks up to 107, 2.5e-6 at blocks up to 355:
-bar 5e-6 of max|sigma|. BF16X2 keeps 16 bits per operand (2^-17
+after at most 8 main steps and added into an FP32 running sum of the item
+(one more rounding per flush group, about 1e-6). Measured: about 1e-6 at
+blocks up to 107, 2.5e-6 at blocks up to 355: bar 5e-6 of max|sigma|. BF16X2 keeps 16 bits per operand (2^-17
 representation error, dropped slice products ~2^-16): measured 6.6e-6, bar
 2e-5. FP16X2 keeps 22 bits per operand (two fp16 slices of operands scaled
 by powers of two, dropped lo x lo products ~2^-22) with the same bounded FP32
