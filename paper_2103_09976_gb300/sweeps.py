@@ -53,7 +53,7 @@ def main():
     ap.add_argument("--K", type=int, default=24)
     ap.add_argument("--M", default="80,80", help="bond dimension per sweep (forward, backward, ...)")
     ap.add_argument("--cut", type=int, nargs="+", default=[-1], help="mixed NC/CN cut(s); -1 = NC everywhere")
-    ap.add_argument("--prec", default="BF16X3", choices=["FP64", "BF16X3", "BF16X2"])
+    ap.add_argument("--prec", default="BF16X3", choices=["FP64", "BF16X3", "BF16X2", "FP16X2"])
     ap.add_argument("--N", type=int, default=None)
     ap.add_argument("--two-sz", type=int, default=None)
     ap.add_argument("--seed", type=int, default=2)
