@@ -312,9 +312,13 @@ int main(int argc, char** argv) {
   //     lands inside its stage (stage 1: operator rows below position 16 KG1,
   //     psi from there on) and reads inside the split arrays
   // (ST tile positions per stage, KG1 K groups per stage-1 stage: 128 / 4 for
-  //     the bf16 kernels, 192 / 6 for FP16X2)
+  //     the bf16 kernels, 192 / 6 for FP16X2). The tile positions copied per
+  //     sigma (operators and psi) give the bytes each kernel requests from
+  //     L2 / HBM (384 B per position for bf16, 256 for fp16).
+  long long copy_tiles[2] = {0, 0};
   for (const auto& geo : {std::pair<int, int>{128, 4}, std::pair<int, int>{192, 6}}) {
     const int ST = geo.first, KG1 = geo.second, PT = 16 * KG1;
+    long long& ctiles = copy_tiles[ST == 128 ? 0 : 1];
     const long long op_tiles = plan.n_tiles, psi_tiles = plan.psi_tiles;
     auto src_ok = [&](long long src, int n, bool psi) {
       return src >= 0 && n > 0 && src + n <= (psi ? psi_tiles : op_tiles);
@@ -332,6 +336,7 @@ int main(int argc, char** argv) {
               for (int q = 0; q < G; ++q)
                 for (int rg = 0; rg < tm8; ++rg) {
                   const int dst = (q * tm8 + rg) * KG1;
+                  ctiles += nk;
                   if (dst + nk > PT || !src_ok(r.t[q].a_tile + (long long)(r.r0g + rg) * r.aC8 + kg0, nk, false))
                     fail("stage-1 operator copy out of bounds");
                 }
@@ -339,6 +344,7 @@ int main(int argc, char** argv) {
             for (int q = 0; q < G; ++q)
               for (int kg = 0; kg < KG1 && kg0 + kg < r.aR8; ++kg) {
                 const int dst = kg * 16 + q * tm8;
+                ctiles += tm8;
                 if (q * tm8 + tm8 > 16 || dst + tm8 > PT ||
                     !src_ok(r.t[q].a_tile + (long long)(kg0 + kg) * r.aC8 + r.r0g, tm8, false))
                   fail("stage-1 transposed operator copy out of bounds");
@@ -346,7 +352,7 @@ int main(int argc, char** argv) {
           }
           const int nn = std::min(16, (int)r.pC8 - 16 * j);
           for (int kg = 0; kg < KG1 && kg0 + kg < r.pR8; ++kg)
-            if (PT + kg * 16 + nn > ST || !src_ok(r.p_tile + (long long)(kg0 + kg) * r.pC8 + 16 * j, nn, true))
+            if ((ctiles += nn), PT + kg * 16 + nn > ST || !src_ok(r.p_tile + (long long)(kg0 + kg) * r.pC8 + 16 * j, nn, true))
               fail("stage-1 psi copy out of bounds");
         }
         const int ncols = std::min(128, r.n - 128 * j);
@@ -361,12 +367,12 @@ int main(int argc, char** argv) {
               if (!(r.flags & TC_TB)) {
                 const int nk = std::min(kg2, (int)r.bC8 - kgx);
                 for (int ng = 0; ng < tn8; ++ng)
-                  if (reg + ng * kg2 + nk > ST ||
+                  if ((ctiles += std::max(nk, 0)), reg + ng * kg2 + nk > ST ||
                       !src_ok(r.t[q].b_tile + (long long)(r.c0g + ng) * r.bC8 + kgx, nk, false))
                     fail("stage-2 operator copy out of bounds");
               } else {
                 for (int kg = 0; kg < kg2 && kgx + kg < r.bR8; ++kg)
-                  if (reg + kg * te + tn8 > ST ||
+                  if ((ctiles += tn8), reg + kg * te + tn8 > ST ||
                       !src_ok(r.t[q].b_tile + (long long)(kgx + kg) * r.bC8 + r.c0g, tn8, false))
                     fail("stage-2 transposed operator copy out of bounds");
               }
@@ -376,11 +382,45 @@ int main(int argc, char** argv) {
     }
   }
 
+  // bytes the FP64 kernel requests per sigma: for every (item, task) the
+  // output tile's rows of the left block, the psi block and the tile's
+  // columns of the right block (identities are not read)
+  double f64_req = 0.0;
+  for (const Item& it : wl.items)
+    for (int t = it.t_begin; t < it.t_end; ++t) {
+      const Task& k = wl.tasks[t];
+      const PsiBlock& ib = blocks[k.in_blk];
+      f64_req += 8.0 * ((k.aoff >= 0 ? (double)it.nrows * ib.mL : 0.0) + (double)ib.mL * ib.mR +
+                        (k.boff >= 0 ? (double)it.ncols * ib.mR : 0.0));
+    }
+  // tile positions the small-class kernels read per sigma: each term's left
+  // and right blocks, and its psi block once per warp and run of terms of
+  // one psi block (warps take every 8th (<= 16 class) or 4th term)
+  long long small_tiles = 0;
+  for (const TcItem& it : plan.items) {
+    if (it.kind != 1 && it.kind != 2) continue;
+    const int nw = it.kind == 2 ? 8 : 4;
+    for (int w = 0; w < nw; ++w) {
+      int cur = -1;
+      for (int k = it.r_begin + w; k < it.r_end; k += nw) {
+        const SmallTerm& x = plan.small[k];
+        const TcPsiBlock& pb = plan.psi[x.in_blk];
+        const int m = pb.m, n = pb.n, tm = it.nrows, tn = it.ncols;
+        if (x.in_blk != cur) small_tiles += (long long)pb.R8 * pb.C8;
+        cur = x.in_blk;
+        if (x.a_tile >= 0) small_tiles += (long long)((tm + 7) / 8) * ((m + 7) / 8);
+        if (x.b_tile >= 0) small_tiles += (long long)((tn + 7) / 8) * ((n + 7) / 8);
+      }
+    }
+  }
   std::printf("{\"psi_size\": %lld, \"blocks\": %zu, \"terms\": %zu, \"tasks\": %zu, \"flops\": %.17g, "
               "\"plan_tasks\": %lld, \"units\": %lld, \"items\": %zu, \"mma_s1\": %lld, \"mma_s2\": %lld, "
-              "\"stages\": %lld, \"layout\": [",
+              "\"stages\": %lld, \"op_elements\": %lld, \"f64_request_bytes\": %.17g, "
+              "\"tc_copy_bytes_bf16\": %lld, \"tc_copy_bytes_fp16\": %lld, \"small_read_bytes_bf16\": %lld, "
+              "\"small_read_bytes_fp16\": %lld, \"layout\": [",
               size, blocks.size(), terms.size(), wl.tasks.size(), wl.flops, plan.n_terms, plan.n_units,
-              plan.items.size(), mma_s1, mma_s2, stages);
+              plan.items.size(), mma_s1, mma_s2, stages, (long long)(oL.elements + oR.elements), f64_req,
+              copy_tiles[0] * 384, copy_tiles[1] * 256, small_tiles * 384, small_tiles * 256);
   for (size_t b = 0; b < blocks.size(); ++b) {
     const PsiBlock& pb = blocks[b];
     std::printf("%s[%d, %d, %d, %d, %d, %d, %lld]", b ? ", " : "", L.q[pb.qL].n, L.q[pb.qL].s, R.q[pb.qR].n,
