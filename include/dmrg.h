@@ -238,15 +238,17 @@ dmrg_status dmrg_sigma_noalloc(dmrg_ctx* ctx, int site, const double* psi, doubl
  * per SM {8, 16, 32} and per-task latency cost {4096, 16384, 65536} (the
  * item split and largest-first order of the persistent kernel's work items,
  * Sec. II.D-E collapsed into one list) on a seeded psi, keeps the fastest
- * and reports it. Mixed precision (BF16X3 / BF16X2): times the tensor-core
- * path for {2, 4, 8, 16} items per SM (how each output tile's units of
- * stacked terms are split into work items) and reports the choice in
- * items_per_sm, with *per_task_cost = 0. Any output may be NULL; best_ms =
- * the chosen setting's time. Results stay bitwise deterministic for the
+ * and reports it. Mixed precision (BF16X3 / BF16X2 / FP16X2): times the
+ * tensor-core path for {4, 8, 16, 32} items per SM x {1, 4, 16} x 2^20
+ * multiply-adds of fixed cost per unit of stacked terms (how each output
+ * tile's units are split into work items and ordered, largest first) and
+ * reports the choice in items_per_sm and per_task_cost. Any output may be
+ * NULL; best_ms = the chosen setting's time. Results stay bitwise deterministic for the
  * chosen setting; they can differ in the last bits from another setting
  * because items sum their terms in another grouping. A tuned FP64 work list
  * may need more scratch than dmrg_sigma_noalloc holds. Defaults without
- * tuning: FP64 8 items per SM and cost 16384; tensor cores 4 items per SM.
+ * tuning: FP64 8 items per SM and cost 16384; tensor cores 4 items per SM
+ * and unit cost 2^20.
  */
 dmrg_status dmrg_autotune(dmrg_ctx* ctx, int site, int* items_per_sm, double* per_task_cost, double* best_ms);
 

@@ -122,7 +122,7 @@ static_assert(sizeof(TcItem) == sizeof(Item), "reduction reads TcItem as Item");
 // operator store is unchanged by it).
 static void prepare_tc_plan(Context& c, Problem& p) {
   cudaStream_t st = c.stream;
-  build_tc_plan(p.blocks, p.L, p.R, p.wl, p.tc, TcShape{c.n_sm * p.tc_items_per_sm});
+  build_tc_plan(p.blocks, p.L, p.R, p.wl, p.tc, TcShape{c.n_sm * p.tc_items_per_sm, p.tc_unit_cost});
   p.d_tc_recs.upload(p.tc.recs, st);
   p.d_tc_items.upload(p.tc.items, st);
   p.d_tc_small.upload(p.tc.small, st);
@@ -162,7 +162,13 @@ static std::vector<SplitJob> split_jobs(const Problem& p) {
   return jobs;
 }
 
-static void check_split_fits(size_t bytes, const char* what) {
+static void check_split_fits(Context& c, size_t bytes, const char* what) {
+  // buffers freed on the stream (a split just dropped) stay in the device's
+  // memory pool until trimmed; return them before asking what is free
+  DMRG_CUDA(cudaStreamSynchronize(c.stream));
+  cudaMemPool_t pool = nullptr;
+  if (cudaDeviceGetDefaultMemPool(&pool, c.device) == cudaSuccess && pool) DMRG_CUDA(cudaMemPoolTrimTo(pool, 0));
+  cudaGetLastError();
   size_t freeb = 0, totb = 0;
   DMRG_CUDA(cudaMemGetInfo(&freeb, &totb));
   if ((double)bytes > 0.92 * (double)freeb)
@@ -182,7 +188,7 @@ static void ensure_split_bf16(Context& c, Problem& p) {
     p.f16_gen = -1;
   }
   const size_t split_bytes = (size_t)p.tc.n_tiles * 384;
-  check_split_fits(split_bytes, "bf16 split operator store");
+  check_split_fits(c, split_bytes, "bf16 split operator store");
   p.split.alloc(split_bytes);
   DMRG_CUDA(cudaMemsetAsync(p.split.p, 0, split_bytes, st));
   p.psi_split.alloc((size_t)p.tc.psi_tiles * 384);
@@ -208,7 +214,7 @@ static void ensure_split_f16(Context& c, Problem& p) {
       p.bf16_split_ready = false;
     }
     const size_t split_bytes = (size_t)p.tc.n_tiles * 256;
-    check_split_fits(split_bytes, "fp16 split operator store");
+    check_split_fits(c, split_bytes, "fp16 split operator store");
     p.split16.alloc(split_bytes);
     DMRG_CUDA(cudaMemsetAsync(p.split16.p, 0, split_bytes, st));
     p.psi_split16.alloc((size_t)p.tc.psi_tiles * 256);
@@ -827,26 +833,33 @@ dmrg_status dmrg_autotune(dmrg_ctx* ctx, int site, int* items_per_sm, double* pe
       // tensor-core path: items per SM of the persistent kernel (the split
       // of each output tile's units into items, largest first)
       if (!tc_ready_for(p, c.opts.sigma_prec)) prepare_tc(c, p);
-      const int cand[4] = {2, 4, 8, 16};
+      // items per SM x fixed unit cost (in multiply-adds: 1 / 4 / 16 MMAs of
+      // 128 x 128 x 64) of the item split
+      const int cand[4] = {4, 8, 16, 32};
+      const double ucand[3] = {128.0 * 128 * 64, 4 * 128.0 * 128 * 64, 16 * 128.0 * 128 * 64};
       double best = 1e300;
       int bi = p.tc_items_per_sm;
+      double bu = p.tc_unit_cost;
       try {
-        for (int wi : cand) {
-          p.tc_items_per_sm = wi;
-          prepare_tc_plan(c, p);
-          prepare_tc(c, p);  // FP16X2: records of the new plan
-          run_sigma_tc_direct(c, p, c.d_psi.as<double>(), c.d_sigma.as<double>());  // warm-up
-          DMRG_CUDA(cudaEventRecord(e0, c.stream));
-          run_sigma_tc_direct(c, p, c.d_psi.as<double>(), c.d_sigma.as<double>());
-          DMRG_CUDA(cudaEventRecord(e1, c.stream));
-          DMRG_CUDA(cudaEventSynchronize(e1));
-          float ms = 0.f;
-          DMRG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-          if (ms < best) {
-            best = ms;
-            bi = wi;
+        for (double uc : ucand)
+          for (int wi : cand) {
+            p.tc_items_per_sm = wi;
+            p.tc_unit_cost = uc;
+            prepare_tc_plan(c, p);
+            prepare_tc(c, p);  // FP16X2: records of the new plan
+            run_sigma_tc_direct(c, p, c.d_psi.as<double>(), c.d_sigma.as<double>());  // warm-up
+            DMRG_CUDA(cudaEventRecord(e0, c.stream));
+            run_sigma_tc_direct(c, p, c.d_psi.as<double>(), c.d_sigma.as<double>());
+            DMRG_CUDA(cudaEventRecord(e1, c.stream));
+            DMRG_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            DMRG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+              best = ms;
+              bi = wi;
+              bu = uc;
+            }
           }
-        }
       } catch (...) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
@@ -855,11 +868,12 @@ dmrg_status dmrg_autotune(dmrg_ctx* ctx, int site, int* items_per_sm, double* pe
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       p.tc_items_per_sm = bi;
+      p.tc_unit_cost = bu;
       prepare_tc_plan(c, p);
       prepare_tc(c, p);
       check_device_error(c, p);
       if (items_per_sm) *items_per_sm = bi;
-      if (per_task_cost) *per_task_cost = 0.0;
+      if (per_task_cost) *per_task_cost = bu;
       if (best_ms) *best_ms = best;
       return;
     }

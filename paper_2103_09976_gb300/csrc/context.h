@@ -164,6 +164,7 @@ struct Problem {
   double per_task_cost = 16384.0;
   // tensor-core plan tuning (dmrg_autotune at a mixed precision): items per SM
   int tc_items_per_sm = 4;
+  double tc_unit_cost = 128.0 * 128 * 64;  // fixed cost of a unit of stacked terms in the item split
   // sub-Hamiltonian parts: (n_ranks, rank) -> work list of that rank's terms
   std::map<std::pair<int, int>, std::unique_ptr<DevWork>> parts;
 };

@@ -550,7 +550,7 @@ void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const Op
     for (int c = 0; c < n; c += 64) s2 += 128.0 * up16(tn) * up16(std::min(64, n - c));
     return s1 + G * s2;
   };
-  const double unit_overhead = 128.0 * 128 * 64;  // fixed cost of a unit in the item split
+  const double unit_overhead = shape.unit_cost;  // fixed cost of a unit in the item split
   double total = 0;
   for (size_t b = 0; b < nblk; ++b) {
     const PsiBlock& ob = blocks[b];

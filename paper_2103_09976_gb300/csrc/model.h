@@ -352,6 +352,7 @@ struct TcPlan {
 
 struct TcShape {
   int want_items;           // items to split the work into (a multiple of the SM count)
+  double unit_cost = 128.0 * 128 * 64;  // fixed cost of a unit in the item split, in multiply-adds
 };
 void build_tc_plan(const std::vector<PsiBlock>& blocks, const OpSet& L, const OpSet& R,
                    const WorkList& wl, TcPlan& plan, const TcShape& shape);

@@ -616,12 +616,13 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
           const int kw = min(64, ccols - 64 * h), kg2 = kg2_of(kw), P = max(1, min(G, STAGE_TILES / (te * kg2)));
           const uint32_t b_lbo = tB ? (uint32_t)te * TILE : TILE;
           const uint32_t b_sbo = tB ? TILE : (uint32_t)kg2 * TILE;
+          int qf = 0;  // position of term q in its flush group (q % F)
           for (int q0 = 0; q0 < G && ok; q0 += P) {
             const uint32_t sst = acquire();
             if (!ok) return;
-            for (int q = q0; q < min(G, q0 + P); ++q) {
-              const bool gstart = whole ? h == 0 : q % F == 0;
-              const bool gend = whole ? h == nh - 1 : (q % F == F - 1 || q == G - 1);
+            for (int q = q0; q < min(G, q0 + P); ++q, qf = qf + 1 == F ? 0 : qf + 1) {
+              const bool gstart = whole ? h == 0 : qf == 0;
+              const bool gend = whole ? h == nh - 1 : (qf == F - 1 || q == G - 1);
               if (gstart) {  // a flush group starts: its tile accumulator must be free
                 if (!mbar_wait<PROF>(bar(B_SEMPTY + sb), (sph_empty >> sb) & 1u, abort_flag, a.err, 2)) {
                   ok = false;

@@ -21,7 +21,7 @@ from . import capi
 K_ORB, N_EL, TWO_SZ, SEED = 108, 30, 0, 1
 
 
-def one(M, steps=2, autotune=True):
+def one(M, steps=2, autotune=True, only=None):
     import torch
     from synth import gaussian_sector_dims, mirrored_sectors, random_unit_vector
     left = gaussian_sector_dims(M, n_spatial=K_ORB // 2, n_tot=N_EL, two_sz_tot=TWO_SZ)
@@ -41,6 +41,8 @@ def one(M, steps=2, autotune=True):
         ref = None
         for name, prec in (("fp64", capi.DMRG_FP64), ("bf16x3", capi.DMRG_BF16X3), ("bf16x2", capi.DMRG_BF16X2),
                            ("fp16x2", capi.DMRG_FP16X2)):
+            if only and name != "fp64" and name not in only:
+                continue
             capi.dmrg_set_precision(ctx, prec)
             t0 = time.perf_counter()
             if prec == capi.DMRG_FP64 and autotune:
@@ -70,7 +72,7 @@ def one(M, steps=2, autotune=True):
                 nprod = 6 if prec == capi.DMRG_BF16X3 else 3
                 # operators once as 3 bf16 slices (2 fp16 slices for FP16X2), psi, sigma
                 alg = (4.0 if prec == capi.DMRG_FP16X2 else 6.0) * info["op_elements"] + 16.0 * n
-                r.update({"tc_items_per_sm": tuned[0], "hbm_gbs": alg / s / 1e9,
+                r.update({"tc_items_per_sm": tuned[0], "tc_unit_cost": tuned[1], "hbm_gbs": alg / s / 1e9,
                           "tensor_tflops_issued": nprod * info["flops"] / s / 1e12})
             if ref is None:
                 ref = y.clone()
@@ -88,9 +90,11 @@ def main():
     ap.add_argument("--M", type=int, nargs="+", default=[4000, 6000])
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--only", nargs="+", default=None, choices=["bf16x3", "bf16x2", "fp16x2"],
+                    help="mixed precisions to run (FP64, the reference, always runs)")
     args = ap.parse_args()
     for M in args.M:
-        print(json.dumps(one(M, args.steps, not args.no_autotune)), flush=True)
+        print(json.dumps(one(M, args.steps, not args.no_autotune, args.only)), flush=True)
 
 
 if __name__ == "__main__":

@@ -74,9 +74,10 @@ def test_autotune_keeps_parity_and_determinism():
 
 
 def test_tensor_core_autotune_keeps_parity_and_determinism():
-    """At a mixed precision the tuner picks the tensor-core work split; the
-    tuned sigma stays within the BF16X3 bar of the oracle and bitwise
-    repeatable, through direct launches and graph replays."""
+    """At a mixed precision the tuner picks the tensor-core work split (items
+    per SM and the fixed cost of a unit); the tuned sigma stays within the
+    BF16X3 bar of the oracle and bitwise repeatable, through direct launches
+    and graph replays."""
     import torch
     from oracle.nc import nc_terms
     from oracle.sigma import psi_layout, sigma_blocks, synthetic_ops
@@ -96,7 +97,7 @@ def test_tensor_core_autotune_keeps_parity_and_determinism():
             ys.append(y.cpu().numpy())
     finally:
         capi.dmrg_destroy(ctx)
-    assert w in (2, 4, 8, 16) and c == 0.0 and ms > 0
+    assert w in (4, 8, 16, 32) and c in (2.0 ** 20, 2.0 ** 22, 2.0 ** 24) and ms > 0
     assert all(np.array_equal(ys[0], y) for y in ys[1:])
     bL, bR, oL, oR, _ = synthetic_ops(left, right, 6, 12, seed=3)
     lay, _ = psi_layout(bL, bR, (6, 0))
