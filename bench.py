@@ -68,17 +68,14 @@ def config(M, prec="fp64"):
             "l2": "inputs larger than L2 (operator store >> 129 MB), no flush"}
 
 
-# DRAM bytes per launch of the FP64 sigma kernel on the default workload,
-# from ncu (dram__bytes_read.sum + dram__bytes_write.sum), recorded in
-# profiles/sigma_f64_middle_bond_m2000_dram.md; valid for M=2000 only.
-F64_TRAFFIC_M2000 = 57.05e9
-
-# DRAM bytes per algorithmic byte of the mixed-precision sigma (small-class
-# and tensor-core kernels) measured by ncu on a smaller case of the same
-# workload and applied to the bench size (traffic grows with the operator
-# store); recorded in profiles/sigma_tc_middle_bond_m800_full.md.
-TC_TRAFFIC_PER_ALG_BYTE = None
-TC_TRAFFIC_SOURCE = "ncu dram bytes of sigma_tc_kernel at M=800 per algorithmic byte, scaled to this M"
+# DRAM bytes per sigma at M=2000, from ncu captures of the small case M=800
+# scaled by the bytes each kernel requests (counted with the kernels' own
+# formulas by tests/host/plan_check.cpp) at both sizes:
+# profiles/sigma_f64_middle_bond_m800_dram.md, sigma_mixed_middle_bond_m800_dram.md.
+F64_TRAFFIC_M2000 = 70.0e9
+MIXED_TRAFFIC_M2000 = {"bf16x3": 32.4e9, "bf16x2": 32.4e9, "fp16x2": 20.6e9}
+TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum at M=800 (small case) per requested byte, "
+                  "times the requested bytes at M=2000")
 
 # ------------------------------------------------------------------ clocks
 class Clocks:
@@ -407,14 +404,14 @@ def main():
         # algorithmic bytes: every stored operator element once (6 B as three
         # bf16 slices, 4 B as two fp16 slices) + psi read + sigma written (FP64)
         alg_bytes = info["op_elements"] * bytes_per_elem + 16.0 * n
-        traffic = TC_TRAFFIC_PER_ALG_BYTE * alg_bytes if (name == "bf16x3" and TC_TRAFFIC_PER_ALG_BYTE) else None
+        traffic = MIXED_TRAFFIC_M2000[name] if args.M == 2000 else None
         mixed[name] = {"value": flops / step / 1e12, "unit": "TFLOP/s", "ms_per_step": step * 1e3,
                        "kernel_ms": kern * 1e3, "rel_err_vs_fp64_maxnorm": d, "rayleigh_rel_err_vs_fp64": rq,
                        "speedup_vs_fp64_kernel": (k_ms / max(1, k_n)) / (kern * 1e3),
                        "autotuned": {"tc_items_per_sm": tc_tuned[0], "tc_unit_cost": tc_tuned[1], "tune_ms": tc_tuned[2]},
                        "roofline": {"bound": "hbm", "achieved": alg_bytes / kern / 1e9, "peak": hbm,
                                     "unit": "GB/s", "frac": alg_bytes / kern / 1e9 / hbm, "traffic": traffic,
-                                    "traffic_source": TC_TRAFFIC_SOURCE if traffic else None,
+                                    "traffic_source": TRAFFIC_SOURCE if traffic else None,
                                     "kernel": "sigma_small_kernel + sigma_tc_kernel (one sigma)",
                                     "peak_source": "MEASURED_PEAKS.json hbm_gbs",
                                     "tensor_tflops_issued": nprod * flops / kern / 1e12,
@@ -436,8 +433,7 @@ def main():
            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
                         "frac": achieved / peak64,
                         "traffic": F64_TRAFFIC_M2000 if args.M == 2000 else None,
-                        "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
-                                          "profiles/sigma_f64_middle_bond_m2000_dram.md",
+                        "traffic_source": TRAFFIC_SOURCE + " (profiles/sigma_f64_middle_bond_m800_dram.md)",
                         "kernel": "sigma_f64_kernel",
                         "peak_source": "cuBLAS DGEMM 4096^3 measured in this run (no FP64 entry in MEASURED_PEAKS.json); "
                                        "cross-check: measured bf16 x nominal FP64/bf16 ratio = "
