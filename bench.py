@@ -238,7 +238,7 @@ def serve_section(n_req, device):
     stream = serve.summarize(res, reqs)
     return {"workload": f"{n_req} Davidson solves per run, middle-bond problems K in {{24,36,54}}, "
                         "M in {250,500,1000}, N ~ U[K/2,K], synthetic operators seeded per request; "
-                        "bf16x3 sigma, FP64 Davidson, tol 1e-8, at most 60 sigma calls; 4 slots, 160 GB budget",
+                        "fp16x2 sigma, FP64 Davidson, tol 1e-8, at most 60 sigma calls; 4 slots, 160 GB budget",
             "burst": {k: burst[k] for k in ("p50_s", "p99_s", "solves_per_s", "ok")},
             "poisson_at_80pct": {k: stream[k] for k in ("p50_s", "p99_s", "solves_per_s", "ok")},
             "rate_per_s": rate, "rejected": len(rej) + len(rej2)}
@@ -250,10 +250,10 @@ def sweeps_section(device):
     included), energies, converged steps."""
     from paper_2103_09976_gb300 import sweeps
     out = {"workload": "K=36 spatial orbitals, N=53, 2Sz=1, FeMoco-shaped integrals (seed 2), M 250 then 250; "
-                       "bf16x3 sigma, FP64 Davidson (tol 1e-6, at most 60 products, carried start vectors), "
+                       "fp16x2 sigma, FP64 Davidson (tol 1e-6, at most 60 products, carried start vectors), "
                        "FP64 decimation and transformation; mixed cut after 18 orbitals"}
     for name, cut in (("nc", -1), ("mixed_nc_cn", 18)):
-        r = sweeps.run(36, [250, 250], cut, "BF16X3", device=device)
+        r = sweeps.run(36, [250, 250], cut, "FP16X2", device=device)
         out[name] = {"s": r["build_s"] + r["sweeps_s"], "energies": r["energies"], "converged": r["converged"],
                      "steps": r["steps"], "phase_s": r["phase_s"]}
     out["nc_over_mixed"] = out["nc"]["s"] / out["mixed_nc_cn"]["s"]

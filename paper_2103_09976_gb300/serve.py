@@ -34,7 +34,7 @@ def request_sectors(K, N, two_sz, M):
     return left, right
 
 
-def run_stream(requests, n_slots=4, budget_bytes=160 << 30, prec=capi.DMRG_BF16X3, tol=1e-8, max_iter=60,
+def run_stream(requests, n_slots=4, budget_bytes=160 << 30, prec=capi.DMRG_FP16X2, tol=1e-8, max_iter=60,
                device=0, rate_scale=1.0):
     """Submit `requests` (dicts from synth.requests.poisson_requests) at their
     arrival times (scaled by rate_scale; 0 = all at once) and collect results."""
@@ -107,7 +107,7 @@ def main():
         return out
 
     common = {"slots": args.slots, "budget_gb": args.budget_gb, "requests": args.requests,
-              "precision": "bf16x3 sigma, FP64 Davidson", "max_iter": args.max_iter}
+              "precision": "fp16x2 sigma, FP64 Davidson", "max_iter": args.max_iter}
     if args.rate == "auto":
         burst = phase(0.0)
         stream = phase(0.8 * burst["solves_per_s"])

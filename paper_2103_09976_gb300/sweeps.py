@@ -17,7 +17,7 @@ import time
 from . import capi
 
 
-def run(K, schedule, cut, prec="BF16X3", N=None, two_sz=None, seed=2, femoco=True, tol=1e-6, max_iter=60,
+def run(K, schedule, cut, prec="FP16X2", N=None, two_sz=None, seed=2, femoco=True, tol=1e-6, max_iter=60,
         noise=0.0, device=0):
     from synth.integrals import femoco_like_integrals, random_integrals
     N = 113 * K // 76 if N is None else N
@@ -53,7 +53,7 @@ def main():
     ap.add_argument("--K", type=int, default=24)
     ap.add_argument("--M", default="80,80", help="bond dimension per sweep (forward, backward, ...)")
     ap.add_argument("--cut", type=int, nargs="+", default=[-1], help="mixed NC/CN cut(s); -1 = NC everywhere")
-    ap.add_argument("--prec", default="BF16X3", choices=["FP64", "BF16X3", "BF16X2", "FP16X2"])
+    ap.add_argument("--prec", default="FP16X2", choices=["FP64", "BF16X3", "BF16X2", "FP16X2"])
     ap.add_argument("--N", type=int, default=None)
     ap.add_argument("--two-sz", type=int, default=None)
     ap.add_argument("--seed", type=int, default=2)

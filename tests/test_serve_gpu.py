@@ -10,7 +10,7 @@ pytestmark = pytest.mark.gpu
 
 # (id, K spatial, N, 2Sz, M, seed, precision name)
 REQS = [(0, 12, 8, 0, 60, 11, "FP64"), (1, 16, 10, 0, 120, 12, "FP64"), (2, 12, 7, 1, 80, 13, "BF16X3"),
-        (3, 20, 12, 0, 200, 14, "FP64"), (4, 16, 9, 1, 150, 15, "BF16X3"), (5, 12, 8, 0, 60, 16, "BF16X2")]
+        (3, 20, 12, 0, 200, 14, "FP64"), (4, 16, 9, 1, 150, 15, "FP16X2"), (5, 12, 8, 0, 60, 16, "BF16X2")]
 TOL, MAX_ITER = 1e-9, 40
 
 
