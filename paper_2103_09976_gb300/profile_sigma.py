@@ -20,6 +20,7 @@ def main():
     ap.add_argument("--M", type=int, default=800)
     ap.add_argument("--prec", type=int, default=capi.DMRG_FP16X2, help="dmrg_prec: 0 FP64, 1 BF16X2, 2 BF16X3, 3 FP16X2")
     ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--autotune", action="store_true", help="tune the work split first (as the bench does)")
     args = ap.parse_args()
     left = gaussian_sector_dims(args.M, n_spatial=54, n_tot=30, two_sz_tot=0)
     right = mirrored_sectors(left, n_tot=30, two_sz_tot=0)
@@ -29,6 +30,8 @@ def main():
         n = capi.dmrg_get_sigma_info(ctx)["psi_size"]
         x = torch.from_numpy(random_unit_vector(n, 1)).cuda()
         y = torch.zeros_like(x)
+        if args.autotune:
+            capi.dmrg_autotune(ctx, -1)
         for _ in range(args.steps):
             capi.dmrg_sigma(ctx, -1, x, y)
         capi.dmrg_sync(ctx)
