@@ -381,7 +381,8 @@ def main():
         capi.dmrg_set_precision(ctx, prec)
         capi.dmrg_sigma(ctx, -1, x, y)  # builds the operator slices of this precision
         capi.dmrg_sync(ctx)
-        tc_tuned = capi.dmrg_autotune(ctx, -1)  # items per SM and unit cost of the tensor-core work split
+        tc_tuned = capi.dmrg_autotune(ctx, -1)  # items per SM, unit cost and producer warps of the tensor-core path
+        tc_producers = capi.dmrg_get_sigma_info(ctx, -1)["tc_producers"]
         for _ in range(max(3, args.warmup)):
             capi.dmrg_sigma(ctx, -1, x, y)
         capi.dmrg_sync(ctx)
@@ -408,7 +409,8 @@ def main():
         mixed[name] = {"value": flops / step / 1e12, "unit": "TFLOP/s", "ms_per_step": step * 1e3,
                        "kernel_ms": kern * 1e3, "rel_err_vs_fp64_maxnorm": d, "rayleigh_rel_err_vs_fp64": rq,
                        "speedup_vs_fp64_kernel": (k_ms / max(1, k_n)) / (kern * 1e3),
-                       "autotuned": {"tc_items_per_sm": tc_tuned[0], "tc_unit_cost": tc_tuned[1], "tune_ms": tc_tuned[2]},
+                       "autotuned": {"tc_items_per_sm": tc_tuned[0], "tc_unit_cost": tc_tuned[1],
+                                     "tc_producers": tc_producers, "tune_ms": tc_tuned[2]},
                        "roofline": {"bound": "hbm", "achieved": alg_bytes / kern / 1e9, "peak": hbm,
                                     "unit": "GB/s", "frac": alg_bytes / kern / 1e9 / hbm, "traffic": traffic,
                                     "traffic_source": TRAFFIC_SOURCE if traffic else None,

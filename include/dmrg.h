@@ -97,9 +97,16 @@ typedef struct {
                                   (8 for BF16X3 and FP16X2; for BF16X2 one accumulation per
                                   64-column half of every unit of stacked terms); -1 = that
                                   unbounded setting for all three. */
+  int tc_producers;            /* tensor-core sigma: warps that fill the kernel's 3-stage operand ring.
+                                  1 = one warp fills every stage in order; 3 = warp w fills stage w,
+                                  three stages prepared at once (faster when units hold many K
+                                  stages, i.e. large blocks); 0 = default: 3 when the plan's units
+                                  average 5 or more stages, else 1, until dmrg_autotune picks one.
+                                  Results are bitwise the same for 1 and 3. */
 } dmrg_opts;
 
-/* Fill *o with defaults: FP64, 24, 200, 0, 0.0, seed 0, device 0, graphs 1, mixed_cut -1, tc_chain 0. */
+/* Fill *o with defaults: FP64, 24, 200, 0, 0.0, seed 0, device 0, graphs 1, mixed_cut -1, tc_chain 0,
+ * tc_producers 0. */
 void dmrg_default_opts(dmrg_opts* o);
 
 /* Create a context on opts->device (NULL opts = defaults). *out is NULL on failure. */
@@ -198,6 +205,12 @@ typedef struct {
   long long op_elements;
   double op_bytes_read;
   long long psi_size;
+  /* tensor-core plan setting at this site for the context's precision
+     (after the plan is built by a mixed-precision sigma or dmrg_autotune;
+     defaults before): items per SM, producer warps, unit cost */
+  int tc_items_per_sm;
+  int tc_producers;
+  double tc_unit_cost;
 } dmrg_sigma_info;
 dmrg_status dmrg_get_sigma_info(dmrg_ctx* ctx, int site, dmrg_sigma_info* info);
 
@@ -242,7 +255,9 @@ dmrg_status dmrg_sigma_noalloc(dmrg_ctx* ctx, int site, const double* psi, doubl
  * tensor-core path for {4, 8, 16, 32} items per SM x {1, 4, 16} x 2^20
  * multiply-adds of fixed cost per unit of stacked terms (how each output
  * tile's units are split into work items and ordered, largest first) and
- * reports the choice in items_per_sm and per_task_cost. Any output may be
+ * reports the choice in items_per_sm and per_task_cost; then, unless
+ * dmrg_opts.tc_producers fixes it, the other producer setting (1 or 3) on the
+ * chosen plan, keeping the faster (dmrg_get_sigma_info reports it). Any output may be
  * NULL; best_ms = the chosen setting's time. Results stay bitwise deterministic for the
  * chosen setting; they can differ in the last bits from another setting
  * because items sum their terms in another grouping. A tuned FP64 work list

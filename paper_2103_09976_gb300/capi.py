@@ -24,13 +24,16 @@ class dmrg_opts(ctypes.Structure):
     _fields_ = [("sigma_prec", ctypes.c_int), ("dav_max_space", ctypes.c_int),
                 ("dav_max_iter", ctypes.c_int), ("keep_one_per_q", ctypes.c_int),
                 ("noise", ctypes.c_double), ("seed", ctypes.c_ulonglong), ("device", ctypes.c_int),
-                ("graphs", ctypes.c_int), ("mixed_cut", ctypes.c_int), ("tc_chain", ctypes.c_int)]
+                ("graphs", ctypes.c_int), ("mixed_cut", ctypes.c_int), ("tc_chain", ctypes.c_int),
+                ("tc_producers", ctypes.c_int)]
 
 
 class dmrg_sigma_info(ctypes.Structure):
     _fields_ = [("n_terms", ctypes.c_longlong), ("n_products", ctypes.c_longlong),
                 ("flops", ctypes.c_double), ("op_elements", ctypes.c_longlong),
-                ("op_bytes_read", ctypes.c_double), ("psi_size", ctypes.c_longlong)]
+                ("op_bytes_read", ctypes.c_double), ("psi_size", ctypes.c_longlong),
+                ("tc_items_per_sm", ctypes.c_int), ("tc_producers", ctypes.c_int),
+                ("tc_unit_cost", ctypes.c_double)]
 
 
 class DMRGError(RuntimeError):
@@ -232,7 +235,9 @@ def dmrg_sigma_part(ctx, site, rank, n_ranks, psi, sigma):
 
 
 def dmrg_autotune(ctx, site=-1):
-    """Tune the FP64 sigma work list; returns (items_per_sm, per_task_cost, best_ms)."""
+    """Tune the sigma work list of the context's precision (FP64, or the
+    tensor-core plan and its producer setting); returns (items_per_sm,
+    per_task_cost, best_ms)."""
     w, c, ms = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
     _check(ctx, lib().dmrg_autotune(ctx, site, ctypes.byref(w), ctypes.byref(c), ctypes.byref(ms)))
     return w.value, c.value, ms.value

@@ -123,6 +123,8 @@ static_assert(sizeof(TcItem) == sizeof(Item), "reduction reads TcItem as Item");
 static void prepare_tc_plan(Context& c, Problem& p) {
   cudaStream_t st = c.stream;
   build_tc_plan(p.blocks, p.L, p.R, p.wl, p.tc, TcShape{c.n_sm * p.tc_items_per_sm, p.tc_unit_cost});
+  p.tc_producers[0] = tc_default_producers(p.tc, false);
+  p.tc_producers[1] = tc_default_producers(p.tc, true);
   p.d_tc_recs.upload(p.tc.recs, st);
   p.d_tc_items.upload(p.tc.items, st);
   p.d_tc_small.upload(p.tc.small, st);
@@ -308,6 +310,7 @@ static void run_sigma_tc(Context& c, Problem& p, const double* d_psi, double* d_
   // flushes once per half of every unit
   const int chain = c.opts.tc_chain;
   t.max_chain = chain > 0 ? chain : (chain == 0 && prec != DMRG_BF16X2 ? 8 : 0);
+  t.producers = c.opts.tc_producers > 0 ? c.opts.tc_producers : p.tc_producers[f16 ? 1 : 0];
   t.wait_prof = nullptr;
   if (c.prof.on && c.prof.waits) {
     if (!c.d_wait_prof.p) {
@@ -664,6 +667,7 @@ void dmrg_default_opts(dmrg_opts* o) {
   o->graphs = 1;
   o->mixed_cut = -1;
   o->tc_chain = 0;
+  o->tc_producers = 0;
 }
 
 dmrg_status dmrg_create(dmrg_ctx** out, const dmrg_opts* opts) {
@@ -683,6 +687,8 @@ dmrg_status dmrg_create(dmrg_ctx** out, const dmrg_opts* opts) {
     if (!(o.noise >= 0.0) || !std::isfinite(o.noise)) throw Error(DMRG_EINVAL, "noise must be finite and >= 0");
     if (o.mixed_cut < -1) throw Error(DMRG_EINVAL, "mixed_cut must be -1 (NC everywhere) or >= 0");
     if (o.tc_chain < -1) throw Error(DMRG_EINVAL, "tc_chain must be -1 (unbounded), 0 (default) or >= 1");
+    if (o.tc_producers != 0 && o.tc_producers != 1 && o.tc_producers != 3)
+      throw Error(DMRG_EINVAL, "tc_producers must be 0 (by the plan or the autotuner), 1 or 3");
     if (o.sigma_prec < DMRG_FP64 || o.sigma_prec > DMRG_FP16X2)
       throw Error(DMRG_EINVAL, "unknown sigma precision");
     int ndev = 0;
@@ -801,6 +807,10 @@ dmrg_status dmrg_get_sigma_info(dmrg_ctx* ctx, int site, dmrg_sigma_info* info) 
     info->op_elements = p.L.elements + p.R.elements;
     info->op_bytes_read = p.wl.bytes_ops;
     info->psi_size = p.psi_size;
+    info->tc_items_per_sm = p.tc_items_per_sm;
+    info->tc_producers = ctx->c.opts.tc_producers > 0 ? ctx->c.opts.tc_producers
+                                                       : p.tc_producers[ctx->c.opts.sigma_prec == DMRG_FP16X2 ? 1 : 0];
+    info->tc_unit_cost = p.tc_unit_cost;
   });
 }
 
@@ -837,9 +847,20 @@ dmrg_status dmrg_autotune(dmrg_ctx* ctx, int site, int* items_per_sm, double* pe
       // 128 x 128 x 64) of the item split
       const int cand[4] = {4, 8, 16, 32};
       const double ucand[3] = {128.0 * 128 * 64, 4 * 128.0 * 128 * 64, 16 * 128.0 * 128 * 64};
+      const int g = c.opts.sigma_prec == DMRG_FP16X2 ? 1 : 0;
       double best = 1e300;
       int bi = p.tc_items_per_sm;
       double bu = p.tc_unit_cost;
+      auto time_one = [&]() -> float {  // one warm-up, one timed sigma
+        run_sigma_tc_direct(c, p, c.d_psi.as<double>(), c.d_sigma.as<double>());
+        DMRG_CUDA(cudaEventRecord(e0, c.stream));
+        run_sigma_tc_direct(c, p, c.d_psi.as<double>(), c.d_sigma.as<double>());
+        DMRG_CUDA(cudaEventRecord(e1, c.stream));
+        DMRG_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        DMRG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        return ms;
+      };
       try {
         for (double uc : ucand)
           for (int wi : cand) {
@@ -847,19 +868,28 @@ dmrg_status dmrg_autotune(dmrg_ctx* ctx, int site, int* items_per_sm, double* pe
             p.tc_unit_cost = uc;
             prepare_tc_plan(c, p);
             prepare_tc(c, p);  // FP16X2: records of the new plan
-            run_sigma_tc_direct(c, p, c.d_psi.as<double>(), c.d_sigma.as<double>());  // warm-up
-            DMRG_CUDA(cudaEventRecord(e0, c.stream));
-            run_sigma_tc_direct(c, p, c.d_psi.as<double>(), c.d_sigma.as<double>());
-            DMRG_CUDA(cudaEventRecord(e1, c.stream));
-            DMRG_CUDA(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            DMRG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            const float ms = time_one();
             if (ms < best) {
               best = ms;
               bi = wi;
               bu = uc;
             }
           }
+        p.tc_items_per_sm = bi;
+        p.tc_unit_cost = bu;
+        prepare_tc_plan(c, p);
+        prepare_tc(c, p);
+        // then the other producer setting on the chosen plan (unless fixed by
+        // the options)
+        if (c.opts.tc_producers == 0) {
+          const int d = p.tc_producers[g];
+          p.tc_producers[g] = d == 1 ? 3 : 1;
+          const float ms = time_one();
+          if (ms < best)
+            best = ms;
+          else
+            p.tc_producers[g] = d;
+        }
       } catch (...) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
@@ -867,10 +897,6 @@ dmrg_status dmrg_autotune(dmrg_ctx* ctx, int site, int* items_per_sm, double* pe
       }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
-      p.tc_items_per_sm = bi;
-      p.tc_unit_cost = bu;
-      prepare_tc_plan(c, p);
-      prepare_tc(c, p);
       check_device_error(c, p);
       if (items_per_sm) *items_per_sm = bi;
       if (per_task_cost) *per_task_cost = bu;

@@ -165,6 +165,9 @@ struct Problem {
   // tensor-core plan tuning (dmrg_autotune at a mixed precision): items per SM
   int tc_items_per_sm = 4;
   double tc_unit_cost = 128.0 * 128 * 64;  // fixed cost of a unit of stacked terms in the item split
+  // producer warps of the tensor-core kernel per tile geometry (bf16, fp16):
+  // the plan's default (tc_default_producers) or the autotuner's choice
+  int tc_producers[2] = {1, 1};
   // sub-Hamiltonian parts: (n_ranks, rank) -> work list of that rank's terms
   std::map<std::pair<int, int>, std::unique_ptr<DevWork>> parts;
 };

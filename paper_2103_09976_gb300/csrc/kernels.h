@@ -74,6 +74,7 @@ struct TcDev {
   int nprod;                  // 6 (three bf16 slices) or 3 (two slices)
   int f16;                    // 1: FP16X2 (fp16 slices, 256-byte tile positions, scaled operands)
   int max_chain;              // main MMA steps per FP32 accumulation (flush group); <= 0: one group per half
+  int producers;              // 1: warp 0 fills every ring slot; 3: producer warp w fills slot w
   unsigned long long* wait_prof;  // optional [17]: wait cycles per barrier kind, total cycles
 };
 
@@ -97,6 +98,10 @@ void launch_split_ops(const double* store, const SplitJob* jobs, long long njobs
 void launch_split_psi(const double* psi, const PsiBlock* blocks, const TcPsiBlock* pb, int nblk, void* out,
                       cudaStream_t st);
 void launch_sigma_tc(const TcDev& a, int n_sm, cudaStream_t st);
+// Default producer setting of the tensor-core kernel for a plan (TcDev::producers):
+// 3 when its units average 5 or more ring stages of the kernel's geometry
+// (bf16 or fp16 tiles), else 1.
+int tc_default_producers(const TcPlan& plan, bool f16);
 
 // FP16X2 split (split_f16.cu). Operator blocks and psi are scaled by powers
 // of two before the split: block b by 2^(14 - exps[b]), psi by

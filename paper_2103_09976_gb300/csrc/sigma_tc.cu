@@ -27,11 +27,15 @@
 // per flush group. (A compensated running sum cost about a fifth of the
 // kernel's time for a few percent of its error.)
 //
-// Warp roles (320 threads): warp 0 streams operator and psi tiles with
-// cp.async.bulk into a 3-stage ring; warp 1 issues the MMAs (one lane of a
-// warp that runs the control flow uniformly); warps 2-9 are
-// the epilogue (two warps per TMEM lane quarter, 64 columns each). Tensor
-// memory: two 128-column X buffers, two 128-column tile accumulators.
+// Warp roles (384 threads): warps 0, 10 and 11 stream operator and psi tiles
+// with cp.async.bulk into a 3-stage ring, warp w filling slot w (a warp
+// issues its copies one lane after another, and preparing a stage costs
+// about as much as the copies: three warps prepare three stages at once);
+// warp 0 also fetches the unit records.
+// Warp 1 issues the MMAs (one elected lane of a warp that runs the control
+// flow uniformly); warps 2-9 are the epilogue (two warps per TMEM lane
+// quarter, 64 columns each). Tensor memory: two 128-column X buffers, two
+// 128-column tile accumulators.
 // Operands are stored in 8x8 core-matrix tiles, so one stored block serves as
 // a K-major operand (S) or an MN-major one (S^T) with no copy: transposed
 // terms only change the shared-memory descriptors.
@@ -51,7 +55,8 @@ namespace dmrg {
 namespace {
 
 constexpr int NEPI = 8;                         // epilogue warps
-constexpr int NTHR = 64 + 32 * NEPI;            // producer + MMA + epilogue
+constexpr int NPW = 3;                          // producer warps (warp 0, then warps 2 + NEPI ..), one per ring slot
+constexpr int NTHR = 32 * (NPW + 1 + NEPI);     // producers + MMA + epilogue
 constexpr int A2_SLICE = 16 * 1024;             // X half: 16 row groups x 8 K groups x 128 B
 constexpr int A2_OFF = 0;                       // A2 first: reads past its last slice land in stage 0
 constexpr int NMETA = 8;                        // unit records in the shared-memory ring
@@ -90,6 +95,7 @@ struct Lay {
   static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
   static_assert(META_OFF % 16 == 0, "records are bulk-copied");
   static_assert(KG1 % 2 == 0 && 2 * PSI_TILE <= STAGE_TILES, "stage-1 stage");
+  static_assert(STAGES == NPW, "one producer warp per ring slot");
 };
 static_assert(sizeof(TcUnitRec) == 464 && offsetof(TcUnitRec, t) == 80, "record layout");
 static_assert(sizeof(TcUnitRec) % 16 == 0, "records are bulk-copied");
@@ -195,14 +201,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 }
 
 // ------------------------------------------------------ unit geometry
-__device__ __forceinline__ int n_chunks(const TcUnitRec& r) { return (r.n + 127) >> 7; }
-__device__ __forceinline__ int chunk_cols(const TcUnitRec& r, int j) { return min(128, r.n - 128 * j); }
-__device__ __forceinline__ int n_halves(const TcUnitRec& r, int j) { return (chunk_cols(r, j) + 63) >> 6; }
-__device__ __forceinline__ int half_cols(const TcUnitRec& r, int j, int h) { return min(64, chunk_cols(r, j) - 64 * h); }
+// (host and device: the host counts ring stages with the same formulas)
+__host__ __device__ __forceinline__ int n_chunks(const TcUnitRec& r) { return (r.n + 127) >> 7; }
+__host__ __device__ __forceinline__ int chunk_cols(const TcUnitRec& r, int j) { return min(128, r.n - 128 * j); }
+__host__ __device__ __forceinline__ int n_halves(const TcUnitRec& r, int j) { return (chunk_cols(r, j) + 63) >> 6; }
+__host__ __device__ __forceinline__ int half_cols(const TcUnitRec& r, int j, int h) { return min(64, chunk_cols(r, j) - 64 * h); }
 template <int KG1>
-__device__ __forceinline__ int k1_stages(const TcUnitRec& r) { return (r.pR8 + KG1 - 1) / KG1; }
-__device__ __forceinline__ int tn8e(const TcUnitRec& r) { return 2 * ((r.tn + 15) >> 4); }  // N groups read by the MMA
-__device__ __forceinline__ int kg2_of(int kw) { return 2 * ((kw + 15) >> 4); }               // K groups of a half
+__host__ __device__ __forceinline__ int k1_stages(const TcUnitRec& r) { return (r.pR8 + KG1 - 1) / KG1; }
+__host__ __device__ __forceinline__ int tn8e(const TcUnitRec& r) { return 2 * ((r.tn + 15) >> 4); }  // N groups read by the MMA
+__host__ __device__ __forceinline__ int kg2_of(int kw) { return 2 * ((kw + 15) >> 4); }               // K groups of a half
 // Terms per flush group: the most whose main K steps in one half stay within
 // max_chain (at least one); max_chain <= 0: the whole unit.
 __device__ __forceinline__ int flush_terms(const TcUnitRec& r, int max_chain) {
@@ -245,21 +252,28 @@ __device__ __forceinline__ UnitGeo geo_of(const TcUnitRec& r) {
 // Copies of one stage-1 stage (psi columns of chunk j, K groups KG1*k ..):
 // the stacked left-operator rows of every term ([M group][K group], or
 // [K group][M group] when the left operator is used transposed) and the psi
-// tiles ([K group][N group] from PSI_TILE on). Each lane issues copies
-// lane, lane + 32, ...; f(src_tile, operand (0 operators, 1 psi), dst_tile,
-// n_tiles) moves n_tiles tile positions (3 slices). Returns the stage's tile
-// count (the same on every lane).
+// tiles ([K group][N group] from PSI_TILE on); the list holds the operator
+// copies, then one psi copy per K group. f(src_tile, operand (0 operators,
+// 1 psi), dst_tile, n_tiles) moves n_tiles tile positions; lane l issues
+// copies l, l + 32, ... count_only: issue nothing, return the stage's tile
+// positions (the same on every lane).
 template <int KG1, class F>
-__device__ __forceinline__ uint32_t copies_s1(const TcUnitRec& r, const UnitGeo& g, int j, int k, int lane, F&& f) {
+__device__ __forceinline__ uint32_t copies_s1(const TcUnitRec& r, const UnitGeo& g, int j, int k, int lane,
+                                              bool count_only, F&& f) {
   constexpr int PSI_TILE = 16 * KG1;
   const int kg0 = KG1 * k;
   const bool tA = g.flags & TC_TA;
   const int nkA = tA ? min(KG1, g.aR8 - kg0) : min(KG1, g.aC8 - kg0);  // K groups of A in this stage
   const int nA = nkA > 0 ? (tA ? g.G * nkA : g.G * g.tm8) : 0;         // A copies
   const int perA = tA ? g.tm8 : nkA;                                    // tiles per A copy
-  const int nkP = min(KG1, g.pR8 - kg0), nn = min(16, g.pC8 - 16 * j);
-  for (int c = lane; c < nA; c += 32) {
-    if (!tA) {
+  const int nkP = max(0, min(KG1, g.pR8 - kg0)), nn = min(16, g.pC8 - 16 * j);
+  const int ntot = nA + nkP;
+  if (count_only) return (uint32_t)(nA * perA + nkP * nn);
+  for (int c = lane; c < ntot; c += 32) {
+    if (c >= nA) {
+      const int kg = c - nA;
+      f(g.p_tile + (long long)(kg0 + kg) * g.pC8 + 16 * j, 1, PSI_TILE + kg * 16, nn);
+    } else if (!tA) {
       const int q = c / g.tm8, rg = c - q * g.tm8;
       f(r.t[q].a_tile + (long long)(g.r0g + rg) * g.aC8 + kg0, 0, (q * g.tm8 + rg) * KG1, perA);
     } else {
@@ -267,8 +281,7 @@ __device__ __forceinline__ uint32_t copies_s1(const TcUnitRec& r, const UnitGeo&
       f(r.t[q].a_tile + (long long)(kg0 + kg) * g.aC8 + g.r0g, 0, kg * 16 + q * g.tm8, perA);
     }
   }
-  if (lane < nkP) f(g.p_tile + (long long)(kg0 + lane) * g.pC8 + 16 * j, 1, PSI_TILE + lane * 16, nn);
-  return (uint32_t)(nA * perA + max(nkP, 0) * nn);
+  return 0;
 }
 
 // Copies of one stage-2 stage: the right-operator tiles (output columns of
@@ -277,13 +290,14 @@ __device__ __forceinline__ uint32_t copies_s1(const TcUnitRec& r, const UnitGeo&
 // group] when the right operator is used transposed). As copies_s1.
 template <class F>
 __device__ __forceinline__ uint32_t copies_s2(const TcUnitRec& r, const UnitGeo& g, int j, int h, int q0, int q1,
-                                              int lane, F&& f) {
+                                              int lane, bool count_only, F&& f) {
   const int kw = min(64, min(128, g.n - 128 * j) - 64 * h), kg2 = kg2_of(kw), kgx = 16 * j + 8 * h;
   const bool tB = g.flags & TC_TB;
   const int nkB = tB ? min(kg2, g.bR8 - kgx) : min(kg2, g.bC8 - kgx);  // K groups of B present
   const int per = tB ? g.tn8 : nkB;
   const int span = tB ? nkB : g.tn8;                                  // copies per term
   const int ncopy = (q1 - q0) * span;
+  if (count_only) return (uint32_t)(ncopy * per);
   for (int c = lane; c < ncopy; c += 32) {
     const int qq = c / span, x = c - qq * span, reg = qq * g.te * kg2;
     if (!tB)
@@ -291,7 +305,7 @@ __device__ __forceinline__ uint32_t copies_s2(const TcUnitRec& r, const UnitGeo&
     else
       f(r.t[q0 + qq].b_tile + (long long)(kgx + x) * g.bC8 + g.c0g, 0, reg + x * g.te, per);
   }
-  return (uint32_t)(ncopy * per);
+  return 0;
 }
 
 }  // namespace
@@ -315,21 +329,31 @@ __device__ __forceinline__ void mma_lohi(uint32_t tmem, uint32_t alo, uint32_t a
                ::"r"(tmem), "r"(alo), "r"(ahi), "r"(blo), "r"(bhi), "r"(idesc), "r"(acc));
 }
 
+// One lane of a converged warp (elect.sync over the full warp: the same
+// lane every time). The MMA warp issues its MMAs and their commits through it,
+// so each commit tracks the MMAs before it.
+__device__ __forceinline__ bool elect_one() {
+  uint32_t p = 0;
+  asm volatile("{\n.reg .b32 rx;\n.reg .pred px;\nelect.sync rx|px, %1;\nselp.u32 %0, 1, 0, px;\n}\n"
+               : "=r"(p) : "r"(0xffffffffu));
+  return p != 0;
+}
+
 // One K chain of slice products into tmem_d: the correction products of all
 // NKS K steps first, then the main (hi x hi) ones. a / b: descriptors;
 // a_slice, b_slice: byte offsets of the mid slice; a_kstep, b_kstep: byte
 // offsets of one K step. All offsets are compile-time multiples after
 // unrolling, so the issuing loop is a run of MMAs on precomputed operands.
-// The whole warp evaluates the (uniform) descriptors; `leader` issues.
+// The whole warp evaluates the (uniform) descriptors; the elected lane issues.
 // `first`: the next MMA overwrites the accumulator (cleared after it).
 template <int NPROD, int NKS>
-__device__ __forceinline__ void mma_chain_k(bool leader, uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t a_slice,
+__device__ __forceinline__ void mma_chain_k(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t a_slice,
                                             uint32_t b_slice, uint32_t a_kstep, uint32_t b_kstep, uint32_t idesc,
                                             bool& first) {
   const uint32_t alo = (uint32_t)a, ahi = (uint32_t)(a >> 32), blo = (uint32_t)b, bhi = (uint32_t)(b >> 32);
   const uint32_t as16 = a_slice >> 4, bs16 = b_slice >> 4, ak16 = a_kstep >> 4, bk16 = b_kstep >> 4;
   uint32_t acc = first ? 0u : 1u;
-  if (leader) {
+  if (elect_one()) {
 #pragma unroll
     for (int ks = 0; ks < NKS; ++ks)
 #pragma unroll
@@ -348,14 +372,14 @@ __device__ __forceinline__ void mma_chain_k(bool leader, uint32_t tmem_d, uint64
 }
 
 template <int NPROD>
-__device__ __forceinline__ void mma_chain(bool leader, uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t a_slice,
+__device__ __forceinline__ void mma_chain(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t a_slice,
                                           uint32_t b_slice, uint32_t a_kstep, uint32_t b_kstep, int nks,
                                           uint32_t idesc, bool& first) {
   switch (nks) {
-    case 1: mma_chain_k<NPROD, 1>(leader, tmem_d, a, b, a_slice, b_slice, a_kstep, b_kstep, idesc, first); break;
-    case 2: mma_chain_k<NPROD, 2>(leader, tmem_d, a, b, a_slice, b_slice, a_kstep, b_kstep, idesc, first); break;
-    case 3: mma_chain_k<NPROD, 3>(leader, tmem_d, a, b, a_slice, b_slice, a_kstep, b_kstep, idesc, first); break;
-    default: mma_chain_k<NPROD, 4>(leader, tmem_d, a, b, a_slice, b_slice, a_kstep, b_kstep, idesc, first); break;
+    case 1: mma_chain_k<NPROD, 1>(tmem_d, a, b, a_slice, b_slice, a_kstep, b_kstep, idesc, first); break;
+    case 2: mma_chain_k<NPROD, 2>(tmem_d, a, b, a_slice, b_slice, a_kstep, b_kstep, idesc, first); break;
+    case 3: mma_chain_k<NPROD, 3>(tmem_d, a, b, a_slice, b_slice, a_kstep, b_kstep, idesc, first); break;
+    default: mma_chain_k<NPROD, 4>(tmem_d, a, b, a_slice, b_slice, a_kstep, b_kstep, idesc, first); break;
   }
 }
 
@@ -402,7 +426,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
     }
     for (int m = 0; m < NMETA; ++m) {
       mbar_init(bar(B_MFULL + m), 1);
-      mbar_init(bar(B_MEMPTY + m), 2 + NEPI);  // producer + MMA + epilogue warps
+      mbar_init(bar(B_MEMPTY + m), (a.producers == 1 ? 1 : NPW) + 1 + NEPI);  // producer, MMA, epilogue warps
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -417,26 +441,38 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
   asm volatile("tcgen05.fence::after_thread_sync;\n");
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 0) {
-    // ------------------------------------------------------------ producer
+  if (warp == 0 || (warp >= 2 + NEPI && a.producers != 1)) {
+    // ------------------------------------------------------------ producers
+    // With a.producers == NPW every producer warp walks the same units and
+    // stages and warp pw fills ring slot pw (NPW = STAGES), so each slot has
+    // one producer and the stages of a unit are filled by three warps at
+    // once; with a.producers == 1 warp 0 fills every slot and the others
+    // stay idle. Warp 0 (pw 0) also fetches the unit records into the ring;
+    // the others read them there.
+    const int pw = warp == 0 ? 0 : warp - 1 - NEPI;  // 0 .. NPW-1
+    const bool all_slots = a.producers == 1;
     uint32_t stage = 0, phase = 1;  // empty barriers: first wait passes
     bool ok = true;
     const char* const ops = (const char*)a.op;
     const char* const ps = (const char*)a.psi;
     // one stage: wait for it to be free, announce its bytes, issue the copies
+    // one stage: if it is this warp's ring slot, wait for the slot to be
+    // free, announce its bytes, issue the copies; every warp counts it
     auto produce = [&](auto&& copies) {
       if (!ok) return;
-      if (!mbar_wait<PROF>(bar(B_EMPTY + stage), phase, abort_flag, a.err, 1)) { ok = false; return; }
-      const uint32_t sdst = sbase + STAGE_OFF + stage * STAGE_BYTES;
-      const uint32_t fb = bar(B_FULL + stage);
-      // the byte count is announced before any copy can complete: lane 0
-      // arrives with the expected bytes first, then all lanes issue copies
-      const uint32_t tiles = copies([&](long long, int, int, int) {}, true);
-      if (lane == 0) mbar_expect_tx(fb, (uint32_t)TILE * tiles);
-      __syncwarp();
-      copies([&](long long src, int which, int dst, int n) {
-        bulk_g2s(sdst + (uint32_t)dst * TILE, (which ? ps : ops) + src * TILE, (uint32_t)TILE * (uint32_t)n, fb);
-      }, false);
+      if (all_slots || stage == (uint32_t)pw) {
+        if (!mbar_wait<PROF>(bar(B_EMPTY + stage), phase, abort_flag, a.err, 1)) { ok = false; return; }
+        const uint32_t sdst = sbase + STAGE_OFF + stage * STAGE_BYTES;
+        const uint32_t fb = bar(B_FULL + stage);
+        // the byte count is announced before any copy can complete: lane 0
+        // arrives with the expected bytes first, then all lanes issue copies
+        const uint32_t tiles = copies([&](long long, int, int, int) {}, true);
+        if (lane == 0) mbar_expect_tx(fb, (uint32_t)TILE * tiles);
+        __syncwarp();
+        copies([&](long long src, int which, int dst, int n) {
+          bulk_g2s(sdst + (uint32_t)dst * TILE, (which ? ps : ops) + src * TILE, (uint32_t)TILE * (uint32_t)n, fb);
+        }, false);
+      }
       if (++stage == STAGES) { stage = 0; phase ^= 1; }
     };
     auto produce_s1 = [&](const TcUnitRec& u, int j) {
@@ -444,8 +480,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
       const int nk1 = (g.pR8 + KG1 - 1) / KG1;
       for (int k = 0; k < nk1; ++k)
         produce([&](auto&& f, bool count_only) -> uint32_t {
-          if (count_only) return copies_s1<KG1>(u, g, j, k, 32, f);  // lane 32 issues nothing
-          return copies_s1<KG1>(u, g, j, k, lane, f);
+          return copies_s1<KG1>(u, g, j, k, lane, count_only, f);
         });
     };
     auto produce_s2 = [&](const TcUnitRec& u, int j) {
@@ -456,7 +491,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
         const int P = max(1, min(g.G, STAGE_TILES / (g.te * kg2_of(kw))));
         for (int q0 = 0; q0 < g.G; q0 += P)
           produce([&](auto&& f, bool count_only) -> uint32_t {
-            return copies_s2(u, g, j, h, q0, min(g.G, q0 + P), count_only ? 32 : lane, f);
+            return copies_s2(u, g, j, h, q0, min(g.G, q0 + P), lane, count_only, f);
           });
       }
     };
@@ -498,13 +533,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
       }
       prev_slot = -1;
     };
-    for (;;) {
-      while (ok && pf_s < s + PREFETCH && prefetch_one()) {
-      }
-      if (!ok) break;
-      if (s == pf_s) break;  // nothing left
-      const int slot = (int)(s % NMETA);
-      if (!mbar_wait<PROF>(bar(B_MFULL + slot), (uint32_t)((s / NMETA) & 1), abort_flag, a.err, 10)) { ok = false; break; }
+    auto unit = [&](int slot) {  // the stages of one record (its slot's full barrier passed)
       const TcUnitRec& u = ring[slot];
       if (u.flags & TC_ZERO) {
         __syncwarp();
@@ -517,36 +546,59 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
           prev_j = j;
         }
       }
-      ++s;
-    }
-    // terminator record, pushed before the last sub-unit's stage-2 operands:
-    // the MMA issuer reads it before it consumes those stages, and they can
-    // be more than the ring holds
-    if (ok) {
-      const int slot = (int)(s % NMETA);
-      const uint32_t par = (uint32_t)(((s / NMETA) & 1) ^ 1);
-      if (mbar_wait<PROF>(bar(B_MEMPTY + slot), par, abort_flag, a.err, 11)) {
-        if (lane == 0) {
-          ring[slot].flags = TC_DONE;
-          mbar_arrive(bar(B_MFULL + slot));
+    };
+    if (pw == 0) {
+      for (;;) {
+        while (ok && pf_s < s + PREFETCH && prefetch_one()) {
         }
-      } else {
-        ok = false;
+        if (!ok) break;
+        if (s == pf_s) break;  // nothing left
+        const int slot = (int)(s % NMETA);
+        if (!mbar_wait<PROF>(bar(B_MFULL + slot), (uint32_t)((s / NMETA) & 1), abort_flag, a.err, 10)) { ok = false; break; }
+        unit(slot);
+        ++s;
       }
+      // terminator record, pushed before the last sub-unit's stage-2
+      // operands: the MMA issuer and the other producers read it before they
+      // reach those stages, and they can be more than the ring holds
+      if (ok) {
+        const int slot = (int)(s % NMETA);
+        const uint32_t par = (uint32_t)(((s / NMETA) & 1) ^ 1);
+        if (mbar_wait<PROF>(bar(B_MEMPTY + slot), par, abort_flag, a.err, 11)) {
+          if (lane == 0) {
+            ring[slot].flags = TC_DONE;
+            mbar_arrive(bar(B_MFULL + slot));
+          }
+        } else {
+          ok = false;
+        }
+        __syncwarp();
+      }
+      if (ok) finish_prev();
       __syncwarp();
-    }
-    if (ok) finish_prev();
-    __syncwarp();
-    // drain: wait (bounded) until the MMA side released every stage we filled
-    for (int k = 0; k < STAGES; ++k) {
-      mbar_wait<PROF>(bar(B_EMPTY + stage), phase, abort_flag, a.err, 0);
-      if (++stage == STAGES) { stage = 0; phase ^= 1; }
+      // drain: wait (bounded) until the MMA side released every stage (the
+      // copies of all producer warps have landed once a stage is released)
+      for (int k = 0; k < STAGES; ++k) {
+        mbar_wait<PROF>(bar(B_EMPTY + stage), phase, abort_flag, a.err, 0);
+        if (++stage == STAGES) { stage = 0; phase ^= 1; }
+      }
+    } else {
+      // records in ring order until the terminator
+      while (ok) {
+        const int slot = (int)(s % NMETA);
+        if (!mbar_wait<PROF>(bar(B_MFULL + slot), (uint32_t)((s / NMETA) & 1), abort_flag, a.err, 10)) { ok = false; break; }
+        if (ring[slot].flags & TC_DONE) break;
+        unit(slot);
+        ++s;
+      }
+      if (ok) finish_prev();
+      __syncwarp();
     }
   } else if (warp == 1) {
     // --------------------------------------------------------------- MMA
     // The whole warp runs this role's control flow, so descriptors and
-    // counters stay warp-uniform; lane 0 alone issues the MMAs, commits and
-    // arrivals.
+    // counters stay warp-uniform; one elected lane issues the MMAs and their
+    // commits, lane 0 the plain arrivals.
     {
       const bool leader = lane == 0;
       // with profiling on, slots 14 / 15 of the wait accounting receive the
@@ -568,7 +620,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
       };
       auto release = [&]() {
         const long long t0 = tick();
-        if (leader) commit(bar(B_EMPTY + stage));
+        if (elect_one()) commit(bar(B_EMPTY + stage));
         tock(15, t0);
         if (++stage == STAGES) { stage = 0; phase ^= 1; }
       };
@@ -588,14 +640,14 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
           const uint32_t sst = acquire();
           if (!ok) return;
           const long long t0 = tick();
-          mma_chain<NPROD>(leader, tmem_x, sdesc(sst, a_lbo, a_sbo), sdesc(sst + PSI_TILE * TILE, 16u * TILE, TILE),
+          mma_chain<NPROD>(tmem_x, sdesc(sst, a_lbo, a_sbo), sdesc(sst + PSI_TILE * TILE, 16u * TILE, TILE),
                            128u, 128u, 2 * a_lbo, 2 * 16u * TILE, min(KG1, pR8 - KG1 * k) / 2, id1, first);
           tock(14, t0);
           release();
         }
         {
           const long long t0 = tick();
-          if (leader) commit(bar(B_XFULL + xb));
+          if (elect_one()) commit(bar(B_XFULL + xb));
           tock(15, t0);
         }
         ++xcnt;
@@ -633,13 +685,13 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
                 first = true;
               }
               const long long t0 = tick();
-              mma_chain<NPROD>(leader, tmem + 256 + sb * 128, sdesc(a2 + (uint32_t)(q * tm8) * 1024u, 128u, 1024u),
+              mma_chain<NPROD>(tmem + 256 + sb * 128, sdesc(a2 + (uint32_t)(q * tm8) * 1024u, 128u, 1024u),
                                sdesc(sst + (uint32_t)((q - q0) * te * kg2) * TILE, b_lbo, b_sbo), A2_SLICE, 128u,
                                2 * 128u, 2 * b_lbo, kg2 / 2, id2, first);
               tock(14, t0);
               if (gend) {  // the group ends: hand the accumulator to the epilogue
                 const long long t1 = tick();
-                if (leader) commit(bar(B_SFULL + sb));
+                if (elect_one()) commit(bar(B_SFULL + sb));
                 tock(15, t1);
                 sb ^= 1;
               }
@@ -647,7 +699,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
             release();
           }
           const long long t1 = tick();
-          if (leader) commit(bar(B_A2EMPTY + hb));
+          if (elect_one()) commit(bar(B_A2EMPTY + hb));
           tock(15, t1);
         }
       };
@@ -681,7 +733,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
       finish_prev();
     }
     __syncwarp();
-  } else {
+  } else if (warp < 2 + NEPI) {
     // ---------------------------------------------------------- epilogue
     const int e = warp - 2;                    // 0 .. NEPI-1
     const int quarter = warp & 3;              // TMEM lanes 32*quarter .. +31
@@ -965,6 +1017,33 @@ void launch_sigma_tc(const TcDev& a, int n_sm, cudaStream_t st) {
     launch_tc<6, false>(a, grid, st);
   else
     launch_tc<3, false>(a, grid, st);
+}
+
+// Ring stages per unit, counted as the producers fill them. Large blocks
+// give units of many K stages, each a long list of copies: the kernel is then
+// bound by preparing and issuing stages, and three producer warps fill the
+// ring faster; with few stages per unit one producer keeps the stages in
+// the order the MMA issuer takes them, which is faster there.
+template <bool F16>
+static int default_producers(const TcPlan& plan) {
+  using L = Lay<F16>;
+  long long units = 0, stages = 0;
+  for (const TcUnitRec& r : plan.recs) {
+    if (r.flags & TC_ZERO) continue;
+    ++units;
+    for (int j = 0; j < n_chunks(r); ++j) {
+      stages += k1_stages<L::KG1>(r);
+      for (int h = 0; h < n_halves(r, j); ++h) {
+        const int P = max(1, min(r.nterm, L::STAGE_TILES / (tn8e(r) * kg2_of(half_cols(r, j, h)))));
+        stages += (r.nterm + P - 1) / P;
+      }
+    }
+  }
+  return units > 0 && stages >= 5 * units ? NPW : 1;
+}
+
+int tc_default_producers(const TcPlan& plan, bool f16) {
+  return f16 ? default_producers<true>(plan) : default_producers<false>(plan);
 }
 
 }  // namespace dmrg

@@ -72,7 +72,8 @@ def one(M, steps=2, autotune=True, only=None):
                 nprod = 6 if prec == capi.DMRG_BF16X3 else 3
                 # operators once as 3 bf16 slices (2 fp16 slices for FP16X2), psi, sigma
                 alg = (4.0 if prec == capi.DMRG_FP16X2 else 6.0) * info["op_elements"] + 16.0 * n
-                r.update({"tc_items_per_sm": tuned[0], "tc_unit_cost": tuned[1], "hbm_gbs": alg / s / 1e9,
+                r.update({"tc_items_per_sm": tuned[0], "tc_unit_cost": tuned[1],
+                          "tc_producers": capi.dmrg_get_sigma_info(ctx, -1)["tc_producers"], "hbm_gbs": alg / s / 1e9,
                           "tensor_tflops_issued": nprod * info["flops"] / s / 1e12})
             if ref is None:
                 ref = y.clone()

@@ -71,12 +71,14 @@ def test_default_opts(libpath):
     o = capi.dmrg_default_opts()
     assert o.dav_max_space == 24 and o.dav_max_iter == 200 and o.sigma_prec == capi.DMRG_FP64
     assert o.mixed_cut == -1 and o.graphs == 1 and o.keep_one_per_q == 0
+    assert o.tc_chain == 0 and o.tc_producers == 0
 
 
 def test_option_checks_come_before_the_device(libpath):
     """Invalid options are rejected with EINVAL whether or not a GPU is present."""
     from paper_2103_09976_gb300 import capi
-    for kw in ({"mixed_cut": -2}, {"keep_one_per_q": 2}, {"noise": -1.0}, {"dav_max_space": 2}):
+    for kw in ({"mixed_cut": -2}, {"keep_one_per_q": 2}, {"noise": -1.0}, {"dav_max_space": 2}, {"tc_chain": -2},
+               {"tc_producers": 2}, {"tc_producers": -1}):
         with pytest.raises(capi.DMRGError) as e:
             capi.dmrg_create(**kw)
         assert e.value.status == capi.DMRG_EINVAL, kw

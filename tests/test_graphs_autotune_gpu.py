@@ -75,7 +75,8 @@ def test_autotune_keeps_parity_and_determinism():
 
 def test_tensor_core_autotune_keeps_parity_and_determinism():
     """At a mixed precision the tuner picks the tensor-core work split (items
-    per SM and the fixed cost of a unit); the tuned sigma stays within the
+    per SM and the fixed cost of a unit) and the producer setting, reported by
+    dmrg_get_sigma_info; the tuned sigma stays within the
     BF16X3 bar of the oracle and bitwise repeatable, through direct launches
     and graph replays."""
     import torch
@@ -86,6 +87,7 @@ def test_tensor_core_autotune_keeps_parity_and_determinism():
     ctx, left, right = _load(capi, 1200, 3, 6, 3, sigma_prec=capi.DMRG_BF16X3)
     try:
         w, c, ms = capi.dmrg_autotune(ctx)
+        info = capi.dmrg_get_sigma_info(ctx)
         n = capi.dmrg_psi_layout(ctx)["size"]
         x_h = random_unit_vector(n, 13)
         x = torch.from_numpy(x_h).cuda()
@@ -98,6 +100,7 @@ def test_tensor_core_autotune_keeps_parity_and_determinism():
     finally:
         capi.dmrg_destroy(ctx)
     assert w in (4, 8, 16, 32) and c in (2.0 ** 20, 2.0 ** 22, 2.0 ** 24) and ms > 0
+    assert (info["tc_items_per_sm"], info["tc_unit_cost"]) == (w, c) and info["tc_producers"] in (1, 3)
     assert all(np.array_equal(ys[0], y) for y in ys[1:])
     bL, bR, oL, oR, _ = synthetic_ops(left, right, 6, 12, seed=3)
     lay, _ = psi_layout(bL, bR, (6, 0))

@@ -70,6 +70,36 @@ def test_sigma_tc_matches_oracle(capi, prec, M, nsp, ntot, seed):
     assert np.array_equal(y, y2), "tensor-core sigma must be bitwise deterministic"
 
 
+@pytest.mark.parametrize("prec", [1, 3])
+@pytest.mark.parametrize("M,nsp,ntot,seed", [(1200, 3, 6, 3), (4000, 3, 6, 4)])
+def test_producer_settings_give_the_same_bits(capi, prec, M, nsp, ntot, seed):
+    """One producer warp filling every ring stage and three warps filling one
+    stage each move the same tiles into the same places: sigma is bitwise the
+    same for both settings and for the plan's default, and within the bar
+    against the oracle."""
+    from synth import gaussian_sector_dims, mirrored_sectors, random_unit_vector
+    left = gaussian_sector_dims(M, n_spatial=nsp, n_tot=ntot)
+    right = mirrored_sectors(left, n_tot=ntot)
+    nL, n = 2 * nsp, 4 * nsp
+    ys, used = {}, {}
+    for producers in (0, 1, 3):
+        ctx = capi.dmrg_create(device=0, sigma_prec=prec, tc_producers=producers)
+        try:
+            capi.dmrg_load_synthetic(ctx, nL, n, ntot, 0, left, right, seed)
+            size = capi.dmrg_psi_layout(ctx)["size"]
+            x = random_unit_vector(size, seed + 10)
+            y = np.zeros_like(x)
+            capi.dmrg_sigma(ctx, -1, x, y)
+            ys[producers] = y
+            used[producers] = capi.dmrg_get_sigma_info(ctx)["tc_producers"]
+        finally:
+            capi.dmrg_destroy(ctx)
+    assert used[1] == 1 and used[3] == 3 and used[0] in (1, 3)
+    assert np.array_equal(ys[1], ys[3]) and np.array_equal(ys[0], ys[1])
+    ref = _oracle_full(left, right, nL, n, (ntot, 0), seed, x)
+    assert np.abs(ys[3] - ref).max() / np.abs(ref).max() <= TOL[prec]
+
+
 def test_sigma_tc_middle_bond_m2000_vs_fp64(capi):
     """K=108 (54|54), N=30, M=2000: BF16X3, BF16X2 and FP16X2 against the
     FP64 GPU path on the same context, plus the Rayleigh-quotient
