@@ -210,6 +210,18 @@ template <int KG1>
 __host__ __device__ __forceinline__ int k1_stages(const TcUnitRec& r) { return (r.pR8 + KG1 - 1) / KG1; }
 __host__ __device__ __forceinline__ int tn8e(const TcUnitRec& r) { return 2 * ((r.tn + 15) >> 4); }  // N groups read by the MMA
 __host__ __device__ __forceinline__ int kg2_of(int kw) { return 2 * ((kw + 15) >> 4); }               // K groups of a half
+// Shared-memory stride (tile positions) of the right operator of a stage-2
+// stage. With runs (one producer warp), copies_s2 moves a term's tiles as
+// one run where the stored block allows, keeping the block's stride: the
+// N-group stride when not transposed (bC8 when the half holds all K groups
+// of the block), the K-group stride when transposed (tn8 when the tile spans
+// all stored columns); otherwise kg2 / te. Runs measured 4% faster with one
+// producer (small blocks) and 3.5% slower with three (large blocks).
+__host__ __device__ __forceinline__ int b_stride(const TcUnitRec& r, int j, int h, bool runs) {
+  const int kg2 = kg2_of(half_cols(r, j, h)), kgx = 16 * j + 8 * h, tn8 = (r.tn + 7) >> 3;
+  if (r.flags & TC_TB) return runs && tn8 == r.bC8 ? tn8 : tn8e(r);
+  return runs && min(kg2, r.bC8 - kgx) == r.bC8 ? r.bC8 : kg2;
+}
 // Terms per flush group: the most whose main K steps in one half stay within
 // max_chain (at least one); max_chain <= 0: the whole unit.
 __device__ __forceinline__ int flush_terms(const TcUnitRec& r, int max_chain) {
@@ -253,10 +265,13 @@ __device__ __forceinline__ UnitGeo geo_of(const TcUnitRec& r) {
 // the stacked left-operator rows of every term ([M group][K group], or
 // [K group][M group] when the left operator is used transposed) and the psi
 // tiles ([K group][N group] from PSI_TILE on); the list holds the operator
-// copies, then one psi copy per K group. f(src_tile, operand (0 operators,
-// 1 psi), dst_tile, n_tiles) moves n_tiles tile positions; lane l issues
-// copies l, l + 32, ... count_only: issue nothing, return the stage's tile
-// positions (the same on every lane).
+// copies, then one psi copy per K group. (Moving the stage's tiles of a term
+// or of psi as one run where the stored block allows, with the run's stride
+// in shared memory, measured slower on large blocks and no faster on small
+// ones: only stage 2 does it.) f(src_tile, operand (0 operators, 1 psi),
+// dst_tile, n_tiles) moves n_tiles tile positions; lane l issues copies l,
+// l + 32, ... count_only: issue nothing, return the stage's tile positions
+// (the same on every lane).
 template <int KG1, class F>
 __device__ __forceinline__ uint32_t copies_s1(const TcUnitRec& r, const UnitGeo& g, int j, int k, int lane,
                                               bool count_only, F&& f) {
@@ -287,20 +302,24 @@ __device__ __forceinline__ uint32_t copies_s1(const TcUnitRec& r, const UnitGeo&
 // Copies of one stage-2 stage: the right-operator tiles (output columns of
 // the tile, K groups of half h of chunk j) of terms q0..q1-1, each term in a
 // region of te x kg2 tile positions ([N group][K group], or [K group][N
-// group] when the right operator is used transposed). As copies_s1.
+// group] when the right operator is used transposed; with runs one copy per
+// term where the block allows, strides as b_stride). As copies_s1.
 template <class F>
 __device__ __forceinline__ uint32_t copies_s2(const TcUnitRec& r, const UnitGeo& g, int j, int h, int q0, int q1,
-                                              int lane, bool count_only, F&& f) {
+                                              bool runs, int lane, bool count_only, F&& f) {
   const int kw = min(64, min(128, g.n - 128 * j) - 64 * h), kg2 = kg2_of(kw), kgx = 16 * j + 8 * h;
   const bool tB = g.flags & TC_TB;
   const int nkB = tB ? min(kg2, g.bR8 - kgx) : min(kg2, g.bC8 - kgx);  // K groups of B present
-  const int per = tB ? g.tn8 : nkB;
-  const int span = tB ? nkB : g.tn8;                                  // copies per term
+  const bool b_run = runs && (tB ? g.tn8 == g.bC8 : nkB == g.bC8);    // one run per term
+  const int per = b_run ? nkB * g.tn8 : (tB ? g.tn8 : nkB);
+  const int span = b_run ? 1 : (tB ? nkB : g.tn8);                    // copies per term
   const int ncopy = (q1 - q0) * span;
   if (count_only) return (uint32_t)(ncopy * per);
   for (int c = lane; c < ncopy; c += 32) {
     const int qq = c / span, x = c - qq * span, reg = qq * g.te * kg2;
-    if (!tB)
+    if (b_run)
+      f(r.t[q0 + qq].b_tile + (long long)(tB ? kgx : g.c0g) * g.bC8, 0, reg, per);
+    else if (!tB)
       f(r.t[q0 + qq].b_tile + (long long)(g.c0g + x) * g.bC8 + kgx, 0, reg + x * kg2, per);
     else
       f(r.t[q0 + qq].b_tile + (long long)(kgx + x) * g.bC8 + g.c0g, 0, reg + x * g.te, per);
@@ -491,7 +510,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
         const int P = max(1, min(g.G, STAGE_TILES / (g.te * kg2_of(kw))));
         for (int q0 = 0; q0 < g.G; q0 += P)
           produce([&](auto&& f, bool count_only) -> uint32_t {
-            return copies_s2(u, g, j, h, q0, min(g.G, q0 + P), lane, count_only, f);
+            return copies_s2(u, g, j, h, q0, min(g.G, q0 + P), all_slots, lane, count_only, f);
           });
       }
     };
@@ -659,6 +678,8 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
         const uint32_t id2 = idesc_of<F16>(16 * ((u.tn + 15) / 16), 0, tB);
         const int nh = n_halves(u, j), tm8 = u.tm8, ccols = chunk_cols(u, j);
         const bool whole = whole_chunk_group(u, j, a.max_chain);
+        const bool runs = a.producers == 1;
+        const int bst0 = b_stride(u, j, 0, runs), bst1 = nh > 1 ? b_stride(u, j, 1, runs) : 0;
         bool first = true;
         for (int h = 0; h < nh && ok; ++h) {
           const uint32_t hb = h2 % NA2;
@@ -666,8 +687,9 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
           ++h2;
           const uint32_t a2 = sbase + A2_OFF + hb * A2_BYTES;
           const int kw = min(64, ccols - 64 * h), kg2 = kg2_of(kw), P = max(1, min(G, STAGE_TILES / (te * kg2)));
-          const uint32_t b_lbo = tB ? (uint32_t)te * TILE : TILE;
-          const uint32_t b_sbo = tB ? TILE : (uint32_t)kg2 * TILE;
+          const uint32_t bs = (uint32_t)(h == 0 ? bst0 : bst1) * TILE;
+          const uint32_t b_lbo = tB ? bs : TILE;
+          const uint32_t b_sbo = tB ? TILE : bs;
           int qf = 0;  // position of term q in its flush group (q % F)
           for (int q0 = 0; q0 < G && ok; q0 += P) {
             const uint32_t sst = acquire();

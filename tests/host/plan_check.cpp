@@ -310,7 +310,11 @@ int main(int argc, char** argv) {
 
   // (6) the kernel's copies, enumerated with its own formulas: every copy
   //     lands inside its stage (stage 1: operator rows below position 16 KG1,
-  //     psi from there on) and reads inside the split arrays
+  //     psi from there on) and reads inside the split arrays; where a term's
+  //     stage-2 tiles form one run in the stored block they move as one copy
+  //     and keep its stride, and every MMA operand read (K steps of 16, N
+  //     rounded up to 16) stays inside the stage, or the term's stage-2
+  //     region
   // (ST tile positions per stage, KG1 K groups per stage-1 stage: 128 / 4 for
   //     the bf16 kernels, 192 / 6 for FP16X2). The tile positions copied per
   //     sigma (operators and psi) give the bytes each kernel requests from
@@ -328,18 +332,22 @@ int main(int argc, char** argv) {
       const int G = r.nterm, tm8 = r.tm8;
       const int nchunk = (r.n + 127) / 128;
       for (int j = 0; j < nchunk; ++j) {
-        for (int k = 0; k < (r.pR8 + KG1 - 1) / KG1; ++k) {
+        const int nk1 = (r.pR8 + KG1 - 1) / KG1;
+        for (int k = 0; k < nk1; ++k) {
           const int kg0 = KG1 * k;
+          const int nks = std::min(KG1, (int)r.pR8 - kg0) / 2;  // MMA K steps of the stage
           if (!(r.flags & TC_TA)) {
             const int nk = std::min(KG1, (int)r.aC8 - kg0);
+            if (2 * nks > KG1) fail("stage-1 left operand read beyond its row group");
             if (nk > 0)
-              for (int q = 0; q < G; ++q)
+              for (int q = 0; q < G; ++q) {
                 for (int rg = 0; rg < tm8; ++rg) {
                   const int dst = (q * tm8 + rg) * KG1;
                   ctiles += nk;
                   if (dst + nk > PT || !src_ok(r.t[q].a_tile + (long long)(r.r0g + rg) * r.aC8 + kg0, nk, false))
                     fail("stage-1 operator copy out of bounds");
                 }
+              }
           } else {
             for (int q = 0; q < G; ++q)
               for (int kg = 0; kg < KG1 && kg0 + kg < r.aR8; ++kg) {
@@ -351,7 +359,10 @@ int main(int argc, char** argv) {
               }
           }
           const int nn = std::min(16, (int)r.pC8 - 16 * j);
-          for (int kg = 0; kg < KG1 && kg0 + kg < r.pR8; ++kg)
+          const int nkP = std::min(KG1, (int)r.pR8 - kg0);
+          const int cc = std::min(128, r.n - 128 * j), nN = 2 * ((cc + 15) / 16);
+          if (PT + (2 * nks - 1) * 16 + nN > ST) fail("stage-1 psi operand read beyond the stage");
+          for (int kg = 0; kg < nkP; ++kg)
             if ((ctiles += nn), PT + kg * 16 + nn > ST || !src_ok(r.p_tile + (long long)(kg0 + kg) * r.pC8 + 16 * j, nn, true))
               fail("stage-1 psi copy out of bounds");
         }
@@ -366,12 +377,25 @@ int main(int argc, char** argv) {
               if (reg + te * kg2 > ST) fail("stage-2 region beyond the stage");
               if (!(r.flags & TC_TB)) {
                 const int nk = std::min(kg2, (int)r.bC8 - kgx);
+                // one producer: a single run (N-group stride bC8) when the
+                // half holds all K groups; three: one copy per N group
+                const bool run = nk == r.bC8;
+                if (run && ((te - 1) * r.bC8 + kg2 > te * kg2 || reg + tn8 * nk > ST ||
+                            !src_ok(r.t[q].b_tile + (long long)r.c0g * r.bC8, tn8 * nk, false)))
+                  fail("stage-2 operator run out of bounds");
                 for (int ng = 0; ng < tn8; ++ng)
                   if ((ctiles += std::max(nk, 0)), reg + ng * kg2 + nk > ST ||
                       !src_ok(r.t[q].b_tile + (long long)(r.c0g + ng) * r.bC8 + kgx, nk, false))
                     fail("stage-2 operator copy out of bounds");
               } else {
-                for (int kg = 0; kg < kg2 && kgx + kg < r.bR8; ++kg)
+                const int nk = std::min(kg2, (int)r.bR8 - kgx);
+                // one producer: a single run (K-group stride tn8) when the
+                // tile spans the stored columns; three: one copy per K group
+                const bool run = tn8 == r.bC8;
+                if (run && ((kg2 - 1) * tn8 + te > te * kg2 || reg + nk * tn8 > ST ||
+                            !src_ok(r.t[q].b_tile + (long long)kgx * r.bC8, nk * tn8, false)))
+                  fail("stage-2 transposed operator run out of bounds");
+                for (int kg = 0; kg < nk; ++kg)
                   if ((ctiles += tn8), reg + kg * te + tn8 > ST ||
                       !src_ok(r.t[q].b_tile + (long long)(kgx + kg) * r.bC8 + r.c0g, tn8, false))
                     fail("stage-2 transposed operator copy out of bounds");
