@@ -404,8 +404,11 @@ __device__ __forceinline__ void mma_chain(uint32_t tmem_d, uint64_t a, uint64_t 
 
 // PROF: record wait accounting and MMA-thread cycles into a.wait_prof.
 // F16: FP16X2 (two fp16 slices of scaled operands; see split_f16.cu).
-template <int NPROD, bool F16, bool PROF>
+// NP: producer warps (TcDev::producers, 1 or NPW), a template parameter so
+// that each setting compiles only its own copy code.
+template <int NPROD, bool F16, bool PROF, int NP>
 __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
+  static_assert(NP == 1 || NP == NPW, "producer warps");
   using L = Lay<F16>;
   constexpr int TILE = L::TILE, STAGES = L::STAGES, STAGE_BYTES = L::STAGE_BYTES, STAGE_OFF = L::STAGE_OFF;
   constexpr int META_OFF = L::META_OFF, BAR_OFF = L::BAR_OFF, STAGE_TILES = L::STAGE_TILES, KG1 = L::KG1,
@@ -445,7 +448,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
     }
     for (int m = 0; m < NMETA; ++m) {
       mbar_init(bar(B_MFULL + m), 1);
-      mbar_init(bar(B_MEMPTY + m), (a.producers == 1 ? 1 : NPW) + 1 + NEPI);  // producer, MMA, epilogue warps
+      mbar_init(bar(B_MEMPTY + m), NP + 1 + NEPI);  // producer, MMA and epilogue warps
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -460,16 +463,16 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
   asm volatile("tcgen05.fence::after_thread_sync;\n");
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 0 || (warp >= 2 + NEPI && a.producers != 1)) {
+  if (warp == 0 || (warp >= 2 + NEPI && NP != 1)) {
     // ------------------------------------------------------------ producers
-    // With a.producers == NPW every producer warp walks the same units and
+    // With NP == NPW every producer warp walks the same units and
     // stages and warp pw fills ring slot pw (NPW = STAGES), so each slot has
     // one producer and the stages of a unit are filled by three warps at
-    // once; with a.producers == 1 warp 0 fills every slot and the others
+    // once; with NP == 1 warp 0 fills every slot and the others
     // stay idle. Warp 0 (pw 0) also fetches the unit records into the ring;
     // the others read them there.
     const int pw = warp == 0 ? 0 : warp - 1 - NEPI;  // 0 .. NPW-1
-    const bool all_slots = a.producers == 1;
+    constexpr bool all_slots = NP == 1;
     uint32_t stage = 0, phase = 1;  // empty barriers: first wait passes
     bool ok = true;
     const char* const ops = (const char*)a.op;
@@ -678,7 +681,7 @@ __global__ void __launch_bounds__(NTHR, 1) sigma_tc_kernel(TcDev a) {
         const uint32_t id2 = idesc_of<F16>(16 * ((u.tn + 15) / 16), 0, tB);
         const int nh = n_halves(u, j), tm8 = u.tm8, ccols = chunk_cols(u, j);
         const bool whole = whole_chunk_group(u, j, a.max_chain);
-        const bool runs = a.producers == 1;
+        constexpr bool runs = NP == 1;
         const int bst0 = b_stride(u, j, 0, runs), bst1 = nh > 1 ? b_stride(u, j, 1, runs) : 0;
         bool first = true;
         for (int h = 0; h < nh && ok; ++h) {
@@ -1018,15 +1021,23 @@ void launch_split_psi(const double* psi, const PsiBlock* blocks, const TcPsiBloc
   split_psi_kernel<<<nblk, 256, 0, st>>>(psi, blocks, pb, nblk, (__nv_bfloat16*)out);
 }
 
+template <int NPROD, bool F16, int NP>
+static void launch_tc_np(const TcDev& a, int grid, cudaStream_t st) {
+  constexpr int SMEM = Lay<F16>::SMEM_BYTES;
+  set_max_dynamic_smem((const void*)sigma_tc_kernel<NPROD, F16, false, NP>, SMEM);
+  set_max_dynamic_smem((const void*)sigma_tc_kernel<NPROD, F16, true, NP>, SMEM);
+  if (a.wait_prof)
+    sigma_tc_kernel<NPROD, F16, true, NP><<<grid, NTHR, SMEM, st>>>(a);
+  else
+    sigma_tc_kernel<NPROD, F16, false, NP><<<grid, NTHR, SMEM, st>>>(a);
+}
+
 template <int NPROD, bool F16>
 static void launch_tc(const TcDev& a, int grid, cudaStream_t st) {
-  constexpr int SMEM = Lay<F16>::SMEM_BYTES;
-  set_max_dynamic_smem((const void*)sigma_tc_kernel<NPROD, F16, false>, SMEM);
-  set_max_dynamic_smem((const void*)sigma_tc_kernel<NPROD, F16, true>, SMEM);
-  if (a.wait_prof)
-    sigma_tc_kernel<NPROD, F16, true><<<grid, NTHR, SMEM, st>>>(a);
+  if (a.producers == NPW)
+    launch_tc_np<NPROD, F16, NPW>(a, grid, st);
   else
-    sigma_tc_kernel<NPROD, F16, false><<<grid, NTHR, SMEM, st>>>(a);
+    launch_tc_np<NPROD, F16, 1>(a, grid, st);
 }
 
 void launch_sigma_tc(const TcDev& a, int n_sm, cudaStream_t st) {
