@@ -419,11 +419,13 @@ dmrg_status dmrg_profile(dmrg_ctx* ctx, int enable);
 
 /* Wait accounting of the tensor-core sigma kernel, summed over its CTAs and
  * launches since dmrg_profile(ctx, 2): cycles[k] for k < 16 = clock cycles
- * spent blocked on barrier kind k (1 stage free, 2 sigma tile free, 3 X tile
- * free, 4 stage loaded, 5 second-product operand written, 6 X tile computed,
- * 7 second-product operand free, 8 sigma tile computed, 9-13 unit-record
- * ring; 14 and 15 are not waits: cycles the MMA-issuing thread spends
- * issuing MMAs and committing them), cycles[16] = total CTA cycles. Fills min(n, 17) entries. */
+ * spent blocked on barrier kind k, summed over the threads that wait (1 stage
+ * free, by each producer warp's lanes; 2 sigma tile free, 3 X tile free, 4
+ * stage loaded, 5 second-product operand written, by the MMA warp's lanes; 6
+ * X tile computed, 7 second-product operand free, 8 sigma tile computed, by
+ * the epilogue's; 9-13 unit-record ring; 14 and 15 are not waits: cycles the
+ * MMA-issuing thread spends issuing MMAs and committing them), cycles[16] =
+ * total CTA cycles. Fills min(n, 17) entries. */
 dmrg_status dmrg_profile_waits(dmrg_ctx* ctx, double* cycles, int n);
 dmrg_status dmrg_profile_read(dmrg_ctx* ctx, int kernel, double* total_ms, long long* launches);
 
