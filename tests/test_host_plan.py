@@ -113,3 +113,24 @@ def test_task_list_and_plan_match_the_oracle_count(checker, tmp_path, nsp, ntot,
     assert abs(got["flops"] - ref) <= 1e-12 * ref
     # sub-Hamiltonian ranks of the terms (Eqs. proc-def-nc / proc-def-cn), 3 ranks
     assert got["ranks3"] == [nc_term_rank(t, 3) for t in terms]
+
+
+def test_bench_size_plan_stays_in_bounds(checker, tmp_path):
+    """The middle-bond plan the bench times (K=108, N=30, 2Sz=0, M=2000: 364k
+    units of stacked terms): every bulk copy of the tensor-core kernel, in both
+    producer settings, lands inside its stage and reads inside the split
+    arrays, and every MMA operand read stays inside its stage or term region;
+    the work list and the plan cover the same products."""
+    left = gaussian_sector_dims(2000, n_spatial=54, n_tot=30, two_sz_tot=0)
+    right = mirrored_sectors(left, n_tot=30, two_sz_tot=0)
+    path = tmp_path / "sectors.txt"
+    with open(path, "w") as f:
+        f.write(f"{len(left)} {len(right)}\n")
+        for s in list(left) + list(right):
+            f.write(" ".join(str(int(x)) for x in s) + "\n")
+    out = subprocess.run([checker, str(path), "108", "216", "30", "0", "nc"], check=True, capture_output=True,
+                         text=True).stdout
+    got = json.loads(out)
+    assert got["errors"] == []
+    assert got["terms"] == 23654 and got["psi_size"] == 106004
+    assert got["units"] > 300000 and got["stages"] > got["units"]
