@@ -21,10 +21,12 @@ def main():
     ap.add_argument("--prec", type=int, default=capi.DMRG_FP16X2, help="dmrg_prec: 0 FP64, 1 BF16X2, 2 BF16X3, 3 FP16X2")
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--autotune", action="store_true", help="tune the work split first (as the bench does)")
+    ap.add_argument("--producers", type=int, default=0, choices=[0, 1, 3],
+                    help="producer warps of the tensor-core kernel (0: the plan's default or the tuner's)")
     args = ap.parse_args()
     left = gaussian_sector_dims(args.M, n_spatial=54, n_tot=30, two_sz_tot=0)
     right = mirrored_sectors(left, n_tot=30, two_sz_tot=0)
-    ctx = capi.dmrg_create(device=0, sigma_prec=args.prec, graphs=0)
+    ctx = capi.dmrg_create(device=0, sigma_prec=args.prec, graphs=0, tc_producers=args.producers)
     try:
         capi.dmrg_load_synthetic(ctx, 108, 216, 30, 0, left, right, 1)
         n = capi.dmrg_get_sigma_info(ctx)["psi_size"]
@@ -35,9 +37,10 @@ def main():
         for _ in range(args.steps):
             capi.dmrg_sigma(ctx, -1, x, y)
         capi.dmrg_sync(ctx)
+        used = capi.dmrg_get_sigma_info(ctx, -1)["tc_producers"]
     finally:
         capi.dmrg_destroy(ctx)
-    print("ok", args.M, args.prec, n)
+    print("ok", args.M, args.prec, n, "producers", used)
 
 
 if __name__ == "__main__":

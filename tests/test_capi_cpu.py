@@ -84,7 +84,7 @@ def test_option_checks_come_before_the_device(libpath):
         assert e.value.status == capi.DMRG_EINVAL, kw
 
 
-@pytest.mark.parametrize("module", ["sweeps", "serve", "precision_sweep"])
+@pytest.mark.parametrize("module", ["sweeps", "serve", "precision_sweep", "profile_sigma", "bond_energy"])
 def test_command_line_tools_start_without_a_gpu(module):
     """The user-facing tools parse their arguments and import the binding
     without touching the device (the device is needed only to run them)."""
